@@ -1,0 +1,106 @@
+"""Pins of the oracle FGMRES (Alg. 1, eq. 4) against scipy's GMRES, exact preconditioning,
+right-preconditioned GMRES, lstsq and the Arnoldi invariants."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle import fgmres as fg
+from oracle import helmholtz as hz
+from oracle import unet
+from paper_2607_16906_b300 import synth
+
+OMEGA = synth.angular_frequency()
+
+
+def _system(seed=1, nx=24, p=4):
+    rng = synth.rng_for(seed)
+    c = synth.skull_velocity(nx, nx, p, rng, thickness=(2, 3))
+    h = synth.grid_spacing(10.0)
+    A = hz.assemble(c, p, h, OMEGA)
+    b = synth.point_sources(nx, nx, p, rng, 2).ravel()
+    return A, b, c, p, h
+
+
+@pytest.mark.parametrize("orth", ["cgs2", "mgs"])
+def test_identity_preconditioner_is_scipy_gmres(orth):
+    A, b, *_ = _system()
+    hist = []
+    spla.gmres(A, b, rtol=1e-10, restart=15, maxiter=3, callback=hist.append, callback_type="pr_norm")
+    x, info = fg.fgmres(lambda u: A @ u, lambda v: v, b, m=15, tol=1e-10, max_cycles=3, orth=orth)
+    n = min(len(hist), len(info.history))
+    assert n >= 40
+    assert np.allclose(info.history[:n], hist[:n], rtol=1e-9, atol=0)
+
+
+def test_exact_inverse_converges_in_one_iteration():
+    A, b, *_ = _system()
+    lu = spla.splu(A.tocsc())
+    x, info = fg.fgmres(lambda u: A @ u, lu.solve, b, m=10, tol=1e-12)
+    assert info.iters == 1 and info.converged
+    assert np.linalg.norm(x - lu.solve(b)) <= 1e-12 * np.linalg.norm(x)
+
+
+def test_fixed_linear_preconditioner_is_right_preconditioned_gmres():
+    """FGMRES with z = M v equals GMRES on A M t = b followed by x = M t (Sec. 2.2)."""
+    A, b, *_ = _system()
+    rng = synth.rng_for(9)
+    M = np.diag(1.0 + 0.3 * rng.standard_normal(A.shape[0])) + 0j
+    x, info = fg.fgmres(lambda u: A @ u, lambda v: M @ v, b, m=20, tol=1e-14, max_cycles=1)
+    AM = spla.LinearOperator(A.shape, matvec=lambda t: A @ (M @ t), dtype=complex)
+    res = fg.cycle(lambda t: AM @ t, lambda v: v, b, 20, 0.0)
+    assert np.linalg.norm(x - M @ res.x) <= 1e-10 * np.linalg.norm(x)
+
+
+@pytest.mark.parametrize("orth", ["cgs2", "mgs"])
+def test_generalised_arnoldi_relation_and_orthonormality(orth):
+    A, b, c, p, h = _system()
+    theta = synth.kaiming_uniform_params(unet.param_segments(), 42)
+    Ny = Nx = int(np.sqrt(b.size))
+
+    def M(v):          # the nonlinear U-Net preconditioner
+        return unet.precondition(theta, v.reshape(1, Ny, Nx), c)[0].ravel()
+
+    res = fg.cycle(lambda u: A @ u, M, b, 12, 0.0, orth=orth)
+    V, Z, Hb = res.V, res.Z, res.Hbar
+    normA = spla.norm(A, 2) if False else abs(A).sum(axis=1).max()
+    lhs = A @ Z.T - V.T @ Hb
+    assert np.linalg.norm(lhs) <= 1e-12 * normA * np.linalg.norm(Z)
+    assert np.abs(V.conj() @ V.T - np.eye(V.shape[0])).max() <= (1e-12 if orth == "cgs2" else 1e-9)
+    # y solves the small least-squares problem
+    rhs = np.zeros(Hb.shape[0], complex)
+    rhs[0] = np.linalg.norm(b)
+    y_ref = np.linalg.lstsq(Hb, rhs, rcond=None)[0]
+    assert np.linalg.norm(res.y - y_ref) <= 1e-9 * np.linalg.norm(y_ref)
+    # the estimate equals the true residual of the cycle's iterate
+    assert abs(res.est - np.linalg.norm(b - A @ res.x)) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_converged_solution_matches_direct_solve():
+    """A strong preconditioner (LU of the operator at a nearby frequency) drives eta_b below 1e-10;
+    the forward error against splu is then within cond-limited rounding."""
+    A, b, c, p, h = _system()
+    lu_near = spla.splu(hz.assemble(c, p, h, OMEGA * 1.02).tocsc())
+    x, info = fg.fgmres(lambda u: A @ u, lu_near.solve, b, m=30, tol=1e-10)
+    assert info.converged and info.relres_true <= 1e-10
+    xs = hz.solve_direct(A, b)
+    assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
+
+
+def test_refinement_with_low_precision_inner_solve():
+    A, b, c, p, h = _system()
+    lu_near = spla.splu(hz.assemble(c, p, h, OMEGA * 1.05).tocsc())
+    x, info = fg.refine(lambda u: A @ u, lambda v: lu_near.solve(v.astype(complex)).astype(np.complex64),
+                        b, m=30, tol=1e-10, inner_tol=1e-4)
+    assert info.converged and info.outer >= 2      # one FP32 inner solve alone cannot reach 1e-10
+    xs = hz.solve_direct(A, b)
+    assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
+
+
+def test_givens_zeroes_second_component():
+    rng = synth.rng_for(3)
+    for _ in range(20):
+        a, bb = rng.standard_normal(2) + 1j * rng.standard_normal(2)
+        c, s = fg.givens(a, bb)
+        assert abs(-np.conj(s) * a + c * bb) <= 1e-15 * (abs(a) + abs(bb))
+        assert abs(c ** 2 + abs(s) ** 2 - 1) <= 1e-15
+    assert fg.givens(0.0, 2.0 + 1j) == (0.0, 1.0 + 0j)
