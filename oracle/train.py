@@ -3,7 +3,8 @@
 Loss (eq. 9): L(b, c) = ||b - A(c) u_hat||^2 / ||b||^2 with u_hat = N_theta(b, c),
 i.e. the squared backward error eta_b(u_hat)^2.  Cost (eq. 8): the batch mean.
 The network sees b scaled to unit RMS (alpha = sqrt(n) / ||b||) and its output is
-scaled back by 1/alpha; the loss is invariant to that scale.
+scaled back by h^2 / alpha (the network approximates the inverse of the
+dimensionless h^2 A, as oracle.unet.precondition does); the loss is invariant to alpha.
 
 Gradient w.r.t. the network output channels (Re u, Im u):
   dL/d(Re u) + i dL/d(Im u) = -2 A^H r / ||b||^2,  r = b - A u_hat,
@@ -40,14 +41,14 @@ def loss_and_grad(theta, b, c, p, h, omega, bf16=False, want_grad=True):
     bt = b * alpha[:, None, None]                       # unit-RMS source, ||bt||^2 = n
     x = unet.network_input(bt, c)
     y, act = unet.forward(theta, x, bf16=bf16, keep=True)
-    u = y[:, 0, :Ny, :Nx] + 1j * y[:, 1, :Ny, :Nx]
+    u = (y[:, 0, :Ny, :Nx] + 1j * y[:, 1, :Ny, :Nx]) * h * h
     losses = np.zeros(B)
     gy = np.zeros_like(y)
     for s in range(B):
         r = bt[s] - hz.apply(u[s], c[s], p, h, omega)
         losses[s] = np.sum(np.abs(r) ** 2) / n
         if want_grad:
-            g = -2.0 * hz.apply_adjoint(r, c[s], p, h, omega) / n / B
+            g = -2.0 * h * h * hz.apply_adjoint(r, c[s], p, h, omega) / n / B
             gy[s, 0, :Ny, :Nx] = g.real
             gy[s, 1, :Ny, :Nx] = g.imag
     if not want_grad:

@@ -314,12 +314,14 @@ def network_input(v, c):
     return pad8(x)
 
 
-def precondition(theta, v, c, bf16=False):
-    """z = N_theta(alpha v, c) / alpha with alpha = sqrt(n) / ||v|| per batch entry (eq. 6).
+def precondition(theta, v, c, h, bf16=False):
+    """z = h^2 N_theta(alpha v, c) / alpha with alpha = sqrt(n) / ||v|| per batch entry (eq. 6).
 
-    v: complex [B][Ny][Nx]; c: [Ny][Nx] (shared) or [B][Ny][Nx].  The scale
-    alpha gives the network input unit RMS; FGMRES is invariant to the scale
-    of each z in exact arithmetic.
+    v: complex [B][Ny][Nx]; c: [Ny][Nx] (shared) or [B][Ny][Nx]; h: grid spacing.
+    The scale alpha gives the network input unit RMS.  The factor h^2 makes the
+    network approximate the inverse of the dimensionless operator h^2 A, whose
+    entries are O(1) as in the paper's omega = 1 setting (Tab. 1); FGMRES is
+    invariant to the scale of each z in exact arithmetic.
     """
     v = np.asarray(v, np.complex128)
     B, Ny, Nx = v.shape
@@ -329,4 +331,4 @@ def precondition(theta, v, c, bf16=False):
     y = forward(theta, x, bf16=bf16)[:, :, :Ny, :Nx]
     z = y[:, 0] + 1j * y[:, 1]
     inv = np.where(alpha > 0, 1.0 / np.where(alpha > 0, alpha, 1.0), 0.0)
-    return z * inv[:, None, None]
+    return z * (h * h * inv)[:, None, None]

@@ -58,7 +58,7 @@ def test_generalised_arnoldi_relation_and_orthonormality(orth):
     Ny = Nx = int(np.sqrt(b.size))
 
     def M(v):          # the nonlinear U-Net preconditioner
-        return unet.precondition(theta, v.reshape(1, Ny, Nx), c)[0].ravel()
+        return unet.precondition(theta, v.reshape(1, Ny, Nx), c, h)[0].ravel()
 
     res = fg.cycle(lambda u: A @ u, M, b, 12, 0.0, orth=orth)
     V, Z, Hb = res.V, res.Z, res.Hbar

@@ -23,7 +23,7 @@ def test_loss_is_squared_backward_error():
     c, b, p, h = _batch()
     L, _, per = train.loss_and_grad(theta, b, c, p, h, OMEGA, want_grad=False)
     for s in range(b.shape[0]):
-        u = unet.precondition(theta, b[s:s + 1], c[s])[0]
+        u = unet.precondition(theta, b[s:s + 1], c[s], h)[0]
         A = hz.assemble(c[s], p, h, OMEGA)
         eta = hz.relres(A, u.ravel(), b[s].ravel())
         assert abs(per[s] - eta ** 2) <= 1e-12 * eta ** 2
@@ -82,7 +82,7 @@ def test_gradient_matches_torch_autograd_dense():
         hh = cv("dec2b", cv("dec2a", torch.cat([s2, up("up2", hh)], 1)))
         hh = cv("dec1b", cv("dec1a", torch.cat([s1, up("up1", hh)], 1)))
         y = cv("final", hh, act=False, pad=0)[0, :, :Ny, :Nx]
-        u = torch.complex(y[0], y[1]).reshape(-1) / a
+        u = torch.complex(y[0], y[1]).reshape(-1) * (h * h / a)
         r = bs - A @ u
         total = total + (r.abs() ** 2).sum() / (bs.abs() ** 2).sum()
     (total / B).backward()

@@ -132,9 +132,9 @@ def test_precondition_pads_to_multiple_of_8_and_is_scale_invariant():
     rng = synth.rng_for(6)
     v = rng.standard_normal((2, 13, 21)) + 1j * rng.standard_normal((2, 13, 21))
     c = 1500.0 + 100 * rng.standard_normal((13, 21))
-    z = unet.precondition(theta, v, c)
+    z = unet.precondition(theta, v, c, 0.5)
     assert z.shape == v.shape
-    z2 = unet.precondition(theta, 3.7 * v, c)
+    z2 = unet.precondition(theta, 3.7 * v, c, 0.5)
     assert np.abs(z2 - 3.7 * z).max() <= 1e-12 * np.abs(z2).max()
     # manual padding reference: zero-pad to 16 x 24, run the network, crop
     a = np.sqrt(13 * 21) / np.linalg.norm(v[0])
@@ -143,4 +143,4 @@ def test_precondition_pads_to_multiple_of_8_and_is_scale_invariant():
     x[0, 1, :13, :21] = (a * v[0]).imag
     x[0, 2, :13, :21] = c / 1500.0
     y = unet.forward(theta, x)[0, :, :13, :21]
-    assert np.abs((y[0] + 1j * y[1]) / a - z[0]).max() <= 1e-12 * np.abs(z[0]).max()
+    assert np.abs(0.25 * (y[0] + 1j * y[1]) / a - z[0]).max() <= 1e-12 * np.abs(z[0]).max()
