@@ -1,0 +1,176 @@
+/*
+ * helm.h - C ABI of libhelm: CNN-preconditioned flexible GMRES for the 2D
+ * heterogeneous Helmholtz equation with a PML, on NVIDIA B300 (sm_103a).
+ *
+ * Problem (eq. 1 with the sign flipped, eq. 3):  -Lap u - (omega / c(x))^2 u = f
+ * on an nx x ny interior grid of spacing h surrounded by `width` PML cells per
+ * side.  The PML damping is quadratic in the depth into the layer (eq. 2) and
+ * enters as the complex coordinate stretch s = 1 + i sigma / omega; the discrete
+ * operator is the complex-symmetric 5-point stencil
+ *
+ *   (A u)_{j,i} = -[ a_{i+1/2}(u_{i+1}-u_i) - a_{i-1/2}(u_i-u_{i-1})
+ *                  + b_{j+1/2}(u_{j+1}-u_j) - b_{j-1/2}(u_j-u_{j-1}) ] / h^2
+ *                 - s_x(i) s_y(j) k^2 u_{j,i},
+ *   a_{i+1/2} = s_y(j) / s_x(i+1/2),  b_{j+1/2} = s_x(i) / s_y(j+1/2),
+ *
+ * with zero values outside the grid.  A = A^T exactly.
+ *
+ * Conventions shared by every call:
+ *  - Grid of a system: Nx = nx + 2 width, Ny = ny + 2 width, n = Nx * Ny points,
+ *    row-major [Ny][Nx] (x fastest).
+ *  - A "batch vector" holds nrhs right-hand sides for every system of a
+ *    context: for system s = 0..nsys-1 in order, nrhs blocks of n_s points.
+ *    Complex values are interleaved (re, im): HELM_C64 = 2 x float (8 B),
+ *    HELM_C128 = 2 x double (16 B).  Pointers must be 16-byte aligned.
+ *  - Every array argument is caller-owned DEVICE memory unless marked host.
+ *    The library owns only its context, network and workspace allocations.
+ *  - Every call is asynchronous on the caller's stream (`stream` is a
+ *    cudaStream_t passed as void*; NULL = legacy default stream), except
+ *    helm_fgmres_solve and helm_train_step, which synchronise that stream
+ *    before they return because they hand back host-side results.
+ *  - Errors: no call aborts, traps or exits.  Each returns a helm_status;
+ *    helm_last_error() gives a message for the calling thread.  Invalid
+ *    arguments are detected on the host before anything is launched.
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HELM_API __attribute__((visibility("default")))
+#else
+#define HELM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct helm_ctx helm_ctx;    /* grids, coefficients, workspace */
+typedef struct helm_unet helm_unet;  /* network weights (FP64 master + BF16 copy), AdamW state */
+
+typedef enum {
+  HELM_OK = 0,
+  HELM_ERR_INVALID_ARG = 1,
+  HELM_ERR_CUDA = 2,
+  HELM_ERR_OOM = 3,
+  HELM_NOT_CONVERGED = 4, /* iteration budget spent before the tolerance was met */
+  HELM_BREAKDOWN = 5,     /* Z rank-deficient: h_{j+1,j} or R_jj vanished before convergence */
+  HELM_NAN = 6,           /* a NaN/Inf appeared in a norm or Hessenberg entry */
+  HELM_TIMEOUT = 7        /* a device-side wait ran out of its iteration budget */
+} helm_status;
+
+typedef enum { HELM_C64 = 0, HELM_C128 = 1 } helm_dtype;
+
+typedef struct {
+  int nx, ny;  /* interior cells */
+  double h;    /* grid spacing (same unit as c / omega) */
+} helm_grid;
+
+typedef struct {
+  int width;         /* PML cells per side (0 = none) */
+  double sigma_max;  /* damping at the outermost node; <= 0 selects 2 omega (Tab. 1: 2 at omega = 1) */
+} helm_pml;
+
+typedef enum { HELM_ORTH_CGS2 = 0 } helm_orth;
+
+typedef struct {
+  int m;            /* Krylov dimension per cycle (Alg. 1), 1..HELM_MAX_M */
+  int max_restarts; /* cycles per inner solve (plain path: total cycles) */
+  int max_outer;    /* FP64 refinement steps (mixed path) */
+  double tol;       /* stop when the FP64 true ||b - A x|| / ||b|| <= tol (eq. 10) */
+  double inner_tol; /* mixed path: relative reduction asked of each FP32 inner solve */
+  int mixed;        /* 0: plain FP64 (C128 vectors, FP64 network); 1: FP32 Krylov + BF16 network + FP64 refinement */
+  int orth;         /* helm_orth */
+} helm_solve_opts;
+
+#define HELM_MAX_M 1024
+
+typedef struct {
+  int iters;           /* preconditioned Krylov iterations spent on this column */
+  int restarts;        /* cycles */
+  int outer;           /* FP64 refinement steps */
+  double relres_true;  /* final FP64 ||b - A x|| / ||b|| */
+  double relres_est;   /* last Givens estimate, relative to ||b|| */
+  helm_status status;  /* HELM_OK, HELM_NOT_CONVERGED, HELM_BREAKDOWN or HELM_NAN */
+} helm_solve_info;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Set up nsys systems (a1: k^2 = (omega/c)^2 and the 1-D PML stretch profiles, eq. 2).
+ * grid[nsys], pml[nsys], omega[nsys]: host arrays, one entry per system
+ * (systems may differ in size: an uneven batch).  c_dev: device array of all
+ * systems' velocities concatenated, each [Ny][Nx], real, in FP64 when
+ * c_is_fp64 != 0 else FP32; read during this call only (stream-ordered).
+ * c must be > 0 and finite (checked on the device; HELM_ERR_INVALID_ARG). */
+HELM_API helm_status helm_create(helm_ctx** out, int nsys, const helm_grid* grid, const helm_pml* pml,
+                        const double* omega, const void* c_dev, int c_is_fp64, void* stream);
+HELM_API helm_status helm_destroy(helm_ctx* ctx);
+/* Total points of one batch vector per right-hand side (sum of n_s), and the system count. */
+HELM_API int64_t helm_points(const helm_ctx* ctx);
+HELM_API int helm_num_systems(const helm_ctx* ctx);
+
+/* ---- operator (a2) ---------------------------------------------------- */
+
+/* y = A x for a batch vector of nrhs right-hand sides per system.  x and y must not overlap. */
+HELM_API helm_status helm_apply(helm_ctx* ctx, const void* x, void* y, helm_dtype dtype, int nrhs, void* stream);
+/* y = A^H x (= conj(A conj(x)) since A = A^T); used by the loss gradient (eq. 9). */
+HELM_API helm_status helm_apply_adjoint(helm_ctx* ctx, const void* x, void* y, helm_dtype dtype, int nrhs, void* stream);
+/* out_host[col] = ||b - A x|| / ||b|| in FP64 for every column (eq. 10); x, b are C128. Synchronises. */
+HELM_API helm_status helm_relres(helm_ctx* ctx, const void* x, const void* b, int nrhs, double* out_host, void* stream);
+
+/* ---- neural operator (a3) ---------------------------------------------- */
+
+/* Network layout (Sec. 3.1, Fig. 2, read as): 4 levels of widths 16/32/64/128, two 3x3 convs
+ * (pad 1, bias, ReLU) per level, 2x2 max-pool down, 2x2 stride-2 transposed conv up (bias, no
+ * activation), decoder input concat[skip, up], final 1x1 conv 16 -> 2.  Inputs
+ * (Re v, Im v, c / 1500 m/s); outputs (Re z, Im z).
+ * weights_host: nweights = helm_unet_param_count() doubles, per layer weight then bias, layers in
+ * the order enc1a enc1b enc2a enc2b enc3a enc3b bota botb up3 dec3a dec3b up2 dec2a dec2b up1
+ * dec1a dec1b final; conv weights [Cout][Cin][kh][kw], transposed-conv weights [Cin][Cout][2][2]. */
+HELM_API size_t helm_unet_param_count(void);
+/* Layer l (0..17): writes c_in, c_out, kind (0 = 3x3 conv, 1 = 2x2 up-conv, 2 = 1x1 conv). */
+HELM_API helm_status helm_unet_layer(int l, int* c_in, int* c_out, int* kind);
+HELM_API helm_status helm_unet_create(helm_unet** out, const double* weights_host, size_t nweights);
+HELM_API helm_status helm_unet_destroy(helm_unet* net);
+/* Copy the FP64 master weights back to the host (after training). */
+HELM_API helm_status helm_unet_get_weights(const helm_unet* net, double* weights_host, size_t nweights);
+
+/* z = N_theta(alpha v, c) / alpha per column, alpha = sqrt(n) / ||v|| (eq. 6).  dtype HELM_C64:
+ * BF16 network with FP32 accumulation; HELM_C128: FP64 network.  v, z batch vectors. */
+HELM_API helm_status helm_precond_apply(helm_ctx* ctx, const helm_unet* net, const void* v, void* z,
+                               helm_dtype dtype, int nrhs, void* stream);
+
+/* ---- solver (a4-a8) ---------------------------------------------------- */
+
+/* Solve A x = b for nrhs right-hand sides per system by FGMRES (Alg. 1) with z_j = N_theta(v_j)
+ * (net = NULL: z_j = v_j, i.e. GMRES).  b, x: C128 batch vectors; x holds x0 on entry and the
+ * solution on exit (the best iterate when not converged).  opts: host.  info: host array of
+ * nsys * nrhs entries (column = system-major, rhs-minor).  Returns HELM_OK when every column met
+ * opts->tol, HELM_NOT_CONVERGED / HELM_BREAKDOWN / HELM_NAN when at least one did not. */
+HELM_API helm_status helm_fgmres_solve(helm_ctx* ctx, const helm_unet* net, const void* b, void* x, int nrhs,
+                              const helm_solve_opts* opts, helm_solve_info* info, void* stream);
+
+/* ---- training (a9) ------------------------------------------------------ */
+
+/* One optimisation step of the physics-informed loss (eqs. 8-9) over a batch of one source per
+ * system: b is a C64 batch vector with nrhs = 1.  Loss = mean_s ||b_s - A_s u_s||^2 / ||b_s||^2,
+ * u_s = N_theta(alpha b_s, c_s) / alpha.  Gradient by the adjoint stencil and the conv backward
+ * kernels; global-norm clip to `clip` (<= 0: none); AdamW (beta 0.9/0.999, eps 1e-8) with
+ * learning rate lr and decoupled weight decay wd.  loss_host: host pointer for the batch loss
+ * before the update (may be NULL).  grad_norm_host: the pre-clip gradient norm (may be NULL). */
+HELM_API helm_status helm_train_step(helm_ctx* ctx, helm_unet* net, const void* b, double lr, double wd,
+                            double clip, double* loss_host, double* grad_norm_host, void* stream);
+/* Loss and its gradient only (no update): grad_dev receives helm_unet_param_count() doubles. */
+HELM_API helm_status helm_loss_grad(helm_ctx* ctx, const helm_unet* net, const void* b, double* loss_host,
+                           double* grad_dev, void* stream);
+
+/* Thread-local message for the last non-OK status returned on this thread. */
+HELM_API const char* helm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

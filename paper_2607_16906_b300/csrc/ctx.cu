@@ -1,0 +1,227 @@
+// Context set-up (a1): wavenumbers, PML stretch profiles, column tables, errors.
+#include <math.h>
+#include <stdio.h>
+
+#include <complex>
+#include <string>
+
+#include "helm_internal.cuh"
+
+namespace helm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+helm_status fail(helm_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+helm_status cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
+  char buf[512];
+  snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s at %s:%d", (int)e, cudaGetErrorString(e), what, file, line);
+  g_last_error = buf;
+  return e == cudaErrorMemoryAllocation ? HELM_ERR_OOM : HELM_ERR_CUDA;
+}
+
+helm_status Workspace::reserve(size_t need) {
+  if (need <= bytes) return HELM_OK;
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+  size_t want = need + need / 8 + 256;
+  cudaError_t e = cudaMalloc(&ptr, want);
+  if (e != cudaSuccess) {
+    ptr = nullptr;
+    cudaGetLastError();
+    return cuda_fail(e, "workspace cudaMalloc", __FILE__, __LINE__);
+  }
+  bytes = want;
+  return HELM_OK;
+}
+
+Workspace::~Workspace() {
+  if (ptr) cudaFree(ptr);
+}
+
+// Depth (same unit as h) of position t (in cells; half-integers allowed) into the PML, and the
+// stretch s = 1 + i sigma / omega with sigma = sigma_max (depth / ell)^2, ell = p h (eq. 2).
+static std::complex<double> stretch_at(double t, int n_int, int p, double h, double omega, double sigma_max) {
+  if (p <= 0) return {1.0, 0.0};
+  double d = fmax(0.0, fmax((double)p - t, t - (double)(p + n_int - 1))) * h;
+  double ell = p * h;
+  double sigma = sigma_max * (d / ell) * (d / ell);
+  return {1.0, sigma / omega};
+}
+
+__global__ void k_wavenumbers(const void* c, int c_is_fp64, int64_t n, double omega, double* k2d, float* k2f,
+                              float* chat, int* bad) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double cv = c_is_fp64 ? ((const double*)c)[i] : (double)((const float*)c)[i];
+  if (!(cv > 0.0) || !isfinite(cv)) {
+    atomicExch(bad, 1);
+    cv = 1.0;
+  }
+  double k = omega / cv;
+  k2d[i] = k * k;
+  k2f[i] = (float)(k * k);
+  chat[i] = (float)(cv / 1500.0);
+}
+
+int num_cols(const helm_ctx* ctx, int nrhs) { return ctx->nsys * nrhs; }
+
+helm_status ensure_cols(helm_ctx* ctx, int nrhs) {
+  if (ctx->cols_nrhs == nrhs) return HELM_OK;
+  std::vector<ColDesc> cols;
+  for (int s = 0; s < ctx->nsys; ++s)
+    for (int r = 0; r < nrhs; ++r) {
+      ColDesc c;
+      c.off = ctx->sys[s].off * nrhs + r * ctx->sys[s].n;
+      c.len = ctx->sys[s].n;
+      c.sys = s;
+      c.h2 = ctx->sys[s].h * ctx->sys[s].h;
+      cols.push_back(c);
+    }
+  if (ctx->cols_dev) cudaFree(ctx->cols_dev);
+  ctx->cols_dev = nullptr;
+  HELM_CK(cudaMalloc(&ctx->cols_dev, sizeof(ColDesc) * cols.size()));
+  HELM_CK(cudaMemcpy(ctx->cols_dev, cols.data(), sizeof(ColDesc) * cols.size(), cudaMemcpyHostToDevice));
+  ctx->cols_host = cols;
+  ctx->cols_nrhs = nrhs;
+  return HELM_OK;
+}
+
+helm_status ensure_pinned(helm_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->pinned_bytes) return HELM_OK;
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  ctx->pinned = nullptr;
+  ctx->pinned_bytes = 0;
+  HELM_CK(cudaMallocHost(&ctx->pinned, bytes));
+  ctx->pinned_bytes = bytes;
+  return HELM_OK;
+}
+
+void unet_buffers_free(helm_ctx* ctx);  // unet.cu
+
+}  // namespace helm
+
+using namespace helm;
+
+extern "C" const char* helm_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" helm_status helm_create(helm_ctx** out, int nsys, const helm_grid* grid, const helm_pml* pml,
+                                   const double* omega, const void* c_dev, int c_is_fp64, void* stream) {
+  if (!out) return fail(HELM_ERR_INVALID_ARG, "helm_create: out is NULL");
+  *out = nullptr;
+  if (nsys <= 0 || !grid || !pml || !omega || !c_dev)
+    return fail(HELM_ERR_INVALID_ARG, "helm_create: nsys must be > 0 and grid, pml, omega, c must be non-NULL");
+  helm_ctx* ctx = new helm_ctx();
+  ctx->nsys = nsys;
+  int64_t off = 0, px = 0;
+  for (int s = 0; s < nsys; ++s) {
+    SysHost h{};
+    h.nx = grid[s].nx;
+    h.ny = grid[s].ny;
+    h.p = pml[s].width;
+    h.h = grid[s].h;
+    h.omega = omega[s];
+    if (h.nx <= 0 || h.ny <= 0 || h.p < 0 || !(h.h > 0) || !(h.omega > 0) || !std::isfinite(h.h) ||
+        !std::isfinite(h.omega)) {
+      delete ctx;
+      return fail(HELM_ERR_INVALID_ARG, "helm_create: system " + std::to_string(s) +
+                                            " needs nx, ny > 0, width >= 0, h > 0 and omega > 0");
+    }
+    h.sigma_max = pml[s].sigma_max > 0 ? pml[s].sigma_max : 2.0 * h.omega;
+    h.Nx = h.nx + 2 * h.p;
+    h.Ny = h.ny + 2 * h.p;
+    if ((int64_t)h.Nx * h.Ny > (int64_t)1 << 31) {
+      delete ctx;
+      return fail(HELM_ERR_INVALID_ARG, "helm_create: grid larger than 2^31 points");
+    }
+    h.n = (int64_t)h.Nx * h.Ny;
+    h.off = off;
+    off += h.n;
+    h.prof_x = px;
+    px += 2 * h.Nx + 1;
+    h.prof_y = px;
+    px += 2 * h.Ny + 1;
+    ctx->sys.push_back(h);
+  }
+  ctx->npts = off;
+  ctx->prof_len = px;
+  // profiles on the host in FP64: [s(node) x N][1/s(half) x (N+1)] per axis
+  std::vector<double2> pd(px);
+  std::vector<float2> pf(px);
+  for (auto& h : ctx->sys) {
+    for (int axis = 0; axis < 2; ++axis) {
+      int N = axis == 0 ? h.Nx : h.Ny;
+      int nint = axis == 0 ? h.nx : h.ny;
+      int64_t base = axis == 0 ? h.prof_x : h.prof_y;
+      for (int i = 0; i < N; ++i) {
+        auto s = stretch_at((double)i, nint, h.p, h.h, h.omega, h.sigma_max);
+        pd[base + i] = make_double2(s.real(), s.imag());
+      }
+      for (int i = 0; i <= N; ++i) {
+        auto s = 1.0 / stretch_at((double)i - 0.5, nint, h.p, h.h, h.omega, h.sigma_max);
+        pd[base + N + i] = make_double2(s.real(), s.imag());
+      }
+    }
+  }
+  for (int64_t i = 0; i < px; ++i) pf[i] = make_float2((float)pd[i].x, (float)pd[i].y);
+  cudaStream_t st = (cudaStream_t)stream;
+  helm_status rc = HELM_OK;
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && rc == HELM_OK) rc = cuda_fail(e, what, __FILE__, __LINE__);
+  };
+  ck(cudaMalloc(&ctx->k2f, sizeof(float) * off), "cudaMalloc k2f");
+  ck(cudaMalloc(&ctx->k2d, sizeof(double) * off), "cudaMalloc k2d");
+  ck(cudaMalloc(&ctx->chat, sizeof(float) * off), "cudaMalloc chat");
+  ck(cudaMalloc(&ctx->prof_d, sizeof(double2) * px), "cudaMalloc prof_d");
+  ck(cudaMalloc(&ctx->prof_f, sizeof(float2) * px), "cudaMalloc prof_f");
+  ck(cudaMalloc(&ctx->flag_dev, sizeof(int) * 16), "cudaMalloc flag");
+  if (rc != HELM_OK) {
+    helm_destroy(ctx);
+    return rc;
+  }
+  ck(cudaMemcpyAsync(ctx->prof_d, pd.data(), sizeof(double2) * px, cudaMemcpyHostToDevice, st), "copy prof_d");
+  ck(cudaMemcpyAsync(ctx->prof_f, pf.data(), sizeof(float2) * px, cudaMemcpyHostToDevice, st), "copy prof_f");
+  ck(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int) * 16, st), "memset flag");
+  for (auto& h : ctx->sys) {
+    const char* cb = (const char*)c_dev + h.off * (c_is_fp64 ? 8 : 4);
+    k_wavenumbers<<<cdiv(h.n, 256), 256, 0, st>>>(cb, c_is_fp64, h.n, h.omega, ctx->k2d + h.off,
+                                                   ctx->k2f + h.off, ctx->chat + h.off, ctx->flag_dev);
+  }
+  ck(cudaGetLastError(), "k_wavenumbers launch");
+  int bad = 0;
+  ck(cudaMemcpyAsync(&bad, ctx->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, st), "read flag");
+  ck(cudaStreamSynchronize(st), "sync");
+  if (rc == HELM_OK && bad) rc = fail(HELM_ERR_INVALID_ARG, "helm_create: c must be positive and finite everywhere");
+  if (rc == HELM_OK) ck(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int) * 16, st), "memset flag");
+  if (rc != HELM_OK) {
+    helm_destroy(ctx);
+    return rc;
+  }
+  *out = ctx;
+  return HELM_OK;
+}
+
+extern "C" helm_status helm_destroy(helm_ctx* ctx) {
+  if (!ctx) return HELM_OK;
+  cudaDeviceSynchronize();
+  unet_buffers_free(ctx);
+  cudaFree(ctx->k2f);
+  cudaFree(ctx->k2d);
+  cudaFree(ctx->chat);
+  cudaFree(ctx->prof_d);
+  cudaFree(ctx->prof_f);
+  cudaFree(ctx->cols_dev);
+  cudaFree(ctx->flag_dev);
+  if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  delete ctx;
+  return HELM_OK;
+}
+
+extern "C" int64_t helm_points(const helm_ctx* ctx) { return ctx ? ctx->npts : 0; }
+extern "C" int helm_num_systems(const helm_ctx* ctx) { return ctx ? ctx->nsys : 0; }

@@ -1,0 +1,134 @@
+// Internal declarations shared by the libhelm translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/helm.h"
+
+namespace helm {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string& msg);
+helm_status fail(helm_status st, const std::string& msg);
+helm_status cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define HELM_CK(call)                                                        \
+  do {                                                                       \
+    cudaError_t e_ = (call);                                                 \
+    if (e_ != cudaSuccess) return ::helm::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define HELM_CK_LAUNCH() HELM_CK(cudaGetLastError())
+
+#define HELM_TRY(expr)                     \
+  do {                                     \
+    helm_status s_ = (expr);               \
+    if (s_ != HELM_OK) return s_;          \
+  } while (0)
+
+// ------------------------------------------------------------------ complex helpers
+
+template <typename R> struct cplx;
+template <> struct cplx<float> { using T = float2; };
+template <> struct cplx<double> { using T = double2; };
+template <typename R> using C = typename cplx<R>::T;
+
+template <typename R> __host__ __device__ __forceinline__ C<R> mk(R a, R b) { C<R> r; r.x = a; r.y = b; return r; }
+template <typename T> __host__ __device__ __forceinline__ T cadd(T a, T b) { a.x += b.x; a.y += b.y; return a; }
+template <typename T> __host__ __device__ __forceinline__ T csub(T a, T b) { a.x -= b.x; a.y -= b.y; return a; }
+template <typename T> __host__ __device__ __forceinline__ T cmul(T a, T b) {
+  T r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename T> __host__ __device__ __forceinline__ T cconj(T a) { a.y = -a.y; return a; }
+template <typename T, typename S> __host__ __device__ __forceinline__ T cscale(T a, S s) { a.x *= s; a.y *= s; return a; }
+// conj(a) * b
+template <typename T> __host__ __device__ __forceinline__ T cdotc(T a, T b) {
+  T r; r.x = a.x * b.x + a.y * b.y; r.y = a.x * b.y - a.y * b.x; return r;
+}
+
+// ------------------------------------------------------------------ context
+
+struct SysHost {
+  int nx, ny, p, Nx, Ny;
+  double h, omega, sigma_max;
+  int64_t off;        // first point of this system within one right-hand side block set
+  int64_t n;          // Nx * Ny
+  int64_t prof_x, prof_y;  // offsets into the profile arrays
+};
+
+// Column = (system, right-hand side).  Device copy used by reduction kernels.
+struct ColDesc {
+  int64_t off;  // first element of the column in a batch vector
+  int64_t len;  // points
+  int sys;
+  double h2;    // h^2 of the column's system (network output scale)
+};
+
+struct Workspace {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  helm_status reserve(size_t need);
+  ~Workspace();
+};
+
+struct UnetBuffers;  // activation storage, defined in unet.cu
+
+struct helm_ctx_impl;
+
+}  // namespace helm
+
+struct helm_ctx {
+  int nsys = 0;
+  std::vector<helm::SysHost> sys;
+  int64_t npts = 0;            // sum of n_s
+  // per point (npts): k^2 in both precisions, c / 1500 m/s
+  float* k2f = nullptr;
+  double* k2d = nullptr;
+  float* chat = nullptr;
+  // per system 1-D profiles: s(node) and 1 / s(half node) in x and y, both precisions
+  double2* prof_d = nullptr;
+  float2* prof_f = nullptr;
+  int64_t prof_len = 0;
+  // per-nrhs column tables (rebuilt on demand)
+  int cols_nrhs = -1;
+  helm::ColDesc* cols_dev = nullptr;
+  std::vector<helm::ColDesc> cols_host;
+  // scratch for reductions and solver state
+  helm::Workspace ws_red, ws_solver, ws_vec, ws_unet, ws_train;
+  helm::UnetBuffers* ub = nullptr;
+  int* flag_dev = nullptr;         // device error/status flag
+  void* pinned = nullptr;          // small pinned host buffer for status reads
+  size_t pinned_bytes = 0;
+};
+
+namespace helm {
+
+// ctx.cu
+helm_status ensure_cols(helm_ctx* ctx, int nrhs);
+helm_status ensure_pinned(helm_ctx* ctx, size_t bytes);
+int num_cols(const helm_ctx* ctx, int nrhs);
+
+// stencil.cu: y = A x (or A^H x) for all systems and right-hand sides
+template <typename R>
+helm_status apply_op(helm_ctx* ctx, const C<R>* x, C<R>* y, int nrhs, bool adjoint, cudaStream_t st);
+// r = b - A x (FP64) and per-column ||r||^2, ||b||^2 into sums[col*2 + {0,1}] (device)
+helm_status residual_fp64(helm_ctx* ctx, const double2* x, const double2* b, double2* r, int nrhs,
+                          double* sums, cudaStream_t st);
+
+// reduce.cu: per-column sum of |v|^2 (FP64) into out[col] (device); deterministic
+template <typename R>
+helm_status col_norm2(helm_ctx* ctx, const C<R>* v, int nrhs, double* out, cudaStream_t st);
+
+// out[col * nvals + v] = sum over the column's partials in a fixed order (stencil.cu)
+__global__ void k_finalize(const double* __restrict__ partial, const int* __restrict__ nparts_col, int nvals,
+                           double* __restrict__ out);
+
+inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace helm

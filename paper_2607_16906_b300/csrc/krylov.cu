@@ -1,0 +1,607 @@
+// Flexible GMRES (Alg. 1, eq. 4) with CGS2 orthogonalisation, FP64 Givens least squares and an
+// FP64 true-residual / iterative-refinement outer loop (a4-a8).
+//
+// Vectors are batch vectors (all columns = (system, rhs) pairs back to back).  Per iteration j:
+//   z_j = N_theta(v_j)                      (unet.cu; z_j = v_j without a network)
+//   w   = A z_j                             (stencil.cu)
+//   CGS2: h1 = V_j^H w; w -= V_j h1; h2 = V_j^H w; w -= V_j h2  (k_mdot / k_hreduce / k_maxpy)
+//   h_{j+1,j} = ||w||, stored unnormalised as V[j+1] with scale 1/||w|| (deferred normalisation)
+//   Givens rotation of the new Hessenberg column, residual estimate |g_{j+1}|  (k_givens, FP64)
+// End of cycle: y = R^{-1} g (k_backsolve, FP64), x += beta Z y (k_xupdate, FP64 accumulation).
+//
+// The inner vectors are complex FP32 (mixed path) or FP64 (plain path); reductions accumulate
+// per thread in the vector precision and across threads and blocks in FP64, in a fixed order.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "helm_internal.cuh"
+#include "unet.cuh"
+
+namespace helm {
+
+constexpr int RED_THREADS = 256;
+constexpr int DOT_G = 8;
+
+// ------------------------------------------------------------------ reductions
+
+struct ColState {
+  int active;   // still iterating in this cycle
+  int k;        // iterations done in this cycle
+  int status;   // helm_status of the cycle
+  int pad;
+  double target;  // stop when |g_{j+1}| <= target (relative to beta = 1)
+  double est;     // last |g_{j+1}|
+  double beta;    // ||r|| of the cycle's starting residual (FP64)
+  double hscale;  // largest |h| seen (breakdown reference)
+};
+
+
+template <int NV>
+__device__ __forceinline__ void block_reduce_store(double (&v)[NV], double* __restrict__ out) {
+  __shared__ double red[RED_THREADS / 32][NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k)
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[w][k] = v[k];
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0;
+    for (int q = 0; q < RED_THREADS / 32; ++q) s += red[q][threadIdx.x];
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ void chunk_range(int64_t len, int nch, int chunk, int64_t& a, int64_t& b) {
+  a = len * chunk / nch;
+  b = len * (chunk + 1) / nch;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_colnorm2(const C<R>* __restrict__ v, const ColDesc* __restrict__ cols,
+                                                          int nch, double* __restrict__ partial) {
+  int col = blockIdx.y, chunk = blockIdx.x;
+  ColDesc cd = cols[col];
+  int64_t a, b;
+  chunk_range(cd.len, nch, chunk, a, b);
+  double s[1] = {0.0};
+  for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
+    C<R> x = v[cd.off + p];
+    s[0] += (double)x.x * x.x + (double)x.y * x.y;
+  }
+  block_reduce_store<1>(s, partial + (int64_t)col * nch + chunk);
+}
+
+// Multi-dot: partial[(col * nch + chunk) * ldp + i] = sum over the chunk of conj(V_i) w, i < nv.
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_mdot(const C<R>* __restrict__ V, int64_t vstride, int nv,
+                                                      const C<R>* __restrict__ w, const ColDesc* __restrict__ cols,
+                                                      const ColState* __restrict__ st, int nch,
+                                                      double2* __restrict__ partial, int ldp) {
+  int col = blockIdx.y, chunk = blockIdx.x;
+  if (!st[col].active) return;
+  ColDesc cd = cols[col];
+  int64_t a, b;
+  chunk_range(cd.len, nch, chunk, a, b);
+  double2* outp = partial + ((int64_t)col * nch + chunk) * ldp;
+  for (int i0 = 0; i0 < nv; i0 += DOT_G) {
+    C<R> acc[DOT_G];
+#pragma unroll
+    for (int g = 0; g < DOT_G; ++g) acc[g] = mk<R>(0, 0);
+    int ng = min(DOT_G, nv - i0);
+    for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
+      C<R> wv = w[cd.off + p];
+#pragma unroll
+      for (int g = 0; g < DOT_G; ++g)
+        if (g < ng) acc[g] = cadd(acc[g], cdotc(V[(int64_t)(i0 + g) * vstride + cd.off + p], wv));
+    }
+    double v[2 * DOT_G];
+#pragma unroll
+    for (int g = 0; g < DOT_G; ++g) {
+      v[2 * g] = acc[g].x;
+      v[2 * g + 1] = acc[g].y;
+    }
+    __shared__ double tmp[2 * DOT_G];
+    block_reduce_store<2 * DOT_G>(v, tmp);
+    if (threadIdx.x < ng) outp[i0 + threadIdx.x] = make_double2(tmp[2 * threadIdx.x], tmp[2 * threadIdx.x + 1]);
+    __syncthreads();
+  }
+}
+
+// h_i = vscale_i * sum_chunks partial;  hbuf (+)= h;  coef_i = h_i * vscale_i (vector precision).
+template <typename R>
+__global__ void k_hreduce(const double2* __restrict__ partial, int nch, int ldp, int nv,
+                          const double* __restrict__ vscale, int ldv, const ColState* __restrict__ st,
+                          double2* __restrict__ hbuf, C<R>* __restrict__ coef, int accumulate) {
+  int col = blockIdx.x;
+  if (!st[col].active) return;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    double2 s = make_double2(0, 0);
+    for (int c = 0; c < nch; ++c) s = cadd(s, partial[((int64_t)col * nch + c) * ldp + i]);
+    double sc = vscale[(int64_t)col * ldv + i];
+    s = cscale(s, sc);
+    double2* hb = hbuf + (int64_t)col * ldp + i;
+    *hb = accumulate ? cadd(*hb, s) : s;
+    coef[(int64_t)col * ldp + i] = mk<R>((R)(s.x * sc), (R)(s.y * sc));
+  }
+}
+
+// w -= sum_i V_i coef_i;  optionally write the result to dst and per-chunk |w|^2 partials.
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_maxpy(const C<R>* __restrict__ V, int64_t vstride, int nv,
+                                                       C<R>* __restrict__ w, const C<R>* __restrict__ coef, int ldc,
+                                                       const ColDesc* __restrict__ cols,
+                                                       const ColState* __restrict__ st, int nch, C<R>* __restrict__ dst,
+                                                       double* __restrict__ npartial) {
+  int col = blockIdx.y, chunk = blockIdx.x;
+  if (!st[col].active) return;
+  extern __shared__ unsigned char smem_raw[];
+  C<R>* cf = (C<R>*)smem_raw;
+  for (int i = threadIdx.x; i < nv; i += RED_THREADS) cf[i] = coef[(int64_t)col * ldc + i];
+  __syncthreads();
+  ColDesc cd = cols[col];
+  int64_t a, b;
+  chunk_range(cd.len, nch, chunk, a, b);
+  double s[1] = {0.0};
+  for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
+    int64_t q = cd.off + p;
+    C<R> acc = w[q];
+    for (int i = 0; i < nv; ++i) acc = csub(acc, cmul(V[(int64_t)i * vstride + q], cf[i]));
+    if (dst) {
+      dst[q] = acc;
+      s[0] += (double)acc.x * acc.x + (double)acc.y * acc.y;
+    } else {
+      w[q] = acc;
+    }
+  }
+  if (npartial) block_reduce_store<1>(s, npartial + (int64_t)col * nch + chunk);
+}
+
+// ------------------------------------------------------------------ per-column scalar kernels
+
+// One thread per column: finish ||w||, rotate the new Hessenberg column, update g.
+template <typename R>
+__global__ void k_givens(int j, int ncol, int m, const double* __restrict__ npartial, int nch,
+                         const double2* __restrict__ hbuf, int ldp, double* __restrict__ vscale,
+                         double2* __restrict__ Rm, double* __restrict__ cs, double2* __restrict__ sn,
+                         double2* __restrict__ g, ColState* __restrict__ st, int* __restrict__ nactive,
+                         double* __restrict__ in_scale, const ColDesc* __restrict__ cols, double breakdown_eps) {
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  ColState& S = st[col];
+  if (!S.active) {
+    in_scale[col] = 0.0;
+    return;
+  }
+  double nn = 0;
+  for (int c = 0; c < nch; ++c) nn += npartial[(int64_t)col * nch + c];
+  double hn = sqrt(nn);
+  const double2* h = hbuf + (int64_t)col * ldp;
+  double2* Rc = Rm + ((int64_t)col * m + j) * (m + 1);  // column j of R
+  double hmax = S.hscale;
+  for (int i = 0; i <= j; ++i) {
+    Rc[i] = h[i];
+    hmax = fmax(hmax, hypot(h[i].x, h[i].y));
+  }
+  hmax = fmax(hmax, hn);
+  S.hscale = hmax;
+  double* csc = cs + (int64_t)col * m;
+  double2* snc = sn + (int64_t)col * m;
+  double2* gc = g + (int64_t)col * (m + 1);
+  for (int i = 0; i < j; ++i) {
+    double2 a = Rc[i], b = Rc[i + 1];
+    double c = csc[i];
+    double2 s = snc[i];
+    Rc[i] = cadd(cscale(a, c), cmul(s, b));
+    Rc[i + 1] = csub(cscale(b, c), cmul(cconj(s), a));
+  }
+  // new rotation zeroing (Rc[j], hn): c = |a| / t, s = (a / |a|) conj(b) / t, b real here
+  double2 a = Rc[j];
+  double aa = hypot(a.x, a.y);
+  double c, t = hypot(aa, hn);
+  double2 s;
+  if (hn == 0.0) {
+    c = 1.0;
+    s = make_double2(0, 0);
+  } else if (aa == 0.0) {
+    c = 0.0;
+    s = make_double2(1, 0);
+  } else {
+    c = aa / t;
+    s = cscale(a, hn / (aa * t));  // (a/|a|) * conj(hn) / t with hn real
+  }
+  csc[j] = c;
+  snc[j] = s;
+  Rc[j] = cadd(cscale(a, c), cscale(s, hn));
+  double2 gj = gc[j];
+  gc[j + 1] = cscale(cmul(cconj(s), gj), -1.0);
+  gc[j] = cscale(gj, c);
+  double est = hypot(gc[j + 1].x, gc[j + 1].y);
+  S.est = est;
+  S.k = j + 1;
+  bool bad = !isfinite(hn) || !isfinite(est) || !isfinite(Rc[j].x) || !isfinite(Rc[j].y);
+  double rjj = hypot(Rc[j].x, Rc[j].y);
+  if (bad) {
+    S.status = HELM_NAN;
+    S.active = 0;
+    S.k = j;  // drop the poisoned column
+  } else if (est <= S.target) {
+    S.status = HELM_OK;
+    S.active = 0;
+  } else if (hn <= breakdown_eps * hmax || rjj <= breakdown_eps * hmax) {
+    S.status = HELM_BREAKDOWN;
+    S.active = 0;
+    if (rjj <= breakdown_eps * hmax) S.k = j;
+  } else if (j + 1 >= m) {
+    S.status = HELM_NOT_CONVERGED;
+    S.active = 0;
+  }
+  double inv = hn > 0 ? 1.0 / hn : 0.0;
+  vscale[(int64_t)col * (m + 1) + j + 1] = inv;
+  in_scale[col] = S.active ? sqrt((double)cols[col].len) * inv : 0.0;
+  if (S.active) atomicAdd(nactive, 1);
+}
+
+// y = R^{-1} g (k x k upper triangular), ycoef_i = beta * y_i.
+__global__ void k_backsolve(int ncol, int m, const double2* __restrict__ Rm, const double2* __restrict__ g,
+                            const ColState* __restrict__ st, double2* __restrict__ y) {
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  const ColState& S = st[col];
+  int k = S.k;
+  double2* yc = y + (int64_t)col * m;
+  const double2* gc = g + (int64_t)col * (m + 1);
+  for (int i = k - 1; i >= 0; --i) {
+    double2 s = gc[i];
+    for (int jj = i + 1; jj < k; ++jj) s = csub(s, cmul(Rm[((int64_t)col * m + jj) * (m + 1) + i], yc[jj]));
+    double2 d = Rm[((int64_t)col * m + i) * (m + 1) + i];
+    double den = d.x * d.x + d.y * d.y;
+    yc[i] = den > 0 ? make_double2((s.x * d.x + s.y * d.y) / den, (s.y * d.x - s.x * d.y) / den) : make_double2(0, 0);
+  }
+  for (int i = 0; i < k; ++i) yc[i] = cscale(yc[i], S.beta);
+}
+
+// x += sum_{i<k} Z_i y_i (FP64 accumulation).  Z_i is v_i scaled by zscale_i when Z aliases V.
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_xupdate(const C<R>* __restrict__ Z, int64_t zstride,
+                                                         const double2* __restrict__ y, int m,
+                                                         const double* __restrict__ zscale,
+                                                         const ColState* __restrict__ st,
+                                                         const ColDesc* __restrict__ cols, int nch,
+                                                         double2* __restrict__ x) {
+  int col = blockIdx.y, chunk = blockIdx.x;
+  int k = st[col].k;
+  if (k == 0) return;
+  __shared__ double2 yc[HELM_MAX_M];
+  for (int i = threadIdx.x; i < k; i += RED_THREADS)
+    yc[i] = zscale ? cscale(y[(int64_t)col * m + i], zscale[(int64_t)col * (m + 1) + i]) : y[(int64_t)col * m + i];
+  __syncthreads();
+  ColDesc cd = cols[col];
+  int64_t a, b;
+  chunk_range(cd.len, nch, chunk, a, b);
+  for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
+    int64_t q = cd.off + p;
+    double2 acc = x[q];
+    for (int i = 0; i < k; ++i) {
+      C<R> z = Z[(int64_t)i * zstride + q];
+      acc.x += (double)z.x * yc[i].x - (double)z.y * yc[i].y;
+      acc.y += (double)z.x * yc[i].y + (double)z.y * yc[i].x;
+    }
+    x[q] = acc;
+  }
+}
+
+// V0 = r / beta in the vector precision for active columns.
+template <typename R>
+__global__ void k_v0(const double2* __restrict__ r, C<R>* __restrict__ V0, const ColState* __restrict__ st,
+                     const ColDesc* __restrict__ cols, int nch) {
+  int col = blockIdx.y, chunk = blockIdx.x;
+  const ColState& S = st[col];
+  ColDesc cd = cols[col];
+  int64_t a, b;
+  chunk_range(cd.len, nch, chunk, a, b);
+  double inv = S.active && S.beta > 0 ? 1.0 / S.beta : 0.0;
+  for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x) {
+    double2 v = r[cd.off + p];
+    V0[cd.off + p] = mk<R>((R)(v.x * inv), (R)(v.y * inv));
+  }
+}
+
+// z = s * v per column (identity preconditioner applied to the deferred-scaled basis vector).
+template <typename R>
+__global__ void k_scale_copy(const C<R>* __restrict__ v, C<R>* __restrict__ z, const double* __restrict__ s,
+                             const ColDesc* __restrict__ cols, int nch, const double* __restrict__ in_scale) {
+  int col = blockIdx.y, chunk = blockIdx.x;
+  ColDesc cd = cols[col];
+  int64_t a, b;
+  chunk_range(cd.len, nch, chunk, a, b);
+  R sc = (R)(in_scale[col] / sqrt((double)cd.len));
+  for (int64_t p = a + threadIdx.x; p < b; p += blockDim.x) z[cd.off + p] = cscale(v[cd.off + p], sc);
+}
+
+// ------------------------------------------------------------------ host helpers
+
+template <typename R>
+helm_status col_norm2(helm_ctx* ctx, const C<R>* v, int nrhs, double* out, cudaStream_t st) {
+  HELM_TRY(ensure_cols(ctx, nrhs));
+  int ncol = num_cols(ctx, nrhs);
+  int nch = std::max(1, std::min(64, (int)(2048 / std::max(1, ncol))));
+  HELM_TRY(ctx->ws_red.reserve(sizeof(double) * ncol * nch + sizeof(int) * ncol + 64));
+  double* partial = (double*)ctx->ws_red.ptr;
+  int* np = (int*)(partial + ncol * nch);
+  std::vector<int> nph(ncol, nch);
+  HELM_CK(cudaMemcpyAsync(np, nph.data(), sizeof(int) * ncol, cudaMemcpyHostToDevice, st));
+  k_colnorm2<R><<<dim3(nch, ncol), RED_THREADS, 0, st>>>(v, ctx->cols_dev, nch, partial);
+  HELM_CK_LAUNCH();
+  k_finalize<<<ncol, 256, 0, st>>>(partial, np, 1, out);
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+template helm_status col_norm2<float>(helm_ctx*, const float2*, int, double*, cudaStream_t);
+template helm_status col_norm2<double>(helm_ctx*, const double2*, int, double*, cudaStream_t);
+
+// Solver workspace layout (one allocation, 256-byte aligned pieces).
+template <typename R>
+struct SolverWs {
+  C<R>* V;       // (m+1) vectors
+  C<R>* Z;       // m vectors (aliases V without a network)
+  C<R>* w;       // 1 vector
+  double2* r;    // FP64 residual
+  double2* partial;
+  double* npartial;
+  double2* hbuf;
+  C<R>* coef;
+  double* vscale;
+  double2* Rm;
+  double* cs;
+  double2* sn;
+  double2* g;
+  double2* y;
+  ColState* st;
+  double* sums;
+  double* in_scale;
+  double* out_scale;
+  int* nactive;
+};
+
+template <typename R>
+static helm_status solver_ws(helm_ctx* ctx, int m, int ncol, int nch, bool has_net, int64_t nvec, SolverWs<R>& W) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  size_t vb = sizeof(C<R>) * nvec;
+  size_t oV = take(vb * (m + 1));
+  size_t oZ = has_net ? take(vb * m) : oV;
+  size_t ow = take(vb);
+  size_t orr = take(sizeof(double2) * nvec);
+  int ldp = m + 1;
+  size_t op = take(sizeof(double2) * ncol * nch * ldp);
+  size_t onp = take(sizeof(double) * ncol * nch);
+  size_t oh = take(sizeof(double2) * ncol * ldp);
+  size_t oc = take(sizeof(C<R>) * ncol * ldp);
+  size_t ovs = take(sizeof(double) * ncol * ldp);
+  size_t oR = take(sizeof(double2) * ncol * m * (m + 1));
+  size_t ocs = take(sizeof(double) * ncol * m);
+  size_t osn = take(sizeof(double2) * ncol * m);
+  size_t og = take(sizeof(double2) * ncol * (m + 1));
+  size_t oy = take(sizeof(double2) * ncol * m);
+  size_t ost = take(sizeof(ColState) * ncol);
+  size_t osu = take(sizeof(double) * 2 * ncol);
+  size_t ois = take(sizeof(double) * ncol);
+  size_t oos = take(sizeof(double) * ncol);
+  size_t ona = take(sizeof(int) * 4);
+  HELM_TRY(ctx->ws_solver.reserve(off));
+  char* b = (char*)ctx->ws_solver.ptr;
+  W.V = (C<R>*)(b + oV);
+  W.Z = (C<R>*)(b + oZ);
+  W.w = (C<R>*)(b + ow);
+  W.r = (double2*)(b + orr);
+  W.partial = (double2*)(b + op);
+  W.npartial = (double*)(b + onp);
+  W.hbuf = (double2*)(b + oh);
+  W.coef = (C<R>*)(b + oc);
+  W.vscale = (double*)(b + ovs);
+  W.Rm = (double2*)(b + oR);
+  W.cs = (double*)(b + ocs);
+  W.sn = (double2*)(b + osn);
+  W.g = (double2*)(b + og);
+  W.y = (double2*)(b + oy);
+  W.st = (ColState*)(b + ost);
+  W.sums = (double*)(b + osu);
+  W.in_scale = (double*)(b + ois);
+  W.out_scale = (double*)(b + oos);
+  W.nactive = (int*)(b + ona);
+  return HELM_OK;
+}
+
+__global__ void k_fill(double* p, int64_t n, double v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = v;
+}
+
+template <typename R>
+helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, double2* x, int nrhs,
+                         const helm_solve_opts& o, helm_solve_info* info, cudaStream_t stream) {
+  HELM_TRY(ensure_cols(ctx, nrhs));
+  const int ncol = num_cols(ctx, nrhs);
+  const int m = o.m;
+  const int64_t nvec = ctx->npts * nrhs;
+  int64_t maxlen = 0;
+  for (auto& c : ctx->cols_host) maxlen = std::max(maxlen, c.len);
+  const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((4 * 148 + ncol - 1) / ncol, (maxlen + 1023) / 1024));
+  SolverWs<R> W;
+  HELM_TRY(solver_ws<R>(ctx, m, ncol, nch, net != nullptr, nvec, W));
+  HELM_TRY(ensure_pinned(ctx, sizeof(double) * 2 * ncol + sizeof(ColState) * ncol + 64));
+  double* h_sums = (double*)ctx->pinned;
+  ColState* h_st = (ColState*)(h_sums + 2 * ncol);
+  int* h_nact = (int*)(h_st + ncol);
+  const bool mixed = sizeof(R) == 4;
+  const int max_cycles = mixed ? std::max(1, o.max_outer) : std::max(1, o.max_restarts);
+  const double breakdown_eps = mixed ? 1e-6 : 1e-14;
+  const int ldp = m + 1;
+  const size_t maxpy_smem = sizeof(C<R>) * ldp;
+  if (maxpy_smem > 48 * 1024)
+    HELM_CK(cudaFuncSetAttribute(k_maxpy<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)maxpy_smem));
+  std::vector<helm_solve_info> inf(ncol);
+  for (auto& v : inf) {
+    v = helm_solve_info{};
+    v.status = HELM_NOT_CONVERGED;
+  }
+  std::vector<double> bnorm(ncol, 0.0), rel(ncol, 0.0);
+  std::vector<int> done(ncol, 0);
+  dim3 vgrid(nch, ncol);
+  for (int cyc = 0; cyc <= max_cycles; ++cyc) {
+    // true residual in FP64 (eq. 10)
+    HELM_TRY(residual_fp64(ctx, x, b, W.r, nrhs, W.sums, stream));
+    HELM_CK(cudaMemcpyAsync(h_sums, W.sums, sizeof(double) * 2 * ncol, cudaMemcpyDeviceToHost, stream));
+    HELM_CK(cudaStreamSynchronize(stream));
+    int nact = 0;
+    for (int c = 0; c < ncol; ++c) {
+      double rr = sqrt(h_sums[2 * c]), bb = sqrt(h_sums[2 * c + 1]);
+      bnorm[c] = bb;
+      rel[c] = bb > 0 ? rr / bb : rr;
+      inf[c].relres_true = rel[c];
+      if (!std::isfinite(rel[c])) {
+        inf[c].status = HELM_NAN;
+        done[c] = 1;
+      } else if (rel[c] <= o.tol) {
+        inf[c].status = HELM_OK;
+        done[c] = 1;
+      } else if (done[c] && inf[c].status == HELM_BREAKDOWN) {
+        // stays done
+      }
+      ColState s{};
+      s.active = !done[c] && cyc < max_cycles;
+      s.beta = rr;
+      s.target = mixed ? std::max(o.inner_tol, o.tol * bb / std::max(rr, 1e-300))
+                       : o.tol * bb / std::max(rr, 1e-300) * 0.5;
+      s.status = HELM_NOT_CONVERGED;
+      h_st[c] = s;
+      nact += s.active;
+    }
+    if (nact == 0) break;
+    HELM_CK(cudaMemcpyAsync(W.st, h_st, sizeof(ColState) * ncol, cudaMemcpyHostToDevice, stream));
+    // g = beta e1 with beta = 1 (the cycle runs on r / ||r||); vscale_0 = 1
+    HELM_CK(cudaMemsetAsync(W.g, 0, sizeof(double2) * ncol * (m + 1), stream));
+    {
+      std::vector<double2> g0(ncol, make_double2(1.0, 0.0));
+      for (int c = 0; c < ncol; ++c)
+        HELM_CK(cudaMemcpyAsync(W.g + (int64_t)c * (m + 1), &g0[c], sizeof(double2), cudaMemcpyHostToDevice, stream));
+      std::vector<double> v0(ncol), is(ncol), os(ncol);
+      for (int c = 0; c < ncol; ++c) {
+        is[c] = sqrt((double)ctx->cols_host[c].len);
+        os[c] = ctx->cols_host[c].h2 / is[c];
+      }
+      HELM_CK(cudaMemcpyAsync(W.in_scale, is.data(), sizeof(double) * ncol, cudaMemcpyHostToDevice, stream));
+      HELM_CK(cudaMemcpyAsync(W.out_scale, os.data(), sizeof(double) * ncol, cudaMemcpyHostToDevice, stream));
+      k_fill<<<cdiv((int64_t)ncol * ldp, 256), 256, 0, stream>>>(W.vscale, (int64_t)ncol * ldp, 1.0);
+      HELM_CK(cudaStreamSynchronize(stream));  // host vectors above go out of scope
+    }
+    k_v0<R><<<vgrid, RED_THREADS, 0, stream>>>(W.r, W.V, W.st, ctx->cols_dev, nch);
+    HELM_CK_LAUNCH();
+    for (int j = 0; j < m; ++j) {
+      C<R>* Vj = W.V + (int64_t)j * nvec;
+      C<R>* Zj = net ? W.Z + (int64_t)j * nvec : Vj;
+      // z_j = N_theta(v_j)
+      if (net) {
+        for (int s = 0; s < ctx->nsys; ++s) {
+          int64_t off = ctx->sys[s].off * nrhs;
+          HELM_TRY(unet_precondition<R>(ctx, net, s, Vj + off, Zj + off, nrhs, W.in_scale + s * nrhs,
+                                        W.out_scale + s * nrhs, stream));
+        }
+      }
+      // w = A z_j  (without a network z_j = vscale_j * Vraw_j: apply to Vraw and fold the scale into h)
+      if (net) {
+        HELM_TRY(apply_op<R>(ctx, Zj, W.w, nrhs, false, stream));
+      } else {
+        // the FP64 residual buffer is free after k_v0: use it for the scaled copy z_j = v_j
+        C<R>* zt = (C<R>*)W.r;
+        k_scale_copy<R><<<vgrid, RED_THREADS, 0, stream>>>(Vj, zt, nullptr, ctx->cols_dev, nch, W.in_scale);
+        HELM_CK_LAUNCH();
+        HELM_TRY(apply_op<R>(ctx, zt, W.w, nrhs, false, stream));
+      }
+      const int nv = j + 1;
+      // CGS2, two passes
+      for (int pass = 0; pass < 2; ++pass) {
+        k_mdot<R><<<vgrid, RED_THREADS, 0, stream>>>(W.V, nvec, nv, W.w, ctx->cols_dev, W.st, nch,
+                                                      W.partial, ldp);
+        HELM_CK_LAUNCH();
+        k_hreduce<R><<<ncol, 128, 0, stream>>>(W.partial, nch, ldp, nv, W.vscale, ldp, W.st, W.hbuf,
+                                                W.coef, pass);
+        HELM_CK_LAUNCH();
+        C<R>* dst = pass == 1 ? W.V + (int64_t)(j + 1) * nvec : nullptr;
+        k_maxpy<R><<<vgrid, RED_THREADS, maxpy_smem, stream>>>(W.V, nvec, nv, W.w, W.coef, ldp, ctx->cols_dev,
+                                                               W.st, nch, dst,
+                                                               pass == 1 ? W.npartial : nullptr);
+        HELM_CK_LAUNCH();
+      }
+      HELM_CK(cudaMemsetAsync(W.nactive, 0, sizeof(int), stream));
+      k_givens<R><<<cdiv(ncol, 64), 64, 0, stream>>>(j, ncol, m, W.npartial, nch, W.hbuf, ldp, W.vscale, W.Rm, W.cs,
+                                                     W.sn, W.g, W.st, W.nactive, W.in_scale, ctx->cols_dev,
+                                                     breakdown_eps);
+      HELM_CK_LAUNCH();
+      HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      HELM_CK(cudaStreamSynchronize(stream));
+      if (*h_nact == 0) break;
+    }
+    k_backsolve<<<cdiv(ncol, 64), 64, 0, stream>>>(ncol, m, W.Rm, W.g, W.st, W.y);
+    HELM_CK_LAUNCH();
+    k_xupdate<R><<<vgrid, RED_THREADS, 0, stream>>>(W.Z, nvec, W.y, m, net ? nullptr : W.vscale, W.st,
+                                                    ctx->cols_dev, nch, x);
+    HELM_CK_LAUNCH();
+    HELM_CK(cudaMemcpyAsync(h_st, W.st, sizeof(ColState) * ncol, cudaMemcpyDeviceToHost, stream));
+    HELM_CK(cudaStreamSynchronize(stream));
+    for (int c = 0; c < ncol; ++c) {
+      if (done[c]) continue;
+      inf[c].iters += h_st[c].k;
+      inf[c].restarts += 1;
+      inf[c].outer += mixed ? 1 : 0;
+      inf[c].relres_est = h_st[c].est * rel[c];
+      if (h_st[c].status == HELM_NAN) {
+        inf[c].status = HELM_NAN;
+        done[c] = 1;
+      } else if (h_st[c].status == HELM_BREAKDOWN && h_st[c].k == 0) {
+        inf[c].status = HELM_BREAKDOWN;
+        done[c] = 1;
+      }
+    }
+  }
+  helm_status worst = HELM_OK;
+  for (int c = 0; c < ncol; ++c) {
+    if (inf[c].status == HELM_OK && !(inf[c].relres_true <= o.tol)) inf[c].status = HELM_NOT_CONVERGED;
+    if (inf[c].status != HELM_OK && worst == HELM_OK) worst = (helm_status)inf[c].status;
+    if (info) info[c] = inf[c];
+  }
+  if (worst != HELM_OK) set_error("helm_fgmres_solve: at least one column did not reach the tolerance");
+  return worst;
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+extern "C" helm_status helm_fgmres_solve(helm_ctx* ctx, const helm_unet* net, const void* b, void* x, int nrhs,
+                                         const helm_solve_opts* opts, helm_solve_info* info, void* stream) {
+  if (!ctx || !b || !x || !opts || nrhs <= 0) return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: bad argument");
+  if (b == x) return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: b and x must not alias");
+  if (((uintptr_t)b | (uintptr_t)x) & 15) return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: pointers must be 16-byte aligned");
+  helm_solve_opts o = *opts;
+  if (o.m < 1 || o.m > HELM_MAX_M) return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: m out of range");
+  if (!(o.tol > 0) || o.max_restarts < 1 || (o.mixed && o.max_outer < 1))
+    return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: tol must be > 0 and iteration budgets >= 1");
+  if (o.mixed && !(o.inner_tol > 0 && o.inner_tol < 1))
+    return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: inner_tol must be in (0, 1)");
+  if (o.orth != HELM_ORTH_CGS2) return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: only CGS2 is implemented");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (o.mixed) return fgmres_solve<float>(ctx, net, (const double2*)b, (double2*)x, nrhs, o, info, st);
+  return fgmres_solve<double>(ctx, net, (const double2*)b, (double2*)x, nrhs, o, info, st);
+}

@@ -1,0 +1,255 @@
+// The complex 5-point Helmholtz stencil with PML stretching (a2), its adjoint, and the fused
+// FP64 true residual r = b - A x with per-column norms (a8, eq. 10).
+//
+// One thread owns one x-column of a strip of STENCIL_ROWS rows and marches down it, keeping the
+// south and centre values in registers; east/west neighbours come from the same row that the
+// neighbouring threads load (L1 hits).  Loads and stores are coalesced across the warp (one complex
+// per thread, 8 B in FP32, 16 B in FP64).  Per point the kernel moves 8 + 8 + 4 B (FP32) or
+// 16 + 16 + 8 B (FP64) of HBM traffic: read u, write A u, read k^2; the 1-D PML profiles are
+// O(Nx + Ny) and stay in L1/L2.
+#include "helm_internal.cuh"
+
+namespace helm {
+
+constexpr int STENCIL_ROWS = 8;
+constexpr int STENCIL_THREADS = 128;
+
+template <typename R, bool ADJ>
+__device__ __forceinline__ C<R> ld_u(const C<R>* __restrict__ x, int j, int i, int Nx, int Ny) {
+  if (j < 0 || j >= Ny || i < 0 || i >= Nx) return mk<R>(0, 0);
+  C<R> v = x[(int64_t)j * Nx + i];
+  if (ADJ) v.y = -v.y;
+  return v;
+}
+
+// Point update: -(1/h^2)[s_y(j)((uE-uC)/s_x(i+1/2) - (uC-uW)/s_x(i-1/2))
+//                      + s_x(i)((uN-uC)/s_y(j+1/2) - (uC-uS)/s_y(j-1/2))] - s_x s_y k^2 uC
+template <typename R>
+__device__ __forceinline__ C<R> stencil_point(C<R> uC, C<R> uE, C<R> uW, C<R> uN, C<R> uS, C<R> sxi, C<R> ixm,
+                                              C<R> ixp, C<R> syj, C<R> iym, C<R> iyp, R k2, R inv_h2) {
+  C<R> fx = csub(cmul(csub(uE, uC), ixp), cmul(csub(uC, uW), ixm));
+  C<R> fy = csub(cmul(csub(uN, uC), iyp), cmul(csub(uC, uS), iym));
+  C<R> acc = cadd(cmul(syj, fx), cmul(sxi, fy));
+  C<R> sxy = cmul(sxi, syj);
+  C<R> diag = cmul(sxy, uC);
+  C<R> r;
+  r.x = -acc.x * inv_h2 - k2 * diag.x;
+  r.y = -acc.y * inv_h2 - k2 * diag.y;
+  return r;
+}
+
+template <typename R, bool ADJ>
+__global__ void __launch_bounds__(STENCIL_THREADS) k_stencil(const C<R>* __restrict__ x, C<R>* __restrict__ y,
+                                                             const R* __restrict__ k2, const C<R>* __restrict__ px,
+                                                             const C<R>* __restrict__ py, int Nx, int Ny,
+                                                             int64_t rhs_stride, R inv_h2) {
+  int i = blockIdx.x * STENCIL_THREADS + threadIdx.x;
+  if (i >= Nx) return;
+  int j0 = blockIdx.y * STENCIL_ROWS;
+  const C<R>* xr = x + blockIdx.z * rhs_stride;
+  C<R>* yr = y + blockIdx.z * rhs_stride;
+  const C<R> sxi = px[i], ixm = px[Nx + i], ixp = px[Nx + i + 1];
+  C<R> uS = ld_u<R, ADJ>(xr, j0 - 1, i, Nx, Ny);
+  C<R> uC = ld_u<R, ADJ>(xr, j0, i, Nx, Ny);
+#pragma unroll
+  for (int r = 0; r < STENCIL_ROWS; ++r) {
+    int j = j0 + r;
+    if (j >= Ny) break;
+    C<R> uN = ld_u<R, ADJ>(xr, j + 1, i, Nx, Ny);
+    C<R> uW = ld_u<R, ADJ>(xr, j, i - 1, Nx, Ny);
+    C<R> uE = ld_u<R, ADJ>(xr, j, i + 1, Nx, Ny);
+    C<R> out = stencil_point<R>(uC, uE, uW, uN, uS, sxi, ixm, ixp, py[j], py[Ny + j], py[Ny + j + 1],
+                                k2[(int64_t)j * Nx + i], inv_h2);
+    if (ADJ) out.y = -out.y;
+    yr[(int64_t)j * Nx + i] = out;
+    uS = uC;
+    uC = uN;
+  }
+}
+
+// r = b - A x in FP64, plus per-block partial sums of |r|^2 and |b|^2 (deterministic order).
+__global__ void __launch_bounds__(STENCIL_THREADS) k_residual(const double2* __restrict__ x,
+                                                              const double2* __restrict__ b, double2* __restrict__ r,
+                                                              const double* __restrict__ k2,
+                                                              const double2* __restrict__ px,
+                                                              const double2* __restrict__ py, int Nx, int Ny,
+                                                              int64_t rhs_stride, double inv_h2, double* partial,
+                                                              int col0) {
+  int i = blockIdx.x * STENCIL_THREADS + threadIdx.x;
+  int j0 = blockIdx.y * STENCIL_ROWS;
+  const double2* xr = x + blockIdx.z * rhs_stride;
+  const double2* br = b + blockIdx.z * rhs_stride;
+  double2* rr = r + blockIdx.z * rhs_stride;
+  double sr = 0.0, sb = 0.0;
+  if (i < Nx) {
+    const double2 sxi = px[i], ixm = px[Nx + i], ixp = px[Nx + i + 1];
+    double2 uS = ld_u<double, false>(xr, j0 - 1, i, Nx, Ny);
+    double2 uC = ld_u<double, false>(xr, j0, i, Nx, Ny);
+#pragma unroll
+    for (int q = 0; q < STENCIL_ROWS; ++q) {
+      int j = j0 + q;
+      if (j >= Ny) break;
+      double2 uN = ld_u<double, false>(xr, j + 1, i, Nx, Ny);
+      double2 uW = ld_u<double, false>(xr, j, i - 1, Nx, Ny);
+      double2 uE = ld_u<double, false>(xr, j, i + 1, Nx, Ny);
+      int64_t idx = (int64_t)j * Nx + i;
+      double2 Au = stencil_point<double>(uC, uE, uW, uN, uS, sxi, ixm, ixp, py[j], py[Ny + j], py[Ny + j + 1],
+                                         k2[idx], inv_h2);
+      double2 bv = br[idx];
+      double2 res = csub(bv, Au);
+      rr[idx] = res;
+      sr += res.x * res.x + res.y * res.y;
+      sb += bv.x * bv.x + bv.y * bv.y;
+      uS = uC;
+      uC = uN;
+    }
+  }
+  // block reduction (fixed order)
+  __shared__ double red[2][STENCIL_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_down_sync(0xffffffffu, sr, o);
+    sb += __shfl_down_sync(0xffffffffu, sb, o);
+  }
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[0][w] = sr;
+    red[1][w] = sb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, c = 0;
+    for (int k = 0; k < STENCIL_THREADS / 32; ++k) {
+      a += red[0][k];
+      c += red[1][k];
+    }
+    int nparts = gridDim.x * gridDim.y;
+    int part = blockIdx.y * gridDim.x + blockIdx.x;
+    int64_t base = ((int64_t)(col0 + blockIdx.z) * nparts + part) * 2;
+    partial[base] = a;
+    partial[base + 1] = c;
+  }
+}
+
+// out[col * nvals + v] = sum_p partial[(col * nparts + p) * nvals + v], one block per column.
+__global__ void k_finalize(const double* __restrict__ partial, const int* __restrict__ nparts_col, int nvals,
+                           double* __restrict__ out) {
+  int col = blockIdx.x;
+  int np = nparts_col[col];
+  int64_t base = 0;
+  for (int c = 0; c < col; ++c) base += (int64_t)nparts_col[c] * nvals;
+  __shared__ double red[256 / 32];
+  for (int v = 0; v < nvals; ++v) {
+    double s = 0;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) s += partial[base + (int64_t)p * nvals + v];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+      out[(int64_t)col * nvals + v] = t;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename R>
+helm_status apply_op(helm_ctx* ctx, const C<R>* x, C<R>* y, int nrhs, bool adjoint, cudaStream_t st) {
+  const bool fp64 = sizeof(R) == 8;
+  for (auto& s : ctx->sys) {
+    const C<R>* xs = x + s.off * nrhs;
+    C<R>* ys = y + s.off * nrhs;
+    const R* k2 = fp64 ? (const R*)(ctx->k2d + s.off) : (const R*)(ctx->k2f + s.off);
+    const C<R>* pr = fp64 ? (const C<R>*)ctx->prof_d : (const C<R>*)ctx->prof_f;
+    dim3 grid(cdiv(s.Nx, STENCIL_THREADS), cdiv(s.Ny, STENCIL_ROWS), nrhs);
+    R inv_h2 = (R)(1.0 / (s.h * s.h));
+    if (adjoint)
+      k_stencil<R, true><<<grid, STENCIL_THREADS, 0, st>>>(xs, ys, k2, pr + s.prof_x, pr + s.prof_y, s.Nx, s.Ny,
+                                                           s.n, inv_h2);
+    else
+      k_stencil<R, false><<<grid, STENCIL_THREADS, 0, st>>>(xs, ys, k2, pr + s.prof_x, pr + s.prof_y, s.Nx, s.Ny,
+                                                            s.n, inv_h2);
+  }
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+template helm_status apply_op<float>(helm_ctx*, const float2*, float2*, int, bool, cudaStream_t);
+template helm_status apply_op<double>(helm_ctx*, const double2*, double2*, int, bool, cudaStream_t);
+
+helm_status residual_fp64(helm_ctx* ctx, const double2* x, const double2* b, double2* r, int nrhs, double* sums,
+                          cudaStream_t st) {
+  HELM_TRY(ensure_cols(ctx, nrhs));
+  int ncol = num_cols(ctx, nrhs);
+  // per-column part counts
+  std::vector<int> np(ncol);
+  int64_t total = 0;
+  for (int c = 0; c < ncol; ++c) {
+    auto& s = ctx->sys[ctx->cols_host[c].sys];
+    np[c] = (int)(cdiv(s.Nx, STENCIL_THREADS) * cdiv(s.Ny, STENCIL_ROWS));
+    total += np[c];
+  }
+  size_t need = sizeof(double) * 2 * total + sizeof(int) * ncol + 64;
+  HELM_TRY(ctx->ws_red.reserve(need));
+  double* partial = (double*)ctx->ws_red.ptr;
+  int* np_dev = (int*)(partial + 2 * total);
+  HELM_CK(cudaMemcpyAsync(np_dev, np.data(), sizeof(int) * ncol, cudaMemcpyHostToDevice, st));
+  // partial layout: column-major blocks; every column of system s has the same part count, so the
+  // kernel's (col * nparts + part) indexing is valid within a system; offset per system below.
+  int col0 = 0;
+  int64_t pbase = 0;
+  for (auto& s : ctx->sys) {
+    dim3 grid(cdiv(s.Nx, STENCIL_THREADS), cdiv(s.Ny, STENCIL_ROWS), nrhs);
+    k_residual<<<grid, STENCIL_THREADS, 0, st>>>(x + s.off * nrhs, b + s.off * nrhs, r + s.off * nrhs,
+                                                 ctx->k2d + s.off, ctx->prof_d + s.prof_x, ctx->prof_d + s.prof_y,
+                                                 s.Nx, s.Ny, s.n, 1.0 / (s.h * s.h), partial + pbase * 2, 0);
+    pbase += (int64_t)grid.x * grid.y * nrhs;
+    col0 += nrhs;
+  }
+  HELM_CK_LAUNCH();
+  k_finalize<<<ncol, 256, 0, st>>>(partial, np_dev, 2, sums);
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+static helm_status apply_entry(helm_ctx* ctx, const void* x, void* y, helm_dtype dtype, int nrhs, void* stream,
+                               bool adj, const char* name) {
+  if (!ctx || !x || !y) return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": NULL argument");
+  if (nrhs <= 0) return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": nrhs must be > 0");
+  if (x == y) return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": x and y must not alias");
+  if (((uintptr_t)x | (uintptr_t)y) & 15) return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": pointers must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == HELM_C64) return apply_op<float>(ctx, (const float2*)x, (float2*)y, nrhs, adj, st);
+  if (dtype == HELM_C128) return apply_op<double>(ctx, (const double2*)x, (double2*)y, nrhs, adj, st);
+  return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": unknown dtype");
+}
+
+extern "C" helm_status helm_apply(helm_ctx* ctx, const void* x, void* y, helm_dtype dtype, int nrhs, void* stream) {
+  return apply_entry(ctx, x, y, dtype, nrhs, stream, false, "helm_apply");
+}
+
+extern "C" helm_status helm_apply_adjoint(helm_ctx* ctx, const void* x, void* y, helm_dtype dtype, int nrhs,
+                                          void* stream) {
+  return apply_entry(ctx, x, y, dtype, nrhs, stream, true, "helm_apply_adjoint");
+}
+
+extern "C" helm_status helm_relres(helm_ctx* ctx, const void* x, const void* b, int nrhs, double* out_host,
+                                   void* stream) {
+  if (!ctx || !x || !b || !out_host || nrhs <= 0) return fail(HELM_ERR_INVALID_ARG, "helm_relres: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  int ncol = num_cols(ctx, nrhs);
+  size_t vec = sizeof(double2) * ctx->npts * nrhs;
+  HELM_TRY(ctx->ws_vec.reserve(vec + sizeof(double) * 2 * ncol + 256));
+  double2* r = (double2*)ctx->ws_vec.ptr;
+  double* sums = (double*)((char*)ctx->ws_vec.ptr + ((vec + 255) / 256) * 256);
+  HELM_TRY(residual_fp64(ctx, (const double2*)x, (const double2*)b, r, nrhs, sums, st));
+  std::vector<double> h(2 * ncol);
+  HELM_CK(cudaMemcpyAsync(h.data(), sums, sizeof(double) * 2 * ncol, cudaMemcpyDeviceToHost, st));
+  HELM_CK(cudaStreamSynchronize(st));
+  for (int c = 0; c < ncol; ++c) out_host[c] = h[2 * c + 1] > 0 ? sqrt(h[2 * c] / h[2 * c + 1]) : sqrt(h[2 * c]);
+  return HELM_OK;
+}

@@ -1,0 +1,524 @@
+// The U-Net neural operator N_theta (a3): weights, activations, forward pass and the
+// preconditioner entry point z = N_theta(alpha v, c) / alpha (eq. 6, eq. 7).
+//
+// Network (Sec. 3.1, Fig. 2, Tab. 2 read for this project): widths 16/32/64/128, two 3x3 convs
+// (pad 1, bias, ReLU) per level, 2x2 max-pool down, 2x2 stride-2 transposed conv up (bias, no
+// activation), decoder input concat[skip, up], final 1x1 conv 16 -> 2.  Inputs
+// (Re v, Im v, c / 1500 m/s); the image is zero-padded at the bottom/right to multiples of 8.
+//
+// Activations are NHWC.  Two arithmetic paths share this driver:
+//   FP64 (plain path): double storage, double accumulation, CUDA cores;
+//   mixed path: BF16 storage and operands with FP32 accumulation.  The dense 3x3 layers run on the
+//   tcgen05 implicit-GEMM kernels (conv_tc.cu) when those are available for the layer shape; the
+//   CUDA-core kernels below cover the rest (first layer, up-convs, final 1x1).
+#include <math.h>
+
+#include "helm_internal.cuh"
+#include "unet.cuh"
+
+namespace helm {
+
+const LayerDesc kLayers[NUM_LAYERS] = {
+    {"enc1a", CONV3, 3, 16},   {"enc1b", CONV3, 16, 16},  {"enc2a", CONV3, 16, 32},  {"enc2b", CONV3, 32, 32},
+    {"enc3a", CONV3, 32, 64},  {"enc3b", CONV3, 64, 64},  {"bota", CONV3, 64, 128},  {"botb", CONV3, 128, 128},
+    {"up3", UP2, 128, 64},     {"dec3a", CONV3, 128, 64}, {"dec3b", CONV3, 64, 64},  {"up2", UP2, 64, 32},
+    {"dec2a", CONV3, 64, 32},  {"dec2b", CONV3, 32, 32},  {"up1", UP2, 32, 16},      {"dec1a", CONV3, 32, 16},
+    {"dec1b", CONV3, 16, 16},  {"final", CONV1, 16, 2},
+};
+
+int taps_of(int kind) { return kind == CONV3 ? 9 : (kind == UP2 ? 4 : 1); }
+
+NetLayout make_layout() {
+  NetLayout L{};
+  int64_t m = 0, c = 0;
+  for (int l = 0; l < NUM_LAYERS; ++l) {
+    const LayerDesc& d = kLayers[l];
+    int64_t nw = (int64_t)taps_of(d.kind) * d.cin * d.cout;
+    L.m_w[l] = m;
+    L.m_b[l] = m + nw;
+    m += nw + d.cout;
+    L.c_w[l] = c;
+    L.c_b[l] = c + nw;
+    c += nw + d.cout;
+  }
+  L.total = m;
+  L.ctotal = c;
+  return L;
+}
+
+// ------------------------------------------------------------------ weight preparation
+
+// Master (PyTorch layout) -> CUDA-core layout [tap][cin][cout] + bias, in FP64 and in FP32 holding
+// BF16-rounded weights (bias unrounded).
+__global__ void k_prep_layer(const double* __restrict__ master, int kind, int cin, int cout, int64_t m_w, int64_t m_b,
+                             int64_t c_w, int64_t c_b, double* __restrict__ w64, float* __restrict__ w32) {
+  int taps = kind == CONV3 ? 9 : (kind == UP2 ? 4 : 1);
+  int64_t nw = (int64_t)taps * cin * cout;
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q < nw) {
+    int tap = (int)(q / ((int64_t)cin * cout));
+    int rem = (int)(q % ((int64_t)cin * cout));
+    int ci = rem / cout, co = rem % cout;
+    int64_t src;
+    if (kind == CONV3)
+      src = m_w + ((int64_t)(co * cin + ci) * 3 + tap / 3) * 3 + tap % 3;
+    else if (kind == UP2)
+      src = m_w + ((int64_t)(ci * cout + co) * 2 + tap / 2) * 2 + tap % 2;
+    else
+      src = m_w + (int64_t)co * cin + ci;
+    double w = master[src];
+    w64[c_w + q] = w;
+    w32[c_w + q] = __bfloat162float(__float2bfloat16_rn((float)w));
+  } else if (q < nw + cout) {
+    int co = (int)(q - nw);
+    w64[c_b + co] = master[m_b + co];
+    w32[c_b + co] = (float)master[m_b + co];
+  }
+}
+
+helm_status unet_prepare(helm_unet* net, cudaStream_t st) {
+  const NetLayout& L = net->L;
+  for (int l = 0; l < NUM_LAYERS; ++l) {
+    const LayerDesc& d = kLayers[l];
+    int64_t n = (int64_t)taps_of(d.kind) * d.cin * d.cout + d.cout;
+    k_prep_layer<<<cdiv(n, 256), 256, 0, st>>>(net->master, d.kind, d.cin, d.cout, L.m_w[l], L.m_b[l], L.c_w[l],
+                                               L.c_b[l], net->w64, net->w32);
+  }
+  HELM_CK_LAUNCH();
+  HELM_TRY(conv_tc_prepare(net, st));
+  return HELM_OK;
+}
+
+// ------------------------------------------------------------------ element conversion
+
+template <typename T> struct Acc;
+template <> struct Acc<double> { using A = double; };
+template <> struct Acc<__nv_bfloat16> { using A = float; };
+
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ void store_act(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void store_act(double* p, double v) { *p = v; }
+
+template <typename T> const typename Acc<T>::A* cc_weights(const helm_unet* net);
+template <> const double* cc_weights<double>(const helm_unet* net) { return net->w64; }
+template <> const float* cc_weights<__nv_bfloat16>(const helm_unet* net) { return net->w32; }
+
+// ------------------------------------------------------------------ CUDA-core kernels
+
+constexpr int CC_THREADS = 128;
+constexpr int CC_COT = 16;  // output channels per thread
+
+// y[b,y,x,co] = bias[co] + sum_{tap,ci} W[tap][ci][co] * in[b, y+ky-r, x+kx-r, ci], in = concat(in0, in1)
+template <typename T, int KS>
+__global__ void __launch_bounds__(CC_THREADS) k_conv_cc(const T* __restrict__ in0, int C0, int S0,
+                                                        const T* __restrict__ in1, int C1, int S1,
+                                                        const typename Acc<T>::A* __restrict__ W,
+                                                        const typename Acc<T>::A* __restrict__ bias,
+                                                        T* __restrict__ out, int Cout, int B, int H, int Wd, int relu) {
+  using A = typename Acc<T>::A;
+  int64_t pix = blockIdx.x * (int64_t)CC_THREADS + threadIdx.x;
+  int64_t npix = (int64_t)B * H * Wd;
+  if (pix >= npix) return;
+  int co0 = blockIdx.y * CC_COT;
+  int x = (int)(pix % Wd);
+  int y = (int)((pix / Wd) % H);
+  int64_t b = pix / ((int64_t)Wd * H);
+  A acc[CC_COT];
+#pragma unroll
+  for (int k = 0; k < CC_COT; ++k) acc[k] = bias[co0 + k];
+  const int Cin = C0 + C1;
+  const int r = KS / 2;
+  for (int ky = 0; ky < KS; ++ky) {
+    int yy = y + ky - r;
+    if (yy < 0 || yy >= H) continue;
+    for (int kx = 0; kx < KS; ++kx) {
+      int xx = x + kx - r;
+      if (xx < 0 || xx >= Wd) continue;
+      int64_t q = (b * H + yy) * Wd + xx;
+      const A* wt = W + (int64_t)(ky * KS + kx) * Cin * Cout + co0;
+      for (int ci = 0; ci < C0; ++ci) {
+        A v = to_acc(in0[q * S0 + ci]);
+        const A* wr = wt + (int64_t)ci * Cout;
+#pragma unroll
+        for (int k = 0; k < CC_COT; ++k) acc[k] += v * wr[k];
+      }
+      for (int ci = 0; ci < C1; ++ci) {
+        A v = to_acc(in1[q * S1 + ci]);
+        const A* wr = wt + (int64_t)(C0 + ci) * Cout;
+#pragma unroll
+        for (int k = 0; k < CC_COT; ++k) acc[k] += v * wr[k];
+      }
+    }
+  }
+  T* o = out + pix * Cout + co0;
+#pragma unroll
+  for (int k = 0; k < CC_COT; ++k) store_act(o + k, relu ? (acc[k] > A(0) ? acc[k] : A(0)) : acc[k]);
+}
+
+// 2x2 stride-2 transposed conv: y[b, 2i+dy, 2j+dx, co] = bias[co] + sum_ci in[b,i,j,ci] W[dy*2+dx][ci][co]
+template <typename T>
+__global__ void __launch_bounds__(CC_THREADS) k_up_cc(const T* __restrict__ in, int Cin,
+                                                      const typename Acc<T>::A* __restrict__ W,
+                                                      const typename Acc<T>::A* __restrict__ bias, T* __restrict__ out,
+                                                      int Cout, int B, int Ho, int Wo) {
+  using A = typename Acc<T>::A;
+  int64_t pix = blockIdx.x * (int64_t)CC_THREADS + threadIdx.x;
+  if (pix >= (int64_t)B * Ho * Wo) return;
+  int co0 = blockIdx.y * CC_COT;
+  int x = (int)(pix % Wo);
+  int y = (int)((pix / Wo) % Ho);
+  int64_t b = pix / ((int64_t)Wo * Ho);
+  int Hi = Ho / 2, Wi = Wo / 2;
+  int tap = (y & 1) * 2 + (x & 1);
+  const T* ip = in + ((b * Hi + (y >> 1)) * Wi + (x >> 1)) * Cin;
+  const A* wt = W + (int64_t)tap * Cin * Cout + co0;
+  A acc[CC_COT];
+#pragma unroll
+  for (int k = 0; k < CC_COT; ++k) acc[k] = bias[co0 + k];
+  for (int ci = 0; ci < Cin; ++ci) {
+    A v = to_acc(ip[ci]);
+    const A* wr = wt + (int64_t)ci * Cout;
+#pragma unroll
+    for (int k = 0; k < CC_COT; ++k) acc[k] += v * wr[k];
+  }
+  T* o = out + pix * Cout + co0;
+#pragma unroll
+  for (int k = 0; k < CC_COT; ++k) store_act(o + k, acc[k]);
+}
+
+// 2x2 max-pool, stride 2.
+template <typename T>
+__global__ void k_pool(const T* __restrict__ in, T* __restrict__ out, int C, int B, int Ho, int Wo) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t n = (int64_t)B * Ho * Wo * C;
+  if (e >= n) return;
+  int c = (int)(e % C);
+  int64_t pix = e / C;
+  int x = (int)(pix % Wo);
+  int y = (int)((pix / Wo) % Ho);
+  int64_t b = pix / ((int64_t)Wo * Ho);
+  int Wi = 2 * Wo, Hi = 2 * Ho;
+  const T* p = in + ((b * Hi + 2 * y) * Wi + 2 * x) * C + c;
+  auto a0 = to_acc(p[0]), a1 = to_acc(p[C]), a2 = to_acc(p[(int64_t)Wi * C]), a3 = to_acc(p[(int64_t)Wi * C + C]);
+  auto m = a0;
+  m = a1 > m ? a1 : m;
+  m = a2 > m ? a2 : m;
+  m = a3 > m ? a3 : m;
+  store_act(out + e, m);
+}
+
+// Network input: (Re(s v), Im(s v), c / 1500) on the padded grid; zero outside the physical grid.
+// Channel stride S0 (extra channels zero).
+template <typename T, typename R>
+__global__ void k_pack_input(const C<R>* __restrict__ v, int64_t col_stride, const double* __restrict__ in_scale,
+                             const float* __restrict__ chat, int Nx, int Ny, int Hp, int Wp, int B, int S0,
+                             T* __restrict__ x0) {
+  int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pix >= (int64_t)B * Hp * Wp) return;
+  int x = (int)(pix % Wp);
+  int y = (int)((pix / Wp) % Hp);
+  int b = (int)(pix / ((int64_t)Wp * Hp));
+  typename Acc<T>::A re = 0, im = 0, cc = 0;
+  if (x < Nx && y < Ny) {
+    int64_t q = (int64_t)y * Nx + x;
+    C<R> val = v[b * col_stride + q];
+    double s = in_scale[b];
+    re = (typename Acc<T>::A)(val.x * s);
+    im = (typename Acc<T>::A)(val.y * s);
+    cc = (typename Acc<T>::A)chat[q];
+  }
+  T* o = x0 + pix * S0;
+  store_act(o + 0, re);
+  store_act(o + 1, im);
+  store_act(o + 2, cc);
+  for (int k = 3; k < S0; ++k) store_act(o + k, (typename Acc<T>::A)0);
+}
+
+// Final 1x1 conv 16 -> 2 and unpacking: z[b][y][x] = (y0 + i y1) * out_scale[b] on the physical grid.
+template <typename T, typename R>
+__global__ void k_final(const T* __restrict__ in, const typename Acc<T>::A* __restrict__ W,
+                        const typename Acc<T>::A* __restrict__ bias, const double* __restrict__ out_scale, int Nx,
+                        int Ny, int Hp, int Wp, int B, C<R>* __restrict__ z, int64_t col_stride, float* raw_out) {
+  using A = typename Acc<T>::A;
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)B * Ny * Nx) return;
+  int x = (int)(e % Nx);
+  int y = (int)((e / Nx) % Ny);
+  int b = (int)(e / ((int64_t)Nx * Ny));
+  const T* ip = in + (((int64_t)b * Hp + y) * Wp + x) * 16;
+  A y0 = bias[0], y1 = bias[1];
+#pragma unroll
+  for (int ci = 0; ci < 16; ++ci) {
+    A v = to_acc(ip[ci]);
+    y0 += v * W[ci * 2 + 0];
+    y1 += v * W[ci * 2 + 1];
+  }
+  double s = out_scale[b];
+  C<R> o;
+  o.x = (R)(y0 * s);
+  o.y = (R)(y1 * s);
+  z[b * col_stride + (int64_t)y * Nx + x] = o;
+}
+
+// ------------------------------------------------------------------ buffers
+
+size_t act_bytes_per_image(int Hp, int Wp, bool fp64) {
+  size_t full = (size_t)Hp * Wp;
+  size_t chans = full * (X0_CH + 16 * 5) + (full / 4) * (16 + 32 * 5) + (full / 16) * (32 + 64 * 5) +
+                 (full / 64) * (64 + 128 * 2);
+  return chans * (fp64 ? 8 : 2);
+}
+
+helm_status ensure_buffers(helm_ctx* ctx, int B, int Hp, int Wp, bool fp64, UnetBuffers** out) {
+  UnetBuffers*& ub = ctx->ub;
+  if (!ub) ub = new UnetBuffers();
+  int idx = fp64 ? 1 : 0;
+  UnetBuffers::Set& S = ub->set[idx];
+  if (S.base && S.B >= B && S.Hp == Hp && S.Wp == Wp) {
+    *out = ub;
+    return HELM_OK;
+  }
+  if (S.base) cudaFree(S.base);
+  S.base = nullptr;
+  size_t es = fp64 ? 8 : 2;
+  size_t per = act_bytes_per_image(Hp, Wp, fp64) + 64 * 24;
+  HELM_CK(cudaMalloc(&S.base, per * B + 4096));
+  S.B = B;
+  S.Hp = Hp;
+  S.Wp = Wp;
+  char* p = (char*)S.base;
+  auto take = [&](int64_t pix, int ch) {
+    char* r = p;
+    size_t bytes = (size_t)B * pix * ch * es;
+    p += (bytes + 255) / 256 * 256;
+    return (void*)r;
+  };
+  int64_t f = (int64_t)Hp * Wp, h2 = f / 4, h4 = f / 16, h8 = f / 64;
+  S.a[A_X0] = take(f, X0_CH);
+  S.a[A_E1A] = take(f, 16);
+  S.a[A_S1] = take(f, 16);
+  S.a[A_P1] = take(h2, 16);
+  S.a[A_E2A] = take(h2, 32);
+  S.a[A_S2] = take(h2, 32);
+  S.a[A_P2] = take(h4, 32);
+  S.a[A_E3A] = take(h4, 64);
+  S.a[A_S3] = take(h4, 64);
+  S.a[A_P3] = take(h8, 64);
+  S.a[A_BA] = take(h8, 128);
+  S.a[A_BB] = take(h8, 128);
+  S.a[A_U3] = take(h4, 64);
+  S.a[A_D3A] = take(h4, 64);
+  S.a[A_D3B] = take(h4, 64);
+  S.a[A_U2] = take(h2, 32);
+  S.a[A_D2A] = take(h2, 32);
+  S.a[A_D2B] = take(h2, 32);
+  S.a[A_U1] = take(f, 16);
+  S.a[A_D1A] = take(f, 16);
+  S.a[A_D1B] = take(f, 16);
+  *out = ub;
+  return HELM_OK;
+}
+
+void unet_buffers_free(helm_ctx* ctx) {
+  if (!ctx->ub) return;
+  for (auto& S : ctx->ub->set)
+    if (S.base) cudaFree(S.base);
+  delete ctx->ub;
+  ctx->ub = nullptr;
+}
+
+// ------------------------------------------------------------------ forward
+
+template <typename T>
+static helm_status conv3(const helm_unet* net, int l, const T* in0, int C0, int S0, const T* in1, int C1, int S1,
+                         T* out, int B, int H, int W, cudaStream_t st) {
+  const LayerDesc& d = kLayers[l];
+  if (conv_tc_enabled<T>(net, l, H, W)) return conv_tc_forward(net, l, in0, C0, in1, C1, out, B, H, W, st);
+  const auto* w = cc_weights<T>(net);
+  dim3 grid(cdiv((int64_t)B * H * W, CC_THREADS), d.cout / CC_COT);
+  k_conv_cc<T, 3><<<grid, CC_THREADS, 0, st>>>(in0, C0, S0, in1, C1, S1, w + net->L.c_w[l], w + net->L.c_b[l], out,
+                                                d.cout, B, H, W, 1);
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+template <typename T>
+static helm_status up2(const helm_unet* net, int l, const T* in, T* out, int B, int Ho, int Wo, cudaStream_t st) {
+  const LayerDesc& d = kLayers[l];
+  const auto* w = cc_weights<T>(net);
+  dim3 grid(cdiv((int64_t)B * Ho * Wo, CC_THREADS), d.cout / CC_COT);
+  k_up_cc<T><<<grid, CC_THREADS, 0, st>>>(in, d.cin, w + net->L.c_w[l], w + net->L.c_b[l], out, d.cout, B, Ho, Wo);
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+template <typename T>
+static helm_status pool(const T* in, T* out, int C, int B, int Ho, int Wo, cudaStream_t st) {
+  int64_t n = (int64_t)B * Ho * Wo * C;
+  k_pool<T><<<cdiv(n, 256), 256, 0, st>>>(in, out, C, B, Ho, Wo);
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+template <typename T>
+helm_status unet_body(const helm_unet* net, UnetBuffers::Set& S, int B, cudaStream_t st) {
+  int H = S.Hp, W = S.Wp;
+  T** a = (T**)S.a;
+  HELM_TRY(conv3<T>(net, L_ENC1A, a[A_X0], 3, X0_CH, nullptr, 0, 0, a[A_E1A], B, H, W, st));
+  HELM_TRY(conv3<T>(net, L_ENC1B, a[A_E1A], 16, 16, nullptr, 0, 0, a[A_S1], B, H, W, st));
+  HELM_TRY(pool<T>(a[A_S1], a[A_P1], 16, B, H / 2, W / 2, st));
+  HELM_TRY(conv3<T>(net, L_ENC2A, a[A_P1], 16, 16, nullptr, 0, 0, a[A_E2A], B, H / 2, W / 2, st));
+  HELM_TRY(conv3<T>(net, L_ENC2B, a[A_E2A], 32, 32, nullptr, 0, 0, a[A_S2], B, H / 2, W / 2, st));
+  HELM_TRY(pool<T>(a[A_S2], a[A_P2], 32, B, H / 4, W / 4, st));
+  HELM_TRY(conv3<T>(net, L_ENC3A, a[A_P2], 32, 32, nullptr, 0, 0, a[A_E3A], B, H / 4, W / 4, st));
+  HELM_TRY(conv3<T>(net, L_ENC3B, a[A_E3A], 64, 64, nullptr, 0, 0, a[A_S3], B, H / 4, W / 4, st));
+  HELM_TRY(pool<T>(a[A_S3], a[A_P3], 64, B, H / 8, W / 8, st));
+  HELM_TRY(conv3<T>(net, L_BOTA, a[A_P3], 64, 64, nullptr, 0, 0, a[A_BA], B, H / 8, W / 8, st));
+  HELM_TRY(conv3<T>(net, L_BOTB, a[A_BA], 128, 128, nullptr, 0, 0, a[A_BB], B, H / 8, W / 8, st));
+  HELM_TRY(up2<T>(net, L_UP3, a[A_BB], a[A_U3], B, H / 4, W / 4, st));
+  HELM_TRY(conv3<T>(net, L_DEC3A, a[A_S3], 64, 64, a[A_U3], 64, 64, a[A_D3A], B, H / 4, W / 4, st));
+  HELM_TRY(conv3<T>(net, L_DEC3B, a[A_D3A], 64, 64, nullptr, 0, 0, a[A_D3B], B, H / 4, W / 4, st));
+  HELM_TRY(up2<T>(net, L_UP2, a[A_D3B], a[A_U2], B, H / 2, W / 2, st));
+  HELM_TRY(conv3<T>(net, L_DEC2A, a[A_S2], 32, 32, a[A_U2], 32, 32, a[A_D2A], B, H / 2, W / 2, st));
+  HELM_TRY(conv3<T>(net, L_DEC2B, a[A_D2A], 32, 32, nullptr, 0, 0, a[A_D2B], B, H / 2, W / 2, st));
+  HELM_TRY(up2<T>(net, L_UP1, a[A_D2B], a[A_U1], B, H, W, st));
+  HELM_TRY(conv3<T>(net, L_DEC1A, a[A_S1], 16, 16, a[A_U1], 16, 16, a[A_D1A], B, H, W, st));
+  HELM_TRY(conv3<T>(net, L_DEC1B, a[A_D1A], 16, 16, nullptr, 0, 0, a[A_D1B], B, H, W, st));
+  return HELM_OK;
+}
+
+template <typename R>
+helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
+                              const double* in_scale, const double* out_scale, cudaStream_t st) {
+  using T = typename std::conditional<sizeof(R) == 8, double, __nv_bfloat16>::type;
+  const SysHost& s = ctx->sys[sys];
+  int Hp = (s.Ny + 7) / 8 * 8, Wp = (s.Nx + 7) / 8 * 8;
+  UnetBuffers* ub;
+  HELM_TRY(ensure_buffers(ctx, B, Hp, Wp, sizeof(R) == 8, &ub));
+  UnetBuffers::Set& S = ub->set[sizeof(R) == 8 ? 1 : 0];
+  T** a = (T**)S.a;
+  int64_t npix = (int64_t)B * Hp * Wp;
+  k_pack_input<T, R><<<cdiv(npix, 256), 256, 0, st>>>(v, s.n, in_scale, ctx->chat + s.off, s.Nx, s.Ny, Hp, Wp, B,
+                                                      X0_CH, a[A_X0]);
+  HELM_CK_LAUNCH();
+  HELM_TRY(unet_body<T>(net, S, B, st));
+  const auto* w = cc_weights<T>(net);
+  int64_t nout = (int64_t)B * s.Ny * s.Nx;
+  k_final<T, R><<<cdiv(nout, 256), 256, 0, st>>>(a[A_D1B], w + net->L.c_w[L_FINAL], w + net->L.c_b[L_FINAL],
+                                                 out_scale, s.Nx, s.Ny, Hp, Wp, B, z, s.n, nullptr);
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+template helm_status unet_precondition<float>(helm_ctx*, const helm_unet*, int, const float2*, float2*, int,
+                                              const double*, const double*, cudaStream_t);
+template helm_status unet_precondition<double>(helm_ctx*, const helm_unet*, int, const double2*, double2*, int,
+                                               const double*, const double*, cudaStream_t);
+
+// in_scale = alpha = sqrt(n) / ||v||, out_scale = h^2 / alpha (0 for a zero column).  The h^2 makes
+// the network approximate the inverse of the dimensionless operator h^2 A (O(1) entries, as in the
+// paper's omega = 1 setting).
+__global__ void k_alpha(const double* __restrict__ norm2, int ncol, const ColDesc* __restrict__ cols,
+                        double* __restrict__ in_scale, double* __restrict__ out_scale) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncol) return;
+  double nv = sqrt(norm2[c]);
+  double a = nv > 0 ? sqrt((double)cols[c].len) / nv : 0.0;
+  in_scale[c] = a;
+  out_scale[c] = a > 0 ? cols[c].h2 / a : 0.0;
+}
+
+template <typename R>
+helm_status precond_entry(helm_ctx* ctx, const helm_unet* net, const C<R>* v, C<R>* z, int nrhs, cudaStream_t st) {
+  HELM_TRY(ensure_cols(ctx, nrhs));
+  int ncol = num_cols(ctx, nrhs);
+  HELM_TRY(ctx->ws_solver.reserve(sizeof(double) * 3 * ncol + 256));
+  double* n2 = (double*)ctx->ws_solver.ptr;
+  double* in_s = n2 + ncol;
+  double* out_s = in_s + ncol;
+  HELM_TRY(col_norm2<R>(ctx, v, nrhs, n2, st));
+  k_alpha<<<cdiv(ncol, 128), 128, 0, st>>>(n2, ncol, ctx->cols_dev, in_s, out_s);
+  HELM_CK_LAUNCH();
+  for (int s = 0; s < ctx->nsys; ++s) {
+    int64_t o = ctx->sys[s].off * nrhs;
+    HELM_TRY(unet_precondition<R>(ctx, net, s, v + o, z + o, nrhs, in_s + s * nrhs, out_s + s * nrhs, st));
+  }
+  return HELM_OK;
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+extern "C" size_t helm_unet_param_count(void) { return (size_t)make_layout().total; }
+
+extern "C" helm_status helm_unet_layer(int l, int* c_in, int* c_out, int* kind) {
+  if (l < 0 || l >= NUM_LAYERS || !c_in || !c_out || !kind) return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer: bad argument");
+  *c_in = kLayers[l].cin;
+  *c_out = kLayers[l].cout;
+  *kind = kLayers[l].kind;
+  return HELM_OK;
+}
+
+extern "C" helm_status helm_unet_create(helm_unet** out, const double* weights_host, size_t nweights) {
+  if (!out || !weights_host) return fail(HELM_ERR_INVALID_ARG, "helm_unet_create: NULL argument");
+  *out = nullptr;
+  NetLayout L = make_layout();
+  if ((int64_t)nweights != L.total)
+    return fail(HELM_ERR_INVALID_ARG, "helm_unet_create: expected " + std::to_string(L.total) + " weights, got " +
+                                          std::to_string(nweights));
+  for (size_t i = 0; i < nweights; ++i)
+    if (!std::isfinite(weights_host[i])) return fail(HELM_ERR_INVALID_ARG, "helm_unet_create: non-finite weight");
+  helm_unet* net = new helm_unet();
+  net->L = L;
+  cudaStream_t st = 0;
+  helm_status rc = HELM_OK;
+  auto ck = [&](cudaError_t e, const char* what) {
+    if (e != cudaSuccess && rc == HELM_OK) rc = cuda_fail(e, what, __FILE__, __LINE__);
+  };
+  ck(cudaMalloc(&net->master, sizeof(double) * L.total), "cudaMalloc master");
+  ck(cudaMalloc(&net->w64, sizeof(double) * L.ctotal), "cudaMalloc w64");
+  ck(cudaMalloc(&net->w32, sizeof(float) * L.ctotal), "cudaMalloc w32");
+  if (rc == HELM_OK) ck(cudaMemcpy(net->master, weights_host, sizeof(double) * L.total, cudaMemcpyHostToDevice), "copy");
+  if (rc == HELM_OK) rc = unet_prepare(net, st);
+  if (rc == HELM_OK) ck(cudaStreamSynchronize(st), "sync");
+  if (rc != HELM_OK) {
+    helm_unet_destroy(net);
+    return rc;
+  }
+  *out = net;
+  return HELM_OK;
+}
+
+extern "C" helm_status helm_unet_destroy(helm_unet* net) {
+  if (!net) return HELM_OK;
+  cudaDeviceSynchronize();
+  conv_tc_release(net);
+  cudaFree(net->master);
+  cudaFree(net->w64);
+  cudaFree(net->w32);
+  cudaFree(net->adam_m);
+  cudaFree(net->adam_v);
+  cudaFree(net->grad);
+  delete net;
+  return HELM_OK;
+}
+
+extern "C" helm_status helm_unet_get_weights(const helm_unet* net, double* weights_host, size_t nweights) {
+  if (!net || !weights_host || (int64_t)nweights != net->L.total)
+    return fail(HELM_ERR_INVALID_ARG, "helm_unet_get_weights: bad argument");
+  HELM_CK(cudaDeviceSynchronize());
+  HELM_CK(cudaMemcpy(weights_host, net->master, sizeof(double) * nweights, cudaMemcpyDeviceToHost));
+  return HELM_OK;
+}
+
+extern "C" helm_status helm_precond_apply(helm_ctx* ctx, const helm_unet* net, const void* v, void* z,
+                                          helm_dtype dtype, int nrhs, void* stream) {
+  if (!ctx || !net || !v || !z || nrhs <= 0) return fail(HELM_ERR_INVALID_ARG, "helm_precond_apply: bad argument");
+  if (((uintptr_t)v | (uintptr_t)z) & 15) return fail(HELM_ERR_INVALID_ARG, "helm_precond_apply: pointers must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == HELM_C64) return precond_entry<float>(ctx, net, (const float2*)v, (float2*)z, nrhs, st);
+  if (dtype == HELM_C128) return precond_entry<double>(ctx, net, (const double2*)v, (double2*)z, nrhs, st);
+  return fail(HELM_ERR_INVALID_ARG, "helm_precond_apply: unknown dtype");
+}

@@ -1,0 +1,71 @@
+// Internal network declarations: layer table, parameter layout, activation buffers.
+#pragma once
+
+#include "helm_internal.cuh"
+
+namespace helm {
+
+enum LayerKind { CONV3 = 0, UP2 = 1, CONV1 = 2 };
+enum LayerId {
+  L_ENC1A = 0, L_ENC1B, L_ENC2A, L_ENC2B, L_ENC3A, L_ENC3B, L_BOTA, L_BOTB, L_UP3, L_DEC3A, L_DEC3B,
+  L_UP2, L_DEC2A, L_DEC2B, L_UP1, L_DEC1A, L_DEC1B, L_FINAL, NUM_LAYERS
+};
+
+struct LayerDesc {
+  const char* name;
+  int kind, cin, cout;
+};
+extern const LayerDesc kLayers[NUM_LAYERS];
+int taps_of(int kind);
+
+struct NetLayout {
+  int64_t m_w[NUM_LAYERS], m_b[NUM_LAYERS];  // offsets in the master vector (PyTorch layouts)
+  int64_t c_w[NUM_LAYERS], c_b[NUM_LAYERS];  // offsets in the CUDA-core buffers ([tap][cin][cout], bias)
+  int64_t total, ctotal;
+};
+NetLayout make_layout();
+
+// Activation slots (NHWC).  X0 holds the packed network input with X0_CH channel stride.
+enum ActId {
+  A_X0 = 0, A_E1A, A_S1, A_P1, A_E2A, A_S2, A_P2, A_E3A, A_S3, A_P3, A_BA, A_BB, A_U3, A_D3A, A_D3B,
+  A_U2, A_D2A, A_D2B, A_U1, A_D1A, A_D1B, NUM_ACTS
+};
+constexpr int X0_CH = 16;  // input channels padded 3 -> 16 (one 32-byte row of BF16 per pixel)
+
+struct UnetBuffers {
+  struct Set {
+    void* base = nullptr;
+    int B = 0, Hp = 0, Wp = 0;
+    void* a[NUM_ACTS] = {};
+  } set[2];  // [0] BF16, [1] FP64
+};
+
+struct TcLayer;  // tcgen05 per-layer state (conv_tc.cu)
+
+helm_status ensure_buffers(helm_ctx* ctx, int B, int Hp, int Wp, bool fp64, UnetBuffers** out);
+
+// tcgen05 implicit-GEMM 3x3 convolutions (conv_tc.cu)
+struct TcState;
+helm_status conv_tc_prepare(helm_unet* net, cudaStream_t st);
+void conv_tc_release(helm_unet* net);
+template <typename T> bool conv_tc_enabled(const helm_unet* net, int layer, int H, int W);
+helm_status conv_tc_forward(const helm_unet* net, int layer, const void* in0, int C0, const void* in1, int C1,
+                            void* out, int B, int H, int W, cudaStream_t st);
+
+template <typename R>
+helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
+                              const double* in_scale, const double* out_scale, cudaStream_t st);
+
+}  // namespace helm
+
+struct helm_unet {
+  helm::NetLayout L;
+  double* master = nullptr;  // FP64 master weights (PyTorch layouts)
+  double* w64 = nullptr;     // CUDA-core layout, FP64
+  float* w32 = nullptr;      // CUDA-core layout, BF16-rounded values held in FP32 (bias unrounded)
+  double* adam_m = nullptr;  // AdamW first moment
+  double* adam_v = nullptr;  // AdamW second moment
+  double* grad = nullptr;    // gradient scratch (FP64)
+  int64_t step = 0;
+  helm::TcState* tc = nullptr;
+};

@@ -1,0 +1,290 @@
+"""Thin ctypes binding of libhelm.so (the C ABI in include/helm.h).
+
+Argument marshalling only: every numerical step runs in the CUDA library.  Device memory and
+streams come from PyTorch tensors.  Importing this module loads the library and raises if it is
+missing (run `python -m paper_2607_16906_b300.build`); there is no CPU fallback.
+
+Batch vectors are CUDA tensors of dtype complex64 (HELM_C64) or complex128 (HELM_C128), laid out
+[system][rhs][Ny][Nx] flattened in system order, contiguous.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhelm.so")
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"libhelm.so not found at {LIB_PATH}; build it with `python -m paper_2607_16906_b300.build`")
+_lib = ct.CDLL(LIB_PATH)
+
+HELM_OK, HELM_ERR_INVALID_ARG, HELM_ERR_CUDA, HELM_ERR_OOM = 0, 1, 2, 3
+HELM_NOT_CONVERGED, HELM_BREAKDOWN, HELM_NAN, HELM_TIMEOUT = 4, 5, 6, 7
+STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "BREAKDOWN", 6: "NAN",
+                7: "TIMEOUT"}
+HELM_C64, HELM_C128 = 0, 1
+HELM_MAX_M = 1024
+
+
+class helm_grid(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("h", ct.c_double)]
+
+
+class helm_pml(ct.Structure):
+    _fields_ = [("width", ct.c_int), ("sigma_max", ct.c_double)]
+
+
+class helm_solve_opts(ct.Structure):
+    _fields_ = [("m", ct.c_int), ("max_restarts", ct.c_int), ("max_outer", ct.c_int), ("tol", ct.c_double),
+                ("inner_tol", ct.c_double), ("mixed", ct.c_int), ("orth", ct.c_int)]
+
+
+class helm_solve_info(ct.Structure):
+    _fields_ = [("iters", ct.c_int), ("restarts", ct.c_int), ("outer", ct.c_int), ("relres_true", ct.c_double),
+                ("relres_est", ct.c_double), ("status", ct.c_int)]
+
+
+_P = ct.c_void_p
+_SIGS = {
+    "helm_create": (ct.c_int, [ct.POINTER(_P), ct.c_int, ct.POINTER(helm_grid), ct.POINTER(helm_pml),
+                               ct.POINTER(ct.c_double), _P, ct.c_int, _P]),
+    "helm_destroy": (ct.c_int, [_P]),
+    "helm_points": (ct.c_int64, [_P]),
+    "helm_num_systems": (ct.c_int, [_P]),
+    "helm_apply": (ct.c_int, [_P, _P, _P, ct.c_int, ct.c_int, _P]),
+    "helm_apply_adjoint": (ct.c_int, [_P, _P, _P, ct.c_int, ct.c_int, _P]),
+    "helm_relres": (ct.c_int, [_P, _P, _P, ct.c_int, ct.POINTER(ct.c_double), _P]),
+    "helm_unet_param_count": (ct.c_size_t, []),
+    "helm_unet_layer": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
+    "helm_unet_create": (ct.c_int, [ct.POINTER(_P), ct.POINTER(ct.c_double), ct.c_size_t]),
+    "helm_unet_destroy": (ct.c_int, [_P]),
+    "helm_unet_get_weights": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.c_size_t]),
+    "helm_precond_apply": (ct.c_int, [_P, _P, _P, _P, ct.c_int, ct.c_int, _P]),
+    "helm_fgmres_solve": (ct.c_int, [_P, _P, _P, _P, ct.c_int, ct.POINTER(helm_solve_opts),
+                                     ct.POINTER(helm_solve_info), _P]),
+    "helm_train_step": (ct.c_int, [_P, _P, _P, ct.c_double, ct.c_double, ct.c_double, ct.POINTER(ct.c_double),
+                                   ct.POINTER(ct.c_double), _P]),
+    "helm_loss_grad": (ct.c_int, [_P, _P, _P, ct.POINTER(ct.c_double), _P, _P]),
+    "helm_last_error": (ct.c_char_p, []),
+}
+for _name, (_res, _args) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+EXPORTED = tuple(_SIGS)
+
+
+class HelmError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(rc, allow=()):
+    if rc != HELM_OK and rc not in allow:
+        raise HelmError(rc, _lib.helm_last_error().decode())
+    return rc
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ct.c_void_p(s.cuda_stream)
+
+
+def _dev_ptr(t: torch.Tensor):
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ct.c_void_p(t.data_ptr())
+
+
+def _dtype_code(t: torch.Tensor):
+    if t.dtype == torch.complex64:
+        return HELM_C64
+    if t.dtype == torch.complex128:
+        return HELM_C128
+    raise TypeError(f"batch vectors must be complex64 or complex128, got {t.dtype}")
+
+
+@dataclass
+class SystemSpec:
+    nx: int
+    ny: int
+    h: float
+    width: int
+    omega: float
+    sigma_max: float = 0.0
+
+    @property
+    def Nx(self):
+        return self.nx + 2 * self.width
+
+    @property
+    def Ny(self):
+        return self.ny + 2 * self.width
+
+    @property
+    def n(self):
+        return self.Nx * self.Ny
+
+
+class Context:
+    """helm_create / helm_destroy: the systems' grids, PMLs, frequencies and velocities."""
+
+    def __init__(self, systems, c: torch.Tensor, stream=None):
+        self.systems = list(systems)
+        ns = len(self.systems)
+        grids = (helm_grid * ns)(*[helm_grid(s.nx, s.ny, s.h) for s in self.systems])
+        pmls = (helm_pml * ns)(*[helm_pml(s.width, s.sigma_max) for s in self.systems])
+        om = (ct.c_double * ns)(*[s.omega for s in self.systems])
+        if c.dtype not in (torch.float64, torch.float32) or c.numel() != sum(s.n for s in self.systems):
+            raise ValueError("c must hold sum(Nx*Ny) float32/float64 velocities")
+        c = c.contiguous()
+        self._h = _P()
+        _check(_lib.helm_create(ct.byref(self._h), ns, grids, pmls, om, _dev_ptr(c), int(c.dtype == torch.float64),
+                                _stream(stream)))
+        self.npts = int(_lib.helm_points(self._h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _lib.helm_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def new_vector(self, nrhs=1, dtype=torch.complex128):
+        return torch.zeros(self.npts * nrhs, dtype=dtype, device="cuda")
+
+
+def helm_apply(ctx: Context, x: torch.Tensor, y: torch.Tensor, nrhs=1, adjoint=False, stream=None):
+    """y = A x (or A^H x) for complex64/complex128 batch vectors."""
+    if x.dtype != y.dtype or x.numel() != ctx.npts * nrhs or y.numel() != x.numel():
+        raise ValueError("x, y must be batch vectors of the same dtype and size npts * nrhs")
+    f = _lib.helm_apply_adjoint if adjoint else _lib.helm_apply
+    _check(f(ctx.handle, _dev_ptr(x), _dev_ptr(y), _dtype_code(x), nrhs, _stream(stream)))
+    return y
+
+
+def helm_apply_adjoint(ctx, x, y, nrhs=1, stream=None):
+    return helm_apply(ctx, x, y, nrhs, adjoint=True, stream=stream)
+
+
+def helm_relres(ctx: Context, x: torch.Tensor, b: torch.Tensor, nrhs=1, stream=None) -> np.ndarray:
+    ncol = len(ctx.systems) * nrhs
+    out = (ct.c_double * ncol)()
+    _check(_lib.helm_relres(ctx.handle, _dev_ptr(x), _dev_ptr(b), nrhs, out, _stream(stream)))
+    return np.array(out[:])
+
+
+def helm_unet_param_count() -> int:
+    return int(_lib.helm_unet_param_count())
+
+
+def helm_unet_layers():
+    """[(c_in, c_out, kind)] with kind 0 = 3x3 conv, 1 = 2x2 up-conv, 2 = 1x1 conv, in parameter order."""
+    out = []
+    for l in range(18):
+        a, b, k = ct.c_int(), ct.c_int(), ct.c_int()
+        _check(_lib.helm_unet_layer(l, ct.byref(a), ct.byref(b), ct.byref(k)))
+        out.append((a.value, b.value, k.value))
+    return out
+
+
+def weight_segments():
+    """(count, fan_in, 'w'|'b') per parameter tensor of the library's network, for the seeded generator."""
+    seg = []
+    for ci, co, k in helm_unet_layers():
+        taps = {0: 9, 1: 4, 2: 1}[k]
+        fan = ci * {0: 9, 1: 1, 2: 1}[k]
+        seg.append((taps * ci * co, fan, "w"))
+        seg.append((co, fan, "b"))
+    return seg
+
+
+class UNet:
+    """helm_unet_create / helm_unet_destroy: network weights (FP64 master) and optimiser state."""
+
+    def __init__(self, weights: np.ndarray):
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        self._h = _P()
+        _check(_lib.helm_unet_create(ct.byref(self._h), w.ctypes.data_as(ct.POINTER(ct.c_double)), w.size))
+        self.nparams = w.size
+
+    @property
+    def handle(self):
+        return self._h
+
+    def weights(self) -> np.ndarray:
+        out = np.zeros(self.nparams)
+        _check(_lib.helm_unet_get_weights(self._h, out.ctypes.data_as(ct.POINTER(ct.c_double)), out.size))
+        return out
+
+    def close(self):
+        if self._h:
+            _lib.helm_unet_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def helm_precond_apply(ctx: Context, net: UNet, v: torch.Tensor, z: torch.Tensor, nrhs=1, stream=None):
+    if v.dtype != z.dtype or v.numel() != ctx.npts * nrhs or z.numel() != v.numel():
+        raise ValueError("v, z must be batch vectors of the same dtype and size npts * nrhs")
+    _check(_lib.helm_precond_apply(ctx.handle, net.handle, _dev_ptr(v), _dev_ptr(z), _dtype_code(v), nrhs,
+                                   _stream(stream)))
+    return z
+
+
+def helm_fgmres_solve(ctx: Context, net, b: torch.Tensor, x: torch.Tensor, nrhs=1, m=30, tol=1e-6,
+                      mixed=True, max_restarts=100, max_outer=100, inner_tol=1e-4, stream=None, raise_on=False):
+    """Solve A x = b (complex128 batch vectors; x holds x0 on entry).  Returns (status, [info dict per column])."""
+    if b.dtype != torch.complex128 or x.dtype != torch.complex128:
+        raise TypeError("b and x are complex128 batch vectors")
+    if b.numel() != ctx.npts * nrhs or x.numel() != b.numel():
+        raise ValueError("b, x must have npts * nrhs entries")
+    ncol = len(ctx.systems) * nrhs
+    opts = helm_solve_opts(m, max_restarts, max_outer, tol, inner_tol, int(bool(mixed)), 0)
+    info = (helm_solve_info * ncol)()
+    rc = _lib.helm_fgmres_solve(ctx.handle, net.handle if net is not None else None, _dev_ptr(b), _dev_ptr(x),
+                                nrhs, ct.byref(opts), info, _stream(stream))
+    _check(rc, allow=() if raise_on else (HELM_NOT_CONVERGED, HELM_BREAKDOWN, HELM_NAN))
+    cols = [dict(iters=i.iters, restarts=i.restarts, outer=i.outer, relres_true=i.relres_true,
+                 relres_est=i.relres_est, status=STATUS_NAMES.get(i.status, i.status)) for i in info]
+    return rc, cols
+
+
+def helm_train_step(ctx: Context, net: UNet, b: torch.Tensor, lr=1e-3, wd=0.01, clip=1.0, stream=None):
+    """One AdamW step on the batch loss (eqs. 8-9); b is a complex64 batch vector, one source per system.
+    Returns (loss before the update, gradient norm before clipping)."""
+    if b.dtype != torch.complex64 or b.numel() != ctx.npts:
+        raise ValueError("b must be a complex64 batch vector with one right-hand side per system")
+    loss, gn = ct.c_double(), ct.c_double()
+    _check(_lib.helm_train_step(ctx.handle, net.handle, _dev_ptr(b), lr, wd, clip, ct.byref(loss), ct.byref(gn),
+                                _stream(stream)))
+    return loss.value, gn.value
+
+
+def helm_loss_grad(ctx: Context, net: UNet, b: torch.Tensor, stream=None):
+    """Loss (eq. 9, batch mean) and its FP64 gradient w.r.t. the flat parameter vector (CUDA tensor)."""
+    if b.dtype != torch.complex64 or b.numel() != ctx.npts:
+        raise ValueError("b must be a complex64 batch vector with one right-hand side per system")
+    g = torch.zeros(net.nparams, dtype=torch.float64, device="cuda")
+    loss = ct.c_double()
+    _check(_lib.helm_loss_grad(ctx.handle, net.handle, _dev_ptr(b), ct.byref(loss), _dev_ptr(g), _stream(stream)))
+    return loss.value, g

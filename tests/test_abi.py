@@ -1,0 +1,47 @@
+"""The C-ABI library loads on a machine without a GPU and exports every entry point the header declares.
+No compute call is made here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_2607_16906_b300", "libhelm.so")
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            names |= set(re.findall(r"HELM_API\s+[\w\s\*]+?\b(helm_\w+)\s*\(", src))
+    return names
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("helm_create", "helm_destroy", "helm_apply", "helm_apply_adjoint", "helm_precond_apply",
+              "helm_fgmres_solve", "helm_train_step", "helm_unet_create", "helm_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    if not os.path.exists(LIB):
+        from paper_2607_16906_b300 import build
+        build.build()
+    lib = ctypes.CDLL(LIB)
+    missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2607_16906_b300 import helm
+    assert _declared() <= set(helm.EXPORTED)
+
+
+def test_param_count_query_needs_no_gpu():
+    from paper_2607_16906_b300 import helm
+    assert helm.helm_unet_param_count() == 482050
+    layers = helm.helm_unet_layers()
+    assert layers[0] == (3, 16, 0) and layers[-1] == (16, 2, 2)

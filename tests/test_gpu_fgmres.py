@@ -1,0 +1,116 @@
+"""Parity of the CUDA FGMRES solver (a4-a8) against the oracle: one full cycle at a fixed
+iteration count (identity and U-Net preconditioners, FP64), converged solves against the sparse
+direct solution (plain FP64 and mixed paths, uneven batches), and status reporting."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import fgmres as fg
+from oracle import helmholtz as hz
+from oracle import unet
+from paper_2607_16906_b300 import synth
+
+from .gpu_util import make_ctx, small_problems, split, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def helm():
+    from paper_2607_16906_b300 import helm as h
+    return h
+
+
+@pytest.fixture(scope="module")
+def theta():
+    return synth.kaiming_uniform_params(unet.param_segments(), 42)
+
+
+def _flat_b(probs):
+    return np.concatenate([p.b.ravel() for p in probs])
+
+
+@pytest.mark.parametrize("use_net,m", [(False, 20), (True, 8)])
+def test_one_cycle_matches_oracle_fp64(helm, theta, use_net, m):
+    """x after one FGMRES(m) cycle from x0 = 0 equals the oracle's cycle (Alg. 1) to rounding."""
+    probs = small_problems(((20, 14, 5),), seed=31)
+    p = probs[0]
+    ctx = make_ctx(probs)
+    net = helm.UNet(theta) if use_net else None
+    b = to_dev(_flat_b(probs), torch.complex128)
+    x = torch.zeros_like(b)
+    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=m, tol=1e-300, mixed=False, max_restarts=1)
+    assert info[0]["iters"] == m and info[0]["restarts"] == 1
+    A = hz.assemble(p.c, p.p, p.h, p.omega)
+    if use_net:
+        pre = lambda v: unet.precondition(theta, v.reshape(1, p.Ny, p.Nx), p.c, p.h)[0].ravel()
+    else:
+        pre = lambda v: v
+    res = fg.cycle(lambda u: A @ u, pre, p.b[0].ravel(), m, 0.0)
+    got = x.cpu().numpy()
+    assert np.linalg.norm(got - res.x) <= 1e-9 * np.linalg.norm(res.x)
+    assert abs(info[0]["relres_est"] - res.est / np.linalg.norm(p.b)) <= 1e-9 * res.est / np.linalg.norm(p.b)
+    assert abs(info[0]["relres_true"] - hz.relres(A, res.x, p.b[0].ravel())) <= 1e-9
+
+
+@pytest.mark.parametrize("mixed,tol", [(False, 1e-8), (True, 1e-6)])
+def test_gmres_converges_to_direct_solution_uneven_batch(helm, mixed, tol):
+    """Unpreconditioned (identity) solves of an uneven batch, 2 RHS per system, reach the FP64
+    true residual tol; the solution error against splu stays within cond-limited bounds."""
+    probs = small_problems(((20, 14, 5), (13, 9, 3)), seed=32, nrhs=2)
+    ctx = make_ctx(probs)
+    b = to_dev(_flat_b(probs), torch.complex128)
+    x = torch.zeros_like(b)
+    rc, info = helm.helm_fgmres_solve(ctx, None, b, x, 2, m=30, tol=tol, mixed=mixed, max_restarts=200,
+                                      max_outer=200, inner_tol=1e-4)
+    assert rc == helm.HELM_OK, info
+    got = split(x.cpu().numpy(), probs, 2)
+    k = 0
+    for p, xs in zip(probs, got):
+        A = hz.assemble(p.c, p.p, p.h, p.omega)
+        for r in range(2):
+            assert info[k]["status"] == "OK"
+            rel = hz.relres(A, xs[r].ravel(), p.b[r].ravel())
+            assert rel <= tol and abs(rel - info[k]["relres_true"]) <= 1e-3 * tol
+            xd = hz.solve_direct(A, p.b[r].ravel())
+            assert np.linalg.norm(xs[r].ravel() - xd) <= 1e3 * tol * np.linalg.norm(xd)
+            k += 1
+    if mixed:
+        assert all(c["outer"] >= 2 for c in info)   # FP32 inner solves needed FP64 refinement
+
+
+def test_mixed_unet_cycle_estimate_tracks_true_residual(helm, theta):
+    """Mixed path (FP32 Krylov, BF16 network): after one cycle the Givens estimate agrees with the
+    FP64 true residual to FP32 accuracy (eq. 4 holds in FP32)."""
+    probs = small_problems(((40, 40, 12),), seed=33)
+    ctx = make_ctx(probs)
+    net = helm.UNet(theta)
+    b = to_dev(_flat_b(probs), torch.complex128)
+    x = torch.zeros_like(b)
+    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=12, tol=1e-300, mixed=True, max_outer=1)
+    assert info[0]["iters"] == 12
+    assert rc == helm.HELM_NOT_CONVERGED
+    c = info[0]
+    assert abs(c["relres_est"] - c["relres_true"]) <= 1e-4 * max(c["relres_true"], 1e-3) + 1e-5
+
+
+def test_status_reporting(helm):
+    probs = small_problems(((20, 14, 5),), seed=34)
+    ctx = make_ctx(probs)
+    b = to_dev(_flat_b(probs), torch.complex128)
+    x = torch.zeros_like(b)
+    rc, info = helm.helm_fgmres_solve(ctx, None, b, x, 1, m=2, tol=1e-10, mixed=False, max_restarts=1)
+    assert rc == helm.HELM_NOT_CONVERGED and info[0]["status"] == "NOT_CONVERGED"
+    assert np.isfinite(info[0]["relres_true"]) and info[0]["relres_true"] < 1.0
+    bn = b.clone()
+    bn[3] = float("nan")
+    x.zero_()
+    rc, info = helm.helm_fgmres_solve(ctx, None, bn, x, 1, m=4, tol=1e-6, mixed=True, max_outer=2)
+    assert rc == helm.HELM_NAN and info[0]["status"] == "NAN"
+    with pytest.raises(helm.HelmError):
+        helm.helm_fgmres_solve(ctx, None, b, x, 1, m=0)
+    # zero right-hand side: x = 0 is exact
+    z = torch.zeros_like(b)
+    x.zero_()
+    rc, info = helm.helm_fgmres_solve(ctx, None, z, x, 1, m=4, tol=1e-6)
+    assert torch.count_nonzero(x).item() == 0
