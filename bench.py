@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark: batched Helmholtz solves per second to a true relative residual of 1e-6.
+
+Workload (the fine-grid multi-RHS configuration): 512 x 512 interior + 32 PML cells per side
+(576 x 576 = 331,776 unknowns), one seeded skull-ring velocity field with noise, 32 random point
+sources solved together, 10 points per water wavelength.  Mixed path: FP32 complex Krylov basis
+and stencil, BF16 U-Net preconditioner with FP32 accumulation, FP64 Givens / true residual /
+iterative refinement.  One step = one batched solve of all 32 right-hand sides from x0 = 0.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cuda|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own replica (weak scaling,
+no collective on the data path); value = converged solves of all ranks / max elapsed time.
+`--impl reference` times the CPU FP64 oracle (the project's reference implementation of the same
+method) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WEIGHTS = os.path.join(ROOT, "paper_2607_16906_b300", "weights", "unet_trained.npy")
+METRIC = "Helmholtz solves/s to rel.res 1e-6: batched mixed vs plain FP64, same B300"
+UNET_FLOP_PER_PT = 70816.0          # 2 x 35,408 MACs per full-resolution pixel (4-level U-Net)
+STENCIL_BYTES_FP32 = 16.0           # read z (8 B) + write A z (8 B) per point; k^2 (4 B/pt) read once per 32 RHS
+# Mean Krylov iterations per solve used to scale the oracle's per-iteration time into solves/s
+# when the reference arm runs in its own process (the CUDA arm prints its own measured mean).
+REF_ITERS_PER_SOLVE = 300
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--m", type=int, default=30)
+    ap.add_argument("--max-outer", type=int, default=100)
+    ap.add_argument("--nrhs", type=int, default=32)
+    ap.add_argument("--weights", default=WEIGHTS)
+    ap.add_argument("--no-plain", action="store_true", help="skip the bounded plain-FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the bounded CPU-oracle baseline")
+    return ap.parse_args()
+
+
+def load_weights(path, segments):
+    from paper_2607_16906_b300 import synth
+    if path and os.path.exists(path):
+        return np.load(path), "trained in-repo by helm_train_step (" + os.path.basename(path) + ")"
+    return synth.kaiming_uniform_params(segments, 42), "seeded Kaiming-uniform (untrained)"
+
+
+def workload(nrhs, seed_offset=0):
+    from paper_2607_16906_b300 import synth
+    return synth.fine_multi_rhs_problem(seed=3000 + seed_offset, nrhs=nrhs)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        load = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_iteration_time(prob, theta, iters=2):
+    """Seconds per FGMRES iteration of the CPU FP64 oracle on one right-hand side of the workload."""
+    from oracle import fgmres as fg
+    from oracle import helmholtz as hz
+    from oracle import unet as ou
+    A = hz.assemble(prob.c, prob.p, prob.h, prob.omega)
+    pre = lambda v: ou.precondition(theta, v.reshape(1, prob.Ny, prob.Nx), prob.c, prob.h)[0].ravel()
+    t0 = time.perf_counter()
+    fg.cycle(lambda u: A @ u, pre, prob.b[0].ravel(), iters, 0.0)
+    return (time.perf_counter() - t0) / iters
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import unet as ou
+    prob = workload(args.nrhs)
+    theta, wdesc = load_weights(args.weights, ou.param_segments())
+    times = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    for _ in range(args.steps):
+        times.append(cpu_oracle_iteration_time(prob, theta, iters=1))
+    t_it = statistics.median(times)
+    val = 1.0 / (t_it * REF_ITERS_PER_SOLVE)
+    cores = os.cpu_count()
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_it * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "fine-grid multi-RHS: 512^2+32 PML (576^2), 32 point-source RHS, skull ring",
+                       "weights": wdesc},
+            "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"1 FGMRES iteration (numpy FP64 U-Net + CSR stencil + CGS2) of one RHS per "
+                                       f"step, scaled by {REF_ITERS_PER_SOLVE} iterations per solve"},
+            "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_cuda(args):
+    import torch
+    from paper_2607_16906_b300 import helm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    prob = workload(args.nrhs, seed_offset=rank)
+    nrhs = args.nrhs
+    spec = helm.SystemSpec(prob.nx, prob.ny, prob.h, prob.p, prob.omega)
+    ctx = helm.Context([spec], torch.tensor(prob.c.ravel(), device="cuda"))
+    theta, wdesc = load_weights(args.weights, helm.weight_segments())
+    net = helm.UNet(theta)
+    b = torch.tensor(prob.b.ravel(), device="cuda")
+    x = torch.zeros_like(b)
+    opts = dict(m=args.m, tol=1e-6, mixed=True, max_outer=args.max_outer, inner_tol=1e-4)
+
+    def step():
+        x.zero_()
+        return helm.helm_fgmres_solve(ctx, net, b, x, nrhs, **opts)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    helm.helm_profile_enable(ctx, True)
+    clocks = ClockSampler(local)
+    l0 = helm.helm_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record()
+    converged, iters, infos = 0, [], []
+    for _ in range(args.steps):
+        rc, info = step()
+        converged += sum(1 for c in info if c["status"] == "OK")
+        iters += [c["iters"] for c in info]
+        infos = info
+    ev1.record()
+    torch.cuda.synchronize()
+    launches = helm.helm_launch_count() - l0
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    prof = helm.helm_profile_read(ctx)
+    helm.helm_profile_enable(ctx, False)
+    if dist:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+        c = torch.tensor([converged], device="cuda", dtype=torch.float64)
+        dist.all_reduce(c)
+        converged = int(c.item())
+    value = converged / (ms / 1e3)
+    mean_iters = float(np.mean(iters)) if iters else 0.0
+
+    # end to end through the public API: pinned host b -> device, solve, device x -> pinned host
+    b_host = torch.tensor(prob.b.ravel()).pin_memory()
+    x_host = torch.empty_like(b_host).pin_memory()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    conv_e2e = 0
+    for _ in range(args.steps):
+        bd = b_host.to("cuda", non_blocking=True)
+        xd = torch.zeros_like(bd)
+        rc, info = helm.helm_fgmres_solve(ctx, net, bd, xd, nrhs, **opts)
+        x_host.copy_(xd, non_blocking=True)
+        conv_e2e += sum(1 for c in info if c["status"] == "OK")
+    e1.record()
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_e2e, conv_e2e], device="cuda", dtype=torch.float64)
+        mx = t[:1].clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t[1:].clone()
+        dist.all_reduce(sm)
+        ms_e2e, conv_e2e = mx.item(), int(sm.item())
+    nbytes = b_host.numel() * b_host.element_size()
+
+    # dominant phase -> roofline
+    peaks = {}
+    pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pk_path):
+        peaks = json.load(open(pk_path))
+    dom = max(prof, key=lambda k: prof[k][0])
+    npix_apply = prob.n * nrhs
+    roof = None
+    if dom == "precond":
+        achieved = UNET_FLOP_PER_PT * npix_apply * prof["precond"][1] / (prof["precond"][0] / 1e3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", 1400.0)
+        roof = {"kernel": "U-Net forward (all layers of one application, BF16)", "bound": "tensor",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured bf16_tflops_sustained" if peaks else "fallback"}
+    else:
+        roof = {"kernel": dom, "bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs", 6400.0),
+                "unit": "GB/s", "frac": None, "traffic": None}
+
+    # stencil alone against HBM (L2 flushed between launches; 32 RHS of the workload)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    z32 = torch.randn(ctx.npts * nrhs, dtype=torch.complex64, device="cuda")
+    w32 = torch.empty_like(z32)
+    tot = 0.0
+    for it in range(13):
+        flush.fill_(it)
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record()
+        helm.helm_apply(ctx, z32, w32, nrhs)
+        s1.record()
+        torch.cuda.synchronize()
+        if it >= 3:
+            tot += s0.elapsed_time(s1)
+    st_ms = tot / 10
+    st_bytes = STENCIL_BYTES_FP32 * ctx.npts * nrhs + 4.0 * ctx.npts
+    st_gbs = st_bytes / (st_ms / 1e3) / 1e9
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    stencil = {"bound": "hbm", "achieved": st_gbs, "peak": hbm, "unit": "GB/s", "frac": st_gbs / hbm,
+               "ms": st_ms, "bytes_per_launch": st_bytes}
+
+    # bounded plain-FP64 comparison: time a few FP64 iterations (FP64 U-Net), scale by the same count
+    plain = None
+    if not args.no_plain:
+        helm.helm_profile_enable(ctx, True)
+        x.zero_()
+        torch.cuda.synchronize()
+        p0 = time.perf_counter()
+        helm.helm_fgmres_solve(ctx, net, b, x, nrhs, m=2, tol=1e-6, mixed=False, max_restarts=1)
+        torch.cuda.synchronize()
+        pt = time.perf_counter() - p0
+        pprof = helm.helm_profile_read(ctx)
+        helm.helm_profile_enable(ctx, False)
+        it_ms = sum(v[0] for k, v in pprof.items() if k in ("precond", "stencil", "orth", "lsq")) / 2
+        plain = {"ms_per_iter_32rhs": it_ms, "solves_per_s_extrapolated":
+                 nrhs / (max(mean_iters, 1.0) * it_ms / 1e3), "sample": "2 FP64 iterations x 32 RHS, scaled to the "
+                 "mixed path's mean iteration count", "wall_s": pt}
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        from oracle import unet as ou  # the bounded CPU-oracle baseline leg
+        th_o, _ = load_weights(args.weights, ou.param_segments())
+        t_it = cpu_oracle_iteration_time(prob, th_o, iters=1)
+        cpu = {"value": 1.0 / (t_it * max(mean_iters, 1.0)), "unit": "solves/s", "cores": os.cpu_count(),
+               "kind": "oracle", "sample": f"1 FGMRES iteration of one RHS ({t_it:.1f} s: numpy FP64 U-Net + CSR "
+                                           f"stencil + CGS2), scaled by the measured {mean_iters:.0f} iterations per solve"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "c64/bf16 (f64 refinement)", "data": "synthetic",
+                "config": {"workload": "fine-grid multi-RHS: 512^2+32 PML (576^2), 32 point-source RHS, skull ring",
+                           "nrhs": nrhs, "m": args.m, "tol": 1e-6, "inner_tol": 1e-4, "ppw": 10,
+                           "weights": wdesc, "l2": "inputs and Krylov basis (GBs) larger than L2",
+                           "parallelism": f"replicas x{world}"},
+                "converged": converged, "columns": args.steps * nrhs * world,
+                "mean_iters_per_solve": mean_iters,
+                "relres_true_max": max(c["relres_true"] for c in infos) if infos else None,
+                "phases_ms": {k: v[0] for k, v in prof.items()},
+                "roofline": roof, "stencil_roofline": stencil, "plain_fp64": plain,
+                "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
+                "e2e": {"value": conv_e2e / (ms_e2e / 1e3), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
+                        "d2h_bytes_per_step": nbytes}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_cuda(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -167,6 +167,19 @@ HELM_API helm_status helm_train_step(helm_ctx* ctx, helm_unet* net, const void* 
 HELM_API helm_status helm_loss_grad(helm_ctx* ctx, const helm_unet* net, const void* b, double* loss_host,
                            double* grad_dev, void* stream);
 
+/* ---- measurement (no paper counterpart: instrumentation of the path above) ---- */
+
+/* Phase timers of helm_fgmres_solve, measured with CUDA events on the solver's stream:
+ * 0 preconditioner (U-Net), 1 stencil w = A z, 2 CGS2 orthogonalisation + norm, 3 Givens / back
+ * substitution, 4 FP64 true residual + v1, 5 solution update.  Enabling (on != 0) resets the
+ * accumulators; timing adds one event pair per phase and iteration. */
+#define HELM_NUM_PHASES 6
+HELM_API helm_status helm_profile_enable(helm_ctx* ctx, int on);
+/* ms_host[HELM_NUM_PHASES]: accumulated milliseconds; counts_host (may be NULL): intervals timed. */
+HELM_API helm_status helm_profile_read(const helm_ctx* ctx, double* ms_host, int64_t* counts_host);
+/* Kernels launched by this library in this process so far (all contexts). */
+HELM_API uint64_t helm_launch_count(void);
+
 /* Thread-local message for the last non-OK status returned on this thread. */
 HELM_API const char* helm_last_error(void);
 

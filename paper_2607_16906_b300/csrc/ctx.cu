@@ -2,6 +2,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <complex>
 #include <string>
 
@@ -56,7 +57,7 @@ static std::complex<double> stretch_at(double t, int n_int, int p, double h, dou
 }
 
 __global__ void k_wavenumbers(const void* c, int c_is_fp64, int64_t n, double omega, double* k2d, float* k2f,
-                              float* chat, int* bad) {
+                              float* chat, double* chat64, int* bad) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double cv = c_is_fp64 ? ((const double*)c)[i] : (double)((const float*)c)[i];
@@ -68,6 +69,7 @@ __global__ void k_wavenumbers(const void* c, int c_is_fp64, int64_t n, double om
   k2d[i] = k * k;
   k2f[i] = (float)(k * k);
   chat[i] = (float)(cv / 1500.0);
+  chat64[i] = cv / 1500.0;
 }
 
 int num_cols(const helm_ctx* ctx, int nrhs) { return ctx->nsys * nrhs; }
@@ -105,7 +107,60 @@ helm_status ensure_pinned(helm_ctx* ctx, size_t bytes) {
 
 void unet_buffers_free(helm_ctx* ctx);  // unet.cu
 
+static std::atomic<uint64_t> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+void prof_begin(helm_ctx* ctx, int ph, cudaStream_t st) {
+  if (!ctx->prof_on) return;
+  cudaEventRecord(ctx->prof_ev[ph][0], st);
+}
+
+void prof_end(helm_ctx* ctx, int ph, cudaStream_t st) {
+  if (!ctx->prof_on) return;
+  cudaEventRecord(ctx->prof_ev[ph][1], st);
+  ctx->prof_pending[ph] = 1;
+}
+
+void prof_collect(helm_ctx* ctx) {
+  if (!ctx->prof_on) return;
+  for (int p = 0; p < NUM_PHASES; ++p) {
+    if (!ctx->prof_pending[p]) continue;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, ctx->prof_ev[p][0], ctx->prof_ev[p][1]) == cudaSuccess) {
+      ctx->prof_ms[p] += ms;
+      ctx->prof_cnt[p] += 1;
+    }
+    ctx->prof_pending[p] = 0;
+  }
+}
+
 }  // namespace helm
+
+extern "C" uint64_t helm_launch_count(void) { return helm::g_launches.load(); }
+
+extern "C" helm_status helm_profile_enable(helm_ctx* ctx, int on) {
+  if (!ctx) return helm::fail(HELM_ERR_INVALID_ARG, "helm_profile_enable: NULL context");
+  if (on && !ctx->prof_ev[0][0]) {
+    for (int p = 0; p < helm::NUM_PHASES; ++p)
+      for (int k = 0; k < 2; ++k) HELM_CK(cudaEventCreate(&ctx->prof_ev[p][k]));
+  }
+  ctx->prof_on = on ? 1 : 0;
+  for (int p = 0; p < helm::NUM_PHASES; ++p) {
+    ctx->prof_ms[p] = 0;
+    ctx->prof_cnt[p] = 0;
+    ctx->prof_pending[p] = 0;
+  }
+  return HELM_OK;
+}
+
+extern "C" helm_status helm_profile_read(const helm_ctx* ctx, double* ms_host, int64_t* counts_host) {
+  if (!ctx || !ms_host) return helm::fail(HELM_ERR_INVALID_ARG, "helm_profile_read: NULL argument");
+  for (int p = 0; p < helm::NUM_PHASES; ++p) {
+    ms_host[p] = ctx->prof_ms[p];
+    if (counts_host) counts_host[p] = ctx->prof_cnt[p];
+  }
+  return HELM_OK;
+}
 
 using namespace helm;
 
@@ -178,6 +233,7 @@ extern "C" helm_status helm_create(helm_ctx** out, int nsys, const helm_grid* gr
   ck(cudaMalloc(&ctx->k2f, sizeof(float) * off), "cudaMalloc k2f");
   ck(cudaMalloc(&ctx->k2d, sizeof(double) * off), "cudaMalloc k2d");
   ck(cudaMalloc(&ctx->chat, sizeof(float) * off), "cudaMalloc chat");
+  ck(cudaMalloc(&ctx->chat64, sizeof(double) * off), "cudaMalloc chat64");
   ck(cudaMalloc(&ctx->prof_d, sizeof(double2) * px), "cudaMalloc prof_d");
   ck(cudaMalloc(&ctx->prof_f, sizeof(float2) * px), "cudaMalloc prof_f");
   ck(cudaMalloc(&ctx->flag_dev, sizeof(int) * 16), "cudaMalloc flag");
@@ -190,8 +246,9 @@ extern "C" helm_status helm_create(helm_ctx** out, int nsys, const helm_grid* gr
   ck(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int) * 16, st), "memset flag");
   for (auto& h : ctx->sys) {
     const char* cb = (const char*)c_dev + h.off * (c_is_fp64 ? 8 : 4);
-    k_wavenumbers<<<cdiv(h.n, 256), 256, 0, st>>>(cb, c_is_fp64, h.n, h.omega, ctx->k2d + h.off,
-                                                   ctx->k2f + h.off, ctx->chat + h.off, ctx->flag_dev);
+    launch(k_wavenumbers, cdiv(h.n, 256), 256, 0, st, cb, c_is_fp64, h.n, h.omega, ctx->k2d + h.off,
+                                                   ctx->k2f + h.off, ctx->chat + h.off, ctx->chat64 + h.off,
+                                                   ctx->flag_dev);
   }
   ck(cudaGetLastError(), "k_wavenumbers launch");
   int bad = 0;
@@ -214,11 +271,15 @@ extern "C" helm_status helm_destroy(helm_ctx* ctx) {
   cudaFree(ctx->k2f);
   cudaFree(ctx->k2d);
   cudaFree(ctx->chat);
+  cudaFree(ctx->chat64);
   cudaFree(ctx->prof_d);
   cudaFree(ctx->prof_f);
   cudaFree(ctx->cols_dev);
   cudaFree(ctx->flag_dev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
+  for (auto& pe : ctx->prof_ev)
+    for (auto& e : pe)
+      if (e) cudaEventDestroy(e);
   delete ctx;
   return HELM_OK;
 }

@@ -91,6 +91,7 @@ struct helm_ctx {
   float* k2f = nullptr;
   double* k2d = nullptr;
   float* chat = nullptr;
+  double* chat64 = nullptr;
   // per system 1-D profiles: s(node) and 1 / s(half node) in x and y, both precisions
   double2* prof_d = nullptr;
   float2* prof_f = nullptr;
@@ -105,6 +106,12 @@ struct helm_ctx {
   int* flag_dev = nullptr;         // device error/status flag
   void* pinned = nullptr;          // small pinned host buffer for status reads
   size_t pinned_bytes = 0;
+  // phase timers
+  int prof_on = 0;
+  cudaEvent_t prof_ev[8][2] = {};
+  int prof_pending[8] = {};
+  double prof_ms[8] = {};
+  int64_t prof_cnt[8] = {};
 };
 
 namespace helm {
@@ -130,5 +137,20 @@ __global__ void k_finalize(const double* __restrict__ partial, const int* __rest
                            double* __restrict__ out);
 
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
+
+// Every kernel of the library is launched through launch(): it keeps a process-wide count of
+// launches (helm_launch_count) for the benchmark's launch accounting.
+void count_launch();
+template <typename... KArgs, typename... Args>
+inline void launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
+  k<<<grid, block, smem, st>>>(args...);
+  count_launch();
+}
+
+// Phase timers of the solver (CUDA events on the solver's stream), enabled by helm_profile_enable.
+enum Phase { PH_PRECOND = 0, PH_STENCIL, PH_ORTH, PH_LSQ, PH_RESIDUAL, PH_UPDATE, NUM_PHASES };
+void prof_begin(helm_ctx* ctx, int ph, cudaStream_t st);
+void prof_end(helm_ctx* ctx, int ph, cudaStream_t st);
+void prof_collect(helm_ctx* ctx);  // after a stream synchronisation: add the recorded intervals
 
 }  // namespace helm

@@ -336,9 +336,9 @@ helm_status col_norm2(helm_ctx* ctx, const C<R>* v, int nrhs, double* out, cudaS
   int* np = (int*)(partial + ncol * nch);
   std::vector<int> nph(ncol, nch);
   HELM_CK(cudaMemcpyAsync(np, nph.data(), sizeof(int) * ncol, cudaMemcpyHostToDevice, st));
-  k_colnorm2<R><<<dim3(nch, ncol), RED_THREADS, 0, st>>>(v, ctx->cols_dev, nch, partial);
+  launch(k_colnorm2<R>, dim3(nch, ncol), RED_THREADS, 0, st, v, ctx->cols_dev, nch, partial);
   HELM_CK_LAUNCH();
-  k_finalize<<<ncol, 256, 0, st>>>(partial, np, 1, out);
+  launch(k_finalize, ncol, 256, 0, st, partial, np, 1, out);
   HELM_CK_LAUNCH();
   return HELM_OK;
 }
@@ -423,9 +423,20 @@ static helm_status solver_ws(helm_ctx* ctx, int m, int ncol, int nch, bool has_n
   return HELM_OK;
 }
 
-__global__ void k_fill(double* p, int64_t n, double v) {
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) p[i] = v;
+// Start of a cycle: g = e1, vscale = 1, network input/output scales for a unit-norm v1
+// (alpha = sqrt(n), output h^2 / alpha).
+__global__ void k_cycle_setup(int ncol, int m, const ColDesc* __restrict__ cols, double2* __restrict__ g,
+                              double* __restrict__ vscale, double* __restrict__ in_scale,
+                              double* __restrict__ out_scale) {
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  for (int i = 0; i <= m; ++i) {
+    g[(int64_t)col * (m + 1) + i] = make_double2(i == 0 ? 1.0 : 0.0, 0.0);
+    vscale[(int64_t)col * (m + 1) + i] = 1.0;
+  }
+  double a = sqrt((double)cols[col].len);
+  in_scale[col] = a;
+  out_scale[col] = cols[col].h2 / a;
 }
 
 template <typename R>
@@ -461,6 +472,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
   dim3 vgrid(nch, ncol);
   for (int cyc = 0; cyc <= max_cycles; ++cyc) {
     // true residual in FP64 (eq. 10)
+    prof_begin(ctx, PH_RESIDUAL, stream);
     HELM_TRY(residual_fp64(ctx, x, b, W.r, nrhs, W.sums, stream));
     HELM_CK(cudaMemcpyAsync(h_sums, W.sums, sizeof(double) * 2 * ncol, cudaMemcpyDeviceToHost, stream));
     HELM_CK(cudaStreamSynchronize(stream));
@@ -476,8 +488,6 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
       } else if (rel[c] <= o.tol) {
         inf[c].status = HELM_OK;
         done[c] = 1;
-      } else if (done[c] && inf[c].status == HELM_BREAKDOWN) {
-        // stays done
       }
       ColState s{};
       s.active = !done[c] && cyc < max_cycles;
@@ -488,78 +498,73 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
       h_st[c] = s;
       nact += s.active;
     }
-    if (nact == 0) break;
-    HELM_CK(cudaMemcpyAsync(W.st, h_st, sizeof(ColState) * ncol, cudaMemcpyHostToDevice, stream));
-    // g = beta e1 with beta = 1 (the cycle runs on r / ||r||); vscale_0 = 1
-    HELM_CK(cudaMemsetAsync(W.g, 0, sizeof(double2) * ncol * (m + 1), stream));
-    {
-      std::vector<double2> g0(ncol, make_double2(1.0, 0.0));
-      for (int c = 0; c < ncol; ++c)
-        HELM_CK(cudaMemcpyAsync(W.g + (int64_t)c * (m + 1), &g0[c], sizeof(double2), cudaMemcpyHostToDevice, stream));
-      std::vector<double> v0(ncol), is(ncol), os(ncol);
-      for (int c = 0; c < ncol; ++c) {
-        is[c] = sqrt((double)ctx->cols_host[c].len);
-        os[c] = ctx->cols_host[c].h2 / is[c];
-      }
-      HELM_CK(cudaMemcpyAsync(W.in_scale, is.data(), sizeof(double) * ncol, cudaMemcpyHostToDevice, stream));
-      HELM_CK(cudaMemcpyAsync(W.out_scale, os.data(), sizeof(double) * ncol, cudaMemcpyHostToDevice, stream));
-      k_fill<<<cdiv((int64_t)ncol * ldp, 256), 256, 0, stream>>>(W.vscale, (int64_t)ncol * ldp, 1.0);
-      HELM_CK(cudaStreamSynchronize(stream));  // host vectors above go out of scope
+    if (nact == 0) {
+      prof_end(ctx, PH_RESIDUAL, stream);
+      break;
     }
-    k_v0<R><<<vgrid, RED_THREADS, 0, stream>>>(W.r, W.V, W.st, ctx->cols_dev, nch);
+    HELM_CK(cudaMemcpyAsync(W.st, h_st, sizeof(ColState) * ncol, cudaMemcpyHostToDevice, stream));
+    // g = e1 (the cycle runs on r / ||r||), vscale = 1, network scales for a unit-norm v1
+    launch(k_cycle_setup, cdiv(ncol, 64), 64, 0, stream, ncol, m, ctx->cols_dev, W.g, W.vscale, W.in_scale,
+           W.out_scale);
+    launch(k_v0<R>, vgrid, RED_THREADS, 0, stream, W.r, W.V, W.st, ctx->cols_dev, nch);
     HELM_CK_LAUNCH();
+    prof_end(ctx, PH_RESIDUAL, stream);
     for (int j = 0; j < m; ++j) {
       C<R>* Vj = W.V + (int64_t)j * nvec;
       C<R>* Zj = net ? W.Z + (int64_t)j * nvec : Vj;
       // z_j = N_theta(v_j)
+      prof_begin(ctx, PH_PRECOND, stream);
       if (net) {
         for (int s = 0; s < ctx->nsys; ++s) {
           int64_t off = ctx->sys[s].off * nrhs;
           HELM_TRY(unet_precondition<R>(ctx, net, s, Vj + off, Zj + off, nrhs, W.in_scale + s * nrhs,
                                         W.out_scale + s * nrhs, stream));
         }
-      }
-      // w = A z_j  (without a network z_j = vscale_j * Vraw_j: apply to Vraw and fold the scale into h)
-      if (net) {
-        HELM_TRY(apply_op<R>(ctx, Zj, W.w, nrhs, false, stream));
       } else {
-        // the FP64 residual buffer is free after k_v0: use it for the scaled copy z_j = v_j
-        C<R>* zt = (C<R>*)W.r;
-        k_scale_copy<R><<<vgrid, RED_THREADS, 0, stream>>>(Vj, zt, nullptr, ctx->cols_dev, nch, W.in_scale);
+        // z_j = v_j = vscale_j Vraw_j into the FP64 residual buffer, free after k_v0
+        launch(k_scale_copy<R>, vgrid, RED_THREADS, 0, stream, Vj, (C<R>*)W.r, nullptr, ctx->cols_dev, nch,
+               W.in_scale);
         HELM_CK_LAUNCH();
-        HELM_TRY(apply_op<R>(ctx, zt, W.w, nrhs, false, stream));
       }
+      prof_end(ctx, PH_PRECOND, stream);
+      // w = A z_j
+      prof_begin(ctx, PH_STENCIL, stream);
+      HELM_TRY(apply_op<R>(ctx, net ? Zj : (C<R>*)W.r, W.w, nrhs, false, stream));
+      prof_end(ctx, PH_STENCIL, stream);
       const int nv = j + 1;
-      // CGS2, two passes
+      // CGS2, two passes; the second writes the unnormalised v_{j+1} and its norm partials
+      prof_begin(ctx, PH_ORTH, stream);
       for (int pass = 0; pass < 2; ++pass) {
-        k_mdot<R><<<vgrid, RED_THREADS, 0, stream>>>(W.V, nvec, nv, W.w, ctx->cols_dev, W.st, nch,
-                                                      W.partial, ldp);
-        HELM_CK_LAUNCH();
-        k_hreduce<R><<<ncol, 128, 0, stream>>>(W.partial, nch, ldp, nv, W.vscale, ldp, W.st, W.hbuf,
-                                                W.coef, pass);
-        HELM_CK_LAUNCH();
+        launch(k_mdot<R>, vgrid, RED_THREADS, 0, stream, W.V, nvec, nv, W.w, ctx->cols_dev, W.st, nch, W.partial,
+               ldp);
+        launch(k_hreduce<R>, ncol, 128, 0, stream, W.partial, nch, ldp, nv, W.vscale, ldp, W.st, W.hbuf, W.coef,
+               pass);
         C<R>* dst = pass == 1 ? W.V + (int64_t)(j + 1) * nvec : nullptr;
-        k_maxpy<R><<<vgrid, RED_THREADS, maxpy_smem, stream>>>(W.V, nvec, nv, W.w, W.coef, ldp, ctx->cols_dev,
-                                                               W.st, nch, dst,
-                                                               pass == 1 ? W.npartial : nullptr);
+        launch(k_maxpy<R>, vgrid, RED_THREADS, maxpy_smem, stream, W.V, nvec, nv, W.w, W.coef, ldp, ctx->cols_dev,
+               W.st, nch, dst, pass == 1 ? W.npartial : nullptr);
         HELM_CK_LAUNCH();
       }
+      prof_end(ctx, PH_ORTH, stream);
+      prof_begin(ctx, PH_LSQ, stream);
       HELM_CK(cudaMemsetAsync(W.nactive, 0, sizeof(int), stream));
-      k_givens<R><<<cdiv(ncol, 64), 64, 0, stream>>>(j, ncol, m, W.npartial, nch, W.hbuf, ldp, W.vscale, W.Rm, W.cs,
-                                                     W.sn, W.g, W.st, W.nactive, W.in_scale, ctx->cols_dev,
-                                                     breakdown_eps);
+      launch(k_givens<R>, cdiv(ncol, 64), 64, 0, stream, j, ncol, m, W.npartial, nch, W.hbuf, ldp, W.vscale, W.Rm,
+             W.cs, W.sn, W.g, W.st, W.nactive, W.in_scale, ctx->cols_dev, breakdown_eps);
       HELM_CK_LAUNCH();
       HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      prof_end(ctx, PH_LSQ, stream);
       HELM_CK(cudaStreamSynchronize(stream));
+      prof_collect(ctx);
       if (*h_nact == 0) break;
     }
-    k_backsolve<<<cdiv(ncol, 64), 64, 0, stream>>>(ncol, m, W.Rm, W.g, W.st, W.y);
-    HELM_CK_LAUNCH();
-    k_xupdate<R><<<vgrid, RED_THREADS, 0, stream>>>(W.Z, nvec, W.y, m, net ? nullptr : W.vscale, W.st,
-                                                    ctx->cols_dev, nch, x);
+    prof_begin(ctx, PH_UPDATE, stream);
+    launch(k_backsolve, cdiv(ncol, 64), 64, 0, stream, ncol, m, W.Rm, W.g, W.st, W.y);
+    launch(k_xupdate<R>, vgrid, RED_THREADS, 0, stream, W.Z, nvec, W.y, m, net ? nullptr : W.vscale, W.st,
+           ctx->cols_dev, nch, x);
     HELM_CK_LAUNCH();
     HELM_CK(cudaMemcpyAsync(h_st, W.st, sizeof(ColState) * ncol, cudaMemcpyDeviceToHost, stream));
+    prof_end(ctx, PH_UPDATE, stream);
     HELM_CK(cudaStreamSynchronize(stream));
+    prof_collect(ctx);
     for (int c = 0; c < ncol; ++c) {
       if (done[c]) continue;
       inf[c].iters += h_st[c].k;

@@ -164,10 +164,10 @@ helm_status apply_op(helm_ctx* ctx, const C<R>* x, C<R>* y, int nrhs, bool adjoi
     dim3 grid(cdiv(s.Nx, STENCIL_THREADS), cdiv(s.Ny, STENCIL_ROWS), nrhs);
     R inv_h2 = (R)(1.0 / (s.h * s.h));
     if (adjoint)
-      k_stencil<R, true><<<grid, STENCIL_THREADS, 0, st>>>(xs, ys, k2, pr + s.prof_x, pr + s.prof_y, s.Nx, s.Ny,
+      launch(k_stencil<R, true>, grid, STENCIL_THREADS, 0, st, xs, ys, k2, pr + s.prof_x, pr + s.prof_y, s.Nx, s.Ny,
                                                            s.n, inv_h2);
     else
-      k_stencil<R, false><<<grid, STENCIL_THREADS, 0, st>>>(xs, ys, k2, pr + s.prof_x, pr + s.prof_y, s.Nx, s.Ny,
+      launch(k_stencil<R, false>, grid, STENCIL_THREADS, 0, st, xs, ys, k2, pr + s.prof_x, pr + s.prof_y, s.Nx, s.Ny,
                                                             s.n, inv_h2);
   }
   HELM_CK_LAUNCH();
@@ -200,14 +200,14 @@ helm_status residual_fp64(helm_ctx* ctx, const double2* x, const double2* b, dou
   int64_t pbase = 0;
   for (auto& s : ctx->sys) {
     dim3 grid(cdiv(s.Nx, STENCIL_THREADS), cdiv(s.Ny, STENCIL_ROWS), nrhs);
-    k_residual<<<grid, STENCIL_THREADS, 0, st>>>(x + s.off * nrhs, b + s.off * nrhs, r + s.off * nrhs,
+    launch(k_residual, grid, STENCIL_THREADS, 0, st, x + s.off * nrhs, b + s.off * nrhs, r + s.off * nrhs,
                                                  ctx->k2d + s.off, ctx->prof_d + s.prof_x, ctx->prof_d + s.prof_y,
                                                  s.Nx, s.Ny, s.n, 1.0 / (s.h * s.h), partial + pbase * 2, 0);
     pbase += (int64_t)grid.x * grid.y * nrhs;
     col0 += nrhs;
   }
   HELM_CK_LAUNCH();
-  k_finalize<<<ncol, 256, 0, st>>>(partial, np_dev, 2, sums);
+  launch(k_finalize, ncol, 256, 0, st, partial, np_dev, 2, sums);
   HELM_CK_LAUNCH();
   return HELM_OK;
 }

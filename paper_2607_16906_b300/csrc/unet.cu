@@ -81,7 +81,7 @@ helm_status unet_prepare(helm_unet* net, cudaStream_t st) {
   for (int l = 0; l < NUM_LAYERS; ++l) {
     const LayerDesc& d = kLayers[l];
     int64_t n = (int64_t)taps_of(d.kind) * d.cin * d.cout + d.cout;
-    k_prep_layer<<<cdiv(n, 256), 256, 0, st>>>(net->master, d.kind, d.cin, d.cout, L.m_w[l], L.m_b[l], L.c_w[l],
+    launch(k_prep_layer, cdiv(n, 256), 256, 0, st, net->master, d.kind, d.cin, d.cout, L.m_w[l], L.m_b[l], L.c_w[l],
                                                L.c_b[l], net->w64, net->w32);
   }
   HELM_CK_LAUNCH();
@@ -212,7 +212,7 @@ __global__ void k_pool(const T* __restrict__ in, T* __restrict__ out, int C, int
 // Channel stride S0 (extra channels zero).
 template <typename T, typename R>
 __global__ void k_pack_input(const C<R>* __restrict__ v, int64_t col_stride, const double* __restrict__ in_scale,
-                             const float* __restrict__ chat, int Nx, int Ny, int Hp, int Wp, int B, int S0,
+                             const typename Acc<T>::A* __restrict__ chat, int Nx, int Ny, int Hp, int Wp, int B, int S0,
                              T* __restrict__ x0) {
   int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (pix >= (int64_t)B * Hp * Wp) return;
@@ -337,7 +337,7 @@ static helm_status conv3(const helm_unet* net, int l, const T* in0, int C0, int 
   if (conv_tc_enabled<T>(net, l, H, W)) return conv_tc_forward(net, l, in0, C0, in1, C1, out, B, H, W, st);
   const auto* w = cc_weights<T>(net);
   dim3 grid(cdiv((int64_t)B * H * W, CC_THREADS), d.cout / CC_COT);
-  k_conv_cc<T, 3><<<grid, CC_THREADS, 0, st>>>(in0, C0, S0, in1, C1, S1, w + net->L.c_w[l], w + net->L.c_b[l], out,
+  launch(k_conv_cc<T, 3>, grid, CC_THREADS, 0, st, in0, C0, S0, in1, C1, S1, w + net->L.c_w[l], w + net->L.c_b[l], out,
                                                 d.cout, B, H, W, 1);
   HELM_CK_LAUNCH();
   return HELM_OK;
@@ -348,7 +348,7 @@ static helm_status up2(const helm_unet* net, int l, const T* in, T* out, int B, 
   const LayerDesc& d = kLayers[l];
   const auto* w = cc_weights<T>(net);
   dim3 grid(cdiv((int64_t)B * Ho * Wo, CC_THREADS), d.cout / CC_COT);
-  k_up_cc<T><<<grid, CC_THREADS, 0, st>>>(in, d.cin, w + net->L.c_w[l], w + net->L.c_b[l], out, d.cout, B, Ho, Wo);
+  launch(k_up_cc<T>, grid, CC_THREADS, 0, st, in, d.cin, w + net->L.c_w[l], w + net->L.c_b[l], out, d.cout, B, Ho, Wo);
   HELM_CK_LAUNCH();
   return HELM_OK;
 }
@@ -356,7 +356,7 @@ static helm_status up2(const helm_unet* net, int l, const T* in, T* out, int B, 
 template <typename T>
 static helm_status pool(const T* in, T* out, int C, int B, int Ho, int Wo, cudaStream_t st) {
   int64_t n = (int64_t)B * Ho * Wo * C;
-  k_pool<T><<<cdiv(n, 256), 256, 0, st>>>(in, out, C, B, Ho, Wo);
+  launch(k_pool<T>, cdiv(n, 256), 256, 0, st, in, out, C, B, Ho, Wo);
   HELM_CK_LAUNCH();
   return HELM_OK;
 }
@@ -399,13 +399,18 @@ helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, cons
   UnetBuffers::Set& S = ub->set[sizeof(R) == 8 ? 1 : 0];
   T** a = (T**)S.a;
   int64_t npix = (int64_t)B * Hp * Wp;
-  k_pack_input<T, R><<<cdiv(npix, 256), 256, 0, st>>>(v, s.n, in_scale, ctx->chat + s.off, s.Nx, s.Ny, Hp, Wp, B,
-                                                      X0_CH, a[A_X0]);
+  const typename Acc<T>::A* chat;
+  if constexpr (sizeof(R) == 8)
+    chat = ctx->chat64 + s.off;
+  else
+    chat = ctx->chat + s.off;
+  launch(k_pack_input<T, R>, cdiv(npix, 256), 256, 0, st, v, s.n, in_scale, chat, s.Nx, s.Ny, Hp, Wp, B, X0_CH,
+                                                      a[A_X0]);
   HELM_CK_LAUNCH();
   HELM_TRY(unet_body<T>(net, S, B, st));
   const auto* w = cc_weights<T>(net);
   int64_t nout = (int64_t)B * s.Ny * s.Nx;
-  k_final<T, R><<<cdiv(nout, 256), 256, 0, st>>>(a[A_D1B], w + net->L.c_w[L_FINAL], w + net->L.c_b[L_FINAL],
+  launch(k_final<T, R>, cdiv(nout, 256), 256, 0, st, a[A_D1B], w + net->L.c_w[L_FINAL], w + net->L.c_b[L_FINAL],
                                                  out_scale, s.Nx, s.Ny, Hp, Wp, B, z, s.n, nullptr);
   HELM_CK_LAUNCH();
   return HELM_OK;
@@ -438,7 +443,7 @@ helm_status precond_entry(helm_ctx* ctx, const helm_unet* net, const C<R>* v, C<
   double* in_s = n2 + ncol;
   double* out_s = in_s + ncol;
   HELM_TRY(col_norm2<R>(ctx, v, nrhs, n2, st));
-  k_alpha<<<cdiv(ncol, 128), 128, 0, st>>>(n2, ncol, ctx->cols_dev, in_s, out_s);
+  launch(k_alpha, cdiv(ncol, 128), 128, 0, st, n2, ncol, ctx->cols_dev, in_s, out_s);
   HELM_CK_LAUNCH();
   for (int s = 0; s < ctx->nsys; ++s) {
     int64_t o = ctx->sys[s].off * nrhs;

@@ -69,8 +69,12 @@ _SIGS = {
     "helm_train_step": (ct.c_int, [_P, _P, _P, ct.c_double, ct.c_double, ct.c_double, ct.POINTER(ct.c_double),
                                    ct.POINTER(ct.c_double), _P]),
     "helm_loss_grad": (ct.c_int, [_P, _P, _P, ct.POINTER(ct.c_double), _P, _P]),
+    "helm_profile_enable": (ct.c_int, [_P, ct.c_int]),
+    "helm_profile_read": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
+    "helm_launch_count": (ct.c_uint64, []),
     "helm_last_error": (ct.c_char_p, []),
 }
+PHASES = ("precond", "stencil", "orth", "lsq", "residual", "update")
 for _name, (_res, _args) in _SIGS.items():
     _f = getattr(_lib, _name)
     _f.restype = _res
@@ -288,3 +292,21 @@ def helm_loss_grad(ctx: Context, net: UNet, b: torch.Tensor, stream=None):
     loss = ct.c_double()
     _check(_lib.helm_loss_grad(ctx.handle, net.handle, _dev_ptr(b), ct.byref(loss), _dev_ptr(g), _stream(stream)))
     return loss.value, g
+
+
+def helm_profile_enable(ctx: Context, on=True):
+    """Enable (and reset) or disable the solver's per-phase CUDA-event timers."""
+    _check(_lib.helm_profile_enable(ctx.handle, int(bool(on))))
+
+
+def helm_profile_read(ctx: Context):
+    """{phase: (milliseconds, intervals)} accumulated since helm_profile_enable."""
+    ms = (ct.c_double * len(PHASES))()
+    cnt = (ct.c_int64 * len(PHASES))()
+    _check(_lib.helm_profile_read(ctx.handle, ms, cnt))
+    return {p: (ms[i], cnt[i]) for i, p in enumerate(PHASES)}
+
+
+def helm_launch_count() -> int:
+    """Kernels launched by libhelm in this process so far."""
+    return int(_lib.helm_launch_count())
