@@ -167,6 +167,24 @@ HELM_API helm_status helm_train_step(helm_ctx* ctx, helm_unet* net, const void* 
 HELM_API helm_status helm_loss_grad(helm_ctx* ctx, const helm_unet* net, const void* b, double* loss_host,
                            double* grad_dev, void* stream);
 
+/* ---- allocation-free relative residual (the paper has no counterpart) ---------
+ * For callers that must not allocate device memory during a call: e.g. a process whose device
+ * memory is reserved up front by another framework's caching allocator, or a latency-critical
+ * loop in which a cudaMalloc would synchronise the device.  Computes the same per-column
+ * ||b - A x|| / ||b|| (FP64) as helm_relres, but writes it to DEVICE memory
+ * relres_dev[nsys * nrhs] (column = system-major, rhs-minor), stores no residual vector, and
+ * calls no cudaMalloc, cudaFree or allocating library routine.  x, b: C128 batch vectors.
+ * Its per-block partial sums live in one fixed device array of 2^20 doubles (8 MiB) that every
+ * GPU loading this library holds until the process exits; a batch needing more than that
+ * (2 x ceil(Nx/128) x ceil(Ny/8) doubles per column, summed over columns) is rejected with
+ * HELM_ERR_INVALID_ARG.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ * capture.  All calls share the array, which keeps the last call's contents (every partial is
+ * written before it is read, so nothing needs clearing): calls that overlap on the GPU, on
+ * different streams or threads, race on it.  Asynchronous on `stream`. */
+HELM_API helm_status helm_relres_noalloc(helm_ctx* ctx, const void* x, const void* b, int nrhs, double* relres_dev,
+                                         void* stream);
+
 /* ---- measurement (no paper counterpart: instrumentation of the path above) ---- */
 
 /* Phase timers of helm_fgmres_solve, measured with CUDA events on the solver's stream:

@@ -7,6 +7,8 @@
 // per thread, 8 B in FP32, 16 B in FP64).  Per point the kernel moves 8 + 8 + 4 B (FP32) or
 // 16 + 16 + 8 B (FP64) of HBM traffic: read u, write A u, read k^2; the 1-D PML profiles are
 // O(Nx + Ny) and stay in L1/L2.
+#include <mutex>
+
 #include "helm_internal.cuh"
 
 namespace helm {
@@ -251,5 +253,160 @@ extern "C" helm_status helm_relres(helm_ctx* ctx, const void* x, const void* b, 
   HELM_CK(cudaMemcpyAsync(h.data(), sums, sizeof(double) * 2 * ncol, cudaMemcpyDeviceToHost, st));
   HELM_CK(cudaStreamSynchronize(st));
   for (int c = 0; c < ncol; ++c) out_host[c] = h[2 * c + 1] > 0 ? sqrt(h[2 * c] / h[2 * c + 1]) : sqrt(h[2 * c]);
+  return HELM_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free relative residual.
+//
+// Some callers may not allocate device memory while they run: a host whose device memory is
+// reserved up front by another framework's caching allocator, or a latency-critical loop in which
+// a cudaMalloc would synchronise the whole device.  helm_relres_noalloc serves them: it computes
+// the same ||b - A x|| / ||b|| as helm_relres, without storing r, and keeps its per-block partial
+// sums in the fixed device array below instead of a workspace.  Every GPU that loads this library
+// holds the array (NOALLOC_SCRATCH_DOUBLES doubles, 8 MiB) until the process exits.  The host-side
+// name of the array is only a stand-in; its device address is looked up once per device.
+namespace helm {
+
+constexpr int64_t NOALLOC_SCRATCH_DOUBLES = (int64_t)1 << 20;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_SCRATCH_DOUBLES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static double* g_noalloc_addr[NOALLOC_MAX_DEVICES] = {};
+static std::mutex g_noalloc_mu;
+
+// Device address of the scratch array on the current device (looked up on first use per device).
+static helm_status noalloc_scratch(double** out) {
+  int dev = -1;
+  HELM_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(HELM_ERR_INVALID_ARG, "helm_relres_noalloc: device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    HELM_CK(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = (double*)p;
+  }
+  *out = g_noalloc_addr[dev];
+  return HELM_OK;
+}
+
+// Like k_residual without the r output: per-block partial sums of |b - A x|^2 and |b|^2 only.
+__global__ void __launch_bounds__(STENCIL_THREADS) k_relres_partials(const double2* __restrict__ x,
+                                                                     const double2* __restrict__ b,
+                                                                     const double* __restrict__ k2,
+                                                                     const double2* __restrict__ px,
+                                                                     const double2* __restrict__ py, int Nx, int Ny,
+                                                                     int64_t rhs_stride, double inv_h2,
+                                                                     double* __restrict__ partial) {
+  int i = blockIdx.x * STENCIL_THREADS + threadIdx.x;
+  int j0 = blockIdx.y * STENCIL_ROWS;
+  const double2* xr = x + blockIdx.z * rhs_stride;
+  const double2* br = b + blockIdx.z * rhs_stride;
+  double sr = 0.0, sb = 0.0;
+  if (i < Nx) {
+    const double2 sxi = px[i], ixm = px[Nx + i], ixp = px[Nx + i + 1];
+    double2 uS = ld_u<double, false>(xr, j0 - 1, i, Nx, Ny);
+    double2 uC = ld_u<double, false>(xr, j0, i, Nx, Ny);
+#pragma unroll
+    for (int q = 0; q < STENCIL_ROWS; ++q) {
+      int j = j0 + q;
+      if (j >= Ny) break;
+      double2 uN = ld_u<double, false>(xr, j + 1, i, Nx, Ny);
+      double2 uW = ld_u<double, false>(xr, j, i - 1, Nx, Ny);
+      double2 uE = ld_u<double, false>(xr, j, i + 1, Nx, Ny);
+      int64_t idx = (int64_t)j * Nx + i;
+      double2 Au = stencil_point<double>(uC, uE, uW, uN, uS, sxi, ixm, ixp, py[j], py[Ny + j], py[Ny + j + 1],
+                                         k2[idx], inv_h2);
+      double2 bv = br[idx];
+      double2 res = csub(bv, Au);
+      sr += res.x * res.x + res.y * res.y;
+      sb += bv.x * bv.x + bv.y * bv.y;
+      uS = uC;
+      uC = uN;
+    }
+  }
+  __shared__ double red[2][STENCIL_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_down_sync(0xffffffffu, sr, o);
+    sb += __shfl_down_sync(0xffffffffu, sb, o);
+  }
+  int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[0][w] = sr;
+    red[1][w] = sb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, c = 0;
+    for (int k = 0; k < STENCIL_THREADS / 32; ++k) {
+      a += red[0][k];
+      c += red[1][k];
+    }
+    int64_t base = ((int64_t)blockIdx.z * gridDim.x * gridDim.y + blockIdx.y * gridDim.x + blockIdx.x) * 2;
+    partial[base] = a;
+    partial[base + 1] = c;
+  }
+}
+
+// out[r] = sqrt(sum |r|^2 / sum |b|^2) for the nrhs columns of one system (one block per column).
+__global__ void k_relres_finalize(const double* __restrict__ partial, int nparts, double* __restrict__ out) {
+  const double* p = partial + (int64_t)blockIdx.x * nparts * 2;
+  double sr = 0, sb = 0;
+  for (int k = threadIdx.x; k < nparts; k += blockDim.x) {
+    sr += p[2 * k];
+    sb += p[2 * k + 1];
+  }
+  __shared__ double red[2][256 / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_down_sync(0xffffffffu, sr, o);
+    sb += __shfl_down_sync(0xffffffffu, sb, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = sr;
+    red[1][threadIdx.x >> 5] = sb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, c = 0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      c += red[1][k];
+    }
+    out[blockIdx.x] = c > 0 ? sqrt(a / c) : sqrt(a);
+  }
+}
+
+}  // namespace helm
+
+extern "C" helm_status helm_relres_noalloc(helm_ctx* ctx, const void* x, const void* b, int nrhs,
+                                           double* relres_dev, void* stream) {
+  using namespace helm;
+  if (!ctx || !x || !b || !relres_dev || nrhs <= 0)
+    return fail(HELM_ERR_INVALID_ARG, "helm_relres_noalloc: NULL argument or nrhs <= 0");
+  if (((uintptr_t)x | (uintptr_t)b) & 15) return fail(HELM_ERR_INVALID_ARG, "helm_relres_noalloc: x, b must be 16-byte aligned");
+  int64_t need = 0;
+  for (auto& s : ctx->sys) need += (int64_t)cdiv(s.Nx, STENCIL_THREADS) * cdiv(s.Ny, STENCIL_ROWS) * nrhs * 2;
+  if (need > NOALLOC_SCRATCH_DOUBLES)
+    return fail(HELM_ERR_INVALID_ARG, "helm_relres_noalloc: the batch needs " + std::to_string(need) +
+                                          " scratch doubles, more than the fixed maximum of " +
+                                          std::to_string(NOALLOC_SCRATCH_DOUBLES) + "; use helm_relres");
+  double* scratch = nullptr;
+  HELM_TRY(noalloc_scratch(&scratch));
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t pbase = 0;
+  int col0 = 0;
+  for (auto& s : ctx->sys) {
+    dim3 grid(cdiv(s.Nx, STENCIL_THREADS), cdiv(s.Ny, STENCIL_ROWS), nrhs);
+    const double2* xs = (const double2*)x + s.off * nrhs;
+    const double2* bs = (const double2*)b + s.off * nrhs;
+    launch(k_relres_partials, grid, STENCIL_THREADS, 0, st, xs, bs, (const double*)(ctx->k2d + s.off),
+           (const double2*)(ctx->prof_d + s.prof_x), (const double2*)(ctx->prof_d + s.prof_y), s.Nx, s.Ny, s.n,
+           1.0 / (s.h * s.h), scratch + pbase);
+    int nparts = (int)(grid.x * grid.y);
+    launch(k_relres_finalize, nrhs, 256, 0, st, (const double*)(scratch + pbase), nparts, relres_dev + col0);
+    pbase += (int64_t)nparts * nrhs * 2;
+    col0 += nrhs;
+  }
+  HELM_CK_LAUNCH();
   return HELM_OK;
 }

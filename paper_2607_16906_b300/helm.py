@@ -69,6 +69,7 @@ _SIGS = {
     "helm_train_step": (ct.c_int, [_P, _P, _P, ct.c_double, ct.c_double, ct.c_double, ct.POINTER(ct.c_double),
                                    ct.POINTER(ct.c_double), _P]),
     "helm_loss_grad": (ct.c_int, [_P, _P, _P, ct.POINTER(ct.c_double), _P, _P]),
+    "helm_relres_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int, _P, _P]),
     "helm_profile_enable": (ct.c_int, [_P, ct.c_int]),
     "helm_profile_read": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
     "helm_launch_count": (ct.c_uint64, []),
@@ -190,6 +191,16 @@ def helm_relres(ctx: Context, x: torch.Tensor, b: torch.Tensor, nrhs=1, stream=N
     out = (ct.c_double * ncol)()
     _check(_lib.helm_relres(ctx.handle, _dev_ptr(x), _dev_ptr(b), nrhs, out, _stream(stream)))
     return np.array(out[:])
+
+
+def helm_relres_noalloc(ctx: Context, x: torch.Tensor, b: torch.Tensor, out: torch.Tensor, nrhs=1, stream=None):
+    """Per-column ||b - A x|| / ||b|| into the float64 CUDA tensor `out` (nsys * nrhs entries) without any
+    device allocation inside the call; the scratch is a fixed array in the library (see include/helm.h)."""
+    ncol = len(ctx.systems) * nrhs
+    if out.dtype != torch.float64 or out.numel() < ncol:
+        raise ValueError("out must be a float64 CUDA tensor with nsys * nrhs entries")
+    _check(_lib.helm_relres_noalloc(ctx.handle, _dev_ptr(x), _dev_ptr(b), nrhs, _dev_ptr(out), _stream(stream)))
+    return out
 
 
 def helm_unet_param_count() -> int:
