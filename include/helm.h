@@ -163,9 +163,11 @@ HELM_API helm_status helm_fgmres_solve(helm_ctx* ctx, const helm_unet* net, cons
  * before the update (may be NULL).  grad_norm_host: the pre-clip gradient norm (may be NULL). */
 HELM_API helm_status helm_train_step(helm_ctx* ctx, helm_unet* net, const void* b, double lr, double wd,
                             double clip, double* loss_host, double* grad_norm_host, void* stream);
-/* Loss and its gradient only (no update): grad_dev receives helm_unet_param_count() doubles. */
-HELM_API helm_status helm_loss_grad(helm_ctx* ctx, const helm_unet* net, const void* b, double* loss_host,
-                           double* grad_dev, void* stream);
+/* Loss and its gradient only (no update): grad_dev receives helm_unet_param_count() doubles in the
+ * weights_host layout.  dtype HELM_C64: b is C64 and the BF16 network path is differentiated (as in
+ * helm_train_step); HELM_C128: b is C128 and the FP64 network path is differentiated. */
+HELM_API helm_status helm_loss_grad(helm_ctx* ctx, const helm_unet* net, const void* b, helm_dtype dtype,
+                                    double* loss_host, double* grad_dev, void* stream);
 
 /* ---- allocation-free relative residual (the paper has no counterpart) ---------
  * For callers that must not allocate device memory during a call: e.g. a process whose device

@@ -127,6 +127,10 @@ helm_status apply_op(helm_ctx* ctx, const C<R>* x, C<R>* y, int nrhs, bool adjoi
 // r = b - A x (FP64) and per-column ||r||^2, ||b||^2 into sums[col*2 + {0,1}] (device)
 helm_status residual_fp64(helm_ctx* ctx, const double2* x, const double2* b, double2* r, int nrhs,
                           double* sums, cudaStream_t st);
+// the same in either precision (sums always FP64)
+template <typename R>
+helm_status residual_op(helm_ctx* ctx, const C<R>* x, const C<R>* b, C<R>* r, int nrhs, double* sums,
+                        cudaStream_t st);
 
 // reduce.cu: per-column sum of |v|^2 (FP64) into out[col] (device); deterministic
 template <typename R>

@@ -518,7 +518,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         for (int s = 0; s < ctx->nsys; ++s) {
           int64_t off = ctx->sys[s].off * nrhs;
           HELM_TRY(unet_precondition<R>(ctx, net, s, Vj + off, Zj + off, nrhs, W.in_scale + s * nrhs,
-                                        W.out_scale + s * nrhs, stream));
+                                        W.out_scale + s * nrhs, stream, 0));
         }
       } else {
         // z_j = v_j = vscale_j Vraw_j into the FP64 residual buffer, free after k_v0

@@ -69,39 +69,39 @@ __global__ void __launch_bounds__(STENCIL_THREADS) k_stencil(const C<R>* __restr
   }
 }
 
-// r = b - A x in FP64, plus per-block partial sums of |r|^2 and |b|^2 (deterministic order).
-__global__ void __launch_bounds__(STENCIL_THREADS) k_residual(const double2* __restrict__ x,
-                                                              const double2* __restrict__ b, double2* __restrict__ r,
-                                                              const double* __restrict__ k2,
-                                                              const double2* __restrict__ px,
-                                                              const double2* __restrict__ py, int Nx, int Ny,
-                                                              int64_t rhs_stride, double inv_h2, double* partial,
+// r = b - A x, plus per-block partial sums of |r|^2 and |b|^2 in FP64 (deterministic order).
+template <typename R>
+__global__ void __launch_bounds__(STENCIL_THREADS) k_residual(const C<R>* __restrict__ x, const C<R>* __restrict__ b,
+                                                              C<R>* __restrict__ r, const R* __restrict__ k2,
+                                                              const C<R>* __restrict__ px,
+                                                              const C<R>* __restrict__ py, int Nx, int Ny,
+                                                              int64_t rhs_stride, R inv_h2, double* partial,
                                                               int col0) {
   int i = blockIdx.x * STENCIL_THREADS + threadIdx.x;
   int j0 = blockIdx.y * STENCIL_ROWS;
-  const double2* xr = x + blockIdx.z * rhs_stride;
-  const double2* br = b + blockIdx.z * rhs_stride;
-  double2* rr = r + blockIdx.z * rhs_stride;
+  const C<R>* xr = x + blockIdx.z * rhs_stride;
+  const C<R>* br = b + blockIdx.z * rhs_stride;
+  C<R>* rr = r + blockIdx.z * rhs_stride;
   double sr = 0.0, sb = 0.0;
   if (i < Nx) {
-    const double2 sxi = px[i], ixm = px[Nx + i], ixp = px[Nx + i + 1];
-    double2 uS = ld_u<double, false>(xr, j0 - 1, i, Nx, Ny);
-    double2 uC = ld_u<double, false>(xr, j0, i, Nx, Ny);
+    const C<R> sxi = px[i], ixm = px[Nx + i], ixp = px[Nx + i + 1];
+    C<R> uS = ld_u<R, false>(xr, j0 - 1, i, Nx, Ny);
+    C<R> uC = ld_u<R, false>(xr, j0, i, Nx, Ny);
 #pragma unroll
     for (int q = 0; q < STENCIL_ROWS; ++q) {
       int j = j0 + q;
       if (j >= Ny) break;
-      double2 uN = ld_u<double, false>(xr, j + 1, i, Nx, Ny);
-      double2 uW = ld_u<double, false>(xr, j, i - 1, Nx, Ny);
-      double2 uE = ld_u<double, false>(xr, j, i + 1, Nx, Ny);
+      C<R> uN = ld_u<R, false>(xr, j + 1, i, Nx, Ny);
+      C<R> uW = ld_u<R, false>(xr, j, i - 1, Nx, Ny);
+      C<R> uE = ld_u<R, false>(xr, j, i + 1, Nx, Ny);
       int64_t idx = (int64_t)j * Nx + i;
-      double2 Au = stencil_point<double>(uC, uE, uW, uN, uS, sxi, ixm, ixp, py[j], py[Ny + j], py[Ny + j + 1],
-                                         k2[idx], inv_h2);
-      double2 bv = br[idx];
-      double2 res = csub(bv, Au);
+      C<R> Au = stencil_point<R>(uC, uE, uW, uN, uS, sxi, ixm, ixp, py[j], py[Ny + j], py[Ny + j + 1], k2[idx],
+                                 inv_h2);
+      C<R> bv = br[idx];
+      C<R> res = csub(bv, Au);
       rr[idx] = res;
-      sr += res.x * res.x + res.y * res.y;
-      sb += bv.x * bv.x + bv.y * bv.y;
+      sr += (double)res.x * res.x + (double)res.y * res.y;
+      sb += (double)bv.x * bv.x + (double)bv.y * bv.y;
       uS = uC;
       uC = uN;
     }
@@ -179,8 +179,9 @@ helm_status apply_op(helm_ctx* ctx, const C<R>* x, C<R>* y, int nrhs, bool adjoi
 template helm_status apply_op<float>(helm_ctx*, const float2*, float2*, int, bool, cudaStream_t);
 template helm_status apply_op<double>(helm_ctx*, const double2*, double2*, int, bool, cudaStream_t);
 
-helm_status residual_fp64(helm_ctx* ctx, const double2* x, const double2* b, double2* r, int nrhs, double* sums,
-                          cudaStream_t st) {
+template <typename R>
+helm_status residual_op(helm_ctx* ctx, const C<R>* x, const C<R>* b, C<R>* r, int nrhs, double* sums, cudaStream_t st) {
+  const bool fp64 = sizeof(R) == 8;
   HELM_TRY(ensure_cols(ctx, nrhs));
   int ncol = num_cols(ctx, nrhs);
   // per-column part counts
@@ -202,9 +203,10 @@ helm_status residual_fp64(helm_ctx* ctx, const double2* x, const double2* b, dou
   int64_t pbase = 0;
   for (auto& s : ctx->sys) {
     dim3 grid(cdiv(s.Nx, STENCIL_THREADS), cdiv(s.Ny, STENCIL_ROWS), nrhs);
-    launch(k_residual, grid, STENCIL_THREADS, 0, st, x + s.off * nrhs, b + s.off * nrhs, r + s.off * nrhs,
-                                                 ctx->k2d + s.off, ctx->prof_d + s.prof_x, ctx->prof_d + s.prof_y,
-                                                 s.Nx, s.Ny, s.n, 1.0 / (s.h * s.h), partial + pbase * 2, 0);
+    const R* k2 = fp64 ? (const R*)(ctx->k2d + s.off) : (const R*)(ctx->k2f + s.off);
+    const C<R>* pr = fp64 ? (const C<R>*)ctx->prof_d : (const C<R>*)ctx->prof_f;
+    launch(k_residual<R>, grid, STENCIL_THREADS, 0, st, x + s.off * nrhs, b + s.off * nrhs, r + s.off * nrhs, k2,
+           pr + s.prof_x, pr + s.prof_y, s.Nx, s.Ny, s.n, (R)(1.0 / (s.h * s.h)), partial + pbase * 2, 0);
     pbase += (int64_t)grid.x * grid.y * nrhs;
     col0 += nrhs;
   }
@@ -212,6 +214,15 @@ helm_status residual_fp64(helm_ctx* ctx, const double2* x, const double2* b, dou
   launch(k_finalize, ncol, 256, 0, st, partial, np_dev, 2, sums);
   HELM_CK_LAUNCH();
   return HELM_OK;
+}
+
+template helm_status residual_op<float>(helm_ctx*, const float2*, const float2*, float2*, int, double*, cudaStream_t);
+template helm_status residual_op<double>(helm_ctx*, const double2*, const double2*, double2*, int, double*,
+                                         cudaStream_t);
+
+helm_status residual_fp64(helm_ctx* ctx, const double2* x, const double2* b, double2* r, int nrhs, double* sums,
+                          cudaStream_t st) {
+  return residual_op<double>(ctx, x, b, r, nrhs, sums, st);
 }
 
 }  // namespace helm

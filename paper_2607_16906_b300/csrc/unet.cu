@@ -91,16 +91,6 @@ helm_status unet_prepare(helm_unet* net, cudaStream_t st) {
 
 // ------------------------------------------------------------------ element conversion
 
-template <typename T> struct Acc;
-template <> struct Acc<double> { using A = double; };
-template <> struct Acc<__nv_bfloat16> { using A = float; };
-
-__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
-__device__ __forceinline__ double to_acc(double v) { return v; }
-__device__ __forceinline__ void store_act(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
-__device__ __forceinline__ void store_act(double* p, double v) { *p = v; }
-
-template <typename T> const typename Acc<T>::A* cc_weights(const helm_unet* net);
 template <> const double* cc_weights<double>(const helm_unet* net) { return net->w64; }
 template <> const float* cc_weights<__nv_bfloat16>(const helm_unet* net) { return net->w32; }
 
@@ -212,7 +202,7 @@ __global__ void k_pool(const T* __restrict__ in, T* __restrict__ out, int C, int
 // Channel stride S0 (extra channels zero).
 template <typename T, typename R>
 __global__ void k_pack_input(const C<R>* __restrict__ v, int64_t col_stride, const double* __restrict__ in_scale,
-                             const typename Acc<T>::A* __restrict__ chat, int Nx, int Ny, int Hp, int Wp, int B, int S0,
+                             const typename Acc<T>::A* __restrict__ chat, int64_t c_stride, int Nx, int Ny, int Hp, int Wp, int B, int S0,
                              T* __restrict__ x0) {
   int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (pix >= (int64_t)B * Hp * Wp) return;
@@ -226,7 +216,7 @@ __global__ void k_pack_input(const C<R>* __restrict__ v, int64_t col_stride, con
     double s = in_scale[b];
     re = (typename Acc<T>::A)(val.x * s);
     im = (typename Acc<T>::A)(val.y * s);
-    cc = (typename Acc<T>::A)chat[q];
+    cc = (typename Acc<T>::A)chat[b * c_stride + q];
   }
   T* o = x0 + pix * S0;
   store_act(o + 0, re);
@@ -390,7 +380,7 @@ helm_status unet_body(const helm_unet* net, UnetBuffers::Set& S, int B, cudaStre
 
 template <typename R>
 helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
-                              const double* in_scale, const double* out_scale, cudaStream_t st) {
+                              const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride) {
   using T = typename std::conditional<sizeof(R) == 8, double, __nv_bfloat16>::type;
   const SysHost& s = ctx->sys[sys];
   int Hp = (s.Ny + 7) / 8 * 8, Wp = (s.Nx + 7) / 8 * 8;
@@ -404,7 +394,8 @@ helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, cons
     chat = ctx->chat64 + s.off;
   else
     chat = ctx->chat + s.off;
-  launch(k_pack_input<T, R>, cdiv(npix, 256), 256, 0, st, v, s.n, in_scale, chat, s.Nx, s.Ny, Hp, Wp, B, X0_CH,
+  launch(k_pack_input<T, R>, cdiv(npix, 256), 256, 0, st, v, s.n, in_scale, chat, c_stride, s.Nx, s.Ny, Hp, Wp, B,
+         X0_CH,
                                                       a[A_X0]);
   HELM_CK_LAUNCH();
   HELM_TRY(unet_body<T>(net, S, B, st));
@@ -417,9 +408,9 @@ helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, cons
 }
 
 template helm_status unet_precondition<float>(helm_ctx*, const helm_unet*, int, const float2*, float2*, int,
-                                              const double*, const double*, cudaStream_t);
+                                              const double*, const double*, cudaStream_t, int64_t);
 template helm_status unet_precondition<double>(helm_ctx*, const helm_unet*, int, const double2*, double2*, int,
-                                               const double*, const double*, cudaStream_t);
+                                               const double*, const double*, cudaStream_t, int64_t);
 
 // in_scale = alpha = sqrt(n) / ||v||, out_scale = h^2 / alpha (0 for a zero column).  The h^2 makes
 // the network approximate the inverse of the dimensionless operator h^2 A (O(1) entries, as in the
@@ -447,7 +438,7 @@ helm_status precond_entry(helm_ctx* ctx, const helm_unet* net, const C<R>* v, C<
   HELM_CK_LAUNCH();
   for (int s = 0; s < ctx->nsys; ++s) {
     int64_t o = ctx->sys[s].off * nrhs;
-    HELM_TRY(unet_precondition<R>(ctx, net, s, v + o, z + o, nrhs, in_s + s * nrhs, out_s + s * nrhs, st));
+    HELM_TRY(unet_precondition<R>(ctx, net, s, v + o, z + o, nrhs, in_s + s * nrhs, out_s + s * nrhs, st, 0));
   }
   return HELM_OK;
 }

@@ -52,9 +52,25 @@ template <typename T> bool conv_tc_enabled(const helm_unet* net, int layer, int 
 helm_status conv_tc_forward(const helm_unet* net, int layer, const void* in0, int C0, const void* in1, int C1,
                             void* out, int B, int H, int W, cudaStream_t st);
 
+// z = out_scale * N(in_scale * v, c) for B columns of system `sys` (column stride n_sys).  Velocity
+// channel: c of system `sys` for every column (c_stride = 0), or of consecutive equal-size systems
+// (c_stride = n_sys, one system per column, as in training batches).
 template <typename R>
 helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
-                              const double* in_scale, const double* out_scale, cudaStream_t st);
+                              const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride);
+
+// Element types of the two network paths: activations T, accumulation / weights A.
+template <typename T> struct Acc;
+template <> struct Acc<double> { using A = double; };
+template <> struct Acc<__nv_bfloat16> { using A = float; };
+__device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ double to_acc(double v) { return v; }
+__device__ __forceinline__ float to_acc(float v) { return v; }
+__device__ __forceinline__ void store_act(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+__device__ __forceinline__ void store_act(double* p, double v) { *p = v; }
+__device__ __forceinline__ void store_act(float* p, float v) { *p = v; }
+template <typename T> const typename Acc<T>::A* cc_weights(const helm_unet* net);
+helm_status unet_prepare(helm_unet* net, cudaStream_t st);
 
 }  // namespace helm
 

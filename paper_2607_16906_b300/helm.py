@@ -68,7 +68,7 @@ _SIGS = {
                                      ct.POINTER(helm_solve_info), _P]),
     "helm_train_step": (ct.c_int, [_P, _P, _P, ct.c_double, ct.c_double, ct.c_double, ct.POINTER(ct.c_double),
                                    ct.POINTER(ct.c_double), _P]),
-    "helm_loss_grad": (ct.c_int, [_P, _P, _P, ct.POINTER(ct.c_double), _P, _P]),
+    "helm_loss_grad": (ct.c_int, [_P, _P, _P, ct.c_int, ct.POINTER(ct.c_double), _P, _P]),
     "helm_relres_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int, _P, _P]),
     "helm_profile_enable": (ct.c_int, [_P, ct.c_int]),
     "helm_profile_read": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
@@ -296,12 +296,14 @@ def helm_train_step(ctx: Context, net: UNet, b: torch.Tensor, lr=1e-3, wd=0.01, 
 
 
 def helm_loss_grad(ctx: Context, net: UNet, b: torch.Tensor, stream=None):
-    """Loss (eq. 9, batch mean) and its FP64 gradient w.r.t. the flat parameter vector (CUDA tensor)."""
-    if b.dtype != torch.complex64 or b.numel() != ctx.npts:
-        raise ValueError("b must be a complex64 batch vector with one right-hand side per system")
+    """Loss (eq. 9, batch mean) and its FP64 gradient w.r.t. the flat parameter vector (CUDA tensor).
+    complex64 b differentiates the BF16 network path, complex128 b the FP64 path."""
+    if b.numel() != ctx.npts:
+        raise ValueError("b must be a batch vector with one right-hand side per system")
     g = torch.zeros(net.nparams, dtype=torch.float64, device="cuda")
     loss = ct.c_double()
-    _check(_lib.helm_loss_grad(ctx.handle, net.handle, _dev_ptr(b), ct.byref(loss), _dev_ptr(g), _stream(stream)))
+    _check(_lib.helm_loss_grad(ctx.handle, net.handle, _dev_ptr(b), _dtype_code(b), ct.byref(loss), _dev_ptr(g),
+                               _stream(stream)))
     return loss.value, g
 
 

@@ -1,0 +1,91 @@
+"""Train the U-Net preconditioner with helm_train_step (eqs. 8-9) on seeded synthetic batches.
+
+    python -m paper_2607_16906_b300.train_precond --steps 3000 --out weights.npy [--log log.json]
+
+Data (Sec. 3.2 describes mixed datasets; the paper's skull and CT data are not available here):
+velocities alternate between skull rings with noise and log-normal Gaussian random fields,
+128 x 128 interior + 16 PML cells at 10 points per water wavelength; each step draws fresh sources
+for a fixed batch of velocities, with the paper's D0-style mix of source types: N(0,1) fields
+(60 %), 1-5 random point sources (30 %) and a 32-element line array (10 %).  Optimiser: AdamW,
+learning rate cosine-decayed from lr_max to lr_min (Tab. 3: 1e-3 -> 1e-5), global-norm clip 1,
+seed 42 (Tab. 3).  Every numerical step runs in libhelm; this script only draws the data.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import helm, synth
+
+
+def make_batch_contexts(nctx, batch, nx, p, ppw, rng):
+    h, om = synth.grid_spacing(ppw), synth.angular_frequency()
+    ctxs = []
+    for _ in range(nctx):
+        cs = [synth.skull_velocity(nx, nx, p, rng) if k % 2 == 0 else synth.grf_velocity(nx, nx, p, rng)
+              for k in range(batch)]
+        specs = [helm.SystemSpec(nx, nx, h, p, om) for _ in range(batch)]
+        ctxs.append(helm.Context(specs, torch.tensor(np.concatenate([c.ravel() for c in cs]), device="cuda")))
+    return ctxs
+
+
+def draw_sources(batch, nx, p, rng):
+    out = []
+    for _ in range(batch):
+        u = rng.uniform()
+        if u < 0.6:
+            out.append(synth.gaussian_sources(nx, nx, p, rng))
+        elif u < 0.9:
+            out.append(synth.point_sources(nx, nx, p, rng, int(rng.integers(1, 6))))
+        else:
+            out.append(synth.line_array(nx, nx, p, rng))
+    return np.concatenate([b.ravel() for b in out]).astype(np.complex64)
+
+
+def train(steps=3000, batch=64, nx=128, p=16, ppw=10.0, lr_max=1e-3, lr_min=1e-5, wd=0.01, clip=1.0, seed=42,
+          nctx=8, init=None, log_every=50, verbose=True):
+    rng = synth.rng_for(seed)
+    theta = init if init is not None else synth.kaiming_uniform_params(helm.weight_segments(), seed)
+    net = helm.UNet(theta)
+    ctxs = make_batch_contexts(nctx, batch, nx, p, ppw, rng)
+    log = []
+    t0 = time.time()
+    for it in range(steps):
+        lr = lr_min + 0.5 * (lr_max - lr_min) * (1.0 + math.cos(math.pi * it / max(1, steps)))
+        b = torch.tensor(draw_sources(batch, nx, p, rng), device="cuda")
+        loss, gn = helm.helm_train_step(ctxs[it % nctx], net, b, lr=lr, wd=wd, clip=clip)
+        if it % log_every == 0 or it == steps - 1:
+            log.append({"step": it, "loss": loss, "grad_norm": gn, "lr": lr, "s": time.time() - t0})
+            if verbose:
+                print(f"step {it:5d} loss {loss:.4f} |g| {gn:.3g} lr {lr:.2e} {time.time() - t0:.1f}s", flush=True)
+    return net.weights(), log
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=64)
+    ap.add_argument("--nx", type=int, default=128)
+    ap.add_argument("--pml", type=int, default=16)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--out", required=True)
+    ap.add_argument("--log", default=None)
+    ap.add_argument("--init", default=None)
+    a = ap.parse_args()
+    init = np.load(a.init) if a.init else None
+    w, log = train(steps=a.steps, batch=a.batch, nx=a.nx, p=a.pml, lr_max=a.lr, init=init)
+    os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+    np.save(a.out, w)
+    if a.log:
+        with open(a.log, "w") as f:
+            json.dump(log, f)
+
+
+if __name__ == "__main__":
+    main()
