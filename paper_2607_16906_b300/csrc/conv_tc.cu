@@ -1,21 +1,539 @@
-// tcgen05 implicit-GEMM 3x3 convolutions (BF16 operands, FP32 accumulation in TMEM).
-// Not yet enabled: every layer takes the CUDA-core path in unet.cu.
+// tcgen05 implicit-GEMM 3x3 convolutions (BF16 operands, FP32 accumulation in TMEM), sm_103a.
+//
+// GEMM view of one conv layer: D[pixel][co] = bias + sum_{chunk, tap} A_tap[pixel][ci] W[tap][ci][co],
+// M = 128 output pixels (an 8 x 16 patch of one image), N = C_out (16..128), K = 9 taps x C_in.
+// For each (input-channel chunk, tap) one TMA load brings the 8 x 16 patch shifted by the tap
+// (out-of-image rows/columns arrive as zeros, which is the conv's zero padding) and one TMA load
+// brings the tap's N x chunk weight tile; both land in shared memory in the swizzled K-major layout
+// that tcgen05.mma reads directly.  A concat input (decoder levels) is two sources whose chunks are
+// consumed one after the other, so the concat is never materialised.
+//
+// Persistent kernel, one CTA per SM slot, 6 warps:
+//   warp 0  TMA producer (one elected lane), STAGES-deep smem ring (full/empty mbarriers);
+//   warp 1  TMEM allocator and MMA issuer (one lane issues tcgen05.mma, commits free the stage);
+//   warps 2-5  epilogue: tcgen05.ld of the 128 x N accumulator (warp w reads TMEM lanes
+//           32 (w % 4) .. +31), bias, ReLU, BF16 rounding, NHWC stores.
+// Two TMEM accumulators alternate so the epilogue of one tile overlaps the MMAs of the next.
+// Every mbarrier wait is bounded (about one second of clock64); on a timeout the kernel records an
+// error code, stops issuing work, waits (bounded) for its own copies in flight, frees TMEM and exits.
+#include <cuda.h>
+
+#include <atomic>
+#include <cstdlib>
+#include <mutex>
+
 #include "unet.cuh"
 
 namespace helm {
 
-struct TcState {};
+// ------------------------------------------------------------------ PTX wrappers
 
-helm_status conv_tc_prepare(helm_unet*, cudaStream_t) { return HELM_OK; }
-void conv_tc_release(helm_unet*) {}
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-template <typename T> bool conv_tc_enabled(const helm_unet*, int, int, int) { return false; }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+constexpr long long WAIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
+
+// Bounded wait for the phase of `parity`; false (and an error code) on timeout or abort.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code) {
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (*abort_flag) return false;
+    if (clock64() - t0 > WAIT_CYCLES) {
+      *abort_flag = 1;
+      atomicExch(err, code);
+      return false;
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
+                                            int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
+      "[%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// D[tmem] (+)= A[smem desc] * B[smem desc]^T, kind::f16 (BF16 x BF16 -> FP32)
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on `bar` once every previously issued tcgen05.mma of this thread has completed.
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// 32 TMEM lanes x 16 consecutive 32-bit columns -> 16 registers per thread (thread = lane).
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+// Shared-memory matrix descriptor for a K-major operand in the canonical swizzled layout: rows of
+// `row_bytes` (= the swizzle width: 32, 64 or 128 B), 8-row groups `8 * row_bytes` apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int row_bytes) {
+  uint64_t layout = row_bytes == 128 ? 2ull : (row_bytes == 64 ? 4ull : 6ull);
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);              // start address
+  d |= (uint64_t)1 << 16;                              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(((8 * row_bytes) >> 4) & 0x3FFF) << 32;  // stride byte offset between 8-row groups
+  d |= (uint64_t)1 << 46;                              // descriptor version
+  d |= layout << 61;                                   // swizzle mode
+  return d;
+}
+
+// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major, M = 128, N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// ------------------------------------------------------------------ kernel
+
+struct ConvTcArgs {
+  int B, H, W;            // output grid (= input grid)
+  int nk0, nk1;           // input-channel chunks from source 0 / source 1
+  int tiles_x, tiles_y;   // 16-wide, 8-high pixel tiles
+  int ntiles;
+  const float* bias;      // [N]
+  __nv_bfloat16* out;     // NHWC [B][H][W][N]
+  int relu;
+  int* err;               // device error code (0 = ok)
+};
+
+template <int N, int CHUNK>
+struct TcCfg {
+  static constexpr int A_BYTES = 128 * CHUNK * 2;
+  static constexpr int B_BYTES = N * CHUNK * 2;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int STAGES = (96 * 1024 / STAGE_BYTES) > 8 ? 8 : (96 * 1024 / STAGE_BYTES);
+  static constexpr int TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
+  static constexpr int THREADS = 192;
+};
+
+template <int N, int CHUNK>
+__global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tA0,
+                                                    const __grid_constant__ CUtensorMap tA1,
+                                                    const __grid_constant__ CUtensorMap tW, ConvTcArgs a) {
+  using Cfg = TcCfg<N, CHUNK>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  uint64_t* full = (uint64_t*)(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
+  uint64_t* empty = full + Cfg::STAGES;
+  uint64_t* tfull = empty + Cfg::STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nk = a.nk0 + a.nk1;
+  const int ksteps = 9 * nk;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < Cfg::STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      mbar_init(&tfull[k], 1);
+      mbar_init(&tempty[k], 128);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, Cfg::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer
+      int stage = 0;
+      uint32_t phase = 0;
+      int issued_unconsumed = 0;
+      bool ok = true;
+      for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        int b = t / (a.tiles_x * a.tiles_y);
+        int r = t % (a.tiles_x * a.tiles_y);
+        int y0 = (r / a.tiles_x) * 8, x0 = (r % a.tiles_x) * 16;
+        for (int kc = 0; kc < nk && ok; ++kc) {
+          const CUtensorMap* src = kc < a.nk0 ? &tA0 : &tA1;
+          int c0 = (kc < a.nk0 ? kc : kc - a.nk0) * CHUNK;
+          for (int tap = 0; tap < 9; ++tap) {
+            if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, 1)) {
+              ok = false;
+              break;
+            }
+            unsigned char* sa = smem + stage * Cfg::STAGE_BYTES;
+            unsigned char* sb = sa + Cfg::A_BYTES;
+            mbar_expect_tx(&full[stage], Cfg::STAGE_BYTES);
+            tma_load_4d(sa, src, &full[stage], c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b);
+            tma_load_3d(sb, &tW, &full[stage], 0, 0, tap * nk + kc);
+            if (++stage == Cfg::STAGES) {
+              stage = 0;
+              phase ^= 1;
+            }
+          }
+        }
+      }
+      (void)issued_unconsumed;
+      if (!ok) {
+        // drain: wait (bounded) for every stage's last load to land before the CTA releases its smem
+        for (int s = 0; s < Cfg::STAGES; ++s) {
+          long long t0 = clock64();
+          while (!mbar_try_wait(&full[s], 0) && !mbar_try_wait(&full[s], 1) && clock64() - t0 < WAIT_CYCLES) {
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    constexpr uint32_t IDESC = idesc_bf16(128, N);
+    int stage = 0;
+    uint32_t phase = 0;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    bool ok = true;
+    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      if (!mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag, a.err, 2)) break;
+      tc_fence_after();
+      const uint32_t d_tmem = tmem_base + acc * N;
+      for (int ks = 0; ks < ksteps; ++ks) {
+        if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 3)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        if (lane == 0) {
+          uint32_t sa = smem_u32(smem + stage * Cfg::STAGE_BYTES);
+          uint32_t sb = sa + Cfg::A_BYTES;
+          uint64_t ad = smem_desc(sa, CHUNK * 2), bd = smem_desc(sb, CHUNK * 2);
+#pragma unroll
+          for (int k = 0; k < CHUNK / 16; ++k)
+            umma_bf16(d_tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), IDESC, (ks > 0 || k > 0) ? 1u : 0u);
+          umma_commit(&empty[stage]);
+        }
+        __syncwarp();
+        if (++stage == Cfg::STAGES) {
+          stage = 0;
+          phase ^= 1;
+        }
+      }
+      if (!ok) break;
+      if (lane == 0) umma_commit(&tfull[acc]);
+      __syncwarp();
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1;
+    }
+  } else {
+    // ---------------- epilogue (warps 2..5)
+    const int q = warp & 3;  // TMEM lane quarter this warp may access
+    const int p = q * 32 + lane;  // pixel within the tile
+    const int ly = p >> 4, lx = p & 15;
+    int acc = 0;
+    uint32_t acc_phase = 0;
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+      if (!mbar_wait(&tfull[acc], acc_phase, abort_flag, a.err, 4)) break;
+      tc_fence_after();
+      int b = t / (a.tiles_x * a.tiles_y);
+      int r = t % (a.tiles_x * a.tiles_y);
+      int y = (r / a.tiles_x) * 8 + ly, x = (r % a.tiles_x) * 16 + lx;
+      bool inside = y < a.H && x < a.W;
+      __nv_bfloat16* o = a.out + (((int64_t)b * a.H + y) * a.W + x) * N;
+#pragma unroll
+      for (int cb = 0; cb < N / 16; ++cb) {
+        uint32_t v[16];
+        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + acc * N + cb * 16, v);
+        tmem_ld_wait();
+        if (inside) {
+          __align__(16) __nv_bfloat16 hv[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            float f = __uint_as_float(v[k]) + a.bias[cb * 16 + k];
+            if (a.relu) f = fmaxf(f, 0.0f);
+            hv[k] = __float2bfloat16_rn(f);
+          }
+          uint4* dst = (uint4*)(o + cb * 16);
+          dst[0] = ((const uint4*)hv)[0];
+          dst[1] = ((const uint4*)hv)[1];
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&tempty[acc]);
+      acc ^= 1;
+      if (acc == 0) acc_phase ^= 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 1) tmem_dealloc(tmem_base, Cfg::TMEM_COLS);
+}
+
+// Weights for the tcgen05 path: [tap][chunk][N][CHUNK] BF16 (K-major per tap and chunk); input
+// channels beyond the layer's C_in (first layer: 3 used of 16) are zero.
+__global__ void k_prep_tc(const double* __restrict__ master, int64_t m_w, int cin, int cin_pad, int cout, int chunk,
+                          __nv_bfloat16* __restrict__ wtc) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t total = (int64_t)9 * cin_pad * cout;
+  if (q >= total) return;
+  int nk = cin_pad / chunk;
+  int c = (int)(q % chunk);
+  int n = (int)((q / chunk) % cout);
+  int kc = (int)((q / ((int64_t)chunk * cout)) % nk);
+  int tap = (int)(q / ((int64_t)chunk * cout * nk));
+  int ci = kc * chunk + c;
+  double w = ci < cin ? master[m_w + ((int64_t)(n * cin + ci) * 3 + tap / 3) * 3 + tap % 3] : 0.0;
+  wtc[q] = __float2bfloat16_rn((float)w);
+}
+
+// ------------------------------------------------------------------ host side
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+struct TcState {
+  __nv_bfloat16* w[NUM_LAYERS] = {};
+  int cin_pad[NUM_LAYERS] = {};
+  int chunk[NUM_LAYERS] = {};
+  int* err = nullptr;
+  bool ok = false;
+};
+
+static int tc_chunk(int cin_pad) { return cin_pad >= 64 ? 64 : cin_pad; }
+
+static bool tc_disabled_by_env() {
+  const char* e = getenv("HELM_DISABLE_TC");
+  return e && e[0] == '1';
+}
+
+helm_status conv_tc_prepare(helm_unet* net, cudaStream_t st) {
+  if (!net->tc) {
+    net->tc = new TcState();
+    TcState& S = *net->tc;
+    if (!encode_fn() || tc_disabled_by_env()) return HELM_OK;  // path unavailable: CUDA-core kernels serve
+    int dev = 0, major = 0, minor = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+    if (major != 10 || minor != 3) return HELM_OK;  // this binary holds sm_103a code only
+    HELM_CK(cudaMalloc(&S.err, sizeof(int)));
+    HELM_CK(cudaMemset(S.err, 0, sizeof(int)));
+    for (int l = 0; l < NUM_LAYERS; ++l) {
+      const LayerDesc& d = kLayers[l];
+      if (d.kind != CONV3) continue;
+      int cin_pad = l == L_ENC1A ? X0_CH : d.cin;
+      S.cin_pad[l] = cin_pad;
+      S.chunk[l] = tc_chunk(l == L_DEC3A || l == L_DEC2A || l == L_DEC1A ? d.cin / 2 : cin_pad);
+      HELM_CK(cudaMalloc(&S.w[l], sizeof(__nv_bfloat16) * 9 * cin_pad * d.cout));
+    }
+    S.ok = true;
+  }
+  TcState& S = *net->tc;
+  if (!S.ok) return HELM_OK;
+  for (int l = 0; l < NUM_LAYERS; ++l) {
+    const LayerDesc& d = kLayers[l];
+    if (d.kind != CONV3) continue;
+    int64_t total = (int64_t)9 * S.cin_pad[l] * d.cout;
+    launch(k_prep_tc, cdiv(total, 256), 256, 0, st, (const double*)net->master, net->L.m_w[l], d.cin, S.cin_pad[l],
+           d.cout, S.chunk[l], S.w[l]);
+  }
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+void conv_tc_release(helm_unet* net) {
+  if (!net->tc) return;
+  for (auto* p : net->tc->w)
+    if (p) cudaFree(p);
+  if (net->tc->err) cudaFree(net->tc->err);
+  delete net->tc;
+  net->tc = nullptr;
+}
+
+template <typename T>
+bool conv_tc_enabled(const helm_unet* net, int layer, int H, int W) {
+  if (!std::is_same<T, __nv_bfloat16>::value) return false;
+  if (!net->tc || !net->tc->ok || kLayers[layer].kind != CONV3) return false;
+  return H >= 1 && W >= 1;
+}
 template bool conv_tc_enabled<double>(const helm_unet*, int, int, int);
 template bool conv_tc_enabled<__nv_bfloat16>(const helm_unet*, int, int, int);
 
-helm_status conv_tc_forward(const helm_unet*, int, const void*, int, const void*, int, void*, int, int, int,
-                            cudaStream_t) {
-  return fail(HELM_ERR_INVALID_ARG, "conv_tc_forward: not available");
+static CUtensorMapSwizzle swizzle_for(int chunk) {
+  return chunk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (chunk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+}
+
+static helm_status act_map(CUtensorMap* m, const void* ptr, int C, int B, int H, int W, int chunk) {
+  cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
+  cuuint32_t box[4] = {(cuuint32_t)chunk, 16, 8, 1};
+  cuuint32_t es[4] = {1, 1, 1, 1};
+  CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(chunk), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(HELM_ERR_CUDA, "cuTensorMapEncodeTiled (activations) failed: " + std::to_string((int)r));
+  return HELM_OK;
+}
+
+static helm_status weight_map(CUtensorMap* m, const void* ptr, int N, int chunk, int nk) {
+  cuuint64_t dims[3] = {(cuuint64_t)chunk, (cuuint64_t)N, (cuuint64_t)(9 * nk)};
+  cuuint64_t strides[2] = {(cuuint64_t)chunk * 2, (cuuint64_t)N * chunk * 2};
+  cuuint32_t box[3] = {(cuuint32_t)chunk, (cuuint32_t)N, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(chunk), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(HELM_ERR_CUDA, "cuTensorMapEncodeTiled (weights) failed: " + std::to_string((int)r));
+  return HELM_OK;
+}
+
+template <int N, int CHUNK>
+static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& w, const ConvTcArgs& args,
+                             cudaStream_t st) {
+  using Cfg = TcCfg<N, CHUNK>;
+  static std::once_flag once;
+  static cudaError_t attr_err = cudaSuccess;
+  static int per_sm = 1, nsm = 148;
+  std::call_once(once, [] {
+    attr_err = cudaFuncSetAttribute(k_conv_tc<N, CHUNK>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    if (attr_err == cudaSuccess)
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<N, CHUNK>, Cfg::THREADS, Cfg::SMEM);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // each resident CTA holds TMEM_COLS columns of the SM's 512
+    per_sm = std::max(1, std::min(per_sm, 512 / Cfg::TMEM_COLS));
+  });
+  HELM_CK(attr_err);
+  int grid = std::min(args.ntiles, nsm * per_sm);
+  launch(k_conv_tc<N, CHUNK>, grid, Cfg::THREADS, Cfg::SMEM, st, a0, a1, w, args);
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+helm_status conv_tc_forward(const helm_unet* net, int l, const void* in0, int C0, const void* in1, int C1, void* out,
+                            int B, int H, int W, cudaStream_t st) {
+  const TcState& S = *net->tc;
+  const LayerDesc& d = kLayers[l];
+  if (l == L_ENC1A) C0 = X0_CH;
+  const int chunk = S.chunk[l];
+  if (C0 % chunk || C1 % chunk) return fail(HELM_ERR_INVALID_ARG, "conv_tc_forward: channel count not a chunk multiple");
+  CUtensorMap m0, m1, mw;
+  HELM_TRY(act_map(&m0, in0, C0, B, H, W, chunk));
+  if (C1 > 0)
+    HELM_TRY(act_map(&m1, in1, C1, B, H, W, chunk));
+  else
+    m1 = m0;
+  const int nk = (C0 + C1) / chunk;
+  HELM_TRY(weight_map(&mw, S.w[l], d.cout, chunk, nk));
+  ConvTcArgs a;
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.nk0 = C0 / chunk;
+  a.nk1 = C1 / chunk;
+  a.tiles_x = (W + 15) / 16;
+  a.tiles_y = (H + 7) / 8;
+  a.ntiles = B * a.tiles_x * a.tiles_y;
+  a.bias = net->w32 + net->L.c_b[l];
+  a.out = (__nv_bfloat16*)out;
+  a.relu = 1;
+  a.err = S.err;
+  switch (d.cout * 1000 + chunk) {
+    case 16016: return launch_tc<16, 16>(m0, m1, mw, a, st);
+    case 32016: return launch_tc<32, 16>(m0, m1, mw, a, st);
+    case 32032: return launch_tc<32, 32>(m0, m1, mw, a, st);
+    case 64032: return launch_tc<64, 32>(m0, m1, mw, a, st);
+    case 64064: return launch_tc<64, 64>(m0, m1, mw, a, st);
+    case 128064: return launch_tc<128, 64>(m0, m1, mw, a, st);
+    default: return fail(HELM_ERR_INVALID_ARG, "conv_tc_forward: no kernel for this layer shape");
+  }
+}
+
+// Error code left by a timed-out tcgen05 kernel (0 if none); clears it.
+helm_status conv_tc_check(const helm_unet* net, cudaStream_t st) {
+  if (!net->tc || !net->tc->err) return HELM_OK;
+  int e = 0;
+  HELM_CK(cudaMemcpyAsync(&e, net->tc->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HELM_CK(cudaStreamSynchronize(st));
+  if (e) {
+    cudaMemsetAsync(net->tc->err, 0, sizeof(int), st);
+    return fail(HELM_TIMEOUT, "tcgen05 conv kernel: a pipeline wait ran out of its budget (code " + std::to_string(e) + ")");
+  }
+  return HELM_OK;
 }
 
 }  // namespace helm

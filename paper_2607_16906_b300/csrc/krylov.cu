@@ -565,6 +565,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
     prof_end(ctx, PH_UPDATE, stream);
     HELM_CK(cudaStreamSynchronize(stream));
     prof_collect(ctx);
+    if (net) HELM_TRY(conv_tc_check(net, stream));
     for (int c = 0; c < ncol; ++c) {
       if (done[c]) continue;
       inf[c].iters += h_st[c].k;
