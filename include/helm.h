@@ -153,6 +153,11 @@ HELM_API helm_status helm_precond_apply(helm_ctx* ctx, const helm_unet* net, con
 HELM_API helm_status helm_fgmres_solve(helm_ctx* ctx, const helm_unet* net, const void* b, void* x, int nrhs,
                               const helm_solve_opts* opts, helm_solve_info* info, void* stream);
 
+/* Residual-estimate history of the last helm_fgmres_solve on this context: for column 0, the Givens
+ * estimate |g_{j+1}| of every iteration scaled to ||b|| (relative to the true residual at the start
+ * of its cycle).  Copies up to max_entries values to est_host (may be NULL); returns the count. */
+HELM_API int helm_solve_history(const helm_ctx* ctx, double* est_host, int max_entries);
+
 /* ---- training (a9) ------------------------------------------------------ */
 
 /* One optimisation step of the physics-informed loss (eqs. 8-9) over a batch of one source per

@@ -106,6 +106,8 @@ struct helm_ctx {
   int* flag_dev = nullptr;         // device error/status flag
   void* pinned = nullptr;          // small pinned host buffer for status reads
   size_t pinned_bytes = 0;
+  // residual-estimate history of column 0 of the last solve (relative to ||b||), one entry per iteration
+  std::vector<double> history;
   // phase timers
   int prof_on = 0;
   cudaEvent_t prof_ev[8][2] = {};

@@ -451,10 +451,12 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
   const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((4 * 148 + ncol - 1) / ncol, (maxlen + 1023) / 1024));
   SolverWs<R> W;
   HELM_TRY(solver_ws<R>(ctx, m, ncol, nch, net != nullptr, nvec, W));
-  HELM_TRY(ensure_pinned(ctx, sizeof(double) * 2 * ncol + sizeof(ColState) * ncol + 64));
+  HELM_TRY(ensure_pinned(ctx, sizeof(double) * 2 * ncol + sizeof(ColState) * ncol + 64 + 64));
   double* h_sums = (double*)ctx->pinned;
   ColState* h_st = (ColState*)(h_sums + 2 * ncol);
   int* h_nact = (int*)(h_st + ncol);
+  double* h_est0 = (double*)(h_nact + 2);
+  ctx->history.clear();
   const bool mixed = sizeof(R) == 4;
   const int max_cycles = mixed ? std::max(1, o.max_outer) : std::max(1, o.max_restarts);
   const double breakdown_eps = mixed ? 1e-6 : 1e-14;
@@ -551,9 +553,11 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
              W.cs, W.sn, W.g, W.st, W.nactive, W.in_scale, ctx->cols_dev, breakdown_eps);
       HELM_CK_LAUNCH();
       HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      HELM_CK(cudaMemcpyAsync(h_est0, &W.st[0].est, sizeof(double), cudaMemcpyDeviceToHost, stream));
       prof_end(ctx, PH_LSQ, stream);
       HELM_CK(cudaStreamSynchronize(stream));
       prof_collect(ctx);
+      if (!done[0]) ctx->history.push_back(*h_est0 * rel[0]);
       if (*h_nact == 0) break;
     }
     prof_begin(ctx, PH_UPDATE, stream);
@@ -594,6 +598,14 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
 }  // namespace helm
 
 using namespace helm;
+
+extern "C" int helm_solve_history(const helm_ctx* ctx, double* est_host, int max_entries) {
+  if (!ctx) return 0;
+  int n = (int)ctx->history.size();
+  if (est_host)
+    for (int i = 0; i < n && i < max_entries; ++i) est_host[i] = ctx->history[i];
+  return n;
+}
 
 extern "C" helm_status helm_fgmres_solve(helm_ctx* ctx, const helm_unet* net, const void* b, void* x, int nrhs,
                                          const helm_solve_opts* opts, helm_solve_info* info, void* stream) {

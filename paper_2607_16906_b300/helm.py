@@ -70,6 +70,7 @@ _SIGS = {
                                    ct.POINTER(ct.c_double), _P]),
     "helm_loss_grad": (ct.c_int, [_P, _P, _P, ct.c_int, ct.POINTER(ct.c_double), _P, _P]),
     "helm_relres_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int, _P, _P]),
+    "helm_solve_history": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.c_int]),
     "helm_profile_enable": (ct.c_int, [_P, ct.c_int]),
     "helm_profile_read": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
     "helm_launch_count": (ct.c_uint64, []),
@@ -282,6 +283,14 @@ def helm_fgmres_solve(ctx: Context, net, b: torch.Tensor, x: torch.Tensor, nrhs=
     cols = [dict(iters=i.iters, restarts=i.restarts, outer=i.outer, relres_true=i.relres_true,
                  relres_est=i.relres_est, status=STATUS_NAMES.get(i.status, i.status)) for i in info]
     return rc, cols
+
+
+def helm_solve_history(ctx: Context) -> np.ndarray:
+    """Per-iteration residual estimates (relative to ||b||) of column 0 of the last solve."""
+    n = _lib.helm_solve_history(ctx.handle, None, 0)
+    buf = (ct.c_double * max(n, 1))()
+    _lib.helm_solve_history(ctx.handle, buf, n)
+    return np.array(buf[:n])
 
 
 def helm_train_step(ctx: Context, net: UNet, b: torch.Tensor, lr=1e-3, wd=0.01, clip=1.0, stream=None):
