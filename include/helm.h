@@ -86,7 +86,7 @@ typedef struct {
   int orth;         /* helm_orth */
 } helm_solve_opts;
 
-#define HELM_MAX_M 1024
+#define HELM_MAX_M 4096
 
 typedef struct {
   int iters;           /* preconditioned Krylov iterations spent on this column */
@@ -138,8 +138,10 @@ HELM_API helm_status helm_unet_destroy(helm_unet* net);
 /* Copy the FP64 master weights back to the host (after training). */
 HELM_API helm_status helm_unet_get_weights(const helm_unet* net, double* weights_host, size_t nweights);
 
-/* z = N_theta(alpha v, c) / alpha per column, alpha = sqrt(n) / ||v|| (eq. 6).  dtype HELM_C64:
- * BF16 network with FP32 accumulation; HELM_C128: FP64 network.  v, z batch vectors. */
+/* z = h^2 N_theta(alpha v, c) / alpha per column, alpha = sqrt(n) / ||v|| (eq. 6): the network sees a
+ * unit-RMS input and approximates the inverse of the dimensionless operator h^2 A.  dtype HELM_C64:
+ * BF16 network with FP32 accumulation (3x3 and up-convs on tcgen05 tensor cores); HELM_C128: FP64
+ * network on CUDA cores.  v, z batch vectors; a zero column gives z = 0. */
 HELM_API helm_status helm_precond_apply(helm_ctx* ctx, const helm_unet* net, const void* v, void* z,
                                helm_dtype dtype, int nrhs, void* stream);
 

@@ -142,7 +142,7 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // ------------------------------------------------------------------ kernel
 
 struct ConvTcArgs {
-  int B, H, W;            // output grid (= input grid)
+  int B, H, W;            // GEMM pixel grid: the output grid (3x3 conv) or the input grid (2x2 up-conv)
   int nk0, nk1;           // input-channel chunks from source 0 / source 1
   int tiles_x, tiles_y;   // 16-wide, 8-high pixel tiles
   int ntiles;
@@ -163,7 +163,10 @@ struct TcCfg {
   static constexpr int THREADS = 192;
 };
 
-template <int N, int CHUNK>
+// MODE 0: 3x3 conv, pad 1 (9 shifted taps per channel chunk), N = C_out, ReLU.
+// MODE 1: 2x2 stride-2 transposed conv as one GEMM with N = 4 C_out (column n = tap C_out + co); the
+//         epilogue scatters column blocks to output pixel (2y + tap / 2, 2x + tap % 2); no activation.
+template <int N, int CHUNK, int MODE>
 __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tA0,
                                                     const __grid_constant__ CUtensorMap tA1,
                                                     const __grid_constant__ CUtensorMap tW, ConvTcArgs a) {
@@ -179,7 +182,8 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = a.nk0 + a.nk1;
-  const int ksteps = 9 * nk;
+  constexpr int TAPS = MODE == 0 ? 9 : 1;
+  const int ksteps = TAPS * nk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -217,7 +221,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
         for (int kc = 0; kc < nk && ok; ++kc) {
           const CUtensorMap* src = kc < a.nk0 ? &tA0 : &tA1;
           int c0 = (kc < a.nk0 ? kc : kc - a.nk0) * CHUNK;
-          for (int tap = 0; tap < 9; ++tap) {
+          for (int tap = 0; tap < TAPS; ++tap) {
             if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, 1)) {
               ok = false;
               break;
@@ -225,7 +229,10 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
             unsigned char* sa = smem + stage * Cfg::STAGE_BYTES;
             unsigned char* sb = sa + Cfg::A_BYTES;
             mbar_expect_tx(&full[stage], Cfg::STAGE_BYTES);
-            tma_load_4d(sa, src, &full[stage], c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b);
+            if (MODE == 0)
+              tma_load_4d(sa, src, &full[stage], c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b);
+            else
+              tma_load_4d(sa, src, &full[stage], c0, x0, y0, b);
             tma_load_3d(sb, &tW, &full[stage], 0, 0, tap * nk + kc);
             if (++stage == Cfg::STAGES) {
               stage = 0;
@@ -297,21 +304,25 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       int r = t % (a.tiles_x * a.tiles_y);
       int y = (r / a.tiles_x) * 8 + ly, x = (r % a.tiles_x) * 16 + lx;
       bool inside = y < a.H && x < a.W;
-      __nv_bfloat16* o = a.out + (((int64_t)b * a.H + y) * a.W + x) * N;
+      constexpr int COUT = MODE == 0 ? N : N / 4;
 #pragma unroll
       for (int cb = 0; cb < N / 16; ++cb) {
         uint32_t v[16];
         tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + acc * N + cb * 16, v);
         tmem_ld_wait();
         if (inside) {
+          const int tap = (cb * 16) / COUT, co0 = (cb * 16) % COUT;
+          int64_t opix = MODE == 0 ? (((int64_t)b * a.H + y) * a.W + x)
+                                   : (((int64_t)b * 2 * a.H + 2 * y + tap / 2) * (2 * a.W) + 2 * x + tap % 2);
+          __nv_bfloat16* o = a.out + opix * COUT + co0;
           __align__(16) __nv_bfloat16 hv[16];
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
-            float f = __uint_as_float(v[k]) + a.bias[cb * 16 + k];
-            if (a.relu) f = fmaxf(f, 0.0f);
+            float f = __uint_as_float(v[k]) + a.bias[co0 + k];
+            if (MODE == 0 && a.relu) f = fmaxf(f, 0.0f);
             hv[k] = __float2bfloat16_rn(f);
           }
-          uint4* dst = (uint4*)(o + cb * 16);
+          uint4* dst = (uint4*)o;
           dst[0] = ((const uint4*)hv)[0];
           dst[1] = ((const uint4*)hv)[1];
         }
@@ -343,6 +354,20 @@ __global__ void k_prep_tc(const double* __restrict__ master, int64_t m_w, int ci
   int ci = kc * chunk + c;
   double w = ci < cin ? master[m_w + ((int64_t)(n * cin + ci) * 3 + tap / 3) * 3 + tap % 3] : 0.0;
   wtc[q] = __float2bfloat16_rn((float)w);
+}
+
+// Up-conv weights for the tcgen05 path: [chunk][n = tap * cout + co][CHUNK] BF16 from the master
+// layout [cin][cout][2][2].
+__global__ void k_prep_tc_up(const double* __restrict__ master, int64_t m_w, int cin, int cout, int chunk,
+                             __nv_bfloat16* __restrict__ wtc) {
+  int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t total = (int64_t)cin * 4 * cout;
+  if (q >= total) return;
+  int c = (int)(q % chunk);
+  int n = (int)((q / chunk) % (4 * cout));
+  int kc = (int)(q / ((int64_t)chunk * 4 * cout));
+  int ci = kc * chunk + c, tap = n / cout, co = n % cout;
+  wtc[q] = __float2bfloat16_rn((float)master[m_w + ((int64_t)(ci * cout + co) * 2 + tap / 2) * 2 + tap % 2]);
 }
 
 // ------------------------------------------------------------------ host side
@@ -393,6 +418,12 @@ helm_status conv_tc_prepare(helm_unet* net, cudaStream_t st) {
     HELM_CK(cudaMemset(S.err, 0, sizeof(int)));
     for (int l = 0; l < NUM_LAYERS; ++l) {
       const LayerDesc& d = kLayers[l];
+      if (d.kind == UP2) {
+        S.cin_pad[l] = d.cin;
+        S.chunk[l] = tc_chunk(d.cin);
+        HELM_CK(cudaMalloc(&S.w[l], sizeof(__nv_bfloat16) * 4 * d.cin * d.cout));
+        continue;
+      }
       if (d.kind != CONV3) continue;
       int cin_pad = l == L_ENC1A ? X0_CH : d.cin;
       S.cin_pad[l] = cin_pad;
@@ -405,6 +436,12 @@ helm_status conv_tc_prepare(helm_unet* net, cudaStream_t st) {
   if (!S.ok) return HELM_OK;
   for (int l = 0; l < NUM_LAYERS; ++l) {
     const LayerDesc& d = kLayers[l];
+    if (d.kind == UP2) {
+      int64_t tot = (int64_t)4 * d.cin * d.cout;
+      launch(k_prep_tc_up, cdiv(tot, 256), 256, 0, st, (const double*)net->master, net->L.m_w[l], d.cin, d.cout,
+             S.chunk[l], S.w[l]);
+      continue;
+    }
     if (d.kind != CONV3) continue;
     int64_t total = (int64_t)9 * S.cin_pad[l] * d.cout;
     launch(k_prep_tc, cdiv(total, 256), 256, 0, st, (const double*)net->master, net->L.m_w[l], d.cin, S.cin_pad[l],
@@ -426,7 +463,7 @@ void conv_tc_release(helm_unet* net) {
 template <typename T>
 bool conv_tc_enabled(const helm_unet* net, int layer, int H, int W) {
   if (!std::is_same<T, __nv_bfloat16>::value) return false;
-  if (!net->tc || !net->tc->ok || kLayers[layer].kind != CONV3) return false;
+  if (!net->tc || !net->tc->ok || (kLayers[layer].kind != CONV3 && kLayers[layer].kind != UP2)) return false;
   return H >= 1 && W >= 1;
 }
 template bool conv_tc_enabled<double>(const helm_unet*, int, int, int);
@@ -448,8 +485,8 @@ static helm_status act_map(CUtensorMap* m, const void* ptr, int C, int B, int H,
   return HELM_OK;
 }
 
-static helm_status weight_map(CUtensorMap* m, const void* ptr, int N, int chunk, int nk) {
-  cuuint64_t dims[3] = {(cuuint64_t)chunk, (cuuint64_t)N, (cuuint64_t)(9 * nk)};
+static helm_status weight_map(CUtensorMap* m, const void* ptr, int N, int chunk, int nk, int taps = 9) {
+  cuuint64_t dims[3] = {(cuuint64_t)chunk, (cuuint64_t)N, (cuuint64_t)(taps * nk)};
   cuuint64_t strides[2] = {(cuuint64_t)chunk * 2, (cuuint64_t)N * chunk * 2};
   cuuint32_t box[3] = {(cuuint32_t)chunk, (cuuint32_t)N, 1};
   cuuint32_t es[3] = {1, 1, 1};
@@ -460,7 +497,7 @@ static helm_status weight_map(CUtensorMap* m, const void* ptr, int N, int chunk,
   return HELM_OK;
 }
 
-template <int N, int CHUNK>
+template <int N, int CHUNK, int MODE>
 static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& w, const ConvTcArgs& args,
                              cudaStream_t st) {
   using Cfg = TcCfg<N, CHUNK>;
@@ -468,9 +505,10 @@ static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const
   static cudaError_t attr_err = cudaSuccess;
   static int per_sm = 1, nsm = 148;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_conv_tc<N, CHUNK>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+    attr_err =
+        cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     if (attr_err == cudaSuccess)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<N, CHUNK>, Cfg::THREADS, Cfg::SMEM);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<N, CHUNK, MODE>, Cfg::THREADS, Cfg::SMEM);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -479,7 +517,7 @@ static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const
   });
   HELM_CK(attr_err);
   int grid = std::min(args.ntiles, nsm * per_sm);
-  launch(k_conv_tc<N, CHUNK>, grid, Cfg::THREADS, Cfg::SMEM, st, a0, a1, w, args);
+  launch(k_conv_tc<N, CHUNK, MODE>, grid, Cfg::THREADS, Cfg::SMEM, st, a0, a1, w, args);
   HELM_CK_LAUNCH();
   return HELM_OK;
 }
@@ -513,13 +551,43 @@ helm_status conv_tc_forward(const helm_unet* net, int l, const void* in0, int C0
   a.relu = 1;
   a.err = S.err;
   switch (d.cout * 1000 + chunk) {
-    case 16016: return launch_tc<16, 16>(m0, m1, mw, a, st);
-    case 32016: return launch_tc<32, 16>(m0, m1, mw, a, st);
-    case 32032: return launch_tc<32, 32>(m0, m1, mw, a, st);
-    case 64032: return launch_tc<64, 32>(m0, m1, mw, a, st);
-    case 64064: return launch_tc<64, 64>(m0, m1, mw, a, st);
-    case 128064: return launch_tc<128, 64>(m0, m1, mw, a, st);
+    case 16016: return launch_tc<16, 16, 0>(m0, m1, mw, a, st);
+    case 32016: return launch_tc<32, 16, 0>(m0, m1, mw, a, st);
+    case 32032: return launch_tc<32, 32, 0>(m0, m1, mw, a, st);
+    case 64032: return launch_tc<64, 32, 0>(m0, m1, mw, a, st);
+    case 64064: return launch_tc<64, 64, 0>(m0, m1, mw, a, st);
+    case 128064: return launch_tc<128, 64, 0>(m0, m1, mw, a, st);
     default: return fail(HELM_ERR_INVALID_ARG, "conv_tc_forward: no kernel for this layer shape");
+  }
+}
+
+// 2x2 stride-2 transposed conv on tensor cores: in [B][Hi][Wi][cin] -> out [B][2Hi][2Wi][cout].
+helm_status conv_tc_up(const helm_unet* net, int l, const void* in, void* out, int B, int Hi, int Wi, cudaStream_t st) {
+  const TcState& S = *net->tc;
+  const LayerDesc& d = kLayers[l];
+  const int chunk = S.chunk[l];
+  const int nk = d.cin / chunk;
+  CUtensorMap m0, mw;
+  HELM_TRY(act_map(&m0, in, d.cin, B, Hi, Wi, chunk));
+  HELM_TRY(weight_map(&mw, S.w[l], 4 * d.cout, chunk, nk, 1));
+  ConvTcArgs a;
+  a.B = B;
+  a.H = Hi;
+  a.W = Wi;
+  a.nk0 = nk;
+  a.nk1 = 0;
+  a.tiles_x = (Wi + 15) / 16;
+  a.tiles_y = (Hi + 7) / 8;
+  a.ntiles = B * a.tiles_x * a.tiles_y;
+  a.bias = net->w32 + net->L.c_b[l];
+  a.out = (__nv_bfloat16*)out;
+  a.relu = 0;
+  a.err = S.err;
+  switch (4 * d.cout * 1000 + chunk) {
+    case 256064: return launch_tc<256, 64, 1>(m0, m0, mw, a, st);
+    case 128064: return launch_tc<128, 64, 1>(m0, m0, mw, a, st);
+    case 64032: return launch_tc<64, 32, 1>(m0, m0, mw, a, st);
+    default: return fail(HELM_ERR_INVALID_ARG, "conv_tc_up: no kernel for this layer shape");
   }
 }
 

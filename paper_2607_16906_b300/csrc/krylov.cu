@@ -150,8 +150,21 @@ __global__ void __launch_bounds__(RED_THREADS) k_maxpy(const C<R>* __restrict__ 
   double s[1] = {0.0};
   for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
     int64_t q = cd.off + p;
-    C<R> acc = w[q];
-    for (int i = 0; i < nv; ++i) acc = csub(acc, cmul(V[(int64_t)i * vstride + q], cf[i]));
+    // eight independent loads in flight per step, two accumulation chains
+    C<R> acc = w[q], acc2 = mk<R>(0, 0);
+    int i = 0;
+    for (; i + 8 <= nv; i += 8) {
+      C<R> v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = V[(int64_t)(i + u) * vstride + q];
+#pragma unroll
+      for (int u = 0; u < 8; u += 2) {
+        acc = csub(acc, cmul(v[u], cf[i + u]));
+        acc2 = csub(acc2, cmul(v[u + 1], cf[i + u + 1]));
+      }
+    }
+    for (; i < nv; ++i) acc = csub(acc, cmul(V[(int64_t)i * vstride + q], cf[i]));
+    acc = cadd(acc, acc2);
     if (dst) {
       dst[q] = acc;
       s[0] += (double)acc.x * acc.x + (double)acc.y * acc.y;
@@ -277,22 +290,29 @@ __global__ void __launch_bounds__(RED_THREADS) k_xupdate(const C<R>* __restrict_
   int col = blockIdx.y, chunk = blockIdx.x;
   int k = st[col].k;
   if (k == 0) return;
-  __shared__ double2 yc[HELM_MAX_M];
-  for (int i = threadIdx.x; i < k; i += RED_THREADS)
-    yc[i] = zscale ? cscale(y[(int64_t)col * m + i], zscale[(int64_t)col * (m + 1) + i]) : y[(int64_t)col * m + i];
-  __syncthreads();
+  constexpr int YC = 1024;  // coefficients staged in shared memory per pass
+  __shared__ double2 yc[YC];
   ColDesc cd = cols[col];
   int64_t a, b;
   chunk_range(cd.len, nch, chunk, a, b);
-  for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
-    int64_t q = cd.off + p;
-    double2 acc = x[q];
-    for (int i = 0; i < k; ++i) {
-      C<R> z = Z[(int64_t)i * zstride + q];
-      acc.x += (double)z.x * yc[i].x - (double)z.y * yc[i].y;
-      acc.y += (double)z.x * yc[i].y + (double)z.y * yc[i].x;
+  for (int i0 = 0; i0 < k; i0 += YC) {
+    int kk = min(YC, k - i0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < kk; i += RED_THREADS) {
+      double2 yv = y[(int64_t)col * m + i0 + i];
+      yc[i] = zscale ? cscale(yv, zscale[(int64_t)col * (m + 1) + i0 + i]) : yv;
     }
-    x[q] = acc;
+    __syncthreads();
+    for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
+      int64_t q = cd.off + p;
+      double2 acc = x[q];
+      for (int i = 0; i < kk; ++i) {
+        C<R> z = Z[(int64_t)(i0 + i) * zstride + q];
+        acc.x += (double)z.x * yc[i].x - (double)z.y * yc[i].y;
+        acc.y += (double)z.x * yc[i].y + (double)z.y * yc[i].x;
+      }
+      x[q] = acc;
+    }
   }
 }
 

@@ -324,7 +324,8 @@ template <typename T>
 static helm_status conv3(const helm_unet* net, int l, const T* in0, int C0, int S0, const T* in1, int C1, int S1,
                          T* out, int B, int H, int W, cudaStream_t st) {
   const LayerDesc& d = kLayers[l];
-  if (conv_tc_enabled<T>(net, l, H, W)) return conv_tc_forward(net, l, in0, C0, in1, C1, out, B, H, W, st);
+  if (conv_tc_enabled<T>(net, l, H, W) && d.kind == CONV3)
+    return conv_tc_forward(net, l, in0, C0, in1, C1, out, B, H, W, st);
   const auto* w = cc_weights<T>(net);
   dim3 grid(cdiv((int64_t)B * H * W, CC_THREADS), d.cout / CC_COT);
   launch(k_conv_cc<T, 3>, grid, CC_THREADS, 0, st, in0, C0, S0, in1, C1, S1, w + net->L.c_w[l], w + net->L.c_b[l], out,
@@ -336,6 +337,7 @@ static helm_status conv3(const helm_unet* net, int l, const T* in0, int C0, int 
 template <typename T>
 static helm_status up2(const helm_unet* net, int l, const T* in, T* out, int B, int Ho, int Wo, cudaStream_t st) {
   const LayerDesc& d = kLayers[l];
+  if (conv_tc_enabled<T>(net, l, Ho / 2, Wo / 2)) return conv_tc_up(net, l, in, out, B, Ho / 2, Wo / 2, st);
   const auto* w = cc_weights<T>(net);
   dim3 grid(cdiv((int64_t)B * Ho * Wo, CC_THREADS), d.cout / CC_COT);
   launch(k_up_cc<T>, grid, CC_THREADS, 0, st, in, d.cin, w + net->L.c_w[l], w + net->L.c_b[l], out, d.cout, B, Ho, Wo);

@@ -51,6 +51,8 @@ void conv_tc_release(helm_unet* net);
 template <typename T> bool conv_tc_enabled(const helm_unet* net, int layer, int H, int W);
 helm_status conv_tc_forward(const helm_unet* net, int layer, const void* in0, int C0, const void* in1, int C1,
                             void* out, int B, int H, int W, cudaStream_t st);
+helm_status conv_tc_up(const helm_unet* net, int layer, const void* in, void* out, int B, int Hi, int Wi,
+                       cudaStream_t st);
 // HELM_TIMEOUT if a tcgen05 conv kernel recorded a pipeline timeout since the last check (synchronises).
 helm_status conv_tc_check(const helm_unet* net, cudaStream_t st);
 

@@ -27,7 +27,7 @@ HELM_NOT_CONVERGED, HELM_BREAKDOWN, HELM_NAN, HELM_TIMEOUT = 4, 5, 6, 7
 STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGED", 5: "BREAKDOWN", 6: "NAN",
                 7: "TIMEOUT"}
 HELM_C64, HELM_C128 = 0, 1
-HELM_MAX_M = 1024
+HELM_MAX_M = 4096
 
 
 class helm_grid(ct.Structure):

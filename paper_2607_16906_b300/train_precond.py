@@ -25,6 +25,7 @@ from . import helm, synth
 
 
 def make_batch_contexts(nctx, batch, nx, p, ppw, rng):
+    """`nctx` contexts of `batch` velocities each (alternately skull ring and log-normal GRF)."""
     h, om = synth.grid_spacing(ppw), synth.angular_frequency()
     ctxs = []
     for _ in range(nctx):
@@ -35,31 +36,37 @@ def make_batch_contexts(nctx, batch, nx, p, ppw, rng):
     return ctxs
 
 
-def draw_sources(batch, nx, p, rng):
+def draw_sources(batch, nx, p, rng, p_gauss=0.6, p_point=0.3):
+    """Sources: N(0,1) fields with probability p_gauss, 1-5 point sources with p_point, else a line array."""
     out = []
     for _ in range(batch):
         u = rng.uniform()
-        if u < 0.6:
+        if u < p_gauss:
             out.append(synth.gaussian_sources(nx, nx, p, rng))
-        elif u < 0.9:
+        elif u < p_gauss + p_point:
             out.append(synth.point_sources(nx, nx, p, rng, int(rng.integers(1, 6))))
         else:
             out.append(synth.line_array(nx, nx, p, rng))
     return np.concatenate([b.ravel() for b in out]).astype(np.complex64)
 
 
-def train(steps=3000, batch=64, nx=128, p=16, ppw=10.0, lr_max=1e-3, lr_min=1e-5, wd=0.01, clip=1.0, seed=42,
-          nctx=8, init=None, log_every=50, verbose=True):
+def train(steps=3000, grids=((128, 64),), p=16, ppw=10.0, lr_max=1e-3, lr_min=1e-5, wd=0.01, clip=1.0, seed=42,
+          nctx=8, init=None, log_every=50, verbose=True, p_gauss=0.6, p_point=0.3):
+    """AdamW on eq. 9 over batches cycling through `grids` = ((interior side, batch size), ...)."""
     rng = synth.rng_for(seed)
     theta = init if init is not None else synth.kaiming_uniform_params(helm.weight_segments(), seed)
     net = helm.UNet(theta)
-    ctxs = make_batch_contexts(nctx, batch, nx, p, ppw, rng)
+    pool = []  # (context, nx, batch)
+    for nx, batch in grids:
+        pool += [(c, nx, batch) for c in make_batch_contexts(nctx, batch, nx, p, ppw, rng)]
+    order = [k for k in range(len(pool))]
     log = []
     t0 = time.time()
     for it in range(steps):
         lr = lr_min + 0.5 * (lr_max - lr_min) * (1.0 + math.cos(math.pi * it / max(1, steps)))
-        b = torch.tensor(draw_sources(batch, nx, p, rng), device="cuda")
-        loss, gn = helm.helm_train_step(ctxs[it % nctx], net, b, lr=lr, wd=wd, clip=clip)
+        ctx, nx, batch = pool[order[it % len(pool)]]
+        b = torch.tensor(draw_sources(batch, nx, p, rng, p_gauss, p_point), device="cuda")
+        loss, gn = helm.helm_train_step(ctx, net, b, lr=lr, wd=wd, clip=clip)
         if it % log_every == 0 or it == steps - 1:
             log.append({"step": it, "loss": loss, "grad_norm": gn, "lr": lr, "s": time.time() - t0})
             if verbose:
@@ -70,16 +77,20 @@ def train(steps=3000, batch=64, nx=128, p=16, ppw=10.0, lr_max=1e-3, lr_min=1e-5
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=3000)
-    ap.add_argument("--batch", type=int, default=64)
-    ap.add_argument("--nx", type=int, default=128)
+    ap.add_argument("--grids", default="128x64", help="comma list of <interior side>x<batch>")
     ap.add_argument("--pml", type=int, default=16)
+    ap.add_argument("--nctx", type=int, default=8)
+    ap.add_argument("--p-gauss", type=float, default=0.6)
+    ap.add_argument("--p-point", type=float, default=0.3)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", required=True)
     ap.add_argument("--log", default=None)
     ap.add_argument("--init", default=None)
     a = ap.parse_args()
     init = np.load(a.init) if a.init else None
-    w, log = train(steps=a.steps, batch=a.batch, nx=a.nx, p=a.pml, lr_max=a.lr, init=init)
+    grids = tuple(tuple(int(v) for v in g.split("x")) for g in a.grids.split(","))
+    w, log = train(steps=a.steps, grids=grids, p=a.pml, lr_max=a.lr, init=init, nctx=a.nctx, p_gauss=a.p_gauss,
+                   p_point=a.p_point)
     os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
     np.save(a.out, w)
     if a.log:
