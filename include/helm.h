@@ -74,7 +74,11 @@ typedef struct {
   double sigma_max;  /* damping at the outermost node; <= 0 selects 2 omega (Tab. 1: 2 at omega = 1) */
 } helm_pml;
 
-typedef enum { HELM_ORTH_CGS2 = 0 } helm_orth;
+/* CGS2: classical Gram-Schmidt, two passes per iteration (4 sweeps over the basis).
+ * DCGS2: the same two passes with the second one delayed into the next iteration, where it shares
+ * the sweep of the first pass (2 sweeps over the basis); the preconditioner then sees each basis
+ * vector after its first pass (admissible in flexible GMRES, eq. 4). */
+typedef enum { HELM_ORTH_CGS2 = 0, HELM_ORTH_DCGS2 = 1 } helm_orth;
 
 typedef struct {
   int m;            /* Krylov dimension per cycle (Alg. 1), 1..HELM_MAX_M */
@@ -204,6 +208,11 @@ HELM_API helm_status helm_relres_noalloc(helm_ctx* ctx, const void* x, const voi
 HELM_API helm_status helm_profile_enable(helm_ctx* ctx, int on);
 /* ms_host[HELM_NUM_PHASES]: accumulated milliseconds; counts_host (may be NULL): intervals timed. */
 HELM_API helm_status helm_profile_read(const helm_ctx* ctx, double* ms_host, int64_t* counts_host);
+/* work_host[HELM_NUM_PHASES]: algorithmic work issued in each phase since helm_profile_enable:
+ * flops for phase 0 (70,816 per pixel and network application), bytes for the others (stencil
+ * 16 B/pt + 4 B/pt of k^2; orthogonalisation 32 nv + 48 B/pt (CGS2) or 16 nv + 48 B/pt (DCGS2) per
+ * iteration with nv basis vectors, counted for the columns active in that iteration). */
+HELM_API helm_status helm_profile_work(const helm_ctx* ctx, double* work_host);
 /* Kernels launched by this library in this process so far (all contexts). */
 HELM_API uint64_t helm_launch_count(void);
 

@@ -149,7 +149,14 @@ extern "C" helm_status helm_profile_enable(helm_ctx* ctx, int on) {
     ctx->prof_ms[p] = 0;
     ctx->prof_cnt[p] = 0;
     ctx->prof_pending[p] = 0;
+    ctx->prof_work[p] = 0;
   }
+  return HELM_OK;
+}
+
+extern "C" helm_status helm_profile_work(const helm_ctx* ctx, double* work_host) {
+  if (!ctx || !work_host) return helm::fail(HELM_ERR_INVALID_ARG, "helm_profile_work: NULL argument");
+  for (int p = 0; p < helm::NUM_PHASES; ++p) work_host[p] = ctx->prof_work[p];
   return HELM_OK;
 }
 

@@ -114,6 +114,7 @@ struct helm_ctx {
   int prof_pending[8] = {};
   double prof_ms[8] = {};
   int64_t prof_cnt[8] = {};
+  double prof_work[8] = {};  // algorithmic flops (preconditioner) or bytes (other phases) issued
 };
 
 namespace helm {

@@ -22,7 +22,6 @@
 namespace helm {
 
 constexpr int RED_THREADS = 256;
-constexpr int DOT_G = 8;
 
 // ------------------------------------------------------------------ reductions
 
@@ -77,39 +76,49 @@ __global__ void __launch_bounds__(RED_THREADS) k_colnorm2(const C<R>* __restrict
   block_reduce_store<1>(s, partial + (int64_t)col * nch + chunk);
 }
 
-// Multi-dot: partial[(col * nch + chunk) * ldp + i] = sum over the chunk of conj(V_i) w, i < nv.
+// Multi-dot: partial[(col * ndc + chunk) * ldp + i] = sum over points [chunk P, chunk P + P) of
+// conj(V_i) w, i < nv.  The chunk of w sits in shared memory; warp k takes basis vectors
+// i = k, k + 8, ...: each lane reads every 32nd point (coalesced 256-byte loads, four in flight),
+// then one warp reduction in FP64 per vector and chunk.
+constexpr int MD_THREADS = 256;
 template <typename R>
-__global__ void __launch_bounds__(RED_THREADS) k_mdot(const C<R>* __restrict__ V, int64_t vstride, int nv,
-                                                      const C<R>* __restrict__ w, const ColDesc* __restrict__ cols,
-                                                      const ColState* __restrict__ st, int nch,
-                                                      double2* __restrict__ partial, int ldp) {
+__global__ void __launch_bounds__(MD_THREADS) k_mdot(const C<R>* __restrict__ V, int64_t vstride, int nv,
+                                                     const C<R>* __restrict__ w, const ColDesc* __restrict__ cols,
+                                                     const ColState* __restrict__ st, int P, int ndc,
+                                                     double2* __restrict__ partial, int ldp) {
   int col = blockIdx.y, chunk = blockIdx.x;
   if (!st[col].active) return;
   ColDesc cd = cols[col];
-  int64_t a, b;
-  chunk_range(cd.len, nch, chunk, a, b);
-  double2* outp = partial + ((int64_t)col * nch + chunk) * ldp;
-  for (int i0 = 0; i0 < nv; i0 += DOT_G) {
-    C<R> acc[DOT_G];
-#pragma unroll
-    for (int g = 0; g < DOT_G; ++g) acc[g] = mk<R>(0, 0);
-    int ng = min(DOT_G, nv - i0);
-    for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
-      C<R> wv = w[cd.off + p];
-#pragma unroll
-      for (int g = 0; g < DOT_G; ++g)
-        if (g < ng) acc[g] = cadd(acc[g], cdotc(V[(int64_t)(i0 + g) * vstride + cd.off + p], wv));
+  double2* outp = partial + ((int64_t)col * ndc + chunk) * ldp;
+  int64_t a = (int64_t)chunk * P;
+  if (a >= cd.len) {
+    for (int i = threadIdx.x; i < nv; i += MD_THREADS) outp[i] = make_double2(0, 0);
+    return;
+  }
+  const int np = (int)min((int64_t)P, cd.len - a);
+  extern __shared__ unsigned char md_smem[];
+  C<R>* ws = (C<R>*)md_smem;
+  for (int p = threadIdx.x; p < np; p += MD_THREADS) ws[p] = w[cd.off + a + p];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < nv; i += MD_THREADS / 32) {
+    const C<R>* vi = V + (int64_t)i * vstride + cd.off + a;
+    C<R> s0 = mk<R>(0, 0), s1 = mk<R>(0, 0);
+    int p = lane;
+    for (; p + 96 < np; p += 128) {
+      C<R> v0 = vi[p], v1 = vi[p + 32], v2 = vi[p + 64], v3 = vi[p + 96];
+      s0 = cadd(s0, cdotc(v0, ws[p]));
+      s1 = cadd(s1, cdotc(v1, ws[p + 32]));
+      s0 = cadd(s0, cdotc(v2, ws[p + 64]));
+      s1 = cadd(s1, cdotc(v3, ws[p + 96]));
     }
-    double v[2 * DOT_G];
-#pragma unroll
-    for (int g = 0; g < DOT_G; ++g) {
-      v[2 * g] = acc[g].x;
-      v[2 * g + 1] = acc[g].y;
+    for (; p < np; p += 32) s0 = cadd(s0, cdotc(vi[p], ws[p]));
+    double dx = (double)s0.x + (double)s1.x, dy = (double)s0.y + (double)s1.y;
+    for (int o = 16; o > 0; o >>= 1) {
+      dx += __shfl_down_sync(0xffffffffu, dx, o);
+      dy += __shfl_down_sync(0xffffffffu, dy, o);
     }
-    __shared__ double tmp[2 * DOT_G];
-    block_reduce_store<2 * DOT_G>(v, tmp);
-    if (threadIdx.x < ng) outp[i0 + threadIdx.x] = make_double2(tmp[2 * threadIdx.x], tmp[2 * threadIdx.x + 1]);
-    __syncthreads();
+    if (lane == 0) outp[i] = make_double2(dx, dy);
   }
 }
 
@@ -177,35 +186,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_maxpy(const C<R>* __restrict__ 
 
 // ------------------------------------------------------------------ per-column scalar kernels
 
-// One thread per column: finish ||w||, rotate the new Hessenberg column, update g.
-template <typename R>
-__global__ void k_givens(int j, int ncol, int m, const double* __restrict__ npartial, int nch,
-                         const double2* __restrict__ hbuf, int ldp, double* __restrict__ vscale,
-                         double2* __restrict__ Rm, double* __restrict__ cs, double2* __restrict__ sn,
-                         double2* __restrict__ g, ColState* __restrict__ st, int* __restrict__ nactive,
-                         double* __restrict__ in_scale, const ColDesc* __restrict__ cols, double breakdown_eps) {
-  int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= ncol) return;
-  ColState& S = st[col];
-  if (!S.active) {
-    in_scale[col] = 0.0;
-    return;
-  }
-  double nn = 0;
-  for (int c = 0; c < nch; ++c) nn += npartial[(int64_t)col * nch + c];
-  double hn = sqrt(nn);
-  const double2* h = hbuf + (int64_t)col * ldp;
-  double2* Rc = Rm + ((int64_t)col * m + j) * (m + 1);  // column j of R
+// Rotate Hessenberg column j (entries 0..j in Rc, subdiagonal hn real >= 0) by the previous
+// rotations, form the new one, update g and the column state (estimate, k, status, active).
+__device__ void givens_update(int j, int m, double2* __restrict__ Rc, double hn, double* __restrict__ csc,
+                              double2* __restrict__ snc, double2* __restrict__ gc, ColState& S,
+                              double breakdown_eps) {
   double hmax = S.hscale;
-  for (int i = 0; i <= j; ++i) {
-    Rc[i] = h[i];
-    hmax = fmax(hmax, hypot(h[i].x, h[i].y));
-  }
+  for (int i = 0; i <= j; ++i) hmax = fmax(hmax, hypot(Rc[i].x, Rc[i].y));
   hmax = fmax(hmax, hn);
   S.hscale = hmax;
-  double* csc = cs + (int64_t)col * m;
-  double2* snc = sn + (int64_t)col * m;
-  double2* gc = g + (int64_t)col * (m + 1);
   for (int i = 0; i < j; ++i) {
     double2 a = Rc[i], b = Rc[i + 1];
     double c = csc[i];
@@ -254,10 +243,255 @@ __global__ void k_givens(int j, int ncol, int m, const double* __restrict__ npar
     S.status = HELM_NOT_CONVERGED;
     S.active = 0;
   }
+}
+
+// One thread per column (CGS2): finish ||w||, rotate the new Hessenberg column, update g.
+template <typename R>
+__global__ void k_givens(int j, int ncol, int m, const double* __restrict__ npartial, int nch,
+                         const double2* __restrict__ hbuf, int ldp, double* __restrict__ vscale,
+                         double2* __restrict__ Rm, double* __restrict__ cs, double2* __restrict__ sn,
+                         double2* __restrict__ g, ColState* __restrict__ st, int* __restrict__ nactive,
+                         double* __restrict__ in_scale, const ColDesc* __restrict__ cols, double breakdown_eps) {
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  ColState& S = st[col];
+  if (!S.active) {
+    in_scale[col] = 0.0;
+    return;
+  }
+  double nn = 0;
+  for (int c = 0; c < nch; ++c) nn += npartial[(int64_t)col * nch + c];
+  double hn = sqrt(nn);
+  const double2* h = hbuf + (int64_t)col * ldp;
+  double2* Rc = Rm + ((int64_t)col * m + j) * (m + 1);  // column j of R
+  for (int i = 0; i <= j; ++i) Rc[i] = h[i];
+  givens_update(j, m, Rc, hn, cs + (int64_t)col * m, sn + (int64_t)col * m, g + (int64_t)col * (m + 1), S,
+                breakdown_eps);
   double inv = hn > 0 ? 1.0 / hn : 0.0;
   vscale[(int64_t)col * (m + 1) + j + 1] = inv;
   in_scale[col] = S.active ? sqrt((double)cols[col].len) * inv : 0.0;
   if (S.active) atomicAdd(nactive, 1);
+}
+
+// ------------------------------------------------------------------ CGS2 with delayed reorthogonalisation
+//
+// Iteration j holds the basis v_0..v_{nv-1} (final, orthonormal) and the pending vector u_j (one CGS
+// pass done, not yet normalised; none at j = 0, where v_0 is final and nv = 1).  z_j = N(u_j) is
+// admissible in FGMRES: the flexible relation A Z = V Hbar only needs w_j = A z_j orthogonalised
+// against the final basis, and u_j equals v_j up to its reorthogonalisation correction.
+//   sweep A (one read of the basis):  a = V^H u_j, b = V^H w, alpha = u_j^H u_j, beta = u_j^H w
+//   column j-1 final:  h[:, j-1] += a,  h[j, j-1] = rho = sqrt(alpha - |a|^2);  Givens on column j-1
+//   v_j = (u_j - V a) / rho,  d = v_j^H w = (beta - a^H b) / rho,  partial column j = (b, d)
+//   sweep B (one read of the basis):  v_j -> slot j,  u_{j+1} = w - V b - v_j d -> slot j+1
+// The second Gram-Schmidt pass of every vector is thus the first half of the next sweep A:
+// 16 nv + 48 bytes per point and iteration instead of 32 nv + 48.
+
+// partial[((col * ndc + chunk) * 2 + t) * ldq + i]: t = 0 dots with u (i < nv; i = nv: u^H u),
+// t = 1 dots with w (i < nv; i = nv: u^H w).  u or w may be null.
+template <typename R>
+__global__ void __launch_bounds__(MD_THREADS) k_dsweepA(const C<R>* __restrict__ V, int64_t vstride, int nv,
+                                                        const C<R>* __restrict__ u, const C<R>* __restrict__ w,
+                                                        const ColDesc* __restrict__ cols,
+                                                        const ColState* __restrict__ st, int P, int ndc,
+                                                        double2* __restrict__ partial, int ldq) {
+  int col = blockIdx.y, chunk = blockIdx.x;
+  if (!st[col].active) return;
+  ColDesc cd = cols[col];
+  double2* pu = partial + ((int64_t)(col * ndc + chunk) * 2) * ldq;
+  double2* pw = pu + ldq;
+  int64_t a = (int64_t)chunk * P;
+  if (a >= cd.len) {
+    for (int i = threadIdx.x; i <= nv; i += MD_THREADS) {
+      pu[i] = make_double2(0, 0);
+      pw[i] = make_double2(0, 0);
+    }
+    return;
+  }
+  const int np = (int)min((int64_t)P, cd.len - a);
+  extern __shared__ unsigned char ds_smem[];
+  C<R>* us = (C<R>*)ds_smem;
+  C<R>* ws = us + P;
+  double uu = 0, uwx = 0, uwy = 0;
+  for (int p = threadIdx.x; p < np; p += MD_THREADS) {
+    C<R> uv = u ? u[cd.off + a + p] : mk<R>(0, 0);
+    C<R> wv = w ? w[cd.off + a + p] : mk<R>(0, 0);
+    us[p] = uv;
+    ws[p] = wv;
+    uu += (double)uv.x * uv.x + (double)uv.y * uv.y;
+    C<R> t = cdotc(uv, wv);
+    uwx += t.x;
+    uwy += t.y;
+  }
+  double sc[3] = {uu, uwx, uwy};
+  __shared__ double red3[3];
+  block_reduce_store<3>(sc, red3);  // ends with __syncthreads: the chunk tiles are complete
+  if (threadIdx.x == 0) {
+    pu[nv] = make_double2(red3[0], 0.0);
+    pw[nv] = make_double2(red3[1], red3[2]);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i < nv; i += MD_THREADS / 32) {
+    const C<R>* vi = V + (int64_t)i * vstride + cd.off + a;
+    C<R> su = mk<R>(0, 0), sw = mk<R>(0, 0), su2 = mk<R>(0, 0), sw2 = mk<R>(0, 0);
+    int p = lane;
+    for (; p + 32 < np; p += 64) {
+      C<R> v0 = vi[p], v1 = vi[p + 32];
+      su = cadd(su, cdotc(v0, us[p]));
+      sw = cadd(sw, cdotc(v0, ws[p]));
+      su2 = cadd(su2, cdotc(v1, us[p + 32]));
+      sw2 = cadd(sw2, cdotc(v1, ws[p + 32]));
+    }
+    for (; p < np; p += 32) {
+      C<R> v0 = vi[p];
+      su = cadd(su, cdotc(v0, us[p]));
+      sw = cadd(sw, cdotc(v0, ws[p]));
+    }
+    double d[4] = {(double)su.x + su2.x, (double)su.y + su2.y, (double)sw.x + sw2.x, (double)sw.y + sw2.y};
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) d[k] += __shfl_down_sync(0xffffffffu, d[k], o);
+    if (lane == 0) {
+      pu[i] = make_double2(d[0], d[1]);
+      pw[i] = make_double2(d[2], d[3]);
+    }
+  }
+}
+
+// Sum sweep-A partials over chunks: red[(col * 2 + t) * ldq + i], i <= nv (one block per column).
+__global__ void k_dreduce(const double2* __restrict__ partial, int ndc, int ldq, int nv,
+                          const ColState* __restrict__ st, double2* __restrict__ red) {
+  int col = blockIdx.x;
+  if (!st[col].active) return;
+  for (int e = threadIdx.x; e < 2 * (nv + 1); e += blockDim.x) {
+    int t = e / (nv + 1), i = e % (nv + 1);
+    double2 s = make_double2(0, 0);
+    for (int c = 0; c < ndc; ++c) s = cadd(s, partial[((int64_t)(col * ndc + c) * 2 + t) * ldq + i]);
+    red[((int64_t)col * 2 + t) * ldq + i] = s;
+  }
+}
+
+// One thread per column: finalise column j-1 (when a pending vector exists), Givens on it, build
+// the partial column j and the sweep-B coefficients ca = a, cb = b (vector precision) and
+// sc = (1 / rho, d).
+template <typename R>
+__global__ void k_dcoef(int j, int nv, int has_u, int has_w, int ncol, int m, const double2* __restrict__ red,
+                        int ldq, double2* __restrict__ Rm, double* __restrict__ cs, double2* __restrict__ sn,
+                        double2* __restrict__ g, ColState* __restrict__ st, C<R>* __restrict__ ca,
+                        C<R>* __restrict__ cb, double2* __restrict__ sc, int* __restrict__ nactive,
+                        double breakdown_eps) {
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  ColState& S = st[col];
+  if (!S.active) return;
+  const double2* ra = red + (int64_t)col * 2 * ldq;  // a_i, i < nv; ra[nv] = (u^H u, 0)
+  const double2* rb = ra + ldq;                      // b_i, i < nv; rb[nv] = u^H w
+  double rho = 1.0;
+  if (has_u) {
+    double aa = 0;
+    for (int i = 0; i < nv; ++i) aa += ra[i].x * ra[i].x + ra[i].y * ra[i].y;
+    double r2 = ra[nv].x - aa;
+    rho = r2 > 0 ? sqrt(r2) : 0.0;
+    double2* Rc = Rm + ((int64_t)col * m + (j - 1)) * (m + 1);  // column j-1: partial (b, d) so far
+    for (int i = 0; i < nv; ++i) Rc[i] = cadd(Rc[i], ra[i]);
+    givens_update(j - 1, m, Rc, rho, cs + (int64_t)col * m, sn + (int64_t)col * m, g + (int64_t)col * (m + 1), S,
+                  breakdown_eps);
+    if (S.active && !has_w) {  // finalisation pass at the end of a cycle of m iterations
+      S.status = HELM_NOT_CONVERGED;
+      S.active = 0;
+    }
+    if (!S.active) return;
+  }
+  if (!has_w) return;
+  double2 d = make_double2(0, 0);
+  double inv = 1.0;
+  if (has_u) {
+    inv = rho > 0 ? 1.0 / rho : 0.0;
+    double2 t = rb[nv];  // u^H w
+    for (int i = 0; i < nv; ++i) t = csub(t, cdotc(ra[i], rb[i]));
+    d = cscale(t, inv);
+  }
+  double2* Rj = Rm + ((int64_t)col * m + j) * (m + 1);  // partial column j
+  for (int i = 0; i < nv; ++i) Rj[i] = rb[i];
+  if (has_u) Rj[nv] = d;
+  C<R>* cac = ca + (int64_t)col * ldq;
+  C<R>* cbc = cb + (int64_t)col * ldq;
+  for (int i = 0; i < nv; ++i) {
+    cac[i] = mk<R>((R)ra[i].x, (R)ra[i].y);
+    cbc[i] = mk<R>((R)rb[i].x, (R)rb[i].y);
+  }
+  sc[col * 2] = make_double2(inv, 0.0);
+  sc[col * 2 + 1] = d;
+  atomicAdd(nactive, 1);
+}
+
+// Sweep B: v_j = (u_j - V a) / rho written over u_j (slot j), u_{j+1} = w - V b - v_j d (slot j+1),
+// and per-chunk |u_{j+1}|^2 partials.
+template <typename R>
+__global__ void __launch_bounds__(RED_THREADS) k_dsweepB(const C<R>* __restrict__ V, int64_t vstride, int nv,
+                                                         C<R>* __restrict__ u, const C<R>* __restrict__ w,
+                                                         C<R>* __restrict__ wout, const C<R>* __restrict__ ca,
+                                                         const C<R>* __restrict__ cb, const double2* __restrict__ sc,
+                                                         int ldq, const ColDesc* __restrict__ cols,
+                                                         const ColState* __restrict__ st, int nch,
+                                                         double* __restrict__ npartial) {
+  int col = blockIdx.y, chunk = blockIdx.x;
+  if (!st[col].active) return;
+  extern __shared__ unsigned char db_smem[];
+  C<R>* sa = (C<R>*)db_smem;
+  C<R>* sb = sa + nv;
+  for (int i = threadIdx.x; i < nv; i += RED_THREADS) {
+    sa[i] = ca[(int64_t)col * ldq + i];
+    sb[i] = cb[(int64_t)col * ldq + i];
+  }
+  __syncthreads();
+  const R inv = (R)sc[col * 2].x;
+  const C<R> d = mk<R>((R)sc[col * 2 + 1].x, (R)sc[col * 2 + 1].y);
+  ColDesc cd = cols[col];
+  int64_t a, b;
+  chunk_range(cd.len, nch, chunk, a, b);
+  double s[1] = {0.0};
+  for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
+    int64_t q = cd.off + p;
+    C<R> au = u ? u[q] : mk<R>(0, 0), aw = w[q];
+    int i = 0;
+    for (; i + 4 <= nv; i += 4) {
+      C<R> v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = V[(int64_t)(i + k) * vstride + q];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        au = csub(au, cmul(v[k], sa[i + k]));
+        aw = csub(aw, cmul(v[k], sb[i + k]));
+      }
+    }
+    for (; i < nv; ++i) {
+      C<R> v = V[(int64_t)i * vstride + q];
+      au = csub(au, cmul(v, sa[i]));
+      aw = csub(aw, cmul(v, sb[i]));
+    }
+    if (u) {
+      C<R> vj = cscale(au, inv);
+      u[q] = vj;
+      aw = csub(aw, cmul(vj, d));
+    }
+    wout[q] = aw;
+    s[0] += (double)aw.x * aw.x + (double)aw.y * aw.y;
+  }
+  block_reduce_store<1>(s, npartial + (int64_t)col * nch + chunk);
+}
+
+// Network input scale for the pending vector: in_scale = sqrt(n) / ||u_{j+1}||.
+__global__ void k_nscale(int ncol, const double* __restrict__ npartial, int nch, const ColState* __restrict__ st,
+                         const ColDesc* __restrict__ cols, double* __restrict__ in_scale) {
+  int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncol) return;
+  if (!st[col].active) {
+    in_scale[col] = 0.0;
+    return;
+  }
+  double nn = 0;
+  for (int c = 0; c < nch; ++c) nn += npartial[(int64_t)col * nch + c];
+  in_scale[col] = nn > 0 ? sqrt((double)cols[col].len / nn) : 0.0;
 }
 
 // y = R^{-1} g (k x k upper triangular), ycoef_i = beta * y_i.
@@ -388,10 +622,16 @@ struct SolverWs {
   double* in_scale;
   double* out_scale;
   int* nactive;
+  // delayed-reorthogonalisation buffers
+  double2* red;  // [ncol][2][ldq]
+  C<R>* ca;      // [ncol][ldq]
+  C<R>* cb;      // [ncol][ldq]
+  double2* sc;   // [ncol][2]
 };
 
 template <typename R>
-static helm_status solver_ws(helm_ctx* ctx, int m, int ncol, int nch, bool has_net, int64_t nvec, SolverWs<R>& W) {
+static helm_status solver_ws(helm_ctx* ctx, int m, int ncol, int nch, int ndc, bool separate_z, int64_t nvec,
+                             SolverWs<R>& W) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -400,11 +640,16 @@ static helm_status solver_ws(helm_ctx* ctx, int m, int ncol, int nch, bool has_n
   };
   size_t vb = sizeof(C<R>) * nvec;
   size_t oV = take(vb * (m + 1));
-  size_t oZ = has_net ? take(vb * m) : oV;
+  size_t oZ = separate_z ? take(vb * m) : oV;
   size_t ow = take(vb);
   size_t orr = take(sizeof(double2) * nvec);
   int ldp = m + 1;
-  size_t op = take(sizeof(double2) * ncol * nch * ldp);
+  const int ldq = m + 2;
+  size_t op = take(sizeof(double2) * ncol * std::max(nch, ndc) * 2 * ldq);
+  size_t ored = take(sizeof(double2) * ncol * 2 * ldq);
+  size_t oca = take(sizeof(C<R>) * ncol * ldq);
+  size_t ocb = take(sizeof(C<R>) * ncol * ldq);
+  size_t osc = take(sizeof(double2) * ncol * 2);
   size_t onp = take(sizeof(double) * ncol * nch);
   size_t oh = take(sizeof(double2) * ncol * ldp);
   size_t oc = take(sizeof(C<R>) * ncol * ldp);
@@ -440,6 +685,10 @@ static helm_status solver_ws(helm_ctx* ctx, int m, int ncol, int nch, bool has_n
   W.in_scale = (double*)(b + ois);
   W.out_scale = (double*)(b + oos);
   W.nactive = (int*)(b + ona);
+  W.red = (double2*)(b + ored);
+  W.ca = (C<R>*)(b + oca);
+  W.cb = (C<R>*)(b + ocb);
+  W.sc = (double2*)(b + osc);
   return HELM_OK;
 }
 
@@ -470,7 +719,22 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
   for (auto& c : ctx->cols_host) maxlen = std::max(maxlen, c.len);
   const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((4 * 148 + ncol - 1) / ncol, (maxlen + 1023) / 1024));
   SolverWs<R> W;
-  HELM_TRY(solver_ws<R>(ctx, m, ncol, nch, net != nullptr, nvec, W));
+  // dot-product chunking: P points per block (multiple of 256, 256..2048), about 600 blocks in all
+  int P = (int)std::max<int64_t>(256, std::min<int64_t>(2048, (maxlen * ncol / 600) / 256 * 256));
+  const int ndc = (int)((maxlen + P - 1) / P);
+  const dim3 dgrid(ndc, ncol);
+  const size_t md_smem = sizeof(C<R>) * P;
+  const bool dcgs2 = o.orth == HELM_ORTH_DCGS2;
+  HELM_TRY(solver_ws<R>(ctx, m, ncol, nch, ndc, net != nullptr || dcgs2, nvec, W));
+  const int ldq = m + 2;
+  const size_t ds_smem = 2 * sizeof(C<R>) * P;
+  const size_t db_smem = 2 * sizeof(C<R>) * m;
+  if (dcgs2) {
+    if (ds_smem > 48 * 1024)
+      HELM_CK(cudaFuncSetAttribute(k_dsweepA<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ds_smem));
+    if (db_smem > 48 * 1024)
+      HELM_CK(cudaFuncSetAttribute(k_dsweepB<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)db_smem));
+  }
   HELM_TRY(ensure_pinned(ctx, sizeof(double) * 2 * ncol + sizeof(ColState) * ncol + 64 + 64));
   double* h_sums = (double*)ctx->pinned;
   ColState* h_st = (ColState*)(h_sums + 2 * ncol);
@@ -531,59 +795,123 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
     launch(k_v0<R>, vgrid, RED_THREADS, 0, stream, W.r, W.V, W.st, ctx->cols_dev, nch);
     HELM_CK_LAUNCH();
     prof_end(ctx, PH_RESIDUAL, stream);
-    for (int j = 0; j < m; ++j) {
-      C<R>* Vj = W.V + (int64_t)j * nvec;
-      C<R>* Zj = net ? W.Z + (int64_t)j * nvec : Vj;
-      // z_j = N_theta(v_j)
-      prof_begin(ctx, PH_PRECOND, stream);
-      if (net) {
-        for (int s = 0; s < ctx->nsys; ++s) {
-          int64_t off = ctx->sys[s].off * nrhs;
-          HELM_TRY(unet_precondition<R>(ctx, net, s, Vj + off, Zj + off, nrhs, W.in_scale + s * nrhs,
-                                        W.out_scale + s * nrhs, stream, 0));
+    if (!dcgs2) {
+      for (int j = 0; j < m; ++j) {
+        C<R>* Vj = W.V + (int64_t)j * nvec;
+        C<R>* Zj = net ? W.Z + (int64_t)j * nvec : Vj;
+        // z_j = N_theta(v_j)
+        prof_begin(ctx, PH_PRECOND, stream);
+        if (ctx->prof_on) {
+          ctx->prof_work[PH_PRECOND] += net ? 70816.0 * ctx->npts * nrhs : 0.0;
+          ctx->prof_work[PH_STENCIL] += 16.0 * ctx->npts * nrhs + 4.0 * ctx->npts;
+          ctx->prof_work[PH_ORTH] += (16.0 * (j > 0 ? j : 1) + 48.0) * ctx->npts * nrhs * (double)nact / ncol;
         }
-      } else {
-        // z_j = v_j = vscale_j Vraw_j into the FP64 residual buffer, free after k_v0
-        launch(k_scale_copy<R>, vgrid, RED_THREADS, 0, stream, Vj, (C<R>*)W.r, nullptr, ctx->cols_dev, nch,
+        if (net) {
+          for (int s = 0; s < ctx->nsys; ++s) {
+            int64_t off = ctx->sys[s].off * nrhs;
+            HELM_TRY(unet_precondition<R>(ctx, net, s, Vj + off, Zj + off, nrhs, W.in_scale + s * nrhs,
+                                          W.out_scale + s * nrhs, stream, 0));
+          }
+        } else {
+          // z_j = v_j = vscale_j Vraw_j into the FP64 residual buffer, free after k_v0
+          launch(k_scale_copy<R>, vgrid, RED_THREADS, 0, stream, Vj, (C<R>*)W.r, nullptr, ctx->cols_dev, nch,
+                 W.in_scale);
+          HELM_CK_LAUNCH();
+        }
+        prof_end(ctx, PH_PRECOND, stream);
+        // w = A z_j
+        prof_begin(ctx, PH_STENCIL, stream);
+        HELM_TRY(apply_op<R>(ctx, net ? Zj : (C<R>*)W.r, W.w, nrhs, false, stream));
+        prof_end(ctx, PH_STENCIL, stream);
+        const int nv = j + 1;
+        // CGS2, two passes; the second writes the unnormalised v_{j+1} and its norm partials
+        prof_begin(ctx, PH_ORTH, stream);
+        for (int pass = 0; pass < 2; ++pass) {
+          launch(k_mdot<R>, dgrid, MD_THREADS, md_smem, stream, W.V, nvec, nv, W.w, ctx->cols_dev, W.st, P, ndc,
+                 W.partial, ldp);
+          launch(k_hreduce<R>, ncol, 256, 0, stream, W.partial, ndc, ldp, nv, W.vscale, ldp, W.st, W.hbuf, W.coef,
+                 pass);
+          C<R>* dst = pass == 1 ? W.V + (int64_t)(j + 1) * nvec : nullptr;
+          launch(k_maxpy<R>, vgrid, RED_THREADS, maxpy_smem, stream, W.V, nvec, nv, W.w, W.coef, ldp, ctx->cols_dev,
+                 W.st, nch, dst, pass == 1 ? W.npartial : nullptr);
+          HELM_CK_LAUNCH();
+        }
+        prof_end(ctx, PH_ORTH, stream);
+        prof_begin(ctx, PH_LSQ, stream);
+        HELM_CK(cudaMemsetAsync(W.nactive, 0, sizeof(int), stream));
+        launch(k_givens<R>, cdiv(ncol, 64), 64, 0, stream, j, ncol, m, W.npartial, nch, W.hbuf, ldp, W.vscale, W.Rm,
+               W.cs, W.sn, W.g, W.st, W.nactive, W.in_scale, ctx->cols_dev, breakdown_eps);
+        HELM_CK_LAUNCH();
+        HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        HELM_CK(cudaMemcpyAsync(h_est0, &W.st[0].est, sizeof(double), cudaMemcpyDeviceToHost, stream));
+        prof_end(ctx, PH_LSQ, stream);
+        HELM_CK(cudaStreamSynchronize(stream));
+        prof_collect(ctx);
+        if (!done[0]) ctx->history.push_back(*h_est0 * rel[0]);
+        if (*h_nact == 0) break;
+      }
+    } else {
+      // CGS2 with delayed reorthogonalisation (kernels k_dsweepA / k_dcoef / k_dsweepB above)
+      for (int j = 0; j < m; ++j) {
+        C<R>* Uj = W.V + (int64_t)j * nvec;  // v_0 at j = 0, else the pending u_j
+        C<R>* Zj = W.Z + (int64_t)j * nvec;
+        prof_begin(ctx, PH_PRECOND, stream);
+        if (net) {
+          for (int s = 0; s < ctx->nsys; ++s) {
+            int64_t off = ctx->sys[s].off * nrhs;
+            HELM_TRY(unet_precondition<R>(ctx, net, s, Uj + off, Zj + off, nrhs, W.in_scale + s * nrhs,
+                                          W.out_scale + s * nrhs, stream, 0));
+          }
+        } else {
+          launch(k_scale_copy<R>, vgrid, RED_THREADS, 0, stream, (const C<R>*)Uj, Zj, nullptr, ctx->cols_dev, nch,
+                 W.in_scale);
+        }
+        HELM_CK_LAUNCH();
+        prof_end(ctx, PH_PRECOND, stream);
+        prof_begin(ctx, PH_STENCIL, stream);
+        HELM_TRY(apply_op<R>(ctx, Zj, W.w, nrhs, false, stream));
+        prof_end(ctx, PH_STENCIL, stream);
+        const int has_u = j > 0;
+        const int nv = j > 0 ? j : 1;
+        prof_begin(ctx, PH_ORTH, stream);
+        HELM_CK(cudaMemsetAsync(W.nactive, 0, sizeof(int), stream));
+        launch(k_dsweepA<R>, dgrid, MD_THREADS, ds_smem, stream, (const C<R>*)W.V, nvec, nv,
+               (const C<R>*)(has_u ? Uj : nullptr), (const C<R>*)W.w, ctx->cols_dev, W.st, P, ndc, W.partial, ldq);
+        launch(k_dreduce, ncol, 256, 0, stream, (const double2*)W.partial, ndc, ldq, nv, W.st, W.red);
+        launch(k_dcoef<R>, cdiv(ncol, 64), 64, 0, stream, j, nv, has_u, 1, ncol, m, (const double2*)W.red, ldq, W.Rm,
+               W.cs, W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps);
+        launch(k_dsweepB<R>, vgrid, RED_THREADS, 2 * sizeof(C<R>) * nv, stream, (const C<R>*)W.V, nvec, nv,
+               has_u ? Uj : nullptr, (const C<R>*)W.w, W.V + (int64_t)(j + 1) * nvec, (const C<R>*)W.ca,
+               (const C<R>*)W.cb, (const double2*)W.sc, ldq, ctx->cols_dev, W.st, nch, W.npartial);
+        launch(k_nscale, cdiv(ncol, 64), 64, 0, stream, ncol, (const double*)W.npartial, nch, W.st, ctx->cols_dev,
                W.in_scale);
         HELM_CK_LAUNCH();
+        prof_end(ctx, PH_ORTH, stream);
+        prof_begin(ctx, PH_LSQ, stream);
+        HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
+        HELM_CK(cudaMemcpyAsync(h_est0, &W.st[0].est, sizeof(double), cudaMemcpyDeviceToHost, stream));
+        prof_end(ctx, PH_LSQ, stream);
+        HELM_CK(cudaStreamSynchronize(stream));
+        prof_collect(ctx);
+        if (!done[0] && j > 0) ctx->history.push_back(*h_est0 * rel[0]);
+        nact = *h_nact;
+        if (*h_nact == 0) break;
       }
-      prof_end(ctx, PH_PRECOND, stream);
-      // w = A z_j
-      prof_begin(ctx, PH_STENCIL, stream);
-      HELM_TRY(apply_op<R>(ctx, net ? Zj : (C<R>*)W.r, W.w, nrhs, false, stream));
-      prof_end(ctx, PH_STENCIL, stream);
-      const int nv = j + 1;
-      // CGS2, two passes; the second writes the unnormalised v_{j+1} and its norm partials
+      // columns that ran all m iterations: finalise column m-1 (reorthogonalise the pending u_m)
       prof_begin(ctx, PH_ORTH, stream);
-      for (int pass = 0; pass < 2; ++pass) {
-        launch(k_mdot<R>, vgrid, RED_THREADS, 0, stream, W.V, nvec, nv, W.w, ctx->cols_dev, W.st, nch, W.partial,
-               ldp);
-        launch(k_hreduce<R>, ncol, 128, 0, stream, W.partial, nch, ldp, nv, W.vscale, ldp, W.st, W.hbuf, W.coef,
-               pass);
-        C<R>* dst = pass == 1 ? W.V + (int64_t)(j + 1) * nvec : nullptr;
-        launch(k_maxpy<R>, vgrid, RED_THREADS, maxpy_smem, stream, W.V, nvec, nv, W.w, W.coef, ldp, ctx->cols_dev,
-               W.st, nch, dst, pass == 1 ? W.npartial : nullptr);
-        HELM_CK_LAUNCH();
-      }
-      prof_end(ctx, PH_ORTH, stream);
-      prof_begin(ctx, PH_LSQ, stream);
-      HELM_CK(cudaMemsetAsync(W.nactive, 0, sizeof(int), stream));
-      launch(k_givens<R>, cdiv(ncol, 64), 64, 0, stream, j, ncol, m, W.npartial, nch, W.hbuf, ldp, W.vscale, W.Rm,
-             W.cs, W.sn, W.g, W.st, W.nactive, W.in_scale, ctx->cols_dev, breakdown_eps);
+      launch(k_dsweepA<R>, dgrid, MD_THREADS, ds_smem, stream, (const C<R>*)W.V, nvec, m,
+             (const C<R>*)(W.V + (int64_t)m * nvec), (const C<R>*)nullptr, ctx->cols_dev, W.st, P, ndc, W.partial,
+             ldq);
+      launch(k_dreduce, ncol, 256, 0, stream, (const double2*)W.partial, ndc, ldq, m, W.st, W.red);
+      launch(k_dcoef<R>, cdiv(ncol, 64), 64, 0, stream, m, m, 1, 0, ncol, m, (const double2*)W.red, ldq, W.Rm, W.cs,
+             W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps);
       HELM_CK_LAUNCH();
-      HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
-      HELM_CK(cudaMemcpyAsync(h_est0, &W.st[0].est, sizeof(double), cudaMemcpyDeviceToHost, stream));
-      prof_end(ctx, PH_LSQ, stream);
-      HELM_CK(cudaStreamSynchronize(stream));
-      prof_collect(ctx);
-      if (!done[0]) ctx->history.push_back(*h_est0 * rel[0]);
-      if (*h_nact == 0) break;
+      prof_end(ctx, PH_ORTH, stream);
     }
     prof_begin(ctx, PH_UPDATE, stream);
     launch(k_backsolve, cdiv(ncol, 64), 64, 0, stream, ncol, m, W.Rm, W.g, W.st, W.y);
-    launch(k_xupdate<R>, vgrid, RED_THREADS, 0, stream, W.Z, nvec, W.y, m, net ? nullptr : W.vscale, W.st,
-           ctx->cols_dev, nch, x);
+    launch(k_xupdate<R>, vgrid, RED_THREADS, 0, stream, W.Z, nvec, W.y, m, (net || dcgs2) ? nullptr : W.vscale,
+           W.st, ctx->cols_dev, nch, x);
     HELM_CK_LAUNCH();
     HELM_CK(cudaMemcpyAsync(h_st, W.st, sizeof(ColState) * ncol, cudaMemcpyDeviceToHost, stream));
     prof_end(ctx, PH_UPDATE, stream);
@@ -638,7 +966,8 @@ extern "C" helm_status helm_fgmres_solve(helm_ctx* ctx, const helm_unet* net, co
     return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: tol must be > 0 and iteration budgets >= 1");
   if (o.mixed && !(o.inner_tol > 0 && o.inner_tol < 1))
     return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: inner_tol must be in (0, 1)");
-  if (o.orth != HELM_ORTH_CGS2) return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: only CGS2 is implemented");
+  if (o.orth != HELM_ORTH_CGS2 && o.orth != HELM_ORTH_DCGS2)
+    return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: unknown orthogonalisation");
   cudaStream_t st = (cudaStream_t)stream;
   if (o.mixed) return fgmres_solve<float>(ctx, net, (const double2*)b, (double2*)x, nrhs, o, info, st);
   return fgmres_solve<double>(ctx, net, (const double2*)b, (double2*)x, nrhs, o, info, st);

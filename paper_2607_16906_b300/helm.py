@@ -73,6 +73,7 @@ _SIGS = {
     "helm_solve_history": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.c_int]),
     "helm_profile_enable": (ct.c_int, [_P, ct.c_int]),
     "helm_profile_read": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
+    "helm_profile_work": (ct.c_int, [_P, ct.POINTER(ct.c_double)]),
     "helm_launch_count": (ct.c_uint64, []),
     "helm_last_error": (ct.c_char_p, []),
 }
@@ -267,15 +268,19 @@ def helm_precond_apply(ctx: Context, net: UNet, v: torch.Tensor, z: torch.Tensor
     return z
 
 
+ORTH = {"cgs2": 0, "dcgs2": 1}
+
+
 def helm_fgmres_solve(ctx: Context, net, b: torch.Tensor, x: torch.Tensor, nrhs=1, m=30, tol=1e-6,
-                      mixed=True, max_restarts=100, max_outer=100, inner_tol=1e-4, stream=None, raise_on=False):
+                      mixed=True, max_restarts=100, max_outer=100, inner_tol=1e-4, orth="cgs2", stream=None,
+                      raise_on=False):
     """Solve A x = b (complex128 batch vectors; x holds x0 on entry).  Returns (status, [info dict per column])."""
     if b.dtype != torch.complex128 or x.dtype != torch.complex128:
         raise TypeError("b and x are complex128 batch vectors")
     if b.numel() != ctx.npts * nrhs or x.numel() != b.numel():
         raise ValueError("b, x must have npts * nrhs entries")
     ncol = len(ctx.systems) * nrhs
-    opts = helm_solve_opts(m, max_restarts, max_outer, tol, inner_tol, int(bool(mixed)), 0)
+    opts = helm_solve_opts(m, max_restarts, max_outer, tol, inner_tol, int(bool(mixed)), ORTH[orth])
     info = (helm_solve_info * ncol)()
     rc = _lib.helm_fgmres_solve(ctx.handle, net.handle if net is not None else None, _dev_ptr(b), _dev_ptr(x),
                                 nrhs, ct.byref(opts), info, _stream(stream))
@@ -327,6 +332,13 @@ def helm_profile_read(ctx: Context):
     cnt = (ct.c_int64 * len(PHASES))()
     _check(_lib.helm_profile_read(ctx.handle, ms, cnt))
     return {p: (ms[i], cnt[i]) for i, p in enumerate(PHASES)}
+
+
+def helm_profile_work(ctx: Context):
+    """{phase: algorithmic flops (precond) or bytes (other phases)} issued since helm_profile_enable."""
+    w = (ct.c_double * len(PHASES))()
+    _check(_lib.helm_profile_work(ctx.handle, w))
+    return {p: w[i] for i, p in enumerate(PHASES)}
 
 
 def helm_launch_count() -> int:

@@ -30,8 +30,9 @@ def _flat_b(probs):
     return np.concatenate([p.b.ravel() for p in probs])
 
 
+@pytest.mark.parametrize("orth", ["cgs2", "dcgs2"])
 @pytest.mark.parametrize("use_net,m", [(False, 20), (True, 8)])
-def test_one_cycle_matches_oracle_fp64(helm, theta, use_net, m):
+def test_one_cycle_matches_oracle_fp64(helm, theta, use_net, m, orth):
     """x after one FGMRES(m) cycle from x0 = 0 equals the oracle's cycle (Alg. 1) to rounding."""
     probs = small_problems(((20, 14, 5),), seed=31)
     p = probs[0]
@@ -39,7 +40,7 @@ def test_one_cycle_matches_oracle_fp64(helm, theta, use_net, m):
     net = helm.UNet(theta) if use_net else None
     b = to_dev(_flat_b(probs), torch.complex128)
     x = torch.zeros_like(b)
-    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=m, tol=1e-300, mixed=False, max_restarts=1)
+    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=m, tol=1e-300, mixed=False, max_restarts=1, orth=orth)
     assert info[0]["iters"] == m and info[0]["restarts"] == 1
     A = hz.assemble(p.c, p.p, p.h, p.omega)
     if use_net:
@@ -53,8 +54,9 @@ def test_one_cycle_matches_oracle_fp64(helm, theta, use_net, m):
     assert abs(info[0]["relres_true"] - hz.relres(A, res.x, p.b[0].ravel())) <= 1e-9
 
 
+@pytest.mark.parametrize("orth", ["cgs2", "dcgs2"])
 @pytest.mark.parametrize("mixed,tol", [(False, 1e-8), (True, 1e-6)])
-def test_gmres_converges_to_direct_solution_uneven_batch(helm, mixed, tol):
+def test_gmres_converges_to_direct_solution_uneven_batch(helm, mixed, tol, orth):
     """Unpreconditioned (identity) solves of an uneven batch, 2 RHS per system, reach the FP64
     true residual tol; the solution error against splu stays within cond-limited bounds."""
     probs = small_problems(((20, 14, 5), (13, 9, 3)), seed=32, nrhs=2)
@@ -62,7 +64,7 @@ def test_gmres_converges_to_direct_solution_uneven_batch(helm, mixed, tol):
     b = to_dev(_flat_b(probs), torch.complex128)
     x = torch.zeros_like(b)
     rc, info = helm.helm_fgmres_solve(ctx, None, b, x, 2, m=30, tol=tol, mixed=mixed, max_restarts=200,
-                                      max_outer=200, inner_tol=1e-4)
+                                      max_outer=200, inner_tol=1e-4, orth=orth)
     assert rc == helm.HELM_OK, info
     got = split(x.cpu().numpy(), probs, 2)
     k = 0
