@@ -336,7 +336,8 @@ def run_cuda(args):
                 "mean_iters_per_solve": mean_iters,
                 "relres_true_max": max(c["relres_true"] for c in infos) if infos else None,
                 "phases_ms": {k: v[0] for k, v in prof.items()},
-                "roofline": roof, "phase_rooflines": phase_rooflines, "stencil_roofline": stencil,
+                "roofline": roof, "phase_rooflines": phase_rooflines, "phase_work": work,
+                "stencil_roofline": stencil,
                 "plain_fp64": plain,
                 "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
                 "e2e": {"value": conv_e2e / (ms_e2e / 1e3), "unit": "solves/s", "h2d_bytes_per_step": nbytes,

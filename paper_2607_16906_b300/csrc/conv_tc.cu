@@ -22,122 +22,10 @@
 #include <cstdlib>
 #include <mutex>
 
+#include "tc_ptx.cuh"
 #include "unet.cuh"
 
 namespace helm {
-
-// ------------------------------------------------------------------ PTX wrappers
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-constexpr long long WAIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
-
-// Bounded wait for the phase of `parity`; false (and an error code) on timeout or abort.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code) {
-  long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
-      *abort_flag = 1;
-      atomicExch(err, code);
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,
-                                            int c3) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5, %6}], "
-      "[%2];" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
-      : "memory");
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(
-          smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
-  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
-               : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-// D[tmem] (+)= A[smem desc] * B[smem desc]^T, kind::f16 (BF16 x BF16 -> FP32)
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                          uint32_t accumulate) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-          d_tmem),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-// Arrive on `bar` once every previously issued tcgen05.mma of this thread has completed.
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-               : "memory");
-}
-
-// 32 TMEM lanes x 16 consecutive 32-bit columns -> 16 registers per thread (thread = lane).
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-// Shared-memory matrix descriptor for a K-major operand in the canonical swizzled layout: rows of
-// `row_bytes` (= the swizzle width: 32, 64 or 128 B), 8-row groups `8 * row_bytes` apart.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, int row_bytes) {
-  uint64_t layout = row_bytes == 128 ? 2ull : (row_bytes == 64 ? 4ull : 6ull);
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr >> 4) & 0x3FFF);              // start address
-  d |= (uint64_t)1 << 16;                              // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(((8 * row_bytes) >> 4) & 0x3FFF) << 32;  // stride byte offset between 8-row groups
-  d |= (uint64_t)1 << 46;                              // descriptor version
-  d |= layout << 61;                                   // swizzle mode
-  return d;
-}
-
-// Instruction descriptor: kind::f16, A = B = BF16, D = FP32, both K-major, M = 128, N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
 
 // ------------------------------------------------------------------ kernel
 
@@ -152,11 +40,14 @@ struct ConvTcArgs {
   int* err;               // device error code (0 = ok)
 };
 
-template <int N, int CHUNK>
+template <int N, int CHUNK, int MODE>
 struct TcCfg {
   static constexpr int A_BYTES = 128 * CHUNK * 2;
   static constexpr int B_BYTES = N * CHUNK * 2;
-  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  // taps per pipeline stage: a whole kernel row (3 taps) for narrow chunks, so that one barrier
+  // round trip carries three MMAs; one tap otherwise
+  static constexpr int TPS = (MODE == 0 && CHUNK <= 32) ? 3 : 1;
+  static constexpr int STAGE_BYTES = TPS * (A_BYTES + B_BYTES);
   static constexpr int STAGES = (96 * 1024 / STAGE_BYTES) > 8 ? 8 : (96 * 1024 / STAGE_BYTES);
   static constexpr int TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
@@ -170,7 +61,7 @@ template <int N, int CHUNK, int MODE>
 __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tA0,
                                                     const __grid_constant__ CUtensorMap tA1,
                                                     const __grid_constant__ CUtensorMap tW, ConvTcArgs a) {
-  using Cfg = TcCfg<N, CHUNK>;
+  using Cfg = TcCfg<N, CHUNK, MODE>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
@@ -183,7 +74,8 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = a.nk0 + a.nk1;
   constexpr int TAPS = MODE == 0 ? 9 : 1;
-  const int ksteps = TAPS * nk;
+  constexpr int TPS = Cfg::TPS;
+  const int ksteps = (TAPS / TPS) * nk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::STAGES; ++s) {
@@ -221,19 +113,23 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
         for (int kc = 0; kc < nk && ok; ++kc) {
           const CUtensorMap* src = kc < a.nk0 ? &tA0 : &tA1;
           int c0 = (kc < a.nk0 ? kc : kc - a.nk0) * CHUNK;
-          for (int tap = 0; tap < TAPS; ++tap) {
+          for (int tg = 0; tg < TAPS / TPS; ++tg) {
             if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, 1)) {
               ok = false;
               break;
             }
             unsigned char* sa = smem + stage * Cfg::STAGE_BYTES;
-            unsigned char* sb = sa + Cfg::A_BYTES;
+            unsigned char* sb = sa + TPS * Cfg::A_BYTES;
             mbar_expect_tx(&full[stage], Cfg::STAGE_BYTES);
-            if (MODE == 0)
-              tma_load_4d(sa, src, &full[stage], c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b);
-            else
-              tma_load_4d(sa, src, &full[stage], c0, x0, y0, b);
-            tma_load_3d(sb, &tW, &full[stage], 0, 0, tap * nk + kc);
+#pragma unroll
+            for (int t = 0; t < TPS; ++t) {
+              const int tap = tg * TPS + t;
+              if (MODE == 0)
+                tma_load_4d(sa + t * Cfg::A_BYTES, src, &full[stage], c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b);
+              else
+                tma_load_4d(sa + t * Cfg::A_BYTES, src, &full[stage], c0, x0, y0, b);
+              tma_load_3d(sb + t * Cfg::B_BYTES, &tW, &full[stage], 0, 0, tap * nk + kc);
+            }
             if (++stage == Cfg::STAGES) {
               stage = 0;
               phase ^= 1;
@@ -271,11 +167,15 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
         tc_fence_after();
         if (lane == 0) {
           uint32_t sa = smem_u32(smem + stage * Cfg::STAGE_BYTES);
-          uint32_t sb = sa + Cfg::A_BYTES;
-          uint64_t ad = smem_desc(sa, CHUNK * 2), bd = smem_desc(sb, CHUNK * 2);
+          uint32_t sb = sa + TPS * Cfg::A_BYTES;
 #pragma unroll
-          for (int k = 0; k < CHUNK / 16; ++k)
-            umma_bf16(d_tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), IDESC, (ks > 0 || k > 0) ? 1u : 0u);
+          for (int t = 0; t < TPS; ++t) {
+            uint64_t ad = smem_desc(sa + t * Cfg::A_BYTES, CHUNK * 2), bd = smem_desc(sb + t * Cfg::B_BYTES, CHUNK * 2);
+#pragma unroll
+            for (int k = 0; k < CHUNK / 16; ++k)
+              umma_bf16(d_tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), IDESC,
+                        (ks > 0 || t > 0 || k > 0) ? 1u : 0u);
+          }
           umma_commit(&empty[stage]);
         }
         __syncwarp();
@@ -389,8 +289,16 @@ static EncodeTiledFn encode_fn() {
   return fn;
 }
 
+// conv_row.cu: row-tile kernels for the narrow 3x3 layers
+bool conv_row_supported(int cin_total, int cout);
+helm_status conv_row_prepare(const double* master, int64_t m_w, int cin, int cin_pad, int cout, __nv_bfloat16** w,
+                             cudaStream_t st);
+helm_status conv_row_forward(const __nv_bfloat16* wrow, const float* bias, int* err, const void* in0, int C0,
+                             const void* in1, int C1, void* out, int cout, int B, int H, int W, cudaStream_t st);
+
 struct TcState {
   __nv_bfloat16* w[NUM_LAYERS] = {};
+  __nv_bfloat16* wrow[NUM_LAYERS] = {};  // row-tile weights where the row kernels serve the layer
   int cin_pad[NUM_LAYERS] = {};
   int chunk[NUM_LAYERS] = {};
   int* err = nullptr;
@@ -434,8 +342,12 @@ helm_status conv_tc_prepare(helm_unet* net, cudaStream_t st) {
   }
   TcState& S = *net->tc;
   if (!S.ok) return HELM_OK;
+  const char* dr = getenv("HELM_DISABLE_ROW");
+  const bool row_ok = !(dr && dr[0] == '1');
   for (int l = 0; l < NUM_LAYERS; ++l) {
     const LayerDesc& d = kLayers[l];
+    if (row_ok && d.kind == CONV3 && conv_row_supported(S.cin_pad[l], d.cout))
+      HELM_TRY(conv_row_prepare(net->master, net->L.m_w[l], d.cin, S.cin_pad[l], d.cout, &S.wrow[l], st));
     if (d.kind == UP2) {
       int64_t tot = (int64_t)4 * d.cin * d.cout;
       launch(k_prep_tc_up, cdiv(tot, 256), 256, 0, st, (const double*)net->master, net->L.m_w[l], d.cin, d.cout,
@@ -454,6 +366,8 @@ helm_status conv_tc_prepare(helm_unet* net, cudaStream_t st) {
 void conv_tc_release(helm_unet* net) {
   if (!net->tc) return;
   for (auto* p : net->tc->w)
+    if (p) cudaFree(p);
+  for (auto* p : net->tc->wrow)
     if (p) cudaFree(p);
   if (net->tc->err) cudaFree(net->tc->err);
   delete net->tc;
@@ -500,20 +414,29 @@ static helm_status weight_map(CUtensorMap* m, const void* ptr, int N, int chunk,
 template <int N, int CHUNK, int MODE>
 static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& w, const ConvTcArgs& args,
                              cudaStream_t st) {
-  using Cfg = TcCfg<N, CHUNK>;
+  using Cfg = TcCfg<N, CHUNK, MODE>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   static int per_sm = 1, nsm = 148;
   std::call_once(once, [] {
     attr_err =
         cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
-    if (attr_err == cudaSuccess)
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv_tc<N, CHUNK, MODE>, Cfg::THREADS, Cfg::SMEM);
-    int dev = 0;
+    int dev = 0, smem_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    // each resident CTA holds TMEM_COLS columns of the SM's 512
-    per_sm = std::max(1, std::min(per_sm, 512 / Cfg::TMEM_COLS));
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // resident CTAs per SM: shared memory (1 KB reserved per CTA), TMEM (512 columns), threads, and
+    // the occupancy calculator (registers)
+    if (attr_err == cudaSuccess)
+      attr_err = cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      100);
+    int by_regs = 8;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k_conv_tc<N, CHUNK, MODE>) == cudaSuccess && fa.numRegs > 0)
+      by_regs = 65536 / (((fa.numRegs + 7) / 8) * 8 * Cfg::THREADS);
+    int by_smem = smem_sm / (Cfg::SMEM + 1024);
+    per_sm = std::min(std::min(by_smem, 512 / Cfg::TMEM_COLS), std::min(2048 / Cfg::THREADS, by_regs));
+    per_sm = std::max(1, per_sm);
   });
   HELM_CK(attr_err);
   int grid = std::min(args.ntiles, nsm * per_sm);
@@ -527,6 +450,8 @@ helm_status conv_tc_forward(const helm_unet* net, int l, const void* in0, int C0
   const TcState& S = *net->tc;
   const LayerDesc& d = kLayers[l];
   if (l == L_ENC1A) C0 = X0_CH;
+  if (S.wrow[l])
+    return conv_row_forward(S.wrow[l], net->w32 + net->L.c_b[l], S.err, in0, C0, in1, C1, out, d.cout, B, H, W, st);
   const int chunk = S.chunk[l];
   if (C0 % chunk || C1 % chunk) return fail(HELM_ERR_INVALID_ARG, "conv_tc_forward: channel count not a chunk multiple");
   CUtensorMap m0, m1, mw;

@@ -450,32 +450,52 @@ __global__ void __launch_bounds__(RED_THREADS) k_dsweepB(const C<R>* __restrict_
   int64_t a, b;
   chunk_range(cd.len, nch, chunk, a, b);
   double s[1] = {0.0};
-  for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
-    int64_t q = cd.off + p;
-    C<R> au = u ? u[q] : mk<R>(0, 0), aw = w[q];
+  // two points per thread per pass: two independent load streams over the basis
+  for (int64_t p0 = a + threadIdx.x; p0 < b; p0 += 2 * RED_THREADS) {
+    const int64_t p1 = p0 + RED_THREADS;
+    const bool two = p1 < b;
+    const int64_t q0 = cd.off + p0, q1 = cd.off + (two ? p1 : p0);
+    C<R> au0 = u ? u[q0] : mk<R>(0, 0), aw0 = w[q0];
+    C<R> au1 = u ? u[q1] : mk<R>(0, 0), aw1 = w[q1];
     int i = 0;
     for (; i + 4 <= nv; i += 4) {
-      C<R> v[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) v[k] = V[(int64_t)(i + k) * vstride + q];
+      C<R> v0[4], v1[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        au = csub(au, cmul(v[k], sa[i + k]));
-        aw = csub(aw, cmul(v[k], sb[i + k]));
+        v0[k] = V[(int64_t)(i + k) * vstride + q0];
+        v1[k] = V[(int64_t)(i + k) * vstride + q1];
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        au0 = csub(au0, cmul(v0[k], sa[i + k]));
+        aw0 = csub(aw0, cmul(v0[k], sb[i + k]));
+        au1 = csub(au1, cmul(v1[k], sa[i + k]));
+        aw1 = csub(aw1, cmul(v1[k], sb[i + k]));
       }
     }
     for (; i < nv; ++i) {
-      C<R> v = V[(int64_t)i * vstride + q];
-      au = csub(au, cmul(v, sa[i]));
-      aw = csub(aw, cmul(v, sb[i]));
+      C<R> x0 = V[(int64_t)i * vstride + q0], x1 = V[(int64_t)i * vstride + q1];
+      au0 = csub(au0, cmul(x0, sa[i]));
+      aw0 = csub(aw0, cmul(x0, sb[i]));
+      au1 = csub(au1, cmul(x1, sa[i]));
+      aw1 = csub(aw1, cmul(x1, sb[i]));
     }
     if (u) {
-      C<R> vj = cscale(au, inv);
-      u[q] = vj;
-      aw = csub(aw, cmul(vj, d));
+      C<R> vj0 = cscale(au0, inv);
+      u[q0] = vj0;
+      aw0 = csub(aw0, cmul(vj0, d));
+      if (two) {
+        C<R> vj1 = cscale(au1, inv);
+        u[q1] = vj1;
+        aw1 = csub(aw1, cmul(vj1, d));
+      }
     }
-    wout[q] = aw;
-    s[0] += (double)aw.x * aw.x + (double)aw.y * aw.y;
+    wout[q0] = aw0;
+    s[0] += (double)aw0.x * aw0.x + (double)aw0.y * aw0.y;
+    if (two) {
+      wout[q1] = aw1;
+      s[0] += (double)aw1.x * aw1.x + (double)aw1.y * aw1.y;
+    }
   }
   block_reduce_store<1>(s, npartial + (int64_t)col * nch + chunk);
 }
@@ -717,7 +737,8 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
   const int64_t nvec = ctx->npts * nrhs;
   int64_t maxlen = 0;
   for (auto& c : ctx->cols_host) maxlen = std::max(maxlen, c.len);
-  const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((4 * 148 + ncol - 1) / ncol, (maxlen + 1023) / 1024));
+  // point-sweep chunking: about 8 blocks of 256 threads per SM in all, at least 256 points per block
+  const int nch = (int)std::max<int64_t>(1, std::min<int64_t>((8 * 148 + ncol - 1) / ncol, (maxlen + 255) / 256));
   SolverWs<R> W;
   // dot-product chunking: P points per block (multiple of 256, 256..2048), about 600 blocks in all
   int P = (int)std::max<int64_t>(256, std::min<int64_t>(2048, (maxlen * ncol / 600) / 256 * 256));
@@ -804,7 +825,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         if (ctx->prof_on) {
           ctx->prof_work[PH_PRECOND] += net ? 70816.0 * ctx->npts * nrhs : 0.0;
           ctx->prof_work[PH_STENCIL] += 16.0 * ctx->npts * nrhs + 4.0 * ctx->npts;
-          ctx->prof_work[PH_ORTH] += (16.0 * (j > 0 ? j : 1) + 48.0) * ctx->npts * nrhs * (double)nact / ncol;
+          ctx->prof_work[PH_ORTH] += (32.0 * (j + 1) + 48.0) * ctx->npts * nrhs * (double)nact / ncol;
         }
         if (net) {
           for (int s = 0; s < ctx->nsys; ++s) {
@@ -856,6 +877,11 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         C<R>* Uj = W.V + (int64_t)j * nvec;  // v_0 at j = 0, else the pending u_j
         C<R>* Zj = W.Z + (int64_t)j * nvec;
         prof_begin(ctx, PH_PRECOND, stream);
+        if (ctx->prof_on) {
+          ctx->prof_work[PH_PRECOND] += net ? 70816.0 * ctx->npts * nrhs : 0.0;
+          ctx->prof_work[PH_STENCIL] += 16.0 * ctx->npts * nrhs + 4.0 * ctx->npts;
+          ctx->prof_work[PH_ORTH] += (16.0 * (j > 0 ? j : 1) + 48.0) * ctx->npts * nrhs * (double)nact / ncol;
+        }
         if (net) {
           for (int s = 0; s < ctx->nsys; ++s) {
             int64_t off = ctx->sys[s].off * nrhs;

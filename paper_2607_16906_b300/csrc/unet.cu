@@ -13,6 +13,8 @@
 //   CUDA-core kernels below cover the rest (first layer, up-convs, final 1x1).
 #include <math.h>
 
+#include <type_traits>
+
 #include "helm_internal.cuh"
 #include "unet.cuh"
 
@@ -178,6 +180,32 @@ __global__ void __launch_bounds__(CC_THREADS) k_up_cc(const T* __restrict__ in, 
 }
 
 // 2x2 max-pool, stride 2.
+// BF16 2x2 max-pool: one thread per output pixel and 8 channels (16-byte loads and stores).
+__global__ void k_pool_bf16x8(const __nv_bfloat16* __restrict__ in, __nv_bfloat16* __restrict__ out, int C, int B,
+                              int Ho, int Wo) {
+  int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int G = C / 8;
+  if (e >= (int64_t)B * Ho * Wo * G) return;
+  int g = (int)(e % G);
+  int64_t pix = e / G;
+  int x = (int)(pix % Wo);
+  int y = (int)((pix / Wo) % Ho);
+  int64_t b = pix / ((int64_t)Wo * Ho);
+  int Wi = 2 * Wo, Hi = 2 * Ho;
+  const __nv_bfloat16* p = in + ((b * Hi + 2 * y) * Wi + 2 * x) * C + g * 8;
+  uint4 q[4] = {*(const uint4*)p, *(const uint4*)(p + C), *(const uint4*)(p + (int64_t)Wi * C),
+                *(const uint4*)(p + (int64_t)Wi * C + C)};
+  const __nv_bfloat162* h0 = (const __nv_bfloat162*)&q[0];
+  const __nv_bfloat162* h1 = (const __nv_bfloat162*)&q[1];
+  const __nv_bfloat162* h2 = (const __nv_bfloat162*)&q[2];
+  const __nv_bfloat162* h3 = (const __nv_bfloat162*)&q[3];
+  uint4 r;
+  __nv_bfloat162* hr = (__nv_bfloat162*)&r;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) hr[k] = __hmax2(__hmax2(h0[k], h1[k]), __hmax2(h2[k], h3[k]));
+  *(uint4*)(out + pix * C + g * 8) = r;
+}
+
 template <typename T>
 __global__ void k_pool(const T* __restrict__ in, T* __restrict__ out, int C, int B, int Ho, int Wo) {
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -219,6 +247,19 @@ __global__ void k_pack_input(const C<R>* __restrict__ v, int64_t col_stride, con
     cc = (typename Acc<T>::A)chat[b * c_stride + q];
   }
   T* o = x0 + pix * S0;
+  if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+    if (S0 == 16) {  // one 32-byte row per pixel: two 16-byte stores
+      __align__(16) __nv_bfloat16 hv[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) hv[k] = __float2bfloat16_rn(0.0f);
+      hv[0] = __float2bfloat16_rn(re);
+      hv[1] = __float2bfloat16_rn(im);
+      hv[2] = __float2bfloat16_rn(cc);
+      ((uint4*)o)[0] = ((const uint4*)hv)[0];
+      ((uint4*)o)[1] = ((const uint4*)hv)[1];
+      return;
+    }
+  }
   store_act(o + 0, re);
   store_act(o + 1, im);
   store_act(o + 2, cc);
@@ -238,11 +279,23 @@ __global__ void k_final(const T* __restrict__ in, const typename Acc<T>::A* __re
   int b = (int)(e / ((int64_t)Nx * Ny));
   const T* ip = in + (((int64_t)b * Hp + y) * Wp + x) * 16;
   A y0 = bias[0], y1 = bias[1];
+  if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+    __align__(16) __nv_bfloat16 hv[16];
+    ((uint4*)hv)[0] = ((const uint4*)ip)[0];
+    ((uint4*)hv)[1] = ((const uint4*)ip)[1];
 #pragma unroll
-  for (int ci = 0; ci < 16; ++ci) {
-    A v = to_acc(ip[ci]);
-    y0 += v * W[ci * 2 + 0];
-    y1 += v * W[ci * 2 + 1];
+    for (int ci = 0; ci < 16; ++ci) {
+      A v = __bfloat162float(hv[ci]);
+      y0 += v * W[ci * 2 + 0];
+      y1 += v * W[ci * 2 + 1];
+    }
+  } else {
+#pragma unroll
+    for (int ci = 0; ci < 16; ++ci) {
+      A v = to_acc(ip[ci]);
+      y0 += v * W[ci * 2 + 0];
+      y1 += v * W[ci * 2 + 1];
+    }
   }
   double s = out_scale[b];
   C<R> o;
@@ -347,6 +400,14 @@ static helm_status up2(const helm_unet* net, int l, const T* in, T* out, int B, 
 
 template <typename T>
 static helm_status pool(const T* in, T* out, int C, int B, int Ho, int Wo, cudaStream_t st) {
+  if constexpr (std::is_same<T, __nv_bfloat16>::value) {
+    if (C % 8 == 0) {
+      int64_t n8 = (int64_t)B * Ho * Wo * (C / 8);
+      launch(k_pool_bf16x8, cdiv(n8, 256), 256, 0, st, in, out, C, B, Ho, Wo);
+      HELM_CK_LAUNCH();
+      return HELM_OK;
+    }
+  }
   int64_t n = (int64_t)B * Ho * Wo * C;
   launch(k_pool<T>, cdiv(n, 256), 256, 0, st, in, out, C, B, Ho, Wo);
   HELM_CK_LAUNCH();

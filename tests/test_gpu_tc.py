@@ -34,9 +34,9 @@ np.save({path!r}, np.concatenate(out))
 """
 
 
-def _run(path, disable):
+def _run(path, disable, disable_row=False):
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    env = dict(os.environ, HELM_DISABLE_TC="1" if disable else "0")
+    env = dict(os.environ, HELM_DISABLE_TC="1" if disable else "0", HELM_DISABLE_ROW="1" if disable_row else "0")
     r = subprocess.run([sys.executable, "-c", CHILD.format(root=root, path=path)], env=env, capture_output=True,
                        text=True, timeout=600)
     assert r.returncode == 0, r.stderr[-2000:]
@@ -44,10 +44,14 @@ def _run(path, disable):
 
 
 def test_tcgen05_convs_match_cuda_core_convs(tmp_path):
+    """Default tcgen05 path (row-tile kernels for the narrow layers, 9-box kernels for the rest), the
+    9-box kernels alone, and the CUDA-core kernels agree pairwise."""
     tc = _run(str(tmp_path / "tc.npy"), disable=False)
+    box = _run(str(tmp_path / "box.npy"), disable=False, disable_row=True)
     cc = _run(str(tmp_path / "cc.npy"), disable=True)
-    assert np.isfinite(tc).all()
+    assert np.isfinite(tc).all() and np.isfinite(box).all()
     n1 = 3 * (40 + 24) * (28 + 24)
     for seg in (slice(0, n1), slice(n1, None)):
-        e = np.linalg.norm(tc[seg] - cc[seg]) / np.linalg.norm(cc[seg])
-        assert e <= 1.5e-2, e
+        for a, b in ((tc, cc), (box, cc), (tc, box)):
+            e = np.linalg.norm(a[seg] - b[seg]) / np.linalg.norm(b[seg])
+            assert e <= 1.5e-2, e
