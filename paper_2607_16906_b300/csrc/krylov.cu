@@ -370,58 +370,98 @@ __global__ void k_dreduce(const double2* __restrict__ partial, int ndc, int ldq,
   }
 }
 
-// One thread per column: finalise column j-1 (when a pending vector exists), Givens on it, build
-// the partial column j and the sweep-B coefficients ca = a, cb = b (vector precision) and
-// sc = (1 / rho, d).
+// One block per column: finalise column j-1 (when a pending vector exists), Givens on it, build the
+// partial column j and the sweep-B coefficients ca = a, cb = b (vector precision) and
+// sc = (1 / rho, d).  The reductions run across the block; the sequential rotation of column j-1
+// runs on one thread with the column and the previous rotations staged in shared memory.
+constexpr int DC_THREADS = 256;
 template <typename R>
-__global__ void k_dcoef(int j, int nv, int has_u, int has_w, int ncol, int m, const double2* __restrict__ red,
-                        int ldq, double2* __restrict__ Rm, double* __restrict__ cs, double2* __restrict__ sn,
-                        double2* __restrict__ g, ColState* __restrict__ st, C<R>* __restrict__ ca,
-                        C<R>* __restrict__ cb, double2* __restrict__ sc, int* __restrict__ nactive,
-                        double breakdown_eps) {
-  int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= ncol) return;
+__global__ void __launch_bounds__(DC_THREADS) k_dcoef(int j, int nv, int has_u, int has_w, int ncol, int m,
+                                                      const double2* __restrict__ red, int ldq,
+                                                      double2* __restrict__ Rm, double* __restrict__ cs,
+                                                      double2* __restrict__ sn, double2* __restrict__ g,
+                                                      ColState* __restrict__ st, C<R>* __restrict__ ca,
+                                                      C<R>* __restrict__ cb, double2* __restrict__ sc,
+                                                      int* __restrict__ nactive, double breakdown_eps) {
+  const int col = blockIdx.x;
   ColState& S = st[col];
   if (!S.active) return;
+  extern __shared__ unsigned char dc_smem[];
+  double2* sR = (double2*)dc_smem;     // column j-1, nv + 1 entries
+  double2* sS = sR + (nv + 1);         // previous sines, nv entries
+  double* sC = (double*)(sS + nv);     // previous cosines, nv entries
+  __shared__ double s_rho, s_inv;
+  __shared__ double2 s_d;
+  __shared__ int s_active;
   const double2* ra = red + (int64_t)col * 2 * ldq;  // a_i, i < nv; ra[nv] = (u^H u, 0)
   const double2* rb = ra + ldq;                      // b_i, i < nv; rb[nv] = u^H w
-  double rho = 1.0;
-  if (has_u) {
-    double aa = 0;
-    for (int i = 0; i < nv; ++i) aa += ra[i].x * ra[i].x + ra[i].y * ra[i].y;
-    double r2 = ra[nv].x - aa;
-    rho = r2 > 0 ? sqrt(r2) : 0.0;
-    double2* Rc = Rm + ((int64_t)col * m + (j - 1)) * (m + 1);  // column j-1: partial (b, d) so far
-    for (int i = 0; i < nv; ++i) Rc[i] = cadd(Rc[i], ra[i]);
-    givens_update(j - 1, m, Rc, rho, cs + (int64_t)col * m, sn + (int64_t)col * m, g + (int64_t)col * (m + 1), S,
-                  breakdown_eps);
-    if (S.active && !has_w) {  // finalisation pass at the end of a cycle of m iterations
-      S.status = HELM_NOT_CONVERGED;
-      S.active = 0;
+  // |a|^2 and a^H b across the block
+  double v[3] = {0.0, 0.0, 0.0};
+  if (has_u)
+    for (int i = threadIdx.x; i < nv; i += DC_THREADS) {
+      double2 ai = ra[i], bi = rb[i];
+      v[0] += ai.x * ai.x + ai.y * ai.y;
+      double2 t = cdotc(ai, bi);
+      v[1] += t.x;
+      v[2] += t.y;
     }
-    if (!S.active) return;
+  __shared__ double red3[3];
+  block_reduce_store<3>(v, red3);
+  if (has_u) {
+    double2* Rc = Rm + ((int64_t)col * m + (j - 1)) * (m + 1);  // column j-1: partial (b, d) so far
+    for (int i = threadIdx.x; i < nv; i += DC_THREADS) {
+      sR[i] = cadd(Rc[i], ra[i]);
+      if (i < j - 1) {
+        sC[i] = cs[(int64_t)col * m + i];
+        sS[i] = sn[(int64_t)col * m + i];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double r2 = ra[nv].x - red3[0];
+      double rho = r2 > 0 ? sqrt(r2) : 0.0;
+      s_rho = rho;
+      givens_update(j - 1, m, sR, rho, sC, sS, g + (int64_t)col * (m + 1), S, breakdown_eps);
+      cs[(int64_t)col * m + j - 1] = sC[j - 1];
+      sn[(int64_t)col * m + j - 1] = sS[j - 1];
+      if (S.active && !has_w) {  // finalisation pass at the end of a cycle of m iterations
+        S.status = HELM_NOT_CONVERGED;
+        S.active = 0;
+      }
+      s_active = S.active;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv; i += DC_THREADS) Rc[i] = sR[i];
+    if (!s_active) return;
+  } else if (threadIdx.x == 0) {
+    s_rho = 1.0;
   }
   if (!has_w) return;
-  double2 d = make_double2(0, 0);
-  double inv = 1.0;
-  if (has_u) {
-    inv = rho > 0 ? 1.0 / rho : 0.0;
-    double2 t = rb[nv];  // u^H w
-    for (int i = 0; i < nv; ++i) t = csub(t, cdotc(ra[i], rb[i]));
-    d = cscale(t, inv);
+  if (threadIdx.x == 0) {
+    double inv = 1.0;
+    double2 d = make_double2(0, 0);
+    if (has_u) {
+      inv = s_rho > 0 ? 1.0 / s_rho : 0.0;
+      double2 t = csub(rb[nv], make_double2(red3[1], red3[2]));  // u^H w - a^H b
+      d = cscale(t, inv);
+    }
+    s_inv = inv;
+    s_d = d;
+    sc[col * 2] = make_double2(inv, 0.0);
+    sc[col * 2 + 1] = d;
+    atomicAdd(nactive, 1);
   }
+  __syncthreads();
   double2* Rj = Rm + ((int64_t)col * m + j) * (m + 1);  // partial column j
-  for (int i = 0; i < nv; ++i) Rj[i] = rb[i];
-  if (has_u) Rj[nv] = d;
   C<R>* cac = ca + (int64_t)col * ldq;
   C<R>* cbc = cb + (int64_t)col * ldq;
-  for (int i = 0; i < nv; ++i) {
-    cac[i] = mk<R>((R)ra[i].x, (R)ra[i].y);
-    cbc[i] = mk<R>((R)rb[i].x, (R)rb[i].y);
+  for (int i = threadIdx.x; i < nv; i += DC_THREADS) {
+    double2 ai = ra[i], bi = rb[i];
+    Rj[i] = bi;
+    cac[i] = mk<R>((R)ai.x, (R)ai.y);
+    cbc[i] = mk<R>((R)bi.x, (R)bi.y);
   }
-  sc[col * 2] = make_double2(inv, 0.0);
-  sc[col * 2 + 1] = d;
-  atomicAdd(nactive, 1);
+  if (has_u && threadIdx.x == 0) Rj[nv] = s_d;
 }
 
 // Sweep B: v_j = (u_j - V a) / rho written over u_j (slot j), u_{j+1} = w - V b - v_j d (slot j+1),
@@ -559,13 +599,33 @@ __global__ void __launch_bounds__(RED_THREADS) k_xupdate(const C<R>* __restrict_
     __syncthreads();
     for (int64_t p = a + threadIdx.x; p < b; p += RED_THREADS) {
       int64_t q = cd.off + p;
-      double2 acc = x[q];
-      for (int i = 0; i < kk; ++i) {
-        C<R> z = Z[(int64_t)(i0 + i) * zstride + q];
-        acc.x += (double)z.x * yc[i].x - (double)z.y * yc[i].y;
-        acc.y += (double)z.x * yc[i].y + (double)z.y * yc[i].x;
+      if constexpr (sizeof(R) == 4) {
+        // mixed path: the correction d = Z y in FP32 (four independent chains), added to x in FP64
+        float2 s0 = make_float2(0, 0), s1 = s0, s2 = s0, s3 = s0;
+        int i = 0;
+        for (; i + 4 <= kk; i += 4) {
+          float2 z0 = Z[(int64_t)(i0 + i) * zstride + q], z1 = Z[(int64_t)(i0 + i + 1) * zstride + q];
+          float2 z2 = Z[(int64_t)(i0 + i + 2) * zstride + q], z3 = Z[(int64_t)(i0 + i + 3) * zstride + q];
+          s0 = cadd(s0, cmul(z0, make_float2((float)yc[i].x, (float)yc[i].y)));
+          s1 = cadd(s1, cmul(z1, make_float2((float)yc[i + 1].x, (float)yc[i + 1].y)));
+          s2 = cadd(s2, cmul(z2, make_float2((float)yc[i + 2].x, (float)yc[i + 2].y)));
+          s3 = cadd(s3, cmul(z3, make_float2((float)yc[i + 3].x, (float)yc[i + 3].y)));
+        }
+        for (; i < kk; ++i)
+          s0 = cadd(s0, cmul(Z[(int64_t)(i0 + i) * zstride + q], make_float2((float)yc[i].x, (float)yc[i].y)));
+        double2 acc = x[q];
+        acc.x += (double)s0.x + (double)s1.x + (double)s2.x + (double)s3.x;
+        acc.y += (double)s0.y + (double)s1.y + (double)s2.y + (double)s3.y;
+        x[q] = acc;
+      } else {
+        double2 acc = x[q];
+        for (int i = 0; i < kk; ++i) {
+          C<R> z = Z[(int64_t)(i0 + i) * zstride + q];
+          acc.x += (double)z.x * yc[i].x - (double)z.y * yc[i].y;
+          acc.y += (double)z.x * yc[i].y + (double)z.y * yc[i].x;
+        }
+        x[q] = acc;
       }
-      x[q] = acc;
     }
   }
 }
@@ -750,7 +810,10 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
   const int ldq = m + 2;
   const size_t ds_smem = 2 * sizeof(C<R>) * P;
   const size_t db_smem = 2 * sizeof(C<R>) * m;
+  auto dc_smem = [](int nv) { return (size_t)(nv + 1) * 16 + (size_t)nv * 24; };
   if (dcgs2) {
+    if (dc_smem(m) > 48 * 1024)
+      HELM_CK(cudaFuncSetAttribute(k_dcoef<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dc_smem(m)));
     if (ds_smem > 48 * 1024)
       HELM_CK(cudaFuncSetAttribute(k_dsweepA<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ds_smem));
     if (db_smem > 48 * 1024)
@@ -904,7 +967,8 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         launch(k_dsweepA<R>, dgrid, MD_THREADS, ds_smem, stream, (const C<R>*)W.V, nvec, nv,
                (const C<R>*)(has_u ? Uj : nullptr), (const C<R>*)W.w, ctx->cols_dev, W.st, P, ndc, W.partial, ldq);
         launch(k_dreduce, ncol, 256, 0, stream, (const double2*)W.partial, ndc, ldq, nv, W.st, W.red);
-        launch(k_dcoef<R>, cdiv(ncol, 64), 64, 0, stream, j, nv, has_u, 1, ncol, m, (const double2*)W.red, ldq, W.Rm,
+        launch(k_dcoef<R>, ncol, DC_THREADS, dc_smem(nv), stream, j, nv, has_u, 1, ncol, m, (const double2*)W.red, ldq,
+               W.Rm,
                W.cs, W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps);
         launch(k_dsweepB<R>, vgrid, RED_THREADS, 2 * sizeof(C<R>) * nv, stream, (const C<R>*)W.V, nvec, nv,
                has_u ? Uj : nullptr, (const C<R>*)W.w, W.V + (int64_t)(j + 1) * nvec, (const C<R>*)W.ca,
@@ -929,7 +993,8 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
              (const C<R>*)(W.V + (int64_t)m * nvec), (const C<R>*)nullptr, ctx->cols_dev, W.st, P, ndc, W.partial,
              ldq);
       launch(k_dreduce, ncol, 256, 0, stream, (const double2*)W.partial, ndc, ldq, m, W.st, W.red);
-      launch(k_dcoef<R>, cdiv(ncol, 64), 64, 0, stream, m, m, 1, 0, ncol, m, (const double2*)W.red, ldq, W.Rm, W.cs,
+      launch(k_dcoef<R>, ncol, DC_THREADS, dc_smem(m), stream, m, m, 1, 0, ncol, m, (const double2*)W.red, ldq, W.Rm,
+             W.cs,
              W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps);
       HELM_CK_LAUNCH();
       prof_end(ctx, PH_ORTH, stream);
