@@ -41,13 +41,14 @@ struct RowCfg {
   static constexpr int W_BYTES = 9 * NSL * N * 16;
   static constexpr int STAGES_RAW = (100 * 1024 - W_BYTES) / STAGE_BYTES;
   static constexpr int STAGES = STAGES_RAW > 4 ? 4 : (STAGES_RAW < 2 ? 2 : STAGES_RAW);
-  static constexpr int TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
+  static constexpr int NACC = 4;  // TMEM accumulators: the MMA warp runs up to 4 tiles ahead
+  static constexpr int TMEM_COLS = NACC * N < 32 ? 32 : NACC * N;
   static constexpr int SMEM = STAGES * STAGE_BYTES + W_BYTES + N * 4 + 1024 + 256;
-  static constexpr int THREADS = 192;
+  static constexpr int THREADS = 320;  // producer, MMA issuer, two 4-warp epilogue groups
 };
 
 template <int N, int NSL>
-__global__ void __launch_bounds__(192, 1) k_conv_row(const __grid_constant__ CUtensorMap tA0,
+__global__ void __launch_bounds__(320, 1) k_conv_row(const __grid_constant__ CUtensorMap tA0,
                                                      const __grid_constant__ CUtensorMap tA1, RowArgs a) {
   using Cfg = RowCfg<N, NSL>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -57,8 +58,8 @@ __global__ void __launch_bounds__(192, 1) k_conv_row(const __grid_constant__ CUt
   uint64_t* full = (uint64_t*)(bsm + N + (N & 1));
   uint64_t* empty = full + Cfg::STAGES;
   uint64_t* tfull = empty + Cfg::STAGES;
-  uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  uint64_t* tempty = tfull + Cfg::NACC;
+  uint32_t* tmem_slot = (uint32_t*)(tempty + Cfg::NACC);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_row(const __grid_constant__ CUt
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < Cfg::NACC; ++k) {
       mbar_init(&tfull[k], 1);
       mbar_init(&tempty[k], 128);
     }
@@ -161,16 +162,20 @@ __global__ void __launch_bounds__(192, 1) k_conv_row(const __grid_constant__ CUt
         stage = 0;
         phase ^= 1;
       }
-      acc ^= 1;
-      if (acc == 0) acc_phase ^= 1;
+      if (++acc == Cfg::NACC) {
+        acc = 0;
+        acc_phase ^= 1;
+      }
     }
   } else {
-    // ---------------- epilogue (warps 2..5): TMEM lane = pixel of the row segment
+    // ---------------- epilogue: group e = 0 (warps 2..5) takes the CTA's even tiles, e = 1 (warps
+    // 6..9) the odd ones; TMEM lane = pixel of the row segment, accumulator = tile index mod 4
+    const int e = (warp - 2) >> 2;
     const int q = warp & 3;
     const int p = q * 32 + lane;
-    int acc = 0;
+    int acc = e;
     uint32_t acc_phase = 0;
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    for (int t = blockIdx.x + e * gridDim.x; t < a.ntiles; t += 2 * gridDim.x) {
       if (!mbar_wait(&tfull[acc], acc_phase, abort_flag, a.err, 14)) break;
       tc_fence_after();
       int b = t / (a.tiles_x * a.H);
@@ -198,8 +203,11 @@ __global__ void __launch_bounds__(192, 1) k_conv_row(const __grid_constant__ CUt
       }
       tc_fence_before();
       mbar_arrive(&tempty[acc]);
-      acc ^= 1;
-      if (acc == 0) acc_phase ^= 1;
+      acc += 2;
+      if (acc >= Cfg::NACC) {
+        acc -= Cfg::NACC;
+        acc_phase ^= 1;
+      }
     }
   }
   tc_fence_before();
@@ -272,6 +280,7 @@ static helm_status launch_row(const CUtensorMap& a0, const CUtensorMap& a1, cons
       by_regs = 65536 / (((fa.numRegs + 7) / 8) * 8 * Cfg::THREADS);
     per_sm = std::min(std::min(smem_sm / (Cfg::SMEM + 1024), 512 / Cfg::TMEM_COLS),
                       std::min(2048 / Cfg::THREADS, by_regs));
+    per_sm = std::max(1, per_sm);
     per_sm = std::max(1, per_sm);
   });
   HELM_CK(attr_err);
