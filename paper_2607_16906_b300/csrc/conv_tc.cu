@@ -294,7 +294,8 @@ bool conv_row_supported(int cin_total, int cout);
 helm_status conv_row_prepare(const double* master, int64_t m_w, int cin, int cin_pad, int cout, __nv_bfloat16** w,
                              cudaStream_t st);
 helm_status conv_row_forward(const __nv_bfloat16* wrow, const float* bias, int* err, const void* in0, int C0,
-                             const void* in1, int C1, void* out, int cout, int B, int H, int W, cudaStream_t st);
+                             const void* in1, int C1, void* out, int cout, int B, int H, int W, cudaStream_t st,
+                             const RowFinal* fin = nullptr);
 
 struct TcState {
   __nv_bfloat16* w[NUM_LAYERS] = {};
@@ -487,6 +488,22 @@ helm_status conv_tc_forward(const helm_unet* net, int l, const void* in0, int C0
 }
 
 // 2x2 stride-2 transposed conv on tensor cores: in [B][Hi][Wi][cin] -> out [B][2Hi][2Wi][cout].
+bool conv_tc_final_ready(const helm_unet* net) { return net->tc && net->tc->ok && net->tc->wrow[L_DEC1B]; }
+
+helm_status conv_tc_final(const helm_unet* net, const void* in, float2* z, const double* out_scale, int Nx, int Ny,
+                          int64_t zstride, int B, int H, int W, cudaStream_t st) {
+  const TcState& S = *net->tc;
+  RowFinal f;
+  f.wf = net->w32 + net->L.c_w[L_FINAL];  // [16][2] followed by the 2 biases
+  f.out_scale = out_scale;
+  f.z = z;
+  f.Nx = Nx;
+  f.Ny = Ny;
+  f.zstride = zstride;
+  return conv_row_forward(S.wrow[L_DEC1B], net->w32 + net->L.c_b[L_DEC1B], S.err, in, 16, nullptr, 0, nullptr, 16, B,
+                          H, W, st, &f);
+}
+
 helm_status conv_tc_up(const helm_unet* net, int l, const void* in, void* out, int B, int Hi, int Wi, cudaStream_t st) {
   const TcState& S = *net->tc;
   const LayerDesc& d = kLayers[l];

@@ -232,6 +232,17 @@ extern "C" helm_status helm_create(helm_ctx** out, int nsys, const helm_grid* gr
     }
   }
   for (int64_t i = 0; i < px; ++i) pf[i] = make_float2((float)pd[i].x, (float)pd[i].y);
+  // unit[base + i] = 1 where node i of that axis has s(i) = 1/s(i - 1/2) = 1/s(i + 1/2) = 1 exactly
+  // in FP32 (outside the PML), so the FP32 stencil may take its short form there
+  std::vector<unsigned char> unit(px, 0);
+  auto one = [](float2 v) { return v.x == 1.0f && v.y == 0.0f; };
+  for (auto& h : ctx->sys)
+    for (int axis = 0; axis < 2; ++axis) {
+      int N = axis == 0 ? h.Nx : h.Ny;
+      int64_t base = axis == 0 ? h.prof_x : h.prof_y;
+      for (int i = 0; i < N; ++i)
+        unit[base + i] = one(pf[base + i]) && one(pf[base + N + i]) && one(pf[base + N + i + 1]);
+    }
   cudaStream_t st = (cudaStream_t)stream;
   helm_status rc = HELM_OK;
   auto ck = [&](cudaError_t e, const char* what) {
@@ -243,6 +254,7 @@ extern "C" helm_status helm_create(helm_ctx** out, int nsys, const helm_grid* gr
   ck(cudaMalloc(&ctx->chat64, sizeof(double) * off), "cudaMalloc chat64");
   ck(cudaMalloc(&ctx->prof_d, sizeof(double2) * px), "cudaMalloc prof_d");
   ck(cudaMalloc(&ctx->prof_f, sizeof(float2) * px), "cudaMalloc prof_f");
+  ck(cudaMalloc(&ctx->unit_f, px), "cudaMalloc unit_f");
   ck(cudaMalloc(&ctx->flag_dev, sizeof(int) * 16), "cudaMalloc flag");
   if (rc != HELM_OK) {
     helm_destroy(ctx);
@@ -250,6 +262,7 @@ extern "C" helm_status helm_create(helm_ctx** out, int nsys, const helm_grid* gr
   }
   ck(cudaMemcpyAsync(ctx->prof_d, pd.data(), sizeof(double2) * px, cudaMemcpyHostToDevice, st), "copy prof_d");
   ck(cudaMemcpyAsync(ctx->prof_f, pf.data(), sizeof(float2) * px, cudaMemcpyHostToDevice, st), "copy prof_f");
+  ck(cudaMemcpyAsync(ctx->unit_f, unit.data(), px, cudaMemcpyHostToDevice, st), "copy unit_f");
   ck(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int) * 16, st), "memset flag");
   for (auto& h : ctx->sys) {
     const char* cb = (const char*)c_dev + h.off * (c_is_fp64 ? 8 : 4);
@@ -281,6 +294,7 @@ extern "C" helm_status helm_destroy(helm_ctx* ctx) {
   cudaFree(ctx->chat64);
   cudaFree(ctx->prof_d);
   cudaFree(ctx->prof_f);
+  cudaFree(ctx->unit_f);
   cudaFree(ctx->cols_dev);
   cudaFree(ctx->flag_dev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);

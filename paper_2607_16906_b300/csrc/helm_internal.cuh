@@ -95,6 +95,7 @@ struct helm_ctx {
   // per system 1-D profiles: s(node) and 1 / s(half node) in x and y, both precisions
   double2* prof_d = nullptr;
   float2* prof_f = nullptr;
+  unsigned char* unit_f = nullptr;  // per profile node: 1 where the FP32 stretch factors are all 1
   int64_t prof_len = 0;
   // per-nrhs column tables (rebuilt on demand)
   int cols_nrhs = -1;
@@ -127,6 +128,14 @@ int num_cols(const helm_ctx* ctx, int nrhs);
 // stencil.cu: y = A x (or A^H x) for all systems and right-hand sides
 template <typename R>
 helm_status apply_op(helm_ctx* ctx, const C<R>* x, C<R>* y, int nrhs, bool adjoint, cudaStream_t st);
+// TMA-tiled FP32 stencil (stencil_tma.cu): even Nx and 16-byte aligned x, y.  A pipeline timeout
+// is recorded in *err (code 21).
+bool stencil_tma_supported(int Nx, int Ny, const void* x, const void* y);
+helm_status stencil_tma(const float2* x, float2* y, const float* k2, const float2* px, const float2* py,
+                        const unsigned char* ux, const unsigned char* uy, int Nx, int Ny, int nrhs, float inv_h2,
+                        bool adjoint, int* err, cudaStream_t st);
+// HELM_TIMEOUT if a stencil launch recorded a TMA wait timeout since the last check (synchronises).
+helm_status stencil_check(helm_ctx* ctx, cudaStream_t st);
 // r = b - A x (FP64) and per-column ||r||^2, ||b||^2 into sums[col*2 + {0,1}] (device)
 helm_status residual_fp64(helm_ctx* ctx, const double2* x, const double2* b, double2* r, int nrhs,
                           double* sums, cudaStream_t st);

@@ -286,6 +286,70 @@ __global__ void k_givens(int j, int ncol, int m, const double* __restrict__ npar
 // The second Gram-Schmidt pass of every vector is thus the first half of the next sweep A:
 // 16 nv + 48 bytes per point and iteration instead of 32 nv + 48.
 
+// conj(v) * u and conj(v) * w accumulated for the two points packed in v, u, w (float4 = 2 complex).
+__device__ __forceinline__ void dot2_acc(float* acc, float4 v, float4 u, float4 w) {
+  acc[0] += v.x * u.x + v.y * u.y + v.z * u.z + v.w * u.w;
+  acc[1] += v.x * u.y - v.y * u.x + v.z * u.w - v.w * u.z;
+  acc[2] += v.x * w.x + v.y * w.y + v.z * w.z + v.w * w.w;
+  acc[3] += v.x * w.y - v.y * w.x + v.z * w.w - v.w * w.z;
+}
+
+// Sweep-A dots of the chunk [base, base + np) for basis vectors (2 warp + 16 k, +1): pu[i] = v_i^H u,
+// pw[i] = v_i^H w.  V + i vstride + base is 16-byte aligned for every i.
+__device__ __forceinline__ void dsweepA_pairs(const float2* __restrict__ V, int64_t vstride, int nv, int64_t base,
+                                              int np, const float4* __restrict__ us4,
+                                              const float4* __restrict__ ws4, int warp, int lane,
+                                              double2* __restrict__ pu, double2* __restrict__ pw) {
+  const int n2 = np >> 1;
+  for (int i0 = 2 * warp; i0 < nv; i0 += 2 * (MD_THREADS / 32)) {
+    const bool has1 = i0 + 1 < nv;
+    const float4* v0 = (const float4*)(V + (int64_t)i0 * vstride + base);
+    const float4* v1 = has1 ? (const float4*)(V + (int64_t)(i0 + 1) * vstride + base) : v0;
+    float a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, b0[4] = {0, 0, 0, 0}, b1[4] = {0, 0, 0, 0};
+    int q = lane;
+    for (; q + 32 < n2; q += 64) {
+      const float4 x0 = __ldcg(v0 + q), x1 = __ldcg(v0 + q + 32);
+      const float4 y0 = __ldcg(v1 + q), y1 = __ldcg(v1 + q + 32);
+      const float4 u0 = us4[q], u1 = us4[q + 32], w0 = ws4[q], w1 = ws4[q + 32];
+      dot2_acc(a0, x0, u0, w0);
+      dot2_acc(a1, x1, u1, w1);
+      dot2_acc(b0, y0, u0, w0);
+      dot2_acc(b1, y1, u1, w1);
+    }
+    for (; q < n2; q += 32) {
+      const float4 x0 = __ldcg(v0 + q), y0 = __ldcg(v1 + q);
+      const float4 u0 = us4[q], w0 = ws4[q];
+      dot2_acc(a0, x0, u0, w0);
+      dot2_acc(b0, y0, u0, w0);
+    }
+    if ((np & 1) && lane == 0) {  // odd chunk length: the last point alone
+      const float2 x = ((const float2*)v0)[np - 1], y = ((const float2*)v1)[np - 1];
+      const float2 u = ((const float2*)us4)[np - 1], w = ((const float2*)ws4)[np - 1];
+      const float4 xv = make_float4(x.x, x.y, 0.f, 0.f), yv = make_float4(y.x, y.y, 0.f, 0.f);
+      const float4 uv = make_float4(u.x, u.y, 0.f, 0.f), wv = make_float4(w.x, w.y, 0.f, 0.f);
+      dot2_acc(a0, xv, uv, wv);
+      dot2_acc(b0, yv, uv, wv);
+    }
+    double d[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      d[k] = (double)a0[k] + a1[k];
+      d[4 + k] = (double)b0[k] + b1[k];
+    }
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) d[k] += __shfl_down_sync(0xffffffffu, d[k], o);
+    if (lane == 0) {
+      pu[i0] = make_double2(d[0], d[1]);
+      pw[i0] = make_double2(d[2], d[3]);
+      if (has1) {
+        pu[i0 + 1] = make_double2(d[4], d[5]);
+        pw[i0 + 1] = make_double2(d[6], d[7]);
+      }
+    }
+  }
+}
+
 // partial[((col * ndc + chunk) * 2 + t) * ldq + i]: t = 0 dots with u (i < nv; i = nv: u^H u),
 // t = 1 dots with w (i < nv; i = nv: u^H w).  u or w may be null.
 template <typename R>
@@ -308,7 +372,7 @@ __global__ void __launch_bounds__(MD_THREADS) k_dsweepA(const C<R>* __restrict__
     return;
   }
   const int np = (int)min((int64_t)P, cd.len - a);
-  extern __shared__ unsigned char ds_smem[];
+  extern __shared__ __align__(16) unsigned char ds_smem[];
   C<R>* us = (C<R>*)ds_smem;
   C<R>* ws = us + P;
   double uu = 0, uwx = 0, uwy = 0;
@@ -330,6 +394,14 @@ __global__ void __launch_bounds__(MD_THREADS) k_dsweepA(const C<R>* __restrict__
     pw[nv] = make_double2(red3[1], red3[2]);
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if constexpr (sizeof(R) == 4) {
+    // 16-byte loads (two points) when every basis column of this chunk starts 16-byte aligned; each
+    // warp takes two basis vectors so that the staged u/w values are read once for both
+    if ((vstride & 1) == 0 && ((cd.off + a) & 1) == 0 && ((uintptr_t)V & 15) == 0) {
+      dsweepA_pairs(V, vstride, nv, cd.off + a, np, (const float4*)us, (const float4*)ws, warp, lane, pu, pw);
+      return;
+    }
+  }
   for (int i = warp; i < nv; i += MD_THREADS / 32) {
     const C<R>* vi = V + (int64_t)i * vstride + cd.off + a;
     C<R> su = mk<R>(0, 0), sw = mk<R>(0, 0), su2 = mk<R>(0, 0), sw2 = mk<R>(0, 0);
@@ -466,6 +538,76 @@ __global__ void __launch_bounds__(DC_THREADS) k_dcoef(int j, int nv, int has_u, 
 
 // Sweep B: v_j = (u_j - V a) / rho written over u_j (slot j), u_{j+1} = w - V b - v_j d (slot j+1),
 // and per-chunk |u_{j+1}|^2 partials.
+// v -= x * c for the two complex values packed in v and x.
+__device__ __forceinline__ float4 cmsub2(float4 v, float4 x, float2 c) {
+  v.x -= x.x * c.x - x.y * c.y;
+  v.y -= x.x * c.y + x.y * c.x;
+  v.z -= x.z * c.x - x.w * c.y;
+  v.w -= x.z * c.y + x.w * c.x;
+  return v;
+}
+
+// Sweep-B update over point pairs (16-byte loads) of one column chunk; returns the chunk's ||w'||^2.
+// Requires V + cd.off and every basis column 16-byte aligned.  An odd last point is taken by
+// thread 0 of the last chunk.
+__device__ __forceinline__ double dsweepB_pairs(const float2* __restrict__ V, int64_t vstride, int nv,
+                                                float2* __restrict__ u, const float2* __restrict__ w,
+                                                float2* __restrict__ wout, const float2* sa, const float2* sb,
+                                                float inv, float2 d, const ColDesc& cd, int nch, int chunk) {
+  const int64_t npair = cd.len >> 1, vs4 = vstride >> 1;
+  int64_t qa, qb;
+  chunk_range(npair, nch, chunk, qa, qb);
+  const float4* V4 = (const float4*)(V + cd.off);
+  float4* u4 = u ? (float4*)(u + cd.off) : nullptr;
+  const float4* w4 = (const float4*)(w + cd.off);
+  float4* o4 = (float4*)(wout + cd.off);
+  double s = 0.0;
+  for (int64_t q = qa + threadIdx.x; q < qb; q += RED_THREADS) {
+    float4 au = u4 ? u4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 aw = w4[q];
+    int i = 0;
+    for (; i + 8 <= nv; i += 8) {
+      float4 x[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) x[k] = __ldcg(V4 + (int64_t)(i + k) * vs4 + q);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        au = cmsub2(au, x[k], sa[i + k]);
+        aw = cmsub2(aw, x[k], sb[i + k]);
+      }
+    }
+    for (; i < nv; ++i) {
+      const float4 x = __ldcg(V4 + (int64_t)i * vs4 + q);
+      au = cmsub2(au, x, sa[i]);
+      aw = cmsub2(aw, x, sb[i]);
+    }
+    if (u4) {
+      const float4 vj = make_float4(au.x * inv, au.y * inv, au.z * inv, au.w * inv);
+      u4[q] = vj;
+      aw = cmsub2(aw, vj, d);
+    }
+    o4[q] = aw;
+    s += (double)aw.x * aw.x + (double)aw.y * aw.y + (double)aw.z * aw.z + (double)aw.w * aw.w;
+  }
+  if ((cd.len & 1) && chunk == nch - 1 && threadIdx.x == 0) {
+    const int64_t p = cd.len - 1;
+    float2 au = u ? u[cd.off + p] : make_float2(0.f, 0.f), aw = w[cd.off + p];
+    for (int i = 0; i < nv; ++i) {
+      const float2 x = V[(int64_t)i * vstride + cd.off + p];
+      au = csub(au, cmul(x, sa[i]));
+      aw = csub(aw, cmul(x, sb[i]));
+    }
+    if (u) {
+      const float2 vj = cscale(au, inv);
+      u[cd.off + p] = vj;
+      aw = csub(aw, cmul(vj, d));
+    }
+    wout[cd.off + p] = aw;
+    s += (double)aw.x * aw.x + (double)aw.y * aw.y;
+  }
+  return s;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(RED_THREADS) k_dsweepB(const C<R>* __restrict__ V, int64_t vstride, int nv,
                                                          C<R>* __restrict__ u, const C<R>* __restrict__ w,
@@ -476,7 +618,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_dsweepB(const C<R>* __restrict_
                                                          double* __restrict__ npartial) {
   int col = blockIdx.y, chunk = blockIdx.x;
   if (!st[col].active) return;
-  extern __shared__ unsigned char db_smem[];
+  extern __shared__ __align__(16) unsigned char db_smem[];
   C<R>* sa = (C<R>*)db_smem;
   C<R>* sb = sa + nv;
   for (int i = threadIdx.x; i < nv; i += RED_THREADS) {
@@ -488,8 +630,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_dsweepB(const C<R>* __restrict_
   const C<R> d = mk<R>((R)sc[col * 2 + 1].x, (R)sc[col * 2 + 1].y);
   ColDesc cd = cols[col];
   int64_t a, b;
-  chunk_range(cd.len, nch, chunk, a, b);
   double s[1] = {0.0};
+  if constexpr (sizeof(R) == 4) {
+    if ((vstride & 1) == 0 && (cd.off & 1) == 0 && ((uintptr_t)V & 15) == 0) {
+      s[0] = dsweepB_pairs(V, vstride, nv, u, w, wout, sa, sb, inv, d, cd, nch, chunk);
+      block_reduce_store<1>(s, npartial + (int64_t)col * nch + chunk);
+      return;
+    }
+  }
+  chunk_range(cd.len, nch, chunk, a, b);
   // two points per thread per pass: two independent load streams over the basis
   for (int64_t p0 = a + threadIdx.x; p0 < b; p0 += 2 * RED_THREADS) {
     const int64_t p1 = p0 + RED_THREADS;
@@ -1009,6 +1158,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
     HELM_CK(cudaStreamSynchronize(stream));
     prof_collect(ctx);
     if (net) HELM_TRY(conv_tc_check(net, stream));
+    HELM_TRY(stencil_check(ctx, stream));
     for (int c = 0; c < ncol; ++c) {
       if (done[c]) continue;
       inf[c].iters += h_st[c].k;

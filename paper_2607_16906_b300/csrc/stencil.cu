@@ -10,6 +10,7 @@
 #include <mutex>
 
 #include "helm_internal.cuh"
+#include "stencil_point.cuh"
 
 namespace helm {
 
@@ -24,22 +25,6 @@ __device__ __forceinline__ C<R> ld_u(const C<R>* __restrict__ x, int j, int i, i
   return v;
 }
 
-// Point update: -(1/h^2)[s_y(j)((uE-uC)/s_x(i+1/2) - (uC-uW)/s_x(i-1/2))
-//                      + s_x(i)((uN-uC)/s_y(j+1/2) - (uC-uS)/s_y(j-1/2))] - s_x s_y k^2 uC
-template <typename R>
-__device__ __forceinline__ C<R> stencil_point(C<R> uC, C<R> uE, C<R> uW, C<R> uN, C<R> uS, C<R> sxi, C<R> ixm,
-                                              C<R> ixp, C<R> syj, C<R> iym, C<R> iyp, R k2, R inv_h2) {
-  C<R> fx = csub(cmul(csub(uE, uC), ixp), cmul(csub(uC, uW), ixm));
-  C<R> fy = csub(cmul(csub(uN, uC), iyp), cmul(csub(uC, uS), iym));
-  C<R> acc = cadd(cmul(syj, fx), cmul(sxi, fy));
-  C<R> sxy = cmul(sxi, syj);
-  C<R> diag = cmul(sxy, uC);
-  C<R> r;
-  r.x = -acc.x * inv_h2 - k2 * diag.x;
-  r.y = -acc.y * inv_h2 - k2 * diag.y;
-  return r;
-}
-
 template <typename R, bool ADJ>
 __global__ void __launch_bounds__(STENCIL_THREADS) k_stencil(const C<R>* __restrict__ x, C<R>* __restrict__ y,
                                                              const R* __restrict__ k2, const C<R>* __restrict__ px,
@@ -51,6 +36,7 @@ __global__ void __launch_bounds__(STENCIL_THREADS) k_stencil(const C<R>* __restr
   const C<R>* xr = x + blockIdx.z * rhs_stride;
   C<R>* yr = y + blockIdx.z * rhs_stride;
   const C<R> sxi = px[i], ixm = px[Nx + i], ixp = px[Nx + i + 1];
+  const bool xunit = unit_c<R>(sxi) && unit_c<R>(ixm) && unit_c<R>(ixp);
   C<R> uS = ld_u<R, ADJ>(xr, j0 - 1, i, Nx, Ny);
   C<R> uC = ld_u<R, ADJ>(xr, j0, i, Nx, Ny);
 #pragma unroll
@@ -60,8 +46,10 @@ __global__ void __launch_bounds__(STENCIL_THREADS) k_stencil(const C<R>* __restr
     C<R> uN = ld_u<R, ADJ>(xr, j + 1, i, Nx, Ny);
     C<R> uW = ld_u<R, ADJ>(xr, j, i - 1, Nx, Ny);
     C<R> uE = ld_u<R, ADJ>(xr, j, i + 1, Nx, Ny);
-    C<R> out = stencil_point<R>(uC, uE, uW, uN, uS, sxi, ixm, ixp, py[j], py[Ny + j], py[Ny + j + 1],
-                                k2[(int64_t)j * Nx + i], inv_h2);
+    const C<R> syj = py[j], iym = py[Ny + j], iyp = py[Ny + j + 1];
+    const R kk = k2[(int64_t)j * Nx + i];
+    C<R> out = stencil_point_any<R>(xunit, unit_c<R>(syj) && unit_c<R>(iym) && unit_c<R>(iyp), uC, uE, uW, uN, uS,
+                                    sxi, ixm, ixp, syj, iym, iyp, kk, inv_h2);
     if (ADJ) out.y = -out.y;
     yr[(int64_t)j * Nx + i] = out;
     uS = uC;
@@ -85,6 +73,7 @@ __global__ void __launch_bounds__(STENCIL_THREADS) k_residual(const C<R>* __rest
   double sr = 0.0, sb = 0.0;
   if (i < Nx) {
     const C<R> sxi = px[i], ixm = px[Nx + i], ixp = px[Nx + i + 1];
+    const bool xunit = unit_c<R>(sxi) && unit_c<R>(ixm) && unit_c<R>(ixp);
     C<R> uS = ld_u<R, false>(xr, j0 - 1, i, Nx, Ny);
     C<R> uC = ld_u<R, false>(xr, j0, i, Nx, Ny);
 #pragma unroll
@@ -95,8 +84,9 @@ __global__ void __launch_bounds__(STENCIL_THREADS) k_residual(const C<R>* __rest
       C<R> uW = ld_u<R, false>(xr, j, i - 1, Nx, Ny);
       C<R> uE = ld_u<R, false>(xr, j, i + 1, Nx, Ny);
       int64_t idx = (int64_t)j * Nx + i;
-      C<R> Au = stencil_point<R>(uC, uE, uW, uN, uS, sxi, ixm, ixp, py[j], py[Ny + j], py[Ny + j + 1], k2[idx],
-                                 inv_h2);
+      const C<R> syj = py[j], iym = py[Ny + j], iyp = py[Ny + j + 1];
+      C<R> Au = stencil_point_any<R>(xunit, unit_c<R>(syj) && unit_c<R>(iym) && unit_c<R>(iyp), uC, uE, uW, uN, uS,
+                                     sxi, ixm, ixp, syj, iym, iyp, k2[idx], inv_h2);
       C<R> bv = br[idx];
       C<R> res = csub(bv, Au);
       rr[idx] = res;
@@ -163,8 +153,14 @@ helm_status apply_op(helm_ctx* ctx, const C<R>* x, C<R>* y, int nrhs, bool adjoi
     C<R>* ys = y + s.off * nrhs;
     const R* k2 = fp64 ? (const R*)(ctx->k2d + s.off) : (const R*)(ctx->k2f + s.off);
     const C<R>* pr = fp64 ? (const C<R>*)ctx->prof_d : (const C<R>*)ctx->prof_f;
-    dim3 grid(cdiv(s.Nx, STENCIL_THREADS), cdiv(s.Ny, STENCIL_ROWS), nrhs);
     R inv_h2 = (R)(1.0 / (s.h * s.h));
+    if (!fp64 && stencil_tma_supported(s.Nx, s.Ny, xs, ys)) {
+      HELM_TRY(stencil_tma((const float2*)xs, (float2*)ys, (const float*)k2, (const float2*)pr + s.prof_x,
+                           (const float2*)pr + s.prof_y, ctx->unit_f + s.prof_x, ctx->unit_f + s.prof_y, s.Nx, s.Ny,
+                           nrhs, (float)inv_h2, adjoint, ctx->flag_dev + 2, st));
+      continue;
+    }
+    dim3 grid(cdiv(s.Nx, STENCIL_THREADS), cdiv(s.Ny, STENCIL_ROWS), nrhs);
     if (adjoint)
       launch(k_stencil<R, true>, grid, STENCIL_THREADS, 0, st, xs, ys, k2, pr + s.prof_x, pr + s.prof_y, s.Nx, s.Ny,
                                                            s.n, inv_h2);

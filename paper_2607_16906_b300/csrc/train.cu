@@ -513,7 +513,7 @@ static helm_status loss_grad_impl(helm_ctx* ctx, helm_unet* net, const C<R>* b, 
   double* coef = sums + 2 * B;
   HELM_TRY(col_norm2<R>(ctx, b, 1, nb2, st));
   launch(k_alpha_b, cdiv(B, 64), 64, 0, st, (const double*)nb2, B, s0.n, s0.h * s0.h, in_s, out_s);
-  HELM_TRY(unet_precondition<R>(ctx, net, 0, b, u, B, in_s, out_s, st, s0.n));
+  HELM_TRY(unet_precondition<R>(ctx, net, 0, b, u, B, in_s, out_s, st, s0.n, /*keep_acts=*/true));
   HELM_TRY(residual_op<R>(ctx, u, b, r, 1, sums, st));
   HELM_TRY(apply_op<R>(ctx, r, ahr, 1, true, st));
   launch(k_loss_coef, cdiv(B, 64), 64, 0, st, (const double*)sums, (const double*)out_s, B, coef);

@@ -415,7 +415,7 @@ static helm_status pool(const T* in, T* out, int C, int B, int Ho, int Wo, cudaS
 }
 
 template <typename T>
-helm_status unet_body(const helm_unet* net, UnetBuffers::Set& S, int B, cudaStream_t st) {
+helm_status unet_body(const helm_unet* net, UnetBuffers::Set& S, int B, cudaStream_t st, bool skip_last) {
   int H = S.Hp, W = S.Wp;
   T** a = (T**)S.a;
   HELM_TRY(conv3<T>(net, L_ENC1A, a[A_X0], 3, X0_CH, nullptr, 0, 0, a[A_E1A], B, H, W, st));
@@ -437,13 +437,15 @@ helm_status unet_body(const helm_unet* net, UnetBuffers::Set& S, int B, cudaStre
   HELM_TRY(conv3<T>(net, L_DEC2B, a[A_D2A], 32, 32, nullptr, 0, 0, a[A_D2B], B, H / 2, W / 2, st));
   HELM_TRY(up2<T>(net, L_UP1, a[A_D2B], a[A_U1], B, H, W, st));
   HELM_TRY(conv3<T>(net, L_DEC1A, a[A_S1], 16, 16, a[A_U1], 16, 16, a[A_D1A], B, H, W, st));
+  if (skip_last) return HELM_OK;
   HELM_TRY(conv3<T>(net, L_DEC1B, a[A_D1A], 16, 16, nullptr, 0, 0, a[A_D1B], B, H, W, st));
   return HELM_OK;
 }
 
 template <typename R>
 helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
-                              const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride) {
+                              const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride,
+                              bool keep_acts) {
   using T = typename std::conditional<sizeof(R) == 8, double, __nv_bfloat16>::type;
   const SysHost& s = ctx->sys[sys];
   int Hp = (s.Ny + 7) / 8 * 8, Wp = (s.Nx + 7) / 8 * 8;
@@ -461,7 +463,16 @@ helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, cons
          X0_CH,
                                                       a[A_X0]);
   HELM_CK_LAUNCH();
-  HELM_TRY(unet_body<T>(net, S, B, st));
+  // BF16 path with the row kernels: the last conv, the final 1x1 conv and the output scaling run as
+  // one kernel (the 16-channel activation of the last layer is never stored)
+  bool fused = false;
+  if constexpr (sizeof(R) == 4)
+    fused = !keep_acts && conv_tc_enabled<T>(net, L_DEC1B, Hp, Wp) && conv_tc_final_ready(net);
+  HELM_TRY(unet_body<T>(net, S, B, st, fused));
+  if constexpr (sizeof(R) == 4) {
+    if (fused)
+      return conv_tc_final(net, a[A_D1A], (float2*)z, out_scale, s.Nx, s.Ny, s.n, B, Hp, Wp, st);
+  }
   const auto* w = cc_weights<T>(net);
   int64_t nout = (int64_t)B * s.Ny * s.Nx;
   launch(k_final<T, R>, cdiv(nout, 256), 256, 0, st, a[A_D1B], w + net->L.c_w[L_FINAL], w + net->L.c_b[L_FINAL],
@@ -471,9 +482,9 @@ helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, cons
 }
 
 template helm_status unet_precondition<float>(helm_ctx*, const helm_unet*, int, const float2*, float2*, int,
-                                              const double*, const double*, cudaStream_t, int64_t);
+                                              const double*, const double*, cudaStream_t, int64_t, bool);
 template helm_status unet_precondition<double>(helm_ctx*, const helm_unet*, int, const double2*, double2*, int,
-                                               const double*, const double*, cudaStream_t, int64_t);
+                                               const double*, const double*, cudaStream_t, int64_t, bool);
 
 // in_scale = alpha = sqrt(n) / ||v||, out_scale = h^2 / alpha (0 for a zero column).  The h^2 makes
 // the network approximate the inverse of the dimensionless operator h^2 A (O(1) entries, as in the

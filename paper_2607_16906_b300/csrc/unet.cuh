@@ -53,15 +53,29 @@ helm_status conv_tc_forward(const helm_unet* net, int layer, const void* in0, in
                             void* out, int B, int H, int W, cudaStream_t st);
 helm_status conv_tc_up(const helm_unet* net, int layer, const void* in, void* out, int B, int Hi, int Wi,
                        cudaStream_t st);
+// Last 3x3 conv (16 -> 16, ReLU) with the final 1x1 conv, the output scale and the crop to the
+// physical grid fused into its epilogue (inference only: the activation is not stored).
+struct RowFinal {
+  const float* wf;  // [16][2] weights, then the 2 biases
+  const double* out_scale;
+  float2* z;
+  int Nx, Ny;
+  int64_t zstride;
+};
+bool conv_tc_final_ready(const helm_unet* net);
+helm_status conv_tc_final(const helm_unet* net, const void* in, float2* z, const double* out_scale, int Nx, int Ny,
+                          int64_t zstride, int B, int H, int W, cudaStream_t st);
 // HELM_TIMEOUT if a tcgen05 conv kernel recorded a pipeline timeout since the last check (synchronises).
 helm_status conv_tc_check(const helm_unet* net, cudaStream_t st);
 
 // z = out_scale * N(in_scale * v, c) for B columns of system `sys` (column stride n_sys).  Velocity
 // channel: c of system `sys` for every column (c_stride = 0), or of consecutive equal-size systems
-// (c_stride = n_sys, one system per column, as in training batches).
+// (c_stride = n_sys, one system per column, as in training batches).  keep_acts: every activation
+// stays in the buffers for a backward pass (no fused last layer).
 template <typename R>
 helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
-                              const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride);
+                              const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride,
+                              bool keep_acts = false);
 
 // Element types of the two network paths: activations T, accumulation / weights A.
 template <typename T> struct Acc;

@@ -51,8 +51,9 @@ def draw_sources(batch, nx, p, rng, p_gauss=0.6, p_point=0.3):
 
 
 def train(steps=3000, grids=((128, 64),), p=16, ppw=10.0, lr_max=1e-3, lr_min=1e-5, wd=0.01, clip=1.0, seed=42,
-          nctx=8, init=None, log_every=50, verbose=True, p_gauss=0.6, p_point=0.3):
-    """AdamW on eq. 9 over batches cycling through `grids` = ((interior side, batch size), ...)."""
+          nctx=8, init=None, log_every=50, verbose=True, p_gauss=0.6, p_point=0.3, checkpoint=None, save_every=0):
+    """AdamW on eq. 9 over batches cycling through `grids` = ((interior side, batch size), ...).
+    With `checkpoint` and `save_every` > 0 the weights are also written there every `save_every` steps."""
     rng = synth.rng_for(seed)
     theta = init if init is not None else synth.kaiming_uniform_params(helm.weight_segments(), seed)
     net = helm.UNet(theta)
@@ -71,7 +72,17 @@ def train(steps=3000, grids=((128, 64),), p=16, ppw=10.0, lr_max=1e-3, lr_min=1e
             log.append({"step": it, "loss": loss, "grad_norm": gn, "lr": lr, "s": time.time() - t0})
             if verbose:
                 print(f"step {it:5d} loss {loss:.4f} |g| {gn:.3g} lr {lr:.2e} {time.time() - t0:.1f}s", flush=True)
+        if checkpoint and save_every > 0 and (it + 1) % save_every == 0:
+            save_weights(checkpoint, net.weights())
     return net.weights(), log
+
+
+def save_weights(path, w):
+    """Write weights atomically (temporary file, then rename)."""
+    os.makedirs(os.path.dirname(os.path.abspath(path)), exist_ok=True)
+    tmp = path + ".tmp.npy"
+    np.save(tmp, w)
+    os.replace(tmp, path)
 
 
 def main():
@@ -86,13 +97,13 @@ def main():
     ap.add_argument("--out", required=True)
     ap.add_argument("--log", default=None)
     ap.add_argument("--init", default=None)
+    ap.add_argument("--save-every", type=int, default=0, help="also write --out every N steps")
     a = ap.parse_args()
     init = np.load(a.init) if a.init else None
     grids = tuple(tuple(int(v) for v in g.split("x")) for g in a.grids.split(","))
     w, log = train(steps=a.steps, grids=grids, p=a.pml, lr_max=a.lr, init=init, nctx=a.nctx, p_gauss=a.p_gauss,
-                   p_point=a.p_point)
-    os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
-    np.save(a.out, w)
+                   p_point=a.p_point, checkpoint=a.out, save_every=a.save_every)
+    save_weights(a.out, w)
     if a.log:
         with open(a.log, "w") as f:
             json.dump(log, f)

@@ -55,6 +55,26 @@ def test_fp32_stencil_matches_oracle(helm):
             assert np.abs(g[k] - r[k]).max() <= 2e-6 * np.abs(r[k]).max()
 
 
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_fp32_stencil_segments_and_fallback(helm, adjoint):
+    """FP32 stencil and adjoint: even-width systems take the TMA-tiled kernel (ragged last tile in x
+    and y, a width of exactly one tile, zero-filled halo at every edge), with the k^2 tile staged by
+    TMA (widths 64 and 100 at 16-byte aligned offsets) or read from global memory (width 114, 30);
+    the odd-width system takes the one-point-per-thread kernel."""
+    probs = small_problems(((60, 5, 2), (80, 30, 10), (100, 37, 7), (20, 14, 5), (13, 9, 3)), seed=23)
+    nrhs = 3
+    ctx = make_ctx(probs)
+    per, flat = random_batch(probs, nrhs, 31, np.complex64)
+    x = to_dev(flat, torch.complex64)
+    y = torch.empty_like(x)
+    helm.helm_apply(ctx, x, y, nrhs, adjoint=adjoint)
+    got = split(y.cpu().numpy().astype(np.complex128), probs, nrhs)
+    ref = _oracle_apply(probs, [a.astype(np.complex128) for a in per], adjoint)
+    for g, r in zip(got, ref):
+        for k in range(nrhs):
+            assert np.abs(g[k] - r[k]).max() <= 2e-6 * np.abs(r[k]).max()
+
+
 def test_adjoint_dot_product_on_gpu(helm):
     probs = small_problems()
     ctx = make_ctx(probs)
