@@ -188,22 +188,23 @@ __global__ void __launch_bounds__(RED_THREADS) k_maxpy(const C<R>* __restrict__ 
 
 // Rotate Hessenberg column j (entries 0..j in Rc, subdiagonal hn real >= 0) by the previous
 // rotations, form the new one, update g and the column state (estimate, k, status, active).
-__device__ void givens_update(int j, int m, double2* __restrict__ Rc, double hn, double* __restrict__ csc,
-                              double2* __restrict__ snc, double2* __restrict__ gc, ColState& S,
-                              double breakdown_eps) {
-  double hmax = S.hscale;
-  for (int i = 0; i <= j; ++i) hmax = fmax(hmax, hypot(Rc[i].x, Rc[i].y));
-  hmax = fmax(hmax, hn);
+// colmax2 = max_{i <= j} |Rc[i]|^2 of the unrotated column (computed by the caller, in parallel where
+// it can).  The rotations form a chain through the entry carried from row i to row i + 1, which
+// stays in a register.
+__device__ void givens_update(int j, int m, double2* __restrict__ Rc, double hn, double colmax2,
+                              double* __restrict__ csc, double2* __restrict__ snc, double2* __restrict__ gc,
+                              ColState& S, double breakdown_eps) {
+  double hmax = fmax(fmax(S.hscale, sqrt(colmax2)), hn);
   S.hscale = hmax;
+  double2 a = Rc[0];
   for (int i = 0; i < j; ++i) {
-    double2 a = Rc[i], b = Rc[i + 1];
-    double c = csc[i];
-    double2 s = snc[i];
+    const double2 b = Rc[i + 1];
+    const double c = csc[i];
+    const double2 s = snc[i];
     Rc[i] = cadd(cscale(a, c), cmul(s, b));
-    Rc[i + 1] = csub(cscale(b, c), cmul(cconj(s), a));
+    a = csub(cscale(b, c), cmul(cconj(s), a));
   }
   // new rotation zeroing (Rc[j], hn): c = |a| / t, s = (a / |a|) conj(b) / t, b real here
-  double2 a = Rc[j];
   double aa = hypot(a.x, a.y);
   double c, t = hypot(aa, hn);
   double2 s;
@@ -264,8 +265,13 @@ __global__ void k_givens(int j, int ncol, int m, const double* __restrict__ npar
   double hn = sqrt(nn);
   const double2* h = hbuf + (int64_t)col * ldp;
   double2* Rc = Rm + ((int64_t)col * m + j) * (m + 1);  // column j of R
-  for (int i = 0; i <= j; ++i) Rc[i] = h[i];
-  givens_update(j, m, Rc, hn, cs + (int64_t)col * m, sn + (int64_t)col * m, g + (int64_t)col * (m + 1), S,
+  double colmax2 = 0.0;
+  for (int i = 0; i <= j; ++i) {
+    const double2 v = h[i];
+    Rc[i] = v;
+    colmax2 = fmax(colmax2, v.x * v.x + v.y * v.y);
+  }
+  givens_update(j, m, Rc, hn, colmax2, cs + (int64_t)col * m, sn + (int64_t)col * m, g + (int64_t)col * (m + 1), S,
                 breakdown_eps);
   double inv = hn > 0 ? 1.0 / hn : 0.0;
   vscale[(int64_t)col * (m + 1) + j + 1] = inv;
@@ -430,16 +436,27 @@ __global__ void __launch_bounds__(MD_THREADS) k_dsweepA(const C<R>* __restrict__
 }
 
 // Sum sweep-A partials over chunks: red[(col * 2 + t) * ldq + i], i <= nv (one block per column).
+// Grid (ceil(2 (nv + 1) / blockDim), ncol): one thread per value, four independent partial sums
+// over the chunks (fixed order, so the result is deterministic).
 __global__ void k_dreduce(const double2* __restrict__ partial, int ndc, int ldq, int nv,
                           const ColState* __restrict__ st, double2* __restrict__ red) {
-  int col = blockIdx.x;
+  const int col = blockIdx.y;
   if (!st[col].active) return;
-  for (int e = threadIdx.x; e < 2 * (nv + 1); e += blockDim.x) {
-    int t = e / (nv + 1), i = e % (nv + 1);
-    double2 s = make_double2(0, 0);
-    for (int c = 0; c < ndc; ++c) s = cadd(s, partial[((int64_t)(col * ndc + c) * 2 + t) * ldq + i]);
-    red[((int64_t)col * 2 + t) * ldq + i] = s;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= 2 * (nv + 1)) return;
+  const int t = e / (nv + 1), i = e % (nv + 1);
+  const double2* p = partial + ((int64_t)col * ndc * 2 + t) * ldq + i;
+  const int64_t step = (int64_t)2 * ldq;
+  double2 s0 = make_double2(0, 0), s1 = s0, s2 = s0, s3 = s0;
+  int c = 0;
+  for (; c + 4 <= ndc; c += 4) {
+    s0 = cadd(s0, p[(c + 0) * step]);
+    s1 = cadd(s1, p[(c + 1) * step]);
+    s2 = cadd(s2, p[(c + 2) * step]);
+    s3 = cadd(s3, p[(c + 3) * step]);
   }
+  for (; c < ndc; ++c) s0 = cadd(s0, p[c * step]);
+  red[((int64_t)col * 2 + t) * ldq + i] = cadd(cadd(s0, s1), cadd(s2, s3));
 }
 
 // One block per column: finalise column j-1 (when a pending vector exists), Givens on it, build the
@@ -481,19 +498,27 @@ __global__ void __launch_bounds__(DC_THREADS) k_dcoef(int j, int nv, int has_u, 
   block_reduce_store<3>(v, red3);
   if (has_u) {
     double2* Rc = Rm + ((int64_t)col * m + (j - 1)) * (m + 1);  // column j-1: partial (b, d) so far
+    double mx = 0.0;
     for (int i = threadIdx.x; i < nv; i += DC_THREADS) {
-      sR[i] = cadd(Rc[i], ra[i]);
+      const double2 v = cadd(Rc[i], ra[i]);
+      sR[i] = v;
+      mx = fmax(mx, v.x * v.x + v.y * v.y);
       if (i < j - 1) {
         sC[i] = cs[(int64_t)col * m + i];
         sS[i] = sn[(int64_t)col * m + i];
       }
     }
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+    __shared__ double s_mx[DC_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) s_mx[threadIdx.x >> 5] = mx;
     __syncthreads();
     if (threadIdx.x == 0) {
+      double colmax2 = 0.0;
+      for (int w = 0; w < DC_THREADS / 32; ++w) colmax2 = fmax(colmax2, s_mx[w]);
       double r2 = ra[nv].x - red3[0];
       double rho = r2 > 0 ? sqrt(r2) : 0.0;
       s_rho = rho;
-      givens_update(j - 1, m, sR, rho, sC, sS, g + (int64_t)col * (m + 1), S, breakdown_eps);
+      givens_update(j - 1, m, sR, rho, colmax2, sC, sS, g + (int64_t)col * (m + 1), S, breakdown_eps);
       cs[(int64_t)col * m + j - 1] = sC[j - 1];
       sn[(int64_t)col * m + j - 1] = sS[j - 1];
       if (S.active && !has_w) {  // finalisation pass at the end of a cycle of m iterations
@@ -548,12 +573,18 @@ __device__ __forceinline__ float4 cmsub2(float4 v, float4 x, float2 c) {
 }
 
 // Sweep-B update over point pairs (16-byte loads) of one column chunk; returns the chunk's ||w'||^2.
-// Requires V + cd.off and every basis column 16-byte aligned.  An odd last point is taken by
-// thread 0 of the last chunk.
+// Each thread takes two pairs RED_THREADS apart, so that one coefficient load serves two basis
+// loads, and keeps 8 basis loads in flight.  Requires V + cd.off and every basis column 16-byte
+// aligned.  An odd last point is taken by thread 0 of the last chunk.
+__device__ __forceinline__ void cmsub2_ab(float4& au, float4& aw, float4 x, float4 ab) {
+  au = cmsub2(au, x, make_float2(ab.x, ab.y));
+  aw = cmsub2(aw, x, make_float2(ab.z, ab.w));
+}
+
 __device__ __forceinline__ double dsweepB_pairs(const float2* __restrict__ V, int64_t vstride, int nv,
                                                 float2* __restrict__ u, const float2* __restrict__ w,
-                                                float2* __restrict__ wout, const float2* sa, const float2* sb,
-                                                float inv, float2 d, const ColDesc& cd, int nch, int chunk) {
+                                                float2* __restrict__ wout, const float4* sab, float inv, float2 d,
+                                                const ColDesc& cd, int nch, int chunk) {
   const int64_t npair = cd.len >> 1, vs4 = vstride >> 1;
   int64_t qa, qb;
   chunk_range(npair, nch, chunk, qa, qb);
@@ -562,40 +593,58 @@ __device__ __forceinline__ double dsweepB_pairs(const float2* __restrict__ V, in
   const float4* w4 = (const float4*)(w + cd.off);
   float4* o4 = (float4*)(wout + cd.off);
   double s = 0.0;
-  for (int64_t q = qa + threadIdx.x; q < qb; q += RED_THREADS) {
-    float4 au = u4 ? u4[q] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 aw = w4[q];
+  for (int64_t q0 = qa + threadIdx.x; q0 < qb; q0 += 2 * RED_THREADS) {
+    const int64_t q1r = q0 + RED_THREADS;
+    const bool two = q1r < qb;
+    const int64_t q1 = two ? q1r : q0;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 au0 = u4 ? u4[q0] : zero, aw0 = w4[q0];
+    float4 au1 = u4 ? u4[q1] : zero, aw1 = w4[q1];
     int i = 0;
-    for (; i + 8 <= nv; i += 8) {
-      float4 x[8];
+    for (; i + 4 <= nv; i += 4) {
+      float4 x0[4], x1[4];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) x[k] = __ldcg(V4 + (int64_t)(i + k) * vs4 + q);
+      for (int k = 0; k < 4; ++k) {
+        x0[k] = __ldcg(V4 + (int64_t)(i + k) * vs4 + q0);
+        x1[k] = __ldcg(V4 + (int64_t)(i + k) * vs4 + q1);
+      }
 #pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        au = cmsub2(au, x[k], sa[i + k]);
-        aw = cmsub2(aw, x[k], sb[i + k]);
+      for (int k = 0; k < 4; ++k) {
+        const float4 ab = sab[i + k];
+        cmsub2_ab(au0, aw0, x0[k], ab);
+        cmsub2_ab(au1, aw1, x1[k], ab);
       }
     }
     for (; i < nv; ++i) {
-      const float4 x = __ldcg(V4 + (int64_t)i * vs4 + q);
-      au = cmsub2(au, x, sa[i]);
-      aw = cmsub2(aw, x, sb[i]);
+      const float4 ab = sab[i];
+      cmsub2_ab(au0, aw0, __ldcg(V4 + (int64_t)i * vs4 + q0), ab);
+      cmsub2_ab(au1, aw1, __ldcg(V4 + (int64_t)i * vs4 + q1), ab);
     }
     if (u4) {
-      const float4 vj = make_float4(au.x * inv, au.y * inv, au.z * inv, au.w * inv);
-      u4[q] = vj;
-      aw = cmsub2(aw, vj, d);
+      const float4 vj0 = make_float4(au0.x * inv, au0.y * inv, au0.z * inv, au0.w * inv);
+      u4[q0] = vj0;
+      aw0 = cmsub2(aw0, vj0, d);
+      if (two) {
+        const float4 vj1 = make_float4(au1.x * inv, au1.y * inv, au1.z * inv, au1.w * inv);
+        u4[q1] = vj1;
+        aw1 = cmsub2(aw1, vj1, d);
+      }
     }
-    o4[q] = aw;
-    s += (double)aw.x * aw.x + (double)aw.y * aw.y + (double)aw.z * aw.z + (double)aw.w * aw.w;
+    o4[q0] = aw0;
+    s += (double)aw0.x * aw0.x + (double)aw0.y * aw0.y + (double)aw0.z * aw0.z + (double)aw0.w * aw0.w;
+    if (two) {
+      o4[q1] = aw1;
+      s += (double)aw1.x * aw1.x + (double)aw1.y * aw1.y + (double)aw1.z * aw1.z + (double)aw1.w * aw1.w;
+    }
   }
   if ((cd.len & 1) && chunk == nch - 1 && threadIdx.x == 0) {
     const int64_t p = cd.len - 1;
     float2 au = u ? u[cd.off + p] : make_float2(0.f, 0.f), aw = w[cd.off + p];
     for (int i = 0; i < nv; ++i) {
       const float2 x = V[(int64_t)i * vstride + cd.off + p];
-      au = csub(au, cmul(x, sa[i]));
-      aw = csub(aw, cmul(x, sb[i]));
+      const float4 ab = sab[i];
+      au = csub(au, cmul(x, make_float2(ab.x, ab.y)));
+      aw = csub(aw, cmul(x, make_float2(ab.z, ab.w)));
     }
     if (u) {
       const float2 vj = cscale(au, inv);
@@ -619,13 +668,6 @@ __global__ void __launch_bounds__(RED_THREADS) k_dsweepB(const C<R>* __restrict_
   int col = blockIdx.y, chunk = blockIdx.x;
   if (!st[col].active) return;
   extern __shared__ __align__(16) unsigned char db_smem[];
-  C<R>* sa = (C<R>*)db_smem;
-  C<R>* sb = sa + nv;
-  for (int i = threadIdx.x; i < nv; i += RED_THREADS) {
-    sa[i] = ca[(int64_t)col * ldq + i];
-    sb[i] = cb[(int64_t)col * ldq + i];
-  }
-  __syncthreads();
   const R inv = (R)sc[col * 2].x;
   const C<R> d = mk<R>((R)sc[col * 2 + 1].x, (R)sc[col * 2 + 1].y);
   ColDesc cd = cols[col];
@@ -633,11 +675,25 @@ __global__ void __launch_bounds__(RED_THREADS) k_dsweepB(const C<R>* __restrict_
   double s[1] = {0.0};
   if constexpr (sizeof(R) == 4) {
     if ((vstride & 1) == 0 && (cd.off & 1) == 0 && ((uintptr_t)V & 15) == 0) {
-      s[0] = dsweepB_pairs(V, vstride, nv, u, w, wout, sa, sb, inv, d, cd, nch, chunk);
+      // coefficients interleaved (a_i, b_i): one 16-byte shared load per basis vector
+      float4* sab = (float4*)db_smem;
+      for (int i = threadIdx.x; i < nv; i += RED_THREADS) {
+        const float2 ai = ca[(int64_t)col * ldq + i], bi = cb[(int64_t)col * ldq + i];
+        sab[i] = make_float4(ai.x, ai.y, bi.x, bi.y);
+      }
+      __syncthreads();
+      s[0] = dsweepB_pairs(V, vstride, nv, u, w, wout, sab, inv, d, cd, nch, chunk);
       block_reduce_store<1>(s, npartial + (int64_t)col * nch + chunk);
       return;
     }
   }
+  C<R>* sa = (C<R>*)db_smem;
+  C<R>* sb = sa + nv;
+  for (int i = threadIdx.x; i < nv; i += RED_THREADS) {
+    sa[i] = ca[(int64_t)col * ldq + i];
+    sb[i] = cb[(int64_t)col * ldq + i];
+  }
+  __syncthreads();
   chunk_range(cd.len, nch, chunk, a, b);
   // two points per thread per pass: two independent load streams over the basis
   for (int64_t p0 = a + threadIdx.x; p0 < b; p0 += 2 * RED_THREADS) {
@@ -860,7 +916,7 @@ struct SolverWs {
 
 template <typename R>
 static helm_status solver_ws(helm_ctx* ctx, int m, int ncol, int nch, int ndc, bool separate_z, int64_t nvec,
-                             SolverWs<R>& W) {
+                             int64_t vst, SolverWs<R>& W) {
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -868,8 +924,9 @@ static helm_status solver_ws(helm_ctx* ctx, int m, int ncol, int nch, int ndc, b
     return o;
   };
   size_t vb = sizeof(C<R>) * nvec;
-  size_t oV = take(vb * (m + 1));
-  size_t oZ = separate_z ? take(vb * m) : oV;
+  size_t sb = sizeof(C<R>) * vst;  // basis slot stride
+  size_t oV = take(sb * (m + 1));
+  size_t oZ = separate_z ? take(sb * m) : oV;
   size_t ow = take(vb);
   size_t orr = take(sizeof(double2) * nvec);
   int ldp = m + 1;
@@ -944,6 +1001,9 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
   const int ncol = num_cols(ctx, nrhs);
   const int m = o.m;
   const int64_t nvec = ctx->npts * nrhs;
+  // basis slots are vst elements apart: nvec rounded to 1 KB plus 768 B, so that the same point of
+  // successive basis vectors does not fall on addresses a large power of two apart
+  const int64_t vst = (nvec + 127) / 128 * 128 + 96;
   int64_t maxlen = 0;
   for (auto& c : ctx->cols_host) maxlen = std::max(maxlen, c.len);
   // point-sweep chunking: about 8 blocks of 256 threads per SM in all, at least 256 points per block
@@ -955,7 +1015,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
   const dim3 dgrid(ndc, ncol);
   const size_t md_smem = sizeof(C<R>) * P;
   const bool dcgs2 = o.orth == HELM_ORTH_DCGS2;
-  HELM_TRY(solver_ws<R>(ctx, m, ncol, nch, ndc, net != nullptr || dcgs2, nvec, W));
+  HELM_TRY(solver_ws<R>(ctx, m, ncol, nch, ndc, net != nullptr || dcgs2, nvec, vst, W));
   const int ldq = m + 2;
   const size_t ds_smem = 2 * sizeof(C<R>) * P;
   const size_t db_smem = 2 * sizeof(C<R>) * m;
@@ -1030,8 +1090,8 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
     prof_end(ctx, PH_RESIDUAL, stream);
     if (!dcgs2) {
       for (int j = 0; j < m; ++j) {
-        C<R>* Vj = W.V + (int64_t)j * nvec;
-        C<R>* Zj = net ? W.Z + (int64_t)j * nvec : Vj;
+        C<R>* Vj = W.V + (int64_t)j * vst;
+        C<R>* Zj = net ? W.Z + (int64_t)j * vst : Vj;
         // z_j = N_theta(v_j)
         prof_begin(ctx, PH_PRECOND, stream);
         if (ctx->prof_on) {
@@ -1060,12 +1120,12 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         // CGS2, two passes; the second writes the unnormalised v_{j+1} and its norm partials
         prof_begin(ctx, PH_ORTH, stream);
         for (int pass = 0; pass < 2; ++pass) {
-          launch(k_mdot<R>, dgrid, MD_THREADS, md_smem, stream, W.V, nvec, nv, W.w, ctx->cols_dev, W.st, P, ndc,
+          launch(k_mdot<R>, dgrid, MD_THREADS, md_smem, stream, W.V, vst, nv, W.w, ctx->cols_dev, W.st, P, ndc,
                  W.partial, ldp);
           launch(k_hreduce<R>, ncol, 256, 0, stream, W.partial, ndc, ldp, nv, W.vscale, ldp, W.st, W.hbuf, W.coef,
                  pass);
-          C<R>* dst = pass == 1 ? W.V + (int64_t)(j + 1) * nvec : nullptr;
-          launch(k_maxpy<R>, vgrid, RED_THREADS, maxpy_smem, stream, W.V, nvec, nv, W.w, W.coef, ldp, ctx->cols_dev,
+          C<R>* dst = pass == 1 ? W.V + (int64_t)(j + 1) * vst : nullptr;
+          launch(k_maxpy<R>, vgrid, RED_THREADS, maxpy_smem, stream, W.V, vst, nv, W.w, W.coef, ldp, ctx->cols_dev,
                  W.st, nch, dst, pass == 1 ? W.npartial : nullptr);
           HELM_CK_LAUNCH();
         }
@@ -1086,8 +1146,8 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
     } else {
       // CGS2 with delayed reorthogonalisation (kernels k_dsweepA / k_dcoef / k_dsweepB above)
       for (int j = 0; j < m; ++j) {
-        C<R>* Uj = W.V + (int64_t)j * nvec;  // v_0 at j = 0, else the pending u_j
-        C<R>* Zj = W.Z + (int64_t)j * nvec;
+        C<R>* Uj = W.V + (int64_t)j * vst;  // v_0 at j = 0, else the pending u_j
+        C<R>* Zj = W.Z + (int64_t)j * vst;
         prof_begin(ctx, PH_PRECOND, stream);
         if (ctx->prof_on) {
           ctx->prof_work[PH_PRECOND] += net ? 70816.0 * ctx->npts * nrhs : 0.0;
@@ -1113,14 +1173,15 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         const int nv = j > 0 ? j : 1;
         prof_begin(ctx, PH_ORTH, stream);
         HELM_CK(cudaMemsetAsync(W.nactive, 0, sizeof(int), stream));
-        launch(k_dsweepA<R>, dgrid, MD_THREADS, ds_smem, stream, (const C<R>*)W.V, nvec, nv,
+        launch(k_dsweepA<R>, dgrid, MD_THREADS, ds_smem, stream, (const C<R>*)W.V, vst, nv,
                (const C<R>*)(has_u ? Uj : nullptr), (const C<R>*)W.w, ctx->cols_dev, W.st, P, ndc, W.partial, ldq);
-        launch(k_dreduce, ncol, 256, 0, stream, (const double2*)W.partial, ndc, ldq, nv, W.st, W.red);
+        launch(k_dreduce, dim3(cdiv(2 * (nv + 1), 128), ncol), 128, 0, stream, (const double2*)W.partial, ndc, ldq,
+               nv, W.st, W.red);
         launch(k_dcoef<R>, ncol, DC_THREADS, dc_smem(nv), stream, j, nv, has_u, 1, ncol, m, (const double2*)W.red, ldq,
                W.Rm,
                W.cs, W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps);
-        launch(k_dsweepB<R>, vgrid, RED_THREADS, 2 * sizeof(C<R>) * nv, stream, (const C<R>*)W.V, nvec, nv,
-               has_u ? Uj : nullptr, (const C<R>*)W.w, W.V + (int64_t)(j + 1) * nvec, (const C<R>*)W.ca,
+        launch(k_dsweepB<R>, vgrid, RED_THREADS, 2 * sizeof(C<R>) * nv, stream, (const C<R>*)W.V, vst, nv,
+               has_u ? Uj : nullptr, (const C<R>*)W.w, W.V + (int64_t)(j + 1) * vst, (const C<R>*)W.ca,
                (const C<R>*)W.cb, (const double2*)W.sc, ldq, ctx->cols_dev, W.st, nch, W.npartial);
         launch(k_nscale, cdiv(ncol, 64), 64, 0, stream, ncol, (const double*)W.npartial, nch, W.st, ctx->cols_dev,
                W.in_scale);
@@ -1138,10 +1199,11 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
       }
       // columns that ran all m iterations: finalise column m-1 (reorthogonalise the pending u_m)
       prof_begin(ctx, PH_ORTH, stream);
-      launch(k_dsweepA<R>, dgrid, MD_THREADS, ds_smem, stream, (const C<R>*)W.V, nvec, m,
-             (const C<R>*)(W.V + (int64_t)m * nvec), (const C<R>*)nullptr, ctx->cols_dev, W.st, P, ndc, W.partial,
+      launch(k_dsweepA<R>, dgrid, MD_THREADS, ds_smem, stream, (const C<R>*)W.V, vst, m,
+             (const C<R>*)(W.V + (int64_t)m * vst), (const C<R>*)nullptr, ctx->cols_dev, W.st, P, ndc, W.partial,
              ldq);
-      launch(k_dreduce, ncol, 256, 0, stream, (const double2*)W.partial, ndc, ldq, m, W.st, W.red);
+      launch(k_dreduce, dim3(cdiv(2 * (m + 1), 128), ncol), 128, 0, stream, (const double2*)W.partial, ndc, ldq, m,
+             W.st, W.red);
       launch(k_dcoef<R>, ncol, DC_THREADS, dc_smem(m), stream, m, m, 1, 0, ncol, m, (const double2*)W.red, ldq, W.Rm,
              W.cs,
              W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps);
@@ -1150,7 +1212,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
     }
     prof_begin(ctx, PH_UPDATE, stream);
     launch(k_backsolve, cdiv(ncol, 64), 64, 0, stream, ncol, m, W.Rm, W.g, W.st, W.y);
-    launch(k_xupdate<R>, vgrid, RED_THREADS, 0, stream, W.Z, nvec, W.y, m, (net || dcgs2) ? nullptr : W.vscale,
+    launch(k_xupdate<R>, vgrid, RED_THREADS, 0, stream, W.Z, vst, W.y, m, (net || dcgs2) ? nullptr : W.vscale,
            W.st, ctx->cols_dev, nch, x);
     HELM_CK_LAUNCH();
     HELM_CK(cudaMemcpyAsync(h_st, W.st, sizeof(ColState) * ncol, cudaMemcpyDeviceToHost, stream));
