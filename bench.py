@@ -38,6 +38,9 @@ STENCIL_BYTES_FP32 = 16.0           # read z (8 B) + write A z (8 B) per point; 
 # Mean Krylov iterations per solve used to scale the oracle's per-iteration time into solves/s
 # when the reference arm runs in its own process (the CUDA arm prints its own measured mean).
 REF_ITERS_PER_SOLVE = 300
+# DRAM bytes per basis vector and point of one DCGS2 step (k_dsweepA 8.00 B + k_dsweepB 8.06 B),
+# from the ncu counters of the current sweep kernels (profiles/k_dsweep_fine_grid_32rhs.md)
+DCGS2_DRAM_B_PER_VPT = 16.06
 
 
 def parse():
@@ -270,11 +273,20 @@ def run_cuda(args):
                                    "ms": prof[ph][0]}
     names = {"precond": "U-Net preconditioner (tcgen05 BF16 convs + CUDA-core glue), all launches of the step",
              "orth": f"{args.orth.upper()} orthogonalisation sweeps (k_dsweepA/k_dsweepB or k_mdot/k_maxpy)",
-             "stencil": "k_stencil<float>"}
+             "stencil": "k_stencil_tma<float>"}
     roof = dict(phase_rooflines.get(dom, {"bound": "hbm", "achieved": None, "peak": None, "unit": "GB/s",
                                           "frac": None}))
     roof.update({"kernel": names.get(dom, dom), "traffic": None,
                  "peak_source": "measured (MEASURED_PEAKS.json)" if peaks else "fallback"})
+    if dom == "orth" and args.orth == "dcgs2" and prof["orth"][1] > 0:
+        # one "launch" of the orthogonalisation = one DCGS2 step (sweep A + sweep B + 3 small
+        # kernels); its algorithmic bytes are 16 nv + 48 B per point, nv the step's basis size
+        npt = ctx.npts * rb  # points per solver call
+        alg_step = work["orth"] / prof["orth"][1]
+        nv_mean = max(0.0, (alg_step / npt - 48.0) / 16.0)
+        roof.update({"traffic": DCGS2_DRAM_B_PER_VPT * nv_mean * npt, "algorithmic_per_step": alg_step,
+                     "mean_basis": nv_mean, "steps": prof["orth"][1],
+                     "traffic_source": "ncu DRAM bytes per basis-vector point x mean basis size"})
 
     # stencil alone against HBM (32 RHS of the workload).  L2 is flushed before every launch by
     # writing one 256 MB buffer and then reading another, so that the write-back of the flush's
