@@ -576,11 +576,18 @@ __device__ __forceinline__ float4 cmsub2(float4 v, float4 x, float2 c) {
 // Each thread takes two pairs RED_THREADS apart, so that one coefficient load serves two basis
 // loads, and keeps 8 basis loads in flight.  Requires V + cd.off and every basis column 16-byte
 // aligned.  An odd last point is taken by thread 0 of the last chunk.
+#ifndef DB_NP
+#define DB_NP 2  // point pairs per thread in sweep B
+#endif
+#ifndef DB_VB
+#define DB_VB 4  // basis vectors per batch of loads in sweep B
+#endif
 __device__ __forceinline__ void cmsub2_ab(float4& au, float4& aw, float4 x, float4 ab) {
   au = cmsub2(au, x, make_float2(ab.x, ab.y));
   aw = cmsub2(aw, x, make_float2(ab.z, ab.w));
 }
 
+template <int NP, int VB>
 __device__ __forceinline__ double dsweepB_pairs(const float2* __restrict__ V, int64_t vstride, int nv,
                                                 float2* __restrict__ u, const float2* __restrict__ w,
                                                 float2* __restrict__ wout, const float4* sab, float inv, float2 d,
@@ -592,67 +599,68 @@ __device__ __forceinline__ double dsweepB_pairs(const float2* __restrict__ V, in
   float4* u4 = u ? (float4*)(u + cd.off) : nullptr;
   const float4* w4 = (const float4*)(w + cd.off);
   float4* o4 = (float4*)(wout + cd.off);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
   double s = 0.0;
-  for (int64_t q0 = qa + threadIdx.x; q0 < qb; q0 += 2 * RED_THREADS) {
-    const int64_t q1r = q0 + RED_THREADS;
-    const bool two = q1r < qb;
-    const int64_t q1 = two ? q1r : q0;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 au0 = u4 ? u4[q0] : zero, aw0 = w4[q0];
-    float4 au1 = u4 ? u4[q1] : zero, aw1 = w4[q1];
+  for (int64_t q0 = qa + threadIdx.x; q0 < qb; q0 += NP * RED_THREADS) {
+    int64_t q[NP];
+    bool ok[NP];
+    float4 au[NP], aw[NP];
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      const int64_t qp = q0 + p * RED_THREADS;
+      ok[p] = qp < qb;
+      q[p] = ok[p] ? qp : q0;  // idle slots repeat pair q0 and are not stored
+      au[p] = u4 ? u4[q[p]] : zero;
+      aw[p] = w4[q[p]];
+    }
     int i = 0;
-    for (; i + 4 <= nv; i += 4) {
-      float4 x0[4], x1[4];
+    for (; i + VB <= nv; i += VB) {
+      float4 x[VB][NP];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        x0[k] = __ldcg(V4 + (int64_t)(i + k) * vs4 + q0);
-        x1[k] = __ldcg(V4 + (int64_t)(i + k) * vs4 + q1);
-      }
+      for (int k = 0; k < VB; ++k)
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+        for (int p = 0; p < NP; ++p) x[k][p] = __ldcg(V4 + (int64_t)(i + k) * vs4 + q[p]);
+#pragma unroll
+      for (int k = 0; k < VB; ++k) {
         const float4 ab = sab[i + k];
-        cmsub2_ab(au0, aw0, x0[k], ab);
-        cmsub2_ab(au1, aw1, x1[k], ab);
+#pragma unroll
+        for (int p = 0; p < NP; ++p) cmsub2_ab(au[p], aw[p], x[k][p], ab);
       }
     }
     for (; i < nv; ++i) {
       const float4 ab = sab[i];
-      cmsub2_ab(au0, aw0, __ldcg(V4 + (int64_t)i * vs4 + q0), ab);
-      cmsub2_ab(au1, aw1, __ldcg(V4 + (int64_t)i * vs4 + q1), ab);
+#pragma unroll
+      for (int p = 0; p < NP; ++p) cmsub2_ab(au[p], aw[p], __ldcg(V4 + (int64_t)i * vs4 + q[p]), ab);
     }
-    if (u4) {
-      const float4 vj0 = make_float4(au0.x * inv, au0.y * inv, au0.z * inv, au0.w * inv);
-      u4[q0] = vj0;
-      aw0 = cmsub2(aw0, vj0, d);
-      if (two) {
-        const float4 vj1 = make_float4(au1.x * inv, au1.y * inv, au1.z * inv, au1.w * inv);
-        u4[q1] = vj1;
-        aw1 = cmsub2(aw1, vj1, d);
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      if (!ok[p]) continue;
+      if (u4) {
+        const float4 vj = make_float4(au[p].x * inv, au[p].y * inv, au[p].z * inv, au[p].w * inv);
+        u4[q[p]] = vj;
+        aw[p] = cmsub2(aw[p], vj, d);
       }
-    }
-    o4[q0] = aw0;
-    s += (double)aw0.x * aw0.x + (double)aw0.y * aw0.y + (double)aw0.z * aw0.z + (double)aw0.w * aw0.w;
-    if (two) {
-      o4[q1] = aw1;
-      s += (double)aw1.x * aw1.x + (double)aw1.y * aw1.y + (double)aw1.z * aw1.z + (double)aw1.w * aw1.w;
+      o4[q[p]] = aw[p];
+      s += (double)aw[p].x * aw[p].x + (double)aw[p].y * aw[p].y + (double)aw[p].z * aw[p].z +
+           (double)aw[p].w * aw[p].w;
     }
   }
   if ((cd.len & 1) && chunk == nch - 1 && threadIdx.x == 0) {
     const int64_t p = cd.len - 1;
-    float2 au = u ? u[cd.off + p] : make_float2(0.f, 0.f), aw = w[cd.off + p];
+    float2 au1 = u ? u[cd.off + p] : make_float2(0.f, 0.f), aw1 = w[cd.off + p];
     for (int i = 0; i < nv; ++i) {
       const float2 x = V[(int64_t)i * vstride + cd.off + p];
       const float4 ab = sab[i];
-      au = csub(au, cmul(x, make_float2(ab.x, ab.y)));
-      aw = csub(aw, cmul(x, make_float2(ab.z, ab.w)));
+      au1 = csub(au1, cmul(x, make_float2(ab.x, ab.y)));
+      aw1 = csub(aw1, cmul(x, make_float2(ab.z, ab.w)));
     }
     if (u) {
-      const float2 vj = cscale(au, inv);
+      const float2 vj = cscale(au1, inv);
       u[cd.off + p] = vj;
-      aw = csub(aw, cmul(vj, d));
+      aw1 = csub(aw1, cmul(vj, d));
     }
-    wout[cd.off + p] = aw;
-    s += (double)aw.x * aw.x + (double)aw.y * aw.y;
+    wout[cd.off + p] = aw1;
+    s += (double)aw1.x * aw1.x + (double)aw1.y * aw1.y;
   }
   return s;
 }
@@ -682,7 +690,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_dsweepB(const C<R>* __restrict_
         sab[i] = make_float4(ai.x, ai.y, bi.x, bi.y);
       }
       __syncthreads();
-      s[0] = dsweepB_pairs(V, vstride, nv, u, w, wout, sab, inv, d, cd, nch, chunk);
+      s[0] = dsweepB_pairs<DB_NP, DB_VB>(V, vstride, nv, u, w, wout, sab, inv, d, cd, nch, chunk);
       block_reduce_store<1>(s, npartial + (int64_t)col * nch + chunk);
       return;
     }
