@@ -154,10 +154,11 @@ def run_cuda(args):
     import torch
     from paper_2607_16906_b300 import helm
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2607_16906_b300 import replicas
+
+    rank, world, local = replicas.env_ranks()
     torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -192,8 +193,7 @@ def run_cuda(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier(dev)
     helm.helm_profile_enable(ctx, True)
     clocks = ClockSampler(local)
     l0 = helm.helm_launch_count()
@@ -208,19 +208,14 @@ def run_cuda(args):
         infos = info
     ev1.record()
     torch.cuda.synchronize()
+    replicas.barrier(dev)
     launches = helm.helm_launch_count() - l0
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
     prof = helm.helm_profile_read(ctx)
     work = helm.helm_profile_work(ctx)
     helm.helm_profile_enable(ctx, False)
-    if dist:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
-        c = torch.tensor([converged], device="cuda", dtype=torch.float64)
-        dist.all_reduce(c)
-        converged = int(c.item())
+    ms, converged = replicas.reduce_step(ms, converged, dev)  # max time, summed solves over ranks
     value = converged / (ms / 1e3)
     mean_iters = float(np.mean(iters)) if iters else 0.0
 
@@ -241,13 +236,7 @@ def run_cuda(args):
     e1.record()
     torch.cuda.synchronize()
     ms_e2e = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms_e2e, conv_e2e], device="cuda", dtype=torch.float64)
-        mx = t[:1].clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t[1:].clone()
-        dist.all_reduce(sm)
-        ms_e2e, conv_e2e = mx.item(), int(sm.item())
+    ms_e2e, conv_e2e = replicas.reduce_step(ms_e2e, conv_e2e, dev)
     nbytes = b_host.numel() * b_host.element_size()
 
     # dominant phase -> roofline (algorithmic work counted by the library for the timed region)

@@ -23,6 +23,9 @@ namespace helm {
 constexpr int ROW_PX = 128;                // output pixels per row segment (one MMA block, M = 128)
 constexpr int ROW_HALO = ROW_PX + 2;       // loaded pixels per row
 constexpr int ROW_PITCH = ROW_HALO * 16;   // bytes per loaded row of one slice (2080)
+#ifndef ROW_EPI_BATCH
+#define ROW_EPI_BATCH 2  // 16-column TMEM loads per epilogue wait
+#endif
 
 struct RowArgs {
   int B, H, W;
@@ -58,12 +61,13 @@ struct RowCfg {
   static constexpr int TMEM_COLS = 2 * ACC_COLS < 32 ? 32 : 2 * ACC_COLS;
   static constexpr int SMEM = STAGES * STAGE_BYTES + FIXED;
   static constexpr int THREADS = 320;  // producer, MMA issuer, two 4-warp epilogue groups
+  static constexpr int MINB = 2 * (SMEM + 1024) <= 228 * 1024 ? 2 : 1;  // CTAs per SM the registers allow
   static_assert((TMEM_COLS & (TMEM_COLS - 1)) == 0 && TMEM_COLS <= 512, "TMEM allocation");
   static_assert(SLB < (1 << 18), "LBO field");
 };
 
 template <int N, int NSL, int RY>
-__global__ void __launch_bounds__(320, 1) k_conv_row(const __grid_constant__ CUtensorMap tA0,
+__global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(const __grid_constant__ CUtensorMap tA0,
                                                      const __grid_constant__ CUtensorMap tA1, RowArgs a) {
   using Cfg = RowCfg<N, NSL, RY>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -159,21 +163,24 @@ __global__ void __launch_bounds__(320, 1) k_conv_row(const __grid_constant__ CUt
       tc_fence_after();
       if (lane == 0) {
         const uint32_t sa = smem_u32(smem + stage * Cfg::STAGE_BYTES);
+        // rows innermost: consecutive MMAs go to different accumulators, so none waits for the
+        // previous one's result
 #pragma unroll
-        for (int ry = 0; ry < RY; ++ry) {
-          const uint32_t d_tmem = tmem_base + acc * Cfg::ACC_COLS + ry * N;
+        for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
-          for (int ky = 0; ky < 3; ++ky)
+          for (int dx = 0; dx < 3; ++dx)
 #pragma unroll
-            for (int dx = 0; dx < 3; ++dx)
+            for (int kk = 0; kk < NSL / 2; ++kk) {
+              const int tap = ky * 3 + dx;
+              const uint64_t bd = smem_desc_noswz(wbase + ((tap * NSL + 2 * kk) * N) * 16, N * 16, 128);
 #pragma unroll
-              for (int kk = 0; kk < NSL / 2; ++kk) {
-                const int tap = ky * 3 + dx;
-                uint64_t ad = smem_desc_noswz(sa + 2 * kk * Cfg::SLB + (ry + ky) * ROW_PITCH + dx * 16, Cfg::SLB, 128);
-                uint64_t bd = smem_desc_noswz(wbase + ((tap * NSL + 2 * kk) * N) * 16, N * 16, 128);
+              for (int ry = 0; ry < RY; ++ry) {
+                const uint32_t d_tmem = tmem_base + acc * Cfg::ACC_COLS + ry * N;
+                const uint64_t ad =
+                    smem_desc_noswz(sa + 2 * kk * Cfg::SLB + (ry + ky) * ROW_PITCH + dx * 16, Cfg::SLB, 128);
                 umma_bf16(d_tmem, ad, bd, IDESC, (ky | dx | kk) ? 1u : 0u);
               }
-        }
+            }
         umma_commit(&empty[stage]);
         umma_commit(&tfull[acc]);
       }
@@ -201,41 +208,46 @@ __global__ void __launch_bounds__(320, 1) k_conv_row(const __grid_constant__ CUt
       int r = t % per_img;
       int y0 = (r / a.tiles_x) * RY, x = (r % a.tiles_x) * ROW_PX + p;
       const bool inside = x < a.W;
+      // the tile's RY x N accumulator columns in batches of up to four 16-column TMEM loads with
+      // one wait per batch
+      constexpr int NLD = Cfg::ACC_COLS / 16;
+      constexpr int LB = NLD < ROW_EPI_BATCH ? NLD : ROW_EPI_BATCH;
 #pragma unroll
-      for (int ry = 0; ry < RY; ++ry) {
-        const int y = y0 + ry;
-        __nv_bfloat16* o = a.out + (((int64_t)b * a.H + y) * a.W + x) * N;
+      for (int l0 = 0; l0 < NLD; l0 += LB) {
+        uint32_t v[LB][16];
 #pragma unroll
-        for (int cb = 0; cb < N / 16; ++cb) {
-          uint32_t v[16];
-          tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + e * Cfg::ACC_COLS + ry * N + cb * 16, v);
-          tmem_ld_wait();
-          if (inside && y < a.H) {
-            __align__(16) __nv_bfloat16 hv[16];
+        for (int l = 0; l < LB; ++l)
+          tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + e * Cfg::ACC_COLS + (l0 + l) * 16, v[l]);
+        tmem_ld_wait();
+#pragma unroll
+        for (int l = 0; l < LB; ++l) {
+          const int ry = ((l0 + l) * 16) / N, cb = (((l0 + l) * 16) % N) / 16;
+          const int y = y0 + ry;
+          if (!inside || y >= a.H) continue;
+          __align__(16) __nv_bfloat16 hv[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            float f = __uint_as_float(v[l][k]) + bsm[cb * 16 + k];
+            if (a.relu) f = fmaxf(f, 0.0f);
+            hv[k] = __float2bfloat16_rn(f);
+          }
+          if (N == 16 && a.z) {
+            // final 1x1 conv 16 -> 2 on the BF16 activation, then the output scale and crop
+            float f0 = fsm[32], f1 = fsm[33];
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
-              float f = __uint_as_float(v[k]) + bsm[cb * 16 + k];
-              if (a.relu) f = fmaxf(f, 0.0f);
-              hv[k] = __float2bfloat16_rn(f);
+              const float f = __bfloat162float(hv[k]);
+              f0 += f * fsm[2 * k];
+              f1 += f * fsm[2 * k + 1];
             }
-            if (N == 16 && a.z) {
-              // final 1x1 conv 16 -> 2 on the BF16 activation, then the output scale and crop
-              float y0 = fsm[32], y1 = fsm[33];
-#pragma unroll
-              for (int k = 0; k < 16; ++k) {
-                const float f = __bfloat162float(hv[k]);
-                y0 += f * fsm[2 * k];
-                y1 += f * fsm[2 * k + 1];
-              }
-              if (x < a.Nx && y < a.Ny) {
-                const double sc = a.out_scale[b];
-                a.z[b * a.zstride + (int64_t)y * a.Nx + x] = make_float2((float)(y0 * sc), (float)(y1 * sc));
-              }
-            } else {
-              uint4* dst = (uint4*)(o + cb * 16);
-              dst[0] = ((const uint4*)hv)[0];
-              dst[1] = ((const uint4*)hv)[1];
+            if (x < a.Nx && y < a.Ny) {
+              const double sc = a.out_scale[b];
+              a.z[b * a.zstride + (int64_t)y * a.Nx + x] = make_float2((float)(f0 * sc), (float)(f1 * sc));
             }
+          } else {
+            uint4* dst = (uint4*)(a.out + (((int64_t)b * a.H + y) * a.W + x) * N + cb * 16);
+            dst[0] = ((const uint4*)hv)[0];
+            dst[1] = ((const uint4*)hv)[1];
           }
         }
       }
