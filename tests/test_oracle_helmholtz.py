@@ -6,6 +6,8 @@ half-node index (symmetry, Green's function, manufactured solution), a
 dropped k^2 or 1/h^2 (manufactured solution), a conjugation error in the
 adjoint (dot-product test).
 """
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -65,6 +67,19 @@ def test_pml_profile_values_at_layer_edges():
     # half nodes inside the interior are undamped; the ones in the layer are damped and increase outward
     assert np.all(sxh[p + 1:Nx - p] == 1.0)
     assert np.all(np.diff(sxh[:p + 1].imag) < 0)
+
+
+def test_pml_profile_matches_table1_configuration():
+    """tests/golden/pml_tab1_profile.txt: eq. 2 with the Tab. 1 PML (l = 4, sigma_max = 2, omega = 1),
+    written out by hand at the nodes and half nodes of a 4-cell layer with unit spacing."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "pml_tab1_profile.txt")
+    rows = np.loadtxt(path, comments="#")
+    t, d = rows[:, 0], rows[:, 1]
+    s = hz.stretch(t, 8, 4, 1.0, 1.0, 2.0)  # 8 interior cells, 4-cell layer
+    assert np.array_equal(s.real, rows[:, 2]) and np.array_equal(s.imag, rows[:, 3])
+    # the mirrored positions on the right edge (first node past the interior is t = 4 + 8)
+    s_r = hz.stretch(4 + 8 - 1 + d, 8, 4, 1.0, 1.0, 2.0)
+    assert np.array_equal(s_r.imag, rows[:, 3])
 
 
 def test_adjoint_dot_product_and_conjugate_transpose():
