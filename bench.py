@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--weights", default=WEIGHTS)
     ap.add_argument("--no-plain", action="store_true", help="skip the bounded plain-FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the bounded CPU-oracle baseline")
+    ap.add_argument("--no-train", action="store_true", help="skip the training-step throughput measurement")
     return ap.parse_args()
 
 
@@ -152,9 +153,7 @@ def run_reference(args):
 
 def run_cuda(args):
     import torch
-    from paper_2607_16906_b300 import helm
-
-    from paper_2607_16906_b300 import replicas
+    from paper_2607_16906_b300 import helm, replicas, synth
 
     rank, world, local = replicas.env_ranks()
     torch.cuda.set_device(local)
@@ -303,6 +302,31 @@ def run_cuda(args):
                "ms": st_ms, "bytes_per_launch": st_bytes, "kernel": "k_stencil_tma<float> (FP32, 32 RHS)",
                "l2": "flushed before each launch (write 256 MB, read 256 MB)"}
 
+    # training-step throughput on the training configuration (64 x (128^2 + 16 PML), mixed skull / GRF
+    # velocities, point-source and line-array sources): helm_train_step = BF16 forward, adjoint
+    # stencil, conv backward, AdamW (eqs. 8-9); 3 warm-up and 10 timed steps on a copy of the weights
+    train = None
+    if not args.no_train:
+        cs, bs, th, om = synth.training_batch()
+        nb, nt = cs.shape[0], cs.shape[1] - 32
+        tctx = helm.Context([helm.SystemSpec(nt, nt, th, 16, om) for _ in range(nb)],
+                            torch.tensor(cs.ravel(), device="cuda"))
+        tnet = helm.UNet(theta)
+        tb = torch.tensor(bs.ravel().astype(np.complex64), device="cuda")
+        for _ in range(3):
+            helm.helm_train_step(tctx, tnet, tb, lr=1e-5)
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record()
+        losses = [helm.helm_train_step(tctx, tnet, tb, lr=1e-5)[0] for _ in range(10)]
+        t1.record()
+        torch.cuda.synchronize()
+        tms = t0.elapsed_time(t1) / 10
+        train = {"steps_per_s": 1e3 / tms, "ms_per_step": tms, "samples_per_s": nb * 1e3 / tms,
+                 "batch": f"{nb} x {nt}^2 + 16 PML (skull / GRF velocities, point / line-array sources)",
+                 "loss_first": losses[0], "loss_last": losses[-1]}
+        del tctx, tnet, tb
+
     # bounded plain-FP64 comparison: time a few FP64 iterations (FP64 U-Net), scale by the same count
     plain = None
     if not args.no_plain:
@@ -345,7 +369,7 @@ def run_cuda(args):
                 "phases_ms": {k: v[0] for k, v in prof.items()},
                 "roofline": roof, "phase_rooflines": phase_rooflines, "phase_work": work,
                 "stencil_roofline": stencil,
-                "plain_fp64": plain,
+                "plain_fp64": plain, "train_step": train,
                 "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
                 "e2e": {"value": conv_e2e / (ms_e2e / 1e3), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                         "d2h_bytes_per_step": nbytes, "steps": e2e_steps}}
