@@ -141,6 +141,12 @@ HELM_API helm_status helm_unet_create(helm_unet** out, const double* weights_hos
 HELM_API helm_status helm_unet_destroy(helm_unet* net);
 /* Copy the FP64 master weights back to the host (after training). */
 HELM_API helm_status helm_unet_get_weights(const helm_unet* net, double* weights_host, size_t nweights);
+/* Replace the weights (same layout as helm_unet_create) from caller-owned DEVICE memory, FP64, e.g.
+ * a parameter tensor updated by an outside optimiser; the BF16 / FP32 / FP64 working copies are
+ * rebuilt on `stream` before the call returns control to the stream's later work.  The AdamW state
+ * of helm_train_step is left as it is.  HELM_ERR_INVALID_ARG on a NULL pointer or a wrong count;
+ * non-finite values are not checked (the next solve reports HELM_NAN). */
+HELM_API helm_status helm_unet_set_weights(helm_unet* net, const double* weights_dev, size_t nweights, void* stream);
 
 /* z = h^2 N_theta(alpha v, c) / alpha per column, alpha = sqrt(n) / ||v|| (eq. 6): the network sees a
  * unit-RMS input and approximates the inverse of the dimensionless operator h^2 A.  dtype HELM_C64:

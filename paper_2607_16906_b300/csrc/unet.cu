@@ -575,6 +575,15 @@ extern "C" helm_status helm_unet_destroy(helm_unet* net) {
   return HELM_OK;
 }
 
+extern "C" helm_status helm_unet_set_weights(helm_unet* net, const double* weights_dev, size_t nweights,
+                                              void* stream) {
+  if (!net || !weights_dev || (int64_t)nweights != net->L.total)
+    return fail(HELM_ERR_INVALID_ARG, "helm_unet_set_weights: bad argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  HELM_CK(cudaMemcpyAsync(net->master, weights_dev, sizeof(double) * net->L.total, cudaMemcpyDeviceToDevice, st));
+  return unet_prepare(net, st);
+}
+
 extern "C" helm_status helm_unet_get_weights(const helm_unet* net, double* weights_host, size_t nweights) {
   if (!net || !weights_host || (int64_t)nweights != net->L.total)
     return fail(HELM_ERR_INVALID_ARG, "helm_unet_get_weights: bad argument");

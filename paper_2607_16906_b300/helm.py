@@ -63,6 +63,7 @@ _SIGS = {
     "helm_unet_create": (ct.c_int, [ct.POINTER(_P), ct.POINTER(ct.c_double), ct.c_size_t]),
     "helm_unet_destroy": (ct.c_int, [_P]),
     "helm_unet_get_weights": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.c_size_t]),
+    "helm_unet_set_weights": (ct.c_int, [_P, _P, ct.c_size_t, _P]),
     "helm_precond_apply": (ct.c_int, [_P, _P, _P, _P, ct.c_int, ct.c_int, _P]),
     "helm_fgmres_solve": (ct.c_int, [_P, _P, _P, _P, ct.c_int, ct.POINTER(helm_solve_opts),
                                      ct.POINTER(helm_solve_info), _P]),
@@ -248,6 +249,12 @@ class UNet:
         _check(_lib.helm_unet_get_weights(self._h, out.ctypes.data_as(ct.POINTER(ct.c_double)), out.size))
         return out
 
+    def set_weights(self, theta: torch.Tensor, stream=None):
+        """helm_unet_set_weights: replace the weights from a CUDA float64 tensor of nparams values."""
+        if theta.dtype != torch.float64 or not theta.is_cuda or theta.numel() != self.nparams:
+            raise ValueError("theta must be a CUDA float64 tensor with one value per parameter")
+        _check(_lib.helm_unet_set_weights(self._h, _dev_ptr(theta.contiguous()), self.nparams, _stream(stream)))
+
     def close(self):
         if self._h:
             _lib.helm_unet_destroy(self._h)
@@ -319,6 +326,25 @@ def helm_loss_grad(ctx: Context, net: UNet, b: torch.Tensor, stream=None):
     _check(_lib.helm_loss_grad(ctx.handle, net.handle, _dev_ptr(b), _dtype_code(b), ct.byref(loss), _dev_ptr(g),
                                _stream(stream)))
     return loss.value, g
+
+
+class HelmholtzLoss(torch.autograd.Function):
+    """Eq. 9 as a differentiable function of the flat parameter vector theta (CUDA float64):
+    forward loads theta into `net` and returns the batch-mean loss; backward returns the library's
+    gradient (adjoint stencil A^H and conv backward kernels), scaled by the incoming gradient.
+    Usage: loss = HelmholtzLoss.apply(theta, ctx, net, b); loss.backward()."""
+
+    @staticmethod
+    def forward(fctx, theta, ctx, net, b):
+        net.set_weights(theta.detach())
+        loss, grad = helm_loss_grad(ctx, net, b)
+        fctx.save_for_backward(grad)
+        return torch.tensor(loss, dtype=torch.float64, device=theta.device)
+
+    @staticmethod
+    def backward(fctx, gout):
+        (grad,) = fctx.saved_tensors
+        return gout * grad, None, None, None
 
 
 def helm_profile_enable(ctx: Context, on=True):

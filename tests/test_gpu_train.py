@@ -60,6 +60,33 @@ def test_fp64_gradient_central_difference(helm):
         assert abs(fd - g @ d) <= 1e-6 * abs(fd), (fd, g @ d)
 
 
+def test_autograd_function_matches_oracle_and_central_difference(helm):
+    """HelmholtzLoss (torch.autograd.Function over the library's loss and gradient, FP64 path):
+    the forward equals the oracle's eq. 9, backward equals the oracle's gradient, and the central
+    difference of the forward along a random direction (weights loaded by helm_unet_set_weights)
+    equals the directional derivative."""
+    c, b, nx, p, h, om = _batch(B=2, seed=64)
+    theta = synth.kaiming_uniform_params(ou.param_segments(), 45)
+    ctx = _ctx(helm, c, nx, p, h, om)
+    net = helm.UNet(np.zeros_like(theta))  # weights come from theta through set_weights
+    bd = torch.tensor(b.ravel(), device="cuda")
+    t = torch.tensor(theta, device="cuda", requires_grad=True)
+    loss = helm.HelmholtzLoss.apply(t, ctx, net, bd)
+    (2.0 * loss).backward()
+    Lr, gr, _ = ot.loss_and_grad(theta, b, c, p, h, om)
+    assert abs(loss.item() - Lr) <= 1e-11 * Lr
+    g = t.grad.cpu().numpy() / 2.0
+    assert np.abs(g - gr).max() <= 1e-9 * np.abs(gr).max()
+    d = synth.rng_for(8).standard_normal(theta.size)
+    eps = 1e-8
+    with torch.no_grad():
+        td = torch.tensor(d, device="cuda")
+        Lp = helm.HelmholtzLoss.apply(t + eps * td, ctx, net, bd).item()
+        Lm = helm.HelmholtzLoss.apply(t - eps * td, ctx, net, bd).item()
+    fd = (Lp - Lm) / (2 * eps)
+    assert abs(fd - g @ d) <= 1e-6 * abs(fd), (fd, g @ d)
+
+
 def test_bf16_gradient_close_to_oracle_emulation(helm):
     """BF16 activations and weights, FP32 gradients: the loss matches the oracle's BF16 emulation
     and the gradient points the same way (cosine > 0.999, normwise error <= 5e-2)."""
