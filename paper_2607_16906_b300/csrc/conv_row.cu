@@ -44,6 +44,7 @@ struct RowArgs {
   float2* z;
   int Nx, Ny;
   int64_t zstride;
+  const UnetIO* io;  // non-null: z and out_scale come from this block (CUDA graph replay)
 };
 
 template <int N, int NSL, int RY>
@@ -88,7 +89,7 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
   for (int i = threadIdx.x; i < Cfg::W_BYTES / 16; i += Cfg::THREADS)
     ((uint4*)wsm)[i] = ((const uint4*)a.wrow)[i];
   for (int i = threadIdx.x; i < N; i += Cfg::THREADS) bsm[i] = a.bias[i];
-  if (a.z)
+  if (a.z || a.io)
     for (int i = threadIdx.x; i < 34; i += Cfg::THREADS) fsm[i] = a.wf[i];
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if (threadIdx.x == 0) {
@@ -200,6 +201,10 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
     const int e = (warp - 2) >> 2;
     const int q = warp & 3;
     const int p = q * 32 + lane;
+    // fused output layer: this call's output pointer and scales (from the block under graph replay)
+    const bool fused_out = N == 16 && (a.z != nullptr || a.io != nullptr);
+    float2* const zp = a.io ? (float2*)a.io->z : a.z;
+    const double* const osc = a.io ? a.io->out_scale : a.out_scale;
     uint32_t acc_phase = 0;
     for (int t = blockIdx.x + e * gridDim.x; t < a.ntiles; t += 2 * gridDim.x) {
       if (!mbar_wait(&tfull[e], acc_phase, abort_flag, a.err, 14)) break;
@@ -231,7 +236,7 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
             if (a.relu) f = fmaxf(f, 0.0f);
             hv[k] = __float2bfloat16_rn(f);
           }
-          if (N == 16 && a.z) {
+          if (fused_out) {
             // final 1x1 conv 16 -> 2 on the BF16 activation, then the output scale and crop
             float f0 = fsm[32], f1 = fsm[33];
 #pragma unroll
@@ -241,8 +246,8 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
               f1 += f * fsm[2 * k + 1];
             }
             if (x < a.Nx && y < a.Ny) {
-              const double sc = a.out_scale[b];
-              a.z[b * a.zstride + (int64_t)y * a.Nx + x] = make_float2((float)(f0 * sc), (float)(f1 * sc));
+              const double sc = osc[b];
+              zp[b * a.zstride + (int64_t)y * a.Nx + x] = make_float2((float)(f0 * sc), (float)(f1 * sc));
             }
           } else {
             uint4* dst = (uint4*)(a.out + (((int64_t)b * a.H + y) * a.W + x) * N + cb * 16);
@@ -371,6 +376,7 @@ helm_status conv_row_forward(const __nv_bfloat16* wrow, const float* bias, int* 
   a.Nx = fin ? fin->Nx : 0;
   a.Ny = fin ? fin->Ny : 0;
   a.zstride = fin ? fin->zstride : 0;
+  a.io = fin ? fin->io : nullptr;
   a.B = B;
   a.H = H;
   a.W = W;

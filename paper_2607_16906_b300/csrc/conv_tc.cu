@@ -491,7 +491,7 @@ helm_status conv_tc_forward(const helm_unet* net, int l, const void* in0, int C0
 bool conv_tc_final_ready(const helm_unet* net) { return net->tc && net->tc->ok && net->tc->wrow[L_DEC1B]; }
 
 helm_status conv_tc_final(const helm_unet* net, const void* in, float2* z, const double* out_scale, int Nx, int Ny,
-                          int64_t zstride, int B, int H, int W, cudaStream_t st) {
+                          int64_t zstride, int B, int H, int W, cudaStream_t st, const UnetIO* io) {
   const TcState& S = *net->tc;
   RowFinal f;
   f.wf = net->w32 + net->L.c_w[L_FINAL];  // [16][2] followed by the 2 biases
@@ -500,6 +500,7 @@ helm_status conv_tc_final(const helm_unet* net, const void* in, float2* z, const
   f.Nx = Nx;
   f.Ny = Ny;
   f.zstride = zstride;
+  f.io = io;
   return conv_row_forward(S.wrow[L_DEC1B], net->w32 + net->L.c_b[L_DEC1B], S.err, in, 16, nullptr, 0, nullptr, 16, B,
                           H, W, st, &f);
 }

@@ -109,6 +109,8 @@ void unet_buffers_free(helm_ctx* ctx);  // unet.cu
 
 static std::atomic<uint64_t> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
 void prof_begin(helm_ctx* ctx, int ph, cudaStream_t st) {
   if (!ctx->prof_on) return;

@@ -157,6 +157,8 @@ inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b);
 // Every kernel of the library is launched through launch(): it keeps a process-wide count of
 // launches (helm_launch_count) for the benchmark's launch accounting.
 void count_launch();
+void count_launches(uint64_t n);    // kernels of a CUDA graph replay
+void uncount_launches(uint64_t n);  // kernels captured into a graph (recorded, not run)
 template <typename... KArgs, typename... Args>
 inline void launch(void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args) {
   k<<<grid, block, smem, st>>>(args...);

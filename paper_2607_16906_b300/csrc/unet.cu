@@ -13,6 +13,8 @@
 //   CUDA-core kernels below cover the rest (first layer, up-convs, final 1x1).
 #include <math.h>
 
+#include <atomic>
+
 #include <type_traits>
 
 #include "helm_internal.cuh"
@@ -231,9 +233,13 @@ __global__ void k_pool(const T* __restrict__ in, T* __restrict__ out, int C, int
 template <typename T, typename R>
 __global__ void k_pack_input(const C<R>* __restrict__ v, int64_t col_stride, const double* __restrict__ in_scale,
                              const typename Acc<T>::A* __restrict__ chat, int64_t c_stride, int Nx, int Ny, int Hp, int Wp, int B, int S0,
-                             T* __restrict__ x0) {
+                             T* __restrict__ x0, const UnetIO* __restrict__ io) {
   int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (pix >= (int64_t)B * Hp * Wp) return;
+  if (io) {  // pointers of this call from the fixed block (graph replay)
+    v = (const C<R>*)io->v;
+    in_scale = io->in_scale;
+  }
   int x = (int)(pix % Wp);
   int y = (int)((pix / Wp) % Hp);
   int b = (int)(pix / ((int64_t)Wp * Hp));
@@ -270,10 +276,15 @@ __global__ void k_pack_input(const C<R>* __restrict__ v, int64_t col_stride, con
 template <typename T, typename R>
 __global__ void k_final(const T* __restrict__ in, const typename Acc<T>::A* __restrict__ W,
                         const typename Acc<T>::A* __restrict__ bias, const double* __restrict__ out_scale, int Nx,
-                        int Ny, int Hp, int Wp, int B, C<R>* __restrict__ z, int64_t col_stride, float* raw_out) {
+                        int Ny, int Hp, int Wp, int B, C<R>* __restrict__ z, int64_t col_stride, float* raw_out,
+                        const UnetIO* __restrict__ io) {
   using A = typename Acc<T>::A;
   int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (e >= (int64_t)B * Ny * Nx) return;
+  if (io) {
+    z = (C<R>*)io->z;
+    out_scale = io->out_scale;
+  }
   int x = (int)(e % Nx);
   int y = (int)((e / Nx) % Ny);
   int b = (int)(e / ((int64_t)Nx * Ny));
@@ -318,15 +329,24 @@ helm_status ensure_buffers(helm_ctx* ctx, int B, int Hp, int Wp, bool fp64, Unet
   if (!ub) ub = new UnetBuffers();
   int idx = fp64 ? 1 : 0;
   UnetBuffers::Set& S = ub->set[idx];
-  if (S.base && S.B >= B && S.Hp == Hp && S.Wp == Wp) {
+  if (S.base && S.B == B && S.Hp == Hp && S.Wp == Wp) {
     *out = ub;
     return HELM_OK;
   }
-  if (S.base) cudaFree(S.base);
-  S.base = nullptr;
   size_t es = fp64 ? 8 : 2;
   size_t per = act_bytes_per_image(Hp, Wp, fp64) + 64 * 24;
-  HELM_CK(cudaMalloc(&S.base, per * B + 4096));
+  const size_t need = per * B + 4096;
+  if (!S.base || S.cap < need) {  // grow; a smaller or differently shaped batch reuses the block
+    if (S.base) {
+      HELM_CK(cudaDeviceSynchronize());  // captured graphs and queued launches may still use it
+      cudaFree(S.base);
+    }
+    S.base = nullptr;
+    S.cap = 0;
+    HELM_CK(cudaMalloc(&S.base, need));
+    S.cap = need;
+    ++ub->gen;
+  }
   S.B = B;
   S.Hp = Hp;
   S.Wp = Wp;
@@ -365,9 +385,16 @@ helm_status ensure_buffers(helm_ctx* ctx, int B, int Hp, int Wp, bool fp64, Unet
 
 void unet_buffers_free(helm_ctx* ctx) {
   if (!ctx->ub) return;
-  for (auto& S : ctx->ub->set)
+  UnetBuffers* ub = ctx->ub;
+  for (auto& kv : ub->graphs)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  if (ub->ev_in) cudaEventDestroy(ub->ev_in);
+  if (ub->ev_out) cudaEventDestroy(ub->ev_out);
+  if (ub->gstream) cudaStreamDestroy(ub->gstream);
+  cudaFree(ub->io);
+  for (auto& S : ub->set)
     if (S.base) cudaFree(S.base);
-  delete ctx->ub;
+  delete ub;
   ctx->ub = nullptr;
 }
 
@@ -442,16 +469,16 @@ helm_status unet_body(const helm_unet* net, UnetBuffers::Set& S, int B, cudaStre
   return HELM_OK;
 }
 
+// The launch sequence of one network application (pack, U-Net body, output layer) on stream `st`;
+// with `io` the input/output pointers and scales are read from the device block instead.
 template <typename R>
-helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
-                              const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride,
-                              bool keep_acts) {
+static helm_status unet_sequence(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
+                                 const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride,
+                                 bool keep_acts, const UnetIO* io) {
   using T = typename std::conditional<sizeof(R) == 8, double, __nv_bfloat16>::type;
   const SysHost& s = ctx->sys[sys];
   int Hp = (s.Ny + 7) / 8 * 8, Wp = (s.Nx + 7) / 8 * 8;
-  UnetBuffers* ub;
-  HELM_TRY(ensure_buffers(ctx, B, Hp, Wp, sizeof(R) == 8, &ub));
-  UnetBuffers::Set& S = ub->set[sizeof(R) == 8 ? 1 : 0];
+  UnetBuffers::Set& S = ctx->ub->set[sizeof(R) == 8 ? 1 : 0];
   T** a = (T**)S.a;
   int64_t npix = (int64_t)B * Hp * Wp;
   const typename Acc<T>::A* chat;
@@ -460,8 +487,7 @@ helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, cons
   else
     chat = ctx->chat + s.off;
   launch(k_pack_input<T, R>, cdiv(npix, 256), 256, 0, st, v, s.n, in_scale, chat, c_stride, s.Nx, s.Ny, Hp, Wp, B,
-         X0_CH,
-                                                      a[A_X0]);
+         X0_CH, a[A_X0], io);
   HELM_CK_LAUNCH();
   // BF16 path with the row kernels: the last conv, the final 1x1 conv and the output scaling run as
   // one kernel (the 16-channel activation of the last layer is never stored)
@@ -471,14 +497,84 @@ helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, cons
   HELM_TRY(unet_body<T>(net, S, B, st, fused));
   if constexpr (sizeof(R) == 4) {
     if (fused)
-      return conv_tc_final(net, a[A_D1A], (float2*)z, out_scale, s.Nx, s.Ny, s.n, B, Hp, Wp, st);
+      return conv_tc_final(net, a[A_D1A], (float2*)z, out_scale, s.Nx, s.Ny, s.n, B, Hp, Wp, st, io);
   }
   const auto* w = cc_weights<T>(net);
   int64_t nout = (int64_t)B * s.Ny * s.Nx;
   launch(k_final<T, R>, cdiv(nout, 256), 256, 0, st, a[A_D1B], w + net->L.c_w[L_FINAL], w + net->L.c_b[L_FINAL],
-                                                 out_scale, s.Nx, s.Ny, Hp, Wp, B, z, s.n, nullptr);
+         out_scale, s.Nx, s.Ny, Hp, Wp, B, z, s.n, nullptr, io);
   HELM_CK_LAUNCH();
   return HELM_OK;
+}
+
+__global__ void k_set_io(UnetIO* io, const void* v, void* z, const double* in_scale, const double* out_scale) {
+  io->v = v;
+  io->z = z;
+  io->in_scale = in_scale;
+  io->out_scale = out_scale;
+}
+
+static bool graphs_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("HELM_DISABLE_GRAPHS");
+    return !(e && e[0] == '1');
+  }();
+  return on;
+}
+
+template <typename R>
+helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
+                              const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride,
+                              bool keep_acts) {
+  const SysHost& s = ctx->sys[sys];
+  int Hp = (s.Ny + 7) / 8 * 8, Wp = (s.Nx + 7) / 8 * 8;
+  UnetBuffers* ub;
+  HELM_TRY(ensure_buffers(ctx, B, Hp, Wp, sizeof(R) == 8, &ub));
+  if (sizeof(R) == 8 || keep_acts)  // FP64 network and training forward: plain launches
+    return unet_sequence<R>(ctx, net, sys, v, z, B, in_scale, out_scale, st, c_stride, keep_acts, nullptr);
+
+  // BF16 inference: pointers of this call into the device block, then the captured network
+  if (!ub->io) {
+    HELM_CK(cudaMalloc(&ub->io, sizeof(UnetIO)));
+    HELM_CK(cudaStreamCreateWithFlags(&ub->gstream, cudaStreamNonBlocking));
+    HELM_CK(cudaEventCreateWithFlags(&ub->ev_in, cudaEventDisableTiming));
+    HELM_CK(cudaEventCreateWithFlags(&ub->ev_out, cudaEventDisableTiming));
+  }
+  launch(k_set_io, 1, 1, 0, st, ub->io, (const void*)v, (void*)z, in_scale, out_scale);
+  HELM_CK_LAUNCH();
+  const UnetGraphKey key{net->id, sys, B, c_stride, ub->gen};
+  auto it = graphs_enabled() ? ub->graphs.find(key) : ub->graphs.end();
+  if (it == ub->graphs.end() && graphs_enabled() && ub->seen.count(key)) {
+    // second use of this key: capture the sequence on the library's own stream
+    const uint64_t l0 = helm_launch_count();
+    HELM_CK(cudaStreamBeginCapture(ub->gstream, cudaStreamCaptureModeThreadLocal));
+    helm_status rc = unet_sequence<R>(ctx, net, sys, v, z, B, in_scale, out_scale, ub->gstream, c_stride, false, ub->io);
+    cudaGraph_t g = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(ub->gstream, &g);
+    const uint64_t nk = helm_launch_count() - l0;
+    uncount_launches(nk);  // captured, not run
+    if (rc != HELM_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture", __FILE__, __LINE__);
+    cudaGraphExec_t ex = nullptr;
+    ce = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ce != cudaSuccess) return cuda_fail(ce, "cudaGraphInstantiate", __FILE__, __LINE__);
+    it = ub->graphs.emplace(key, UnetGraph{ex, nk}).first;
+  }
+  if (it != ub->graphs.end()) {
+    HELM_CK(cudaEventRecord(ub->ev_in, st));
+    HELM_CK(cudaStreamWaitEvent(ub->gstream, ub->ev_in, 0));
+    HELM_CK(cudaGraphLaunch(it->second.exec, ub->gstream));
+    count_launches(it->second.kernels);
+    HELM_CK(cudaEventRecord(ub->ev_out, ub->gstream));
+    HELM_CK(cudaStreamWaitEvent(st, ub->ev_out, 0));
+    return HELM_OK;
+  }
+  if (graphs_enabled()) ub->seen.insert(key);
+  return unet_sequence<R>(ctx, net, sys, v, z, B, in_scale, out_scale, st, c_stride, false, ub->io);
 }
 
 template helm_status unet_precondition<float>(helm_ctx*, const helm_unet*, int, const float2*, float2*, int,
@@ -540,7 +636,9 @@ extern "C" helm_status helm_unet_create(helm_unet** out, const double* weights_h
                                           std::to_string(nweights));
   for (size_t i = 0; i < nweights; ++i)
     if (!std::isfinite(weights_host[i])) return fail(HELM_ERR_INVALID_ARG, "helm_unet_create: non-finite weight");
+  static std::atomic<uint64_t> next_id{1};
   helm_unet* net = new helm_unet();
+  net->id = next_id.fetch_add(1);
   net->L = L;
   cudaStream_t st = 0;
   helm_status rc = HELM_OK;

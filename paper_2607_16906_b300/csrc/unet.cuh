@@ -1,6 +1,9 @@
 // Internal network declarations: layer table, parameter layout, activation buffers.
 #pragma once
 
+#include <map>
+#include <set>
+
 #include "helm_internal.cuh"
 
 namespace helm {
@@ -32,12 +35,50 @@ enum ActId {
 };
 constexpr int X0_CH = 16;  // input channels padded 3 -> 16 (one 32-byte row of BF16 per pixel)
 
+// Pointers of one BF16 inference call that change from call to call (the Krylov slot read, the
+// slot written, the per-column scales), read by the input and output kernels from a fixed device
+// block so that a captured CUDA graph of the whole network stays valid.
+struct UnetIO {
+  const void* v;
+  void* z;
+  const double* in_scale;
+  const double* out_scale;
+};
+
+// Captured network applications, keyed by (network id, system, columns, velocity stride, buffer
+// generation).  A key is captured on its second use (the first runs eagerly, so that every
+// allocation and one-time set-up has happened) and replayed afterwards.
+struct UnetGraphKey {
+  uint64_t net_id;
+  int sys, B;
+  int64_t c_stride;
+  uint64_t gen;
+  bool operator<(const UnetGraphKey& o) const {
+    if (net_id != o.net_id) return net_id < o.net_id;
+    if (sys != o.sys) return sys < o.sys;
+    if (B != o.B) return B < o.B;
+    if (c_stride != o.c_stride) return c_stride < o.c_stride;
+    return gen < o.gen;
+  }
+};
+struct UnetGraph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;  // kernel nodes per replay
+};
+
 struct UnetBuffers {
   struct Set {
     void* base = nullptr;
+    size_t cap = 0;  // bytes allocated at base
     int B = 0, Hp = 0, Wp = 0;
     void* a[NUM_ACTS] = {};
   } set[2];  // [0] BF16, [1] FP64
+  uint64_t gen = 0;  // bumped whenever an allocation moves (invalidates captured graphs)
+  UnetIO* io = nullptr;  // device block read by the BF16 inference kernels
+  cudaStream_t gstream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::map<UnetGraphKey, UnetGraph> graphs;
+  std::set<UnetGraphKey> seen;
 };
 
 struct TcLayer;  // tcgen05 per-layer state (conv_tc.cu)
@@ -61,10 +102,11 @@ struct RowFinal {
   float2* z;
   int Nx, Ny;
   int64_t zstride;
+  const UnetIO* io;  // non-null: z and out_scale are read from this block at run time
 };
 bool conv_tc_final_ready(const helm_unet* net);
 helm_status conv_tc_final(const helm_unet* net, const void* in, float2* z, const double* out_scale, int Nx, int Ny,
-                          int64_t zstride, int B, int H, int W, cudaStream_t st);
+                          int64_t zstride, int B, int H, int W, cudaStream_t st, const UnetIO* io = nullptr);
 // HELM_TIMEOUT if a tcgen05 conv kernel recorded a pipeline timeout since the last check (synchronises).
 helm_status conv_tc_check(const helm_unet* net, cudaStream_t st);
 
@@ -93,6 +135,7 @@ helm_status unet_prepare(helm_unet* net, cudaStream_t st);
 }  // namespace helm
 
 struct helm_unet {
+  uint64_t id = 0;  // unique per created network (keys of captured graphs)
   helm::NetLayout L;
   double* master = nullptr;  // FP64 master weights (PyTorch layouts)
   double* w64 = nullptr;     // CUDA-core layout, FP64
