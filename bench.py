@@ -370,6 +370,8 @@ def run_cuda(args):
                 "roofline": roof, "phase_rooflines": phase_rooflines, "phase_work": work,
                 "stencil_roofline": stencil,
                 "plain_fp64": plain, "train_step": train,
+                "autotune": [f"{t['c_out']}<-{8 * t['slices']} {t['images']}x{t['H']}x{t['W']}: RY={t['rows_per_tile']}"
+                             for t in helm.helm_tuned_tiles()],
                 "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
                 "e2e": {"value": conv_e2e / (ms_e2e / 1e3), "unit": "solves/s", "h2d_bytes_per_step": nbytes,
                         "d2h_bytes_per_step": nbytes, "steps": e2e_steps}}

@@ -221,6 +221,11 @@ HELM_API helm_status helm_profile_read(const helm_ctx* ctx, double* ms_host, int
 HELM_API helm_status helm_profile_work(const helm_ctx* ctx, double* work_host);
 /* Kernels launched by this library in this process so far (all contexts). */
 HELM_API uint64_t helm_launch_count(void);
+/* Tile heights the autotuner chose so far for the row-tile convolutions (no counterpart in the
+ * paper: the library picks, per layer shape, the fastest of a few rows-per-tile variants the first
+ * time the shape runs).  Writes up to max_entries records of 6 ints {C_out, 8-channel input slices,
+ * images, H, W, rows per tile} to out (host) and returns how many it wrote. */
+HELM_API int helm_tuned_tiles(int* out, int max_entries);
 
 /* Thread-local message for the last non-OK status returned on this thread. */
 HELM_API const char* helm_last_error(void);

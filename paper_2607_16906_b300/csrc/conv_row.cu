@@ -13,7 +13,10 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "tc_ptx.cuh"
 #include "unet.cuh"
@@ -364,6 +367,116 @@ helm_status conv_row_prepare(const double* master, int64_t m_w, int cin, int cin
   return HELM_OK;
 }
 
+// ------------------------------------------------------------------ autotuner
+//
+// The rows per tile (RY) trade halo re-reads (RY + 2 loaded rows per RY output rows) against
+// pipeline depth and CTAs per SM (shared memory, TMEM columns).  On the first call for a layer
+// shape (C_out, slices, B, H, W) every candidate runs once untimed (one-time set-up) and once timed
+// with CUDA events on the caller's stream; the fastest is kept for that shape.  All candidates
+// produce bit-identical outputs (same MMA order per output pixel), so tuning does not perturb
+// results.  HELM_AUTOTUNE=0 keeps the first candidate; calls during a CUDA-graph capture use the
+// cached choice or the first candidate.
+
+typedef helm_status (*RowLaunchFn)(const void*, int, const void*, int, RowArgs, cudaStream_t);
+struct RowCand {
+  int ry;
+  RowLaunchFn fn;
+};
+struct RowKey {
+  int cout, nsl, B, H, W;
+  bool operator<(const RowKey& o) const {
+    return std::tie(cout, nsl, B, H, W) < std::tie(o.cout, o.nsl, o.B, o.H, o.W);
+  }
+};
+
+static const std::vector<RowCand>& row_candidates(int cout, int nsl) {
+  static const std::vector<RowCand> none;
+  static const std::vector<RowCand> c1602 = {
+      {4, launch_row<16, 2, 4>}, {2, launch_row<16, 2, 2>}, {8, launch_row<16, 2, 8>}};
+  static const std::vector<RowCand> c1604 = {{4, launch_row<16, 4, 4>}, {2, launch_row<16, 4, 2>}};
+  static const std::vector<RowCand> c3202 = {{4, launch_row<32, 2, 4>}, {2, launch_row<32, 2, 2>}};
+  static const std::vector<RowCand> c3204 = {{2, launch_row<32, 4, 2>}, {4, launch_row<32, 4, 4>}};
+  static const std::vector<RowCand> c3208 = {{2, launch_row<32, 8, 2>}, {1, launch_row<32, 8, 1>}};
+  static const std::vector<RowCand> c6404 = {{2, launch_row<64, 4, 2>}, {4, launch_row<64, 4, 4>}};
+  switch (cout * 100 + nsl) {
+    case 1602: return c1602;
+    case 1604: return c1604;
+    case 3202: return c3202;
+    case 3204: return c3204;
+    case 3208: return c3208;
+    case 6404: return c6404;
+    default: return none;
+  }
+}
+
+static bool autotune_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("HELM_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+static std::mutex g_row_mu;
+static std::map<RowKey, int> g_row_choice;  // index into the candidate list
+
+static helm_status row_autotuned(const std::vector<RowCand>& cands, const RowKey& key, const void* in0, int C0,
+                                 const void* in1, int C1, const RowArgs& a, cudaStream_t st) {
+  {
+    std::lock_guard<std::mutex> lk(g_row_mu);
+    auto it = g_row_choice.find(key);
+    if (it != g_row_choice.end()) return cands[it->second].fn(in0, C0, in1, C1, a, st);
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  HELM_CK(cudaStreamIsCapturing(st, &cap));
+  if (!autotune_enabled() || cands.size() == 1 || cap != cudaStreamCaptureStatusNone)
+    return cands[0].fn(in0, C0, in1, C1, a, st);
+  cudaEvent_t e0, e1;
+  HELM_CK(cudaEventCreate(&e0));
+  HELM_CK(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  helm_status rc = HELM_OK;
+  for (size_t i = 0; i < cands.size() && rc == HELM_OK; ++i) {
+    rc = cands[i].fn(in0, C0, in1, C1, a, st);  // one-time set-up and warm-up
+    if (rc != HELM_OK) break;
+    cudaEventRecord(e0, st);
+    rc = cands[i].fn(in0, C0, in1, C1, a, st);
+    cudaEventRecord(e1, st);
+    if (rc != HELM_OK) break;
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+        (i == 0 || ms < best_ms)) {
+      best = (int)i;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HELM_OK) return rc;
+  std::lock_guard<std::mutex> lk(g_row_mu);
+  g_row_choice[key] = best;
+  return HELM_OK;
+}
+
+// Rows per tile chosen for each tuned layer shape so far: out[k] = {cout, slices, B, H, W, RY}.
+int conv_row_tuned(int (*out)[6], int max) {
+  std::lock_guard<std::mutex> lk(g_row_mu);
+  int k = 0;
+  for (auto& kv : g_row_choice) {
+    if (k >= max) break;
+    const RowKey& r = kv.first;
+    out[k][0] = r.cout;
+    out[k][1] = r.nsl;
+    out[k][2] = r.B;
+    out[k][3] = r.H;
+    out[k][4] = r.W;
+    out[k][5] = row_candidates(r.cout, r.nsl)[kv.second].ry;
+    ++k;
+  }
+  return k;
+}
+
 helm_status conv_row_forward(const __nv_bfloat16* wrow, const float* bias, int* err, const void* in0, int C0,
                              const void* in1, int C1, void* out, int cout, int B, int H, int W, cudaStream_t st,
                              const RowFinal* fin) {
@@ -390,15 +503,14 @@ helm_status conv_row_forward(const __nv_bfloat16* wrow, const float* bias, int* 
   a.relu = 1;
   a.err = err;
   const int nsl = (C0 + C1) / 8;
-  switch (cout * 100 + nsl) {
-    case 1602: return launch_row<16, 2, 4>(in0, C0, in1, C1, a, st);
-    case 1604: return launch_row<16, 4, 4>(in0, C0, in1, C1, a, st);
-    case 3202: return launch_row<32, 2, 4>(in0, C0, in1, C1, a, st);
-    case 3204: return launch_row<32, 4, 2>(in0, C0, in1, C1, a, st);
-    case 3208: return launch_row<32, 8, 2>(in0, C0, in1, C1, a, st);
-    case 6404: return launch_row<64, 4, 2>(in0, C0, in1, C1, a, st);
-    default: return fail(HELM_ERR_INVALID_ARG, "conv_row_forward: unsupported layer shape");
-  }
+  const std::vector<RowCand>& cands = row_candidates(cout, nsl);
+  if (cands.empty()) return fail(HELM_ERR_INVALID_ARG, "conv_row_forward: unsupported layer shape");
+  return row_autotuned(cands, RowKey{cout, nsl, B, H, W}, in0, C0, in1, C1, a, st);
 }
 
 }  // namespace helm
+
+extern "C" int helm_tuned_tiles(int* out, int max_entries) {
+  if (!out || max_entries <= 0) return 0;
+  return helm::conv_row_tuned(reinterpret_cast<int (*)[6]>(out), max_entries);
+}

@@ -76,6 +76,7 @@ _SIGS = {
     "helm_profile_read": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
     "helm_profile_work": (ct.c_int, [_P, ct.POINTER(ct.c_double)]),
     "helm_launch_count": (ct.c_uint64, []),
+    "helm_tuned_tiles": (ct.c_int, [ct.POINTER(ct.c_int), ct.c_int]),
     "helm_last_error": (ct.c_char_p, []),
 }
 PHASES = ("precond", "stencil", "orth", "lsq", "residual", "update")
@@ -365,6 +366,14 @@ def helm_profile_work(ctx: Context):
     w = (ct.c_double * len(PHASES))()
     _check(_lib.helm_profile_work(ctx.handle, w))
     return {p: w[i] for i, p in enumerate(PHASES)}
+
+
+def helm_tuned_tiles():
+    """Rows per tile the autotuner chose per row-conv layer shape: list of dicts."""
+    buf = (ct.c_int * (6 * 256))()
+    n = _lib.helm_tuned_tiles(buf, 256)
+    keys = ("c_out", "slices", "images", "H", "W", "rows_per_tile")
+    return [dict(zip(keys, buf[6 * k: 6 * k + 6])) for k in range(n)]
 
 
 def helm_launch_count() -> int:
