@@ -10,7 +10,8 @@ this from the current x (Sec. 4: l cycles of m iterations).
 Readings where the paper is silent:
   * h_ij = v_i^H w (the w update removes the component along v_i);
   * orthogonalisation "mgs" is the paper's inner loop; "cgs2" is classical
-    Gram-Schmidt applied twice, h = h1 + h2;
+    Gram-Schmidt applied twice, h = h1 + h2; "dcgs2" delays the second pass by
+    one step (the preconditioner then sees the once-orthogonalised vector);
   * the least-squares problem is solved by complex Givens rotations
     (c real = |a| / sqrt(|a|^2 + |b|^2), s = (a / |a|) conj(b) / sqrt(...),
     c = 0, s = 1 when a = 0) applied as the columns arrive; |g_{j+1}| is the
@@ -73,8 +74,112 @@ def givens(a, b):
     return c, s
 
 
+def _rotate_column(col, j, cs, sn):
+    """Apply the rotations 0..j-1 to Hessenberg column j (length j + 2), then form rotation j."""
+    col = col.copy()
+    for i in range(j):
+        a, b_ = col[i], col[i + 1]
+        col[i] = cs[i] * a + sn[i] * b_
+        col[i + 1] = -np.conj(sn[i]) * a + cs[i] * b_
+    cs[j], sn[j] = givens(col[j], col[j + 1])
+    col[j] = cs[j] * col[j] + sn[j] * col[j + 1]
+    col[j + 1] = 0.0
+    return col
+
+
+def _back_substitute(R, g, k):
+    y = np.zeros(k, np.complex128)
+    for i in range(k - 1, -1, -1):
+        y[i] = (g[i] - R[i, i + 1:k] @ y[i + 1:k]) / R[i, i]
+    return y
+
+
+def _cycle_dcgs2(apply_A, precond, r0, m, target, dtype):
+    """One FGMRES(m) cycle with classical Gram-Schmidt whose second pass is delayed by one step.
+
+    The vector u_j entering step j has been orthogonalised once.  Step j preconditions it,
+    z_j = M(u_j / ||u_j||), forms w_j = A z_j and, from one pass over V_j = (v_0..v_{j-1}),
+    a = V_j^H u_j and b = V_j^H w_j.  The second pass of u_j then finishes column j-1 of Hbar:
+    h_{:j, j-1} += a, h_{j, j-1} = rho = sqrt(||u_j||^2 - ||a||^2), v_j = (u_j - V_j a) / rho; and the
+    first pass of w_j gives column j: h_{:j, j} = b, h_{j, j} = d = (u_j^H w_j - a^H b) / rho and
+    u_{j+1} = w_j - V_j b - v_j d.  Column j-1 is rotated (and the stopping test made) at step j;
+    after the last step a final pass finishes column m-1.  v_0 = r0 / ||r0|| needs no second pass.
+    Any z_j is admissible in flexible GMRES: A Z = V Hbar holds with the V and Hbar formed here.
+    """
+    n = r0.size
+    beta = np.linalg.norm(r0)
+    V = np.zeros((m + 1, n), dtype)
+    Z = np.zeros((m, n), dtype)
+    H = np.zeros((m + 1, m), np.complex128)
+    R = np.zeros((m + 1, m), np.complex128)
+    cs = np.zeros(m)
+    sn = np.zeros(m, np.complex128)
+    g = np.zeros(m + 1, np.complex128)
+    g[0] = beta
+    V[0] = (r0 / beta).astype(dtype)
+    u = V[0].copy()
+    wnorm = np.zeros(m)
+    history = []
+    k, est, breakdown = 0, beta, False
+
+    def finish(j, u):
+        """Second pass of u = u_{j+1}: completes column j, sets V[j + 1]; returns (rho, a)."""
+        Vp = V[:j + 1]
+        a = Vp.conj() @ u
+        rho = np.sqrt(max(np.vdot(u, u).real - np.vdot(a, a).real, 0.0))
+        H[:j + 1, j] += a
+        H[j + 1, j] = rho
+        if rho > 0:
+            V[j + 1] = ((u - Vp.T @ a.astype(dtype)) / rho).astype(dtype)
+        return rho, a
+
+    def rotate(j):
+        R[:j + 2, j] = _rotate_column(H[:j + 2, j], j, cs, sn)
+        g[j + 1] = -np.conj(sn[j]) * g[j]
+        g[j] = cs[j] * g[j]
+        return abs(g[j + 1])
+
+    stopped = False
+    for j in range(m):
+        nu = np.linalg.norm(u)
+        Z[j] = np.asarray(precond((u / nu).astype(dtype)), dtype)  # the preconditioner sees unit norm
+        w = np.asarray(apply_A(Z[j]), np.complex128).astype(dtype)
+        wnorm[j] = np.linalg.norm(w)
+        rho, a = 1.0, np.zeros(j, np.complex128)  # v_0 needs no second pass
+        u_j = u
+        if j > 0:
+            rho, a = finish(j - 1, u)        # v_j and column j-1
+            k = j
+            est = rotate(j - 1)
+            history.append(est)
+            if rho <= 1e-14 * max(wnorm[j - 1], np.finfo(float).tiny):
+                breakdown, stopped = True, True
+                break
+            if est <= target:
+                stopped = True
+                break
+        Vp = V[:j + 1]
+        b = Vp[:j].conj() @ w
+        H[:j, j] = b
+        H[j, j] = (np.vdot(u_j, w) - np.vdot(a, b)) / rho  # = v_j^H w_j
+        u = (w - Vp.T @ H[:j + 1, j].astype(dtype)).astype(dtype)
+    if not stopped:
+        rho, _ = finish(m - 1, u)
+        k = m
+        est = rotate(m - 1)
+        history.append(est)
+        breakdown = rho <= 1e-14 * max(wnorm[m - 1], np.finfo(float).tiny)
+    y = _back_substitute(R, g, k)
+    d = Z[:k].T.astype(np.complex128) @ y
+    return CycleResult(d, k, est, V[:k + 1], Z[:k], H[:k + 1, :k], y, breakdown, history)
+
+
 def cycle(apply_A, precond, r0, m, target, orth="cgs2", dtype=np.complex128):
-    """One FGMRES(m) cycle on A d = r0 from d0 = 0.  Returns the correction d in CycleResult.x."""
+    """One FGMRES(m) cycle on A d = r0 from d0 = 0.  Returns the correction d in CycleResult.x.
+    orth: "mgs" (Alg. 1's loop), "cgs2" (classical Gram-Schmidt twice) or "dcgs2" (second pass
+    delayed by one step, see _cycle_dcgs2)."""
+    if orth == "dcgs2":
+        return _cycle_dcgs2(apply_A, precond, r0, m, target, dtype)
     n = r0.size
     beta = np.linalg.norm(r0)
     V = np.zeros((m + 1, n), dtype)

@@ -33,7 +33,8 @@ def _flat_b(probs):
 @pytest.mark.parametrize("orth", ["cgs2", "dcgs2"])
 @pytest.mark.parametrize("use_net,m", [(False, 20), (True, 8)])
 def test_one_cycle_matches_oracle_fp64(helm, theta, use_net, m, orth):
-    """x after one FGMRES(m) cycle from x0 = 0 equals the oracle's cycle (Alg. 1) to rounding."""
+    """x after one FGMRES(m) cycle from x0 = 0 equals the oracle's cycle (Alg. 1) with the same
+    orthogonalisation (CGS2, or DCGS2 with its lagged second pass) to rounding."""
     probs = small_problems(((20, 14, 5),), seed=31)
     p = probs[0]
     ctx = make_ctx(probs)
@@ -47,7 +48,7 @@ def test_one_cycle_matches_oracle_fp64(helm, theta, use_net, m, orth):
         pre = lambda v: unet.precondition(theta, v.reshape(1, p.Ny, p.Nx), p.c, p.h)[0].ravel()
     else:
         pre = lambda v: v
-    res = fg.cycle(lambda u: A @ u, pre, p.b[0].ravel(), m, 0.0)
+    res = fg.cycle(lambda u: A @ u, pre, p.b[0].ravel(), m, 0.0, orth=orth)
     got = x.cpu().numpy()
     assert np.linalg.norm(got - res.x) <= 1e-9 * np.linalg.norm(res.x)
     assert abs(info[0]["relres_est"] - res.est / np.linalg.norm(p.b)) <= 1e-9 * res.est / np.linalg.norm(p.b)
