@@ -31,6 +31,14 @@
  *  - Errors: no call aborts, traps or exits.  Each returns a helm_status;
  *    helm_last_error() gives a message for the calling thread.  Invalid
  *    arguments are detected on the host before anything is launched.
+ *  - Environment switches: HELM_DISABLE_GRAPHS=1 runs the
+ *    BF16 network eagerly instead of replaying captured CUDA graphs;
+ *    HELM_AUTOTUNE=0 keeps the first rows-per-tile variant of every row-tile
+ *    convolution instead of timing the variants on first use; HELM_DISABLE_TC=1
+ *    runs the BF16 convolutions on CUDA cores, HELM_DISABLE_ROW=1 the narrow
+ *    layers on the 9-box tcgen05 kernels (comparison and testing aids).  The first
+ *    two are read once per process, the last two when a network is created.  None
+ *    changes a result beyond FP32 summation order, and the first two none at all.
  */
 #ifndef HELM_H
 #define HELM_H
