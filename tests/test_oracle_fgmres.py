@@ -111,11 +111,12 @@ def test_converged_solution_matches_direct_solve():
     assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
 
 
-def test_refinement_with_low_precision_inner_solve():
+@pytest.mark.parametrize("orth", ["cgs2", "dcgs2"])
+def test_refinement_with_low_precision_inner_solve(orth):
     A, b, c, p, h = _system()
     lu_near = spla.splu(hz.assemble(c, p, h, OMEGA * 1.05).tocsc())
     x, info = fg.refine(lambda u: A @ u, lambda v: lu_near.solve(v.astype(complex)).astype(np.complex64),
-                        b, m=30, tol=1e-10, inner_tol=1e-4)
+                        b, m=30, tol=1e-10, inner_tol=1e-4, orth=orth)
     assert info.converged and info.outer >= 2      # one FP32 inner solve alone cannot reach 1e-10
     xs = hz.solve_direct(A, b)
     assert np.linalg.norm(x - xs) <= 1e-7 * np.linalg.norm(xs)
