@@ -159,7 +159,11 @@ HELM_API helm_status helm_unet_set_weights(helm_unet* net, const double* weights
 /* z = h^2 N_theta(alpha v, c) / alpha per column, alpha = sqrt(n) / ||v|| (eq. 6): the network sees a
  * unit-RMS input and approximates the inverse of the dimensionless operator h^2 A.  dtype HELM_C64:
  * BF16 network with FP32 accumulation (3x3 and up-convs on tcgen05 tensor cores); HELM_C128: FP64
- * network on CUDA cores.  v, z batch vectors; a zero column gives z = 0. */
+ * network on CUDA cores.  v, z batch vectors; a zero column gives z = 0.
+ * HELM_C64 runs: the second call for the same (network, system, nrhs) captures the network's launch
+ * sequence into a CUDA graph that later calls replay on the library's own stream (ordered after and
+ * before the caller's stream by events); the first call that meets a new row-tile conv layer shape
+ * times its tile variants once, which synchronises the caller's stream that one time. */
 HELM_API helm_status helm_precond_apply(helm_ctx* ctx, const helm_unet* net, const void* v, void* z,
                                helm_dtype dtype, int nrhs, void* stream);
 
