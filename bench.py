@@ -318,7 +318,7 @@ def run_cuda(args):
     # velocities, point-source and line-array sources): helm_train_step = BF16 forward, adjoint
     # stencil, conv backward, AdamW (eqs. 8-9); 3 warm-up and 10 timed steps on a copy of the weights
     train = None
-    if not args.no_train:
+    if rank == 0 and not args.no_train:
         cs, bs, th, om = synth.training_batch()
         nb, nt = cs.shape[0], cs.shape[1] - 32
         tctx = helm.Context([helm.SystemSpec(nt, nt, th, 16, om) for _ in range(nb)],
@@ -341,7 +341,7 @@ def run_cuda(args):
 
     # bounded plain-FP64 comparison: time a few FP64 iterations (FP64 U-Net), scale by the same count
     plain = None
-    if not args.no_plain:
+    if rank == 0 and not args.no_plain:
         helm.helm_profile_enable(ctx, True)
         x.zero_()
         torch.cuda.synchronize()
@@ -357,7 +357,7 @@ def run_cuda(args):
                  "stencil, CGS2 at j <= 2), scaled by the mixed path's mean iteration count; the growth of the "
                  "orthogonalisation with j is not included, so this bounds the plain path from above", "wall_s": pt}
     cpu = None
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:  # the CPU baseline is quoted at N = 1 only
         from oracle import unet as ou  # the bounded CPU-oracle baseline leg
         th_o, _ = load_weights(args.weights, ou.param_segments())
         t_it = cpu_oracle_iteration_time(prob, th_o, iters=1)
