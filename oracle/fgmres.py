@@ -26,7 +26,8 @@ reduction `inner_tol` (inner arithmetic optionally cast through complex64
 and a BF16-emulated network), x += ||r|| d, until the true eta_b <= tol.
 
 Pins (tests/test_oracle_fgmres.py): identity preconditioner == textbook
-GMRES == scipy.sparse.linalg.gmres residual history; exact inverse
+GMRES == scipy.sparse.linalg.gmres residual history (MGS, CGS2 and DCGS2);
+DCGS2 == CGS2 under a fixed linear preconditioner and at a lagged stop; exact inverse
 preconditioner converges in one iteration; a fixed linear preconditioner
 equals right-preconditioned GMRES; ||A Z - V Hbar|| and ||V^H V - I|| at
 rounding level; y equals numpy.linalg.lstsq on Hbar; the converged x is
