@@ -98,21 +98,28 @@ class ClockSampler:
         self.p.terminate()
         self.p.wait()
         self.f.seek(0)
-        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in rows:
-            try:
-                sm.append(float(r[1]))
-                smax.append(float(r[2]))
-                for k, nm in enumerate(names):
-                    if r[5 + k].strip().lower() == "active":
-                        reasons.add(nm)
-            except (ValueError, IndexError):
-                continue
-        load = [s for s in sm if s > 0.5 * max(sm)] if sm else []
-        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(smax) if smax else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+        return parse_clock_samples(self.f.read())
+
+
+def parse_clock_samples(text):
+    """Median SM clock under load (samples above half the highest), the maximum clock and the
+    throttle reasons seen, from nvidia-smi rows `index, sm MHz, max MHz, power, active mask,
+    hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap`."""
+    rows = [r.split(",") for r in text.strip().splitlines() if r.strip()]
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        try:
+            s_, m_ = float(r[1]), float(r[2])
+            act = [r[5 + k].strip().lower() == "active" for k in range(len(names))]
+        except (ValueError, IndexError):
+            continue
+        sm.append(s_)
+        smax.append(m_)
+        reasons.update(nm for nm, a in zip(names, act) if a)
+    load = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+    return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons), "samples": len(sm)}
 
 
 def cpu_oracle_iteration_time(prob, theta, iters=2):
