@@ -45,3 +45,21 @@ def test_param_count_query_needs_no_gpu():
     assert helm.helm_unet_param_count() == 482050
     layers = helm.helm_unet_layers()
     assert layers[0] == (3, 16, 0) and layers[-1] == (16, 2, 2)
+
+
+def test_argument_errors_are_reported_without_a_gpu():
+    """Host-side validation: bad arguments come back as HELM_ERR_INVALID_ARG with a message for the
+    calling thread, before anything touches a device."""
+    from paper_2607_16906_b300 import helm
+    lib = helm._lib
+    c_in, c_out, kind = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert lib.helm_unet_layer(99, ctypes.byref(c_in), ctypes.byref(c_out), ctypes.byref(kind)) == \
+        helm.HELM_ERR_INVALID_ARG
+    assert b"helm_unet_layer" in lib.helm_last_error()
+    w = (ctypes.c_double * 10)()
+    h = ctypes.c_void_p()
+    assert lib.helm_unet_create(ctypes.byref(h), w, 10) == helm.HELM_ERR_INVALID_ARG  # wrong count
+    assert b"expected 482050" in lib.helm_last_error()
+    assert lib.helm_apply(None, None, None, 0, 1, None) == helm.HELM_ERR_INVALID_ARG
+    assert lib.helm_fgmres_solve(None, None, None, None, 1, None, None, None) == helm.HELM_ERR_INVALID_ARG
+    assert lib.helm_tuned_tiles(None, 4) == 0
