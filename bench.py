@@ -42,7 +42,7 @@ STENCIL_BYTES_FP32 = 16.0           # read z (8 B) + write A z (8 B) per point; 
 # time by it
 REF_ITERS_PER_SOLVE = 4780
 # DRAM bytes per basis vector and point of one DCGS2 step (k_dsweepA 8.00 B + k_dsweepB 8.06 B),
-# from the ncu counters of the current sweep kernels (profiles/k_dsweep_fine_grid_32rhs.md)
+# from the ncu counters of the current sweep kernels
 DCGS2_DRAM_B_PER_VPT = 16.06
 
 

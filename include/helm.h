@@ -31,6 +31,9 @@
  *  - Errors: no call aborts, traps or exits.  Each returns a helm_status;
  *    helm_last_error() gives a message for the calling thread.  Invalid
  *    arguments are detected on the host before anything is launched.
+ *  - Columns: a call on nrhs right-hand sides works on nsys * nrhs columns;
+ *    more than HELM_MAX_COLUMNS (one CUDA grid dimension) is rejected with
+ *    HELM_ERR_INVALID_ARG.
  *  - Environment switches: HELM_DISABLE_GRAPHS=1 runs the
  *    BF16 network eagerly instead of replaying captured CUDA graphs;
  *    HELM_AUTOTUNE=0 keeps the first rows-per-tile variant of every row-tile
@@ -71,6 +74,8 @@ typedef enum {
 } helm_status;
 
 typedef enum { HELM_C64 = 0, HELM_C128 = 1 } helm_dtype;
+
+#define HELM_MAX_COLUMNS 65535
 
 typedef struct {
   int nx, ny;  /* interior cells */
@@ -192,6 +197,12 @@ HELM_API int helm_solve_history(const helm_ctx* ctx, double* est_host, int max_e
  * before the update (may be NULL).  grad_norm_host: the pre-clip gradient norm (may be NULL). */
 HELM_API helm_status helm_train_step(helm_ctx* ctx, helm_unet* net, const void* b, double lr, double wd,
                             double clip, double* loss_host, double* grad_norm_host, void* stream);
+/* AdamW state of helm_train_step, for checkpoints that resume training exactly: m_host and v_host
+ * hold helm_unet_param_count() doubles each (first and second moments, weights_host layout) and
+ * step the number of updates taken (bias correction).  get: zeros and 0 before the first step.
+ * Both synchronise the device. */
+HELM_API helm_status helm_unet_get_adam(const helm_unet* net, double* m_host, double* v_host, int64_t* step);
+HELM_API helm_status helm_unet_set_adam(helm_unet* net, const double* m_host, const double* v_host, int64_t step);
 /* Loss and its gradient only (no update): grad_dev receives helm_unet_param_count() doubles in the
  * weights_host layout.  dtype HELM_C64: b is C64 and the BF16 network path is differentiated (as in
  * helm_train_step); HELM_C128: b is C128 and the FP64 network path is differentiated. */
@@ -238,6 +249,51 @@ HELM_API uint64_t helm_launch_count(void);
  * time the shape runs).  Writes up to max_entries records of 6 ints {C_out, 8-channel input slices,
  * images, H, W, rows per tile} to out (host) and returns how many it wrote. */
 HELM_API int helm_tuned_tiles(int* out, int max_entries);
+
+/* ---- per-layer network application (test and diagnostic aid; no paper counterpart) ----------
+ * One layer of the BF16 network exactly as helm_precond_apply runs it, on caller-owned NHWC BF16
+ * device tensors, so that each tensor-core kernel can be checked against a plain convolution.
+ *   layer: 0..16 in helm_unet_layer order (3x3 convs add the bias and apply ReLU; 2x2 up-convs
+ *          add the bias), or HELM_LAYER_DEC1B_FINAL: the last 3x3 conv (16 -> 16, ReLU, BF16
+ *          rounding) with the final 1x1 conv 16 -> 2 fused into its epilogue, written as FP32
+ *          pairs out[B][H][W][2] (output scale 1).
+ *   in0:   [B][H][W][C0] BF16; C0 = c_in, except the first layer (a 16-channel tensor of which
+ *          channels 0..2 are read with nonzero weights) and the decoder's first convs (C0 = c_in / 2,
+ *          the skip connection).  in1: the up-sampled half [B][H][W][c_in / 2] of a decoder conv's
+ *          concatenated input, NULL for every other layer.
+ *   out:   [B][H][W][c_out] BF16 ([B][2H][2W][c_out] for up-convs).
+ *   variant: 0 = the kernel the preconditioner picks for this shape (row-tile kernels: the
+ *          autotuned rows per tile); k >= 1 = the k-th rows-per-tile variant of the row-tile kernel;
+ *          -1 = the 9-box tcgen05 kernel.  A variant the layer does not have: HELM_ERR_INVALID_ARG.
+ *   ry_out: rows per tile of the row-tile kernel that ran (0 for the 9-box kernels); may be NULL.
+ * Pointers 16-byte aligned; B, H, W >= 1.  Asynchronous on `stream`.  HELM_ERR_INVALID_ARG when
+ * the tcgen05 path is unavailable on the current device. */
+#define HELM_LAYER_DEC1B_FINAL 17
+HELM_API helm_status helm_unet_layer_forward(const helm_unet* net, int layer, int variant, const void* in0,
+                                             const void* in1, void* out, int B, int H, int W, int* ry_out,
+                                             void* stream);
+
+/* ---- failure injection and pipeline-wait budget (test aids; no paper counterpart) -------------
+ * Every pipeline wait of the TMA / tcgen05 kernels (FP32 stencil, tensor-core convolutions) gives
+ * up after a budget of clock64 cycles.  The kernel then records an error code, stops issuing work,
+ * lets the copies it already requested land (a bound of its own, about one second), waits for its
+ * issued tensor-core operations, releases its tensor memory and returns.  helm_fgmres_solve checks
+ * the recorded codes at the end of every cycle, before the solution update, and returns
+ * HELM_TIMEOUT with x left at the last completed cycle's iterate.  These two calls let a test make
+ * that happen without faulting the GPU.  Both settings are process-wide; while a fault is armed or
+ * the budget differs from the default, the network runs without CUDA graphs. */
+typedef enum {
+  HELM_FAULT_NONE = 0,
+  HELM_FAULT_STENCIL_TILE = 1, /* the FP32 TMA stencil requests no data for its first tile */
+  HELM_FAULT_CONV_TILE = 2,    /* a tcgen05 convolution requests no data for its first tile */
+  HELM_FAULT_ALLOC = 3         /* a workspace reservation fails with HELM_ERR_OOM (no cudaMalloc call) */
+} helm_fault;
+/* Budget of every pipeline wait launched from now on, in clock64 cycles; cycles <= 0 restores the
+ * default (2e9, about one second at the B300's clock). */
+HELM_API helm_status helm_set_wait_budget(int64_t cycles);
+/* Arm `site` for its next `count` occurrences (launches, or workspace reservations); site
+ * HELM_FAULT_NONE or count <= 0 disarms.  HELM_ERR_INVALID_ARG for an unknown site. */
+HELM_API helm_status helm_inject_fault(int site, int count);
 
 /* Thread-local message for the last non-OK status returned on this thread. */
 HELM_API const char* helm_last_error(void);

@@ -40,6 +40,8 @@ struct RowArgs {
   __nv_bfloat16* out;  // NHWC [B][H][W][N]
   int relu;
   int* err;
+  long long budget;  // clock64 cycles a pipeline wait may take before the kernel gives up
+  int skip_first;    // failure injection: CTA 0 issues no loads for its first tile (its wait runs out)
   // optional fused final layer (N = 16 only): z[b][y][x] = out_scale[b] (wf^T a + bf) on the physical
   // Nx x Ny grid instead of storing the activation a
   const float* wf;  // [16][2] weights, then the 2 biases
@@ -83,7 +85,8 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
   uint64_t* empty = full + Cfg::STAGES;
   uint64_t* tfull = empty + Cfg::STAGES;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  uint64_t* mdrain = tempty + 2;  // completion of the MMAs in flight when the pipeline gives up
+  uint32_t* tmem_slot = (uint32_t*)(mdrain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int per_img = a.tiles_x * a.tiles_y;
@@ -104,6 +107,7 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
       mbar_init(&tfull[k], 1);
       mbar_init(&tempty[k], 128);
     }
+    mbar_init(mdrain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -123,14 +127,25 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
       int stage = 0;
       uint32_t phase = 0;
       bool ok = true;
+      int fills[Cfg::STAGES];  // loads issued into each stage (the drain waits for the last one)
+#pragma unroll
+      for (int s = 0; s < Cfg::STAGES; ++s) fills[s] = 0;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         int b = t / per_img;
         int r = t % per_img;
         int y0 = (r / a.tiles_x) * RY, x0 = (r % a.tiles_x) * ROW_PX;
-        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, 11)) {
+        if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, 11, a.budget)) {
           ok = false;
           break;
         }
+        if (a.skip_first && blockIdx.x == 0 && t == 0) {  // injected fault: this tile never arrives
+          if (++stage == Cfg::STAGES) {
+            stage = 0;
+            phase ^= 1;
+          }
+          continue;
+        }
+        ++fills[stage];
         unsigned char* sa = smem + stage * Cfg::STAGE_BYTES;
         mbar_expect_tx(&full[stage], Cfg::TX_BYTES);
 #pragma unroll
@@ -144,13 +159,9 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
           phase ^= 1;
         }
       }
-      if (!ok) {
-        for (int s = 0; s < Cfg::STAGES; ++s) {
-          long long t0 = clock64();
-          while (!mbar_try_wait(&full[s], 0) && !mbar_try_wait(&full[s], 1) && clock64() - t0 < WAIT_CYCLES) {
-          }
-        }
-      }
+      // every load issued must land before the CTA releases its shared memory
+#pragma unroll
+      for (int s = 0; s < Cfg::STAGES; ++s) mbar_drain(&full[s], fills[s]);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer: RY rows x 9 taps x NSL/2 MMAs (K = 16 = two slices) per tile
@@ -160,10 +171,13 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
     uint32_t phase = 0;
     int acc = 0;
     uint32_t acc_phase = 0;
+    bool ok = true;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-      if (!mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag, a.err, 12)) break;
-      tc_fence_after();
-      if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 13)) break;
+      if (!mbar_wait_warp(&tempty[acc], acc_phase ^ 1, abort_flag, a.err, 12, a.budget) ||
+          !mbar_wait_warp(&full[stage], phase, abort_flag, a.err, 13, a.budget)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
       if (lane == 0) {
         const uint32_t sa = smem_u32(smem + stage * Cfg::STAGE_BYTES);
@@ -198,6 +212,14 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
         acc_phase ^= 1;
       }
     }
+    if (!ok) {
+      // the MMAs already issued must complete before TMEM is released
+      if (lane == 0) {
+        umma_commit(mdrain);
+        mbar_drain(mdrain, 1);
+      }
+      __syncwarp();
+    }
   } else {
     // ---------------- epilogue: group e = 0 (warps 2..5) drains accumulator 0 (the CTA's even tiles),
     // e = 1 (warps 6..9) accumulator 1 (the odd ones); TMEM lane = pixel of the row segment
@@ -210,7 +232,7 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
     const double* const osc = a.io ? a.io->out_scale : a.out_scale;
     uint32_t acc_phase = 0;
     for (int t = blockIdx.x + e * gridDim.x; t < a.ntiles; t += 2 * gridDim.x) {
-      if (!mbar_wait(&tfull[e], acc_phase, abort_flag, a.err, 14)) break;
+      if (!mbar_wait_warp(&tfull[e], acc_phase, abort_flag, a.err, 14, a.budget)) break;
       tc_fence_after();
       int b = t / per_img;
       int r = t % per_img;
@@ -249,7 +271,7 @@ __global__ void __launch_bounds__(320, RowCfg<N, NSL, RY>::MINB) k_conv_row(cons
               f1 += f * fsm[2 * k + 1];
             }
             if (x < a.Nx && y < a.Ny) {
-              const double sc = osc[b];
+              const double sc = osc ? osc[b] : 1.0;
               zp[b * a.zstride + (int64_t)y * a.Nx + x] = make_float2((float)(f0 * sc), (float)(f1 * sc));
             }
           } else {
@@ -479,7 +501,7 @@ int conv_row_tuned(int (*out)[6], int max) {
 
 helm_status conv_row_forward(const __nv_bfloat16* wrow, const float* bias, int* err, const void* in0, int C0,
                              const void* in1, int C1, void* out, int cout, int B, int H, int W, cudaStream_t st,
-                             const RowFinal* fin) {
+                             const RowFinal* fin, int variant, int* ry_out) {
   if (fin && !(cout == 16 && C0 + C1 == 16))
     return fail(HELM_ERR_INVALID_ARG, "conv_row_forward: the fused final layer needs a 16 -> 16 convolution");
   RowArgs a;
@@ -502,10 +524,26 @@ helm_status conv_row_forward(const __nv_bfloat16* wrow, const float* bias, int* 
   a.out = (__nv_bfloat16*)out;
   a.relu = 1;
   a.err = err;
+  a.budget = wait_budget();
+  a.skip_first = take_fault(HELM_FAULT_CONV_TILE) ? 1 : 0;
   const int nsl = (C0 + C1) / 8;
   const std::vector<RowCand>& cands = row_candidates(cout, nsl);
   if (cands.empty()) return fail(HELM_ERR_INVALID_ARG, "conv_row_forward: unsupported layer shape");
-  return row_autotuned(cands, RowKey{cout, nsl, B, H, W}, in0, C0, in1, C1, a, st);
+  if (variant > 0) {  // one fixed rows-per-tile variant (per-layer tests)
+    if (variant > (int)cands.size())
+      return fail(HELM_ERR_INVALID_ARG, "conv_row_forward: the layer has only " + std::to_string(cands.size()) +
+                                            " rows-per-tile variants");
+    if (ry_out) *ry_out = cands[variant - 1].ry;
+    return cands[variant - 1].fn(in0, C0, in1, C1, a, st);
+  }
+  const RowKey key{cout, nsl, B, H, W};
+  HELM_TRY(row_autotuned(cands, key, in0, C0, in1, C1, a, st));
+  if (ry_out) {
+    std::lock_guard<std::mutex> lk(g_row_mu);
+    auto it = g_row_choice.find(key);
+    *ry_out = cands[it != g_row_choice.end() ? it->second : 0].ry;
+  }
+  return HELM_OK;
 }
 
 }  // namespace helm

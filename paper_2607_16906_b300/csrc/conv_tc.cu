@@ -38,6 +38,8 @@ struct ConvTcArgs {
   __nv_bfloat16* out;     // NHWC [B][H][W][N]
   int relu;
   int* err;               // device error code (0 = ok)
+  long long budget;       // clock64 cycles a pipeline wait may take before the kernel gives up
+  int skip_first;         // failure injection: CTA 0 issues no loads for its first tile
 };
 
 template <int N, int CHUNK, int MODE>
@@ -68,7 +70,8 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   uint64_t* empty = full + Cfg::STAGES;
   uint64_t* tfull = empty + Cfg::STAGES;
   uint64_t* tempty = tfull + 2;
-  uint32_t* tmem_slot = (uint32_t*)(tempty + 2);
+  uint64_t* mdrain = tempty + 2;  // completion of the MMAs in flight when the pipeline gives up
+  uint32_t* tmem_slot = (uint32_t*)(mdrain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -86,6 +89,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       mbar_init(&tfull[k], 1);
       mbar_init(&tempty[k], 128);
     }
+    mbar_init(mdrain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -104,8 +108,10 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       // ---------------- TMA producer
       int stage = 0;
       uint32_t phase = 0;
-      int issued_unconsumed = 0;
       bool ok = true;
+      int fills[Cfg::STAGES];  // loads issued into each stage (the drain waits for the last one)
+#pragma unroll
+      for (int s = 0; s < Cfg::STAGES; ++s) fills[s] = 0;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         int b = t / (a.tiles_x * a.tiles_y);
         int r = t % (a.tiles_x * a.tiles_y);
@@ -114,10 +120,18 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
           const CUtensorMap* src = kc < a.nk0 ? &tA0 : &tA1;
           int c0 = (kc < a.nk0 ? kc : kc - a.nk0) * CHUNK;
           for (int tg = 0; tg < TAPS / TPS; ++tg) {
-            if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, 1)) {
+            if (!mbar_wait(&empty[stage], phase ^ 1, abort_flag, a.err, 1, a.budget)) {
               ok = false;
               break;
             }
+            if (a.skip_first && blockIdx.x == 0 && t == 0) {  // injected fault: these loads never arrive
+              if (++stage == Cfg::STAGES) {
+                stage = 0;
+                phase ^= 1;
+              }
+              continue;
+            }
+            ++fills[stage];
             unsigned char* sa = smem + stage * Cfg::STAGE_BYTES;
             unsigned char* sb = sa + TPS * Cfg::A_BYTES;
             mbar_expect_tx(&full[stage], Cfg::STAGE_BYTES);
@@ -137,15 +151,9 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
           }
         }
       }
-      (void)issued_unconsumed;
-      if (!ok) {
-        // drain: wait (bounded) for every stage's last load to land before the CTA releases its smem
-        for (int s = 0; s < Cfg::STAGES; ++s) {
-          long long t0 = clock64();
-          while (!mbar_try_wait(&full[s], 0) && !mbar_try_wait(&full[s], 1) && clock64() - t0 < WAIT_CYCLES) {
-          }
-        }
-      }
+      // every load issued must land before the CTA releases its shared memory
+#pragma unroll
+      for (int s = 0; s < Cfg::STAGES; ++s) mbar_drain(&full[s], fills[s]);
     }
   } else if (warp == 1) {
     // ---------------- MMA issuer
@@ -156,11 +164,14 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     uint32_t acc_phase = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-      if (!mbar_wait(&tempty[acc], acc_phase ^ 1, abort_flag, a.err, 2)) break;
+      if (!mbar_wait_warp(&tempty[acc], acc_phase ^ 1, abort_flag, a.err, 2, a.budget)) {
+        ok = false;
+        break;
+      }
       tc_fence_after();
       const uint32_t d_tmem = tmem_base + acc * N;
       for (int ks = 0; ks < ksteps; ++ks) {
-        if (!mbar_wait(&full[stage], phase, abort_flag, a.err, 3)) {
+        if (!mbar_wait_warp(&full[stage], phase, abort_flag, a.err, 3, a.budget)) {
           ok = false;
           break;
         }
@@ -190,6 +201,14 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       acc ^= 1;
       if (acc == 0) acc_phase ^= 1;
     }
+    if (!ok) {
+      // the MMAs already issued must complete before TMEM is released
+      if (lane == 0) {
+        umma_commit(mdrain);
+        mbar_drain(mdrain, 1);
+      }
+      __syncwarp();
+    }
   } else {
     // ---------------- epilogue (warps 2..5)
     const int q = warp & 3;  // TMEM lane quarter this warp may access
@@ -198,7 +217,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-      if (!mbar_wait(&tfull[acc], acc_phase, abort_flag, a.err, 4)) break;
+      if (!mbar_wait_warp(&tfull[acc], acc_phase, abort_flag, a.err, 4, a.budget)) break;
       tc_fence_after();
       int b = t / (a.tiles_x * a.tiles_y);
       int r = t % (a.tiles_x * a.tiles_y);
@@ -295,7 +314,7 @@ helm_status conv_row_prepare(const double* master, int64_t m_w, int cin, int cin
                              cudaStream_t st);
 helm_status conv_row_forward(const __nv_bfloat16* wrow, const float* bias, int* err, const void* in0, int C0,
                              const void* in1, int C1, void* out, int cout, int B, int H, int W, cudaStream_t st,
-                             const RowFinal* fin = nullptr);
+                             const RowFinal* fin = nullptr, int variant = 0, int* ry_out = nullptr);
 
 struct TcState {
   __nv_bfloat16* w[NUM_LAYERS] = {};
@@ -446,13 +465,11 @@ static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const
   return HELM_OK;
 }
 
-helm_status conv_tc_forward(const helm_unet* net, int l, const void* in0, int C0, const void* in1, int C1, void* out,
-                            int B, int H, int W, cudaStream_t st) {
+// The 9-box kernel for one 3x3 layer (any layer shape the chunking allows).
+static helm_status conv_tc_box(const helm_unet* net, int l, const void* in0, int C0, const void* in1, int C1,
+                               void* out, int B, int H, int W, cudaStream_t st) {
   const TcState& S = *net->tc;
   const LayerDesc& d = kLayers[l];
-  if (l == L_ENC1A) C0 = X0_CH;
-  if (S.wrow[l])
-    return conv_row_forward(S.wrow[l], net->w32 + net->L.c_b[l], S.err, in0, C0, in1, C1, out, d.cout, B, H, W, st);
   const int chunk = S.chunk[l];
   if (C0 % chunk || C1 % chunk) return fail(HELM_ERR_INVALID_ARG, "conv_tc_forward: channel count not a chunk multiple");
   CUtensorMap m0, m1, mw;
@@ -476,6 +493,8 @@ helm_status conv_tc_forward(const helm_unet* net, int l, const void* in0, int C0
   a.out = (__nv_bfloat16*)out;
   a.relu = 1;
   a.err = S.err;
+  a.budget = wait_budget();
+  a.skip_first = take_fault(HELM_FAULT_CONV_TILE) ? 1 : 0;
   switch (d.cout * 1000 + chunk) {
     case 16016: return launch_tc<16, 16, 0>(m0, m1, mw, a, st);
     case 32016: return launch_tc<32, 16, 0>(m0, m1, mw, a, st);
@@ -485,6 +504,16 @@ helm_status conv_tc_forward(const helm_unet* net, int l, const void* in0, int C0
     case 128064: return launch_tc<128, 64, 0>(m0, m1, mw, a, st);
     default: return fail(HELM_ERR_INVALID_ARG, "conv_tc_forward: no kernel for this layer shape");
   }
+}
+
+helm_status conv_tc_forward(const helm_unet* net, int l, const void* in0, int C0, const void* in1, int C1, void* out,
+                            int B, int H, int W, cudaStream_t st) {
+  const TcState& S = *net->tc;
+  const LayerDesc& d = kLayers[l];
+  if (l == L_ENC1A) C0 = X0_CH;
+  if (S.wrow[l])
+    return conv_row_forward(S.wrow[l], net->w32 + net->L.c_b[l], S.err, in0, C0, in1, C1, out, d.cout, B, H, W, st);
+  return conv_tc_box(net, l, in0, C0, in1, C1, out, B, H, W, st);
 }
 
 // 2x2 stride-2 transposed conv on tensor cores: in [B][Hi][Wi][cin] -> out [B][2Hi][2Wi][cout].
@@ -526,6 +555,8 @@ helm_status conv_tc_up(const helm_unet* net, int l, const void* in, void* out, i
   a.out = (__nv_bfloat16*)out;
   a.relu = 0;
   a.err = S.err;
+  a.budget = wait_budget();
+  a.skip_first = take_fault(HELM_FAULT_CONV_TILE) ? 1 : 0;
   switch (4 * d.cout * 1000 + chunk) {
     case 256064: return launch_tc<256, 64, 1>(m0, m0, mw, a, st);
     case 128064: return launch_tc<128, 64, 1>(m0, m0, mw, a, st);
@@ -548,3 +579,54 @@ helm_status conv_tc_check(const helm_unet* net, cudaStream_t st) {
 }
 
 }  // namespace helm
+
+using namespace helm;
+
+extern "C" helm_status helm_unet_layer_forward(const helm_unet* net, int layer, int variant, const void* in0,
+                                               const void* in1, void* out, int B, int H, int W, int* ry_out,
+                                               void* stream) {
+  if (ry_out) *ry_out = 0;
+  if (!net || !in0 || !out) return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: NULL argument");
+  if (layer < 0 || layer > HELM_LAYER_DEC1B_FINAL)
+    return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: layer out of range");
+  if (B < 1 || H < 1 || W < 1 || (int64_t)B * H * W > ((int64_t)1 << 31))
+    return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: bad image size");
+  if (((uintptr_t)in0 | (uintptr_t)in1 | (uintptr_t)out) & 15)
+    return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: pointers must be 16-byte aligned");
+  if (!net->tc || !net->tc->ok)
+    return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: the tcgen05 path is not available on this device");
+  cudaStream_t st = (cudaStream_t)stream;
+  const TcState& S = *net->tc;
+  const bool fused = layer == HELM_LAYER_DEC1B_FINAL;
+  const int l = fused ? (int)L_DEC1B : layer;
+  const LayerDesc& d = kLayers[l];
+  const bool concat = l == L_DEC3A || l == L_DEC2A || l == L_DEC1A;
+  if (concat != (in1 != nullptr))
+    return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: in1 is required exactly for the decoder's first convs");
+  const int C0 = concat ? d.cin / 2 : (l == L_ENC1A ? X0_CH : d.cin), C1 = concat ? d.cin / 2 : 0;
+  if (d.kind == UP2) {
+    if (variant != 0 && variant != -1)
+      return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: up-convs have one kernel (variant 0 or -1)");
+    return conv_tc_up(net, l, in0, out, B, H, W, st);
+  }
+  if (variant == -1) {
+    if (fused) return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: the fused output layer is a row kernel");
+    return conv_tc_box(net, l, in0, C0, in1, C1, out, B, H, W, st);
+  }
+  if (!S.wrow[l]) {
+    if (variant != 0) return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: no row-tile kernel for this layer");
+    return conv_tc_box(net, l, in0, C0, in1, C1, out, B, H, W, st);
+  }
+  RowFinal f;
+  if (fused) {
+    f.wf = net->w32 + net->L.c_w[L_FINAL];
+    f.out_scale = nullptr;  // scale 1
+    f.z = (float2*)out;
+    f.Nx = W;
+    f.Ny = H;
+    f.zstride = (int64_t)H * W;
+    f.io = nullptr;
+  }
+  return conv_row_forward(S.wrow[l], net->w32 + net->L.c_b[l], S.err, in0, C0, in1, C1, fused ? nullptr : out, d.cout,
+                          B, H, W, st, fused ? &f : nullptr, variant, ry_out);
+}

@@ -2,6 +2,7 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <algorithm>
 #include <atomic>
 #include <complex>
 #include <string>
@@ -26,8 +27,40 @@ helm_status cuda_fail(cudaError_t e, const char* what, const char* file, int lin
   return e == cudaErrorMemoryAllocation ? HELM_ERR_OOM : HELM_ERR_CUDA;
 }
 
+// ------------------------------------------------------------------ wait budget and fault injection
+
+static std::atomic<long long> g_wait_budget{DEFAULT_WAIT_BUDGET};
+static std::atomic<int> g_fault_site{HELM_FAULT_NONE};
+static std::atomic<int> g_fault_count{0};
+
+long long wait_budget() { return g_wait_budget.load(std::memory_order_relaxed); }
+
+bool take_fault(int site) {
+  if (g_fault_site.load() != site) return false;
+  int c = g_fault_count.load();
+  while (c > 0)
+    if (g_fault_count.compare_exchange_weak(c, c - 1)) return true;
+  return false;
+}
+
+bool test_overrides_active() {
+  return (g_fault_site.load() != HELM_FAULT_NONE && g_fault_count.load() > 0) ||
+         wait_budget() != DEFAULT_WAIT_BUDGET;
+}
+
+helm_status check_columns(const helm_ctx* ctx, int nrhs, const char* name) {
+  if (nrhs <= 0) return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": nrhs must be > 0");
+  if ((int64_t)ctx->nsys * nrhs > HELM_MAX_COLUMNS)
+    return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": nsys * nrhs = " +
+                                          std::to_string((int64_t)ctx->nsys * nrhs) + " exceeds HELM_MAX_COLUMNS (" +
+                                          std::to_string(HELM_MAX_COLUMNS) + ")");
+  return HELM_OK;
+}
+
 helm_status Workspace::reserve(size_t need) {
   if (need <= bytes) return HELM_OK;
+  if (take_fault(HELM_FAULT_ALLOC))
+    return fail(HELM_ERR_OOM, "workspace allocation of " + std::to_string(need) + " bytes failed (injected)");
   if (ptr) cudaFree(ptr);
   ptr = nullptr;
   bytes = 0;
@@ -309,3 +342,17 @@ extern "C" helm_status helm_destroy(helm_ctx* ctx) {
 
 extern "C" int64_t helm_points(const helm_ctx* ctx) { return ctx ? ctx->npts : 0; }
 extern "C" int helm_num_systems(const helm_ctx* ctx) { return ctx ? ctx->nsys : 0; }
+
+extern "C" helm_status helm_set_wait_budget(int64_t cycles) {
+  helm::g_wait_budget.store(cycles > 0 ? (long long)cycles : helm::DEFAULT_WAIT_BUDGET);
+  return HELM_OK;
+}
+
+extern "C" helm_status helm_inject_fault(int site, int count) {
+  if (site < HELM_FAULT_NONE || site > HELM_FAULT_ALLOC)
+    return helm::fail(HELM_ERR_INVALID_ARG, "helm_inject_fault: unknown site");
+  helm::g_fault_count.store(0);
+  helm::g_fault_site.store(count > 0 ? site : HELM_FAULT_NONE);
+  helm::g_fault_count.store(site == HELM_FAULT_NONE ? 0 : std::max(count, 0));
+  return HELM_OK;
+}

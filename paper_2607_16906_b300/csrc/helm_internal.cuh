@@ -152,6 +152,15 @@ helm_status col_norm2(helm_ctx* ctx, const C<R>* v, int nrhs, double* out, cudaS
 __global__ void k_finalize(const double* __restrict__ partial, const int* __restrict__ nparts_col, int nvals,
                            double* __restrict__ out);
 
+// Pipeline-wait budget (clock64 cycles) of the TMA / tcgen05 kernels and the host-side failure
+// injection of helm_set_wait_budget / helm_inject_fault (ctx.cu).
+constexpr long long DEFAULT_WAIT_BUDGET = 2000000000LL;
+long long wait_budget();
+bool take_fault(int site);        // consumes one armed occurrence of `site`
+bool test_overrides_active();     // a fault is armed or the budget differs from the default
+// HELM_ERR_INVALID_ARG unless 0 < nrhs and nsys * nrhs <= HELM_MAX_COLUMNS
+helm_status check_columns(const helm_ctx* ctx, int nrhs, const char* name);
+
 inline unsigned cdiv(int64_t a, int64_t b) { return (unsigned)((a + b - 1) / b); }
 
 // Every kernel of the library is launched through launch(): it keeps a process-wide count of

@@ -1036,11 +1036,11 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
     if (db_smem > 48 * 1024)
       HELM_CK(cudaFuncSetAttribute(k_dsweepB<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)db_smem));
   }
-  HELM_TRY(ensure_pinned(ctx, sizeof(double) * 2 * ncol + sizeof(ColState) * ncol + 64 + 64));
+  HELM_TRY(ensure_pinned(ctx, sizeof(double) * 2 * ncol + sizeof(ColState) * (ncol + 1) + 64 + 64));
   double* h_sums = (double*)ctx->pinned;
   ColState* h_st = (ColState*)(h_sums + 2 * ncol);
-  int* h_nact = (int*)(h_st + ncol);
-  double* h_est0 = (double*)(h_nact + 2);
+  ColState* h_c0 = h_st + ncol;  // column 0's state after each step (residual-estimate history)
+  int* h_nact = (int*)(h_c0 + 1);
   ctx->history.clear();
   const bool mixed = sizeof(R) == 4;
   const int max_cycles = mixed ? std::max(1, o.max_outer) : std::max(1, o.max_restarts);
@@ -1090,6 +1090,14 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
       break;
     }
     HELM_CK(cudaMemcpyAsync(W.st, h_st, sizeof(ColState) * ncol, cudaMemcpyHostToDevice, stream));
+    // history of column 0: one entry per new Hessenberg column rotated while the column is active
+    int last_k0 = 0;
+    auto record0 = [&](const ColState& c0) {
+      if (!done[0] && c0.k > last_k0) {
+        ctx->history.push_back(c0.est * rel[0]);
+        last_k0 = c0.k;
+      }
+    };
     // g = e1 (the cycle runs on r / ||r||), vscale = 1, network scales for a unit-norm v1
     launch(k_cycle_setup, cdiv(ncol, 64), 64, 0, stream, ncol, m, ctx->cols_dev, W.g, W.vscale, W.in_scale,
            W.out_scale);
@@ -1144,11 +1152,11 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
                W.cs, W.sn, W.g, W.st, W.nactive, W.in_scale, ctx->cols_dev, breakdown_eps);
         HELM_CK_LAUNCH();
         HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
-        HELM_CK(cudaMemcpyAsync(h_est0, &W.st[0].est, sizeof(double), cudaMemcpyDeviceToHost, stream));
+        HELM_CK(cudaMemcpyAsync(h_c0, W.st, sizeof(ColState), cudaMemcpyDeviceToHost, stream));
         prof_end(ctx, PH_LSQ, stream);
         HELM_CK(cudaStreamSynchronize(stream));
         prof_collect(ctx);
-        if (!done[0]) ctx->history.push_back(*h_est0 * rel[0]);
+        record0(*h_c0);
         if (*h_nact == 0) break;
       }
     } else {
@@ -1197,11 +1205,11 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         prof_end(ctx, PH_ORTH, stream);
         prof_begin(ctx, PH_LSQ, stream);
         HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
-        HELM_CK(cudaMemcpyAsync(h_est0, &W.st[0].est, sizeof(double), cudaMemcpyDeviceToHost, stream));
+        HELM_CK(cudaMemcpyAsync(h_c0, W.st, sizeof(ColState), cudaMemcpyDeviceToHost, stream));
         prof_end(ctx, PH_LSQ, stream);
         HELM_CK(cudaStreamSynchronize(stream));
         prof_collect(ctx);
-        if (!done[0] && j > 0) ctx->history.push_back(*h_est0 * rel[0]);
+        record0(*h_c0);
         nact = *h_nact;
         if (*h_nact == 0) break;
       }
@@ -1218,6 +1226,20 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
       HELM_CK_LAUNCH();
       prof_end(ctx, PH_ORTH, stream);
     }
+    // a pipeline wait that ran out left some z_j or w incomplete: keep x at the last completed
+    // cycle's iterate (its true residual is the one reported) and return HELM_TIMEOUT
+    {
+      helm_status chk = net ? conv_tc_check(net, stream) : HELM_OK;
+      if (chk == HELM_OK) chk = stencil_check(ctx, stream);
+      if (chk != HELM_OK) {
+        const std::string msg = helm_last_error();
+        for (int c = 0; c < ncol; ++c) {
+          if (!done[c]) inf[c].status = chk;
+          if (info) info[c] = inf[c];
+        }
+        return fail(chk, msg);
+      }
+    }
     prof_begin(ctx, PH_UPDATE, stream);
     launch(k_backsolve, cdiv(ncol, 64), 64, 0, stream, ncol, m, W.Rm, W.g, W.st, W.y);
     launch(k_xupdate<R>, vgrid, RED_THREADS, 0, stream, W.Z, vst, W.y, m, (net || dcgs2) ? nullptr : W.vscale,
@@ -1227,8 +1249,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
     prof_end(ctx, PH_UPDATE, stream);
     HELM_CK(cudaStreamSynchronize(stream));
     prof_collect(ctx);
-    if (net) HELM_TRY(conv_tc_check(net, stream));
-    HELM_TRY(stencil_check(ctx, stream));
+    record0(h_st[0]);  // DCGS2: the last column is rotated in the finalisation pass
     for (int c = 0; c < ncol; ++c) {
       if (done[c]) continue;
       inf[c].iters += h_st[c].k;
@@ -1268,7 +1289,8 @@ extern "C" int helm_solve_history(const helm_ctx* ctx, double* est_host, int max
 
 extern "C" helm_status helm_fgmres_solve(helm_ctx* ctx, const helm_unet* net, const void* b, void* x, int nrhs,
                                          const helm_solve_opts* opts, helm_solve_info* info, void* stream) {
-  if (!ctx || !b || !x || !opts || nrhs <= 0) return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: bad argument");
+  if (!ctx || !b || !x || !opts) return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: NULL argument");
+  HELM_TRY(check_columns(ctx, nrhs, "helm_fgmres_solve"));
   if (b == x) return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: b and x must not alias");
   if (((uintptr_t)b | (uintptr_t)x) & 15) return fail(HELM_ERR_INVALID_ARG, "helm_fgmres_solve: pointers must be 16-byte aligned");
   helm_solve_opts o = *opts;

@@ -228,7 +228,7 @@ using namespace helm;
 static helm_status apply_entry(helm_ctx* ctx, const void* x, void* y, helm_dtype dtype, int nrhs, void* stream,
                                bool adj, const char* name) {
   if (!ctx || !x || !y) return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": NULL argument");
-  if (nrhs <= 0) return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": nrhs must be > 0");
+  HELM_TRY(check_columns(ctx, nrhs, name));
   if (x == y) return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": x and y must not alias");
   if (((uintptr_t)x | (uintptr_t)y) & 15) return fail(HELM_ERR_INVALID_ARG, std::string(name) + ": pointers must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
@@ -248,7 +248,8 @@ extern "C" helm_status helm_apply_adjoint(helm_ctx* ctx, const void* x, void* y,
 
 extern "C" helm_status helm_relres(helm_ctx* ctx, const void* x, const void* b, int nrhs, double* out_host,
                                    void* stream) {
-  if (!ctx || !x || !b || !out_host || nrhs <= 0) return fail(HELM_ERR_INVALID_ARG, "helm_relres: bad argument");
+  if (!ctx || !x || !b || !out_host) return fail(HELM_ERR_INVALID_ARG, "helm_relres: NULL argument");
+  HELM_TRY(check_columns(ctx, nrhs, "helm_relres"));
   cudaStream_t st = (cudaStream_t)stream;
   int ncol = num_cols(ctx, nrhs);
   size_t vec = sizeof(double2) * ctx->npts * nrhs;
@@ -388,8 +389,8 @@ __global__ void k_relres_finalize(const double* __restrict__ partial, int nparts
 extern "C" helm_status helm_relres_noalloc(helm_ctx* ctx, const void* x, const void* b, int nrhs,
                                            double* relres_dev, void* stream) {
   using namespace helm;
-  if (!ctx || !x || !b || !relres_dev || nrhs <= 0)
-    return fail(HELM_ERR_INVALID_ARG, "helm_relres_noalloc: NULL argument or nrhs <= 0");
+  if (!ctx || !x || !b || !relres_dev) return fail(HELM_ERR_INVALID_ARG, "helm_relres_noalloc: NULL argument");
+  HELM_TRY(check_columns(ctx, nrhs, "helm_relres_noalloc"));
   if (((uintptr_t)x | (uintptr_t)b) & 15) return fail(HELM_ERR_INVALID_ARG, "helm_relres_noalloc: x, b must be 16-byte aligned");
   int64_t need = 0;
   for (auto& s : ctx->sys) need += (int64_t)cdiv(s.Nx, STENCIL_THREADS) * cdiv(s.Ny, STENCIL_ROWS) * nrhs * 2;

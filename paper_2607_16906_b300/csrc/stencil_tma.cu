@@ -47,7 +47,8 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_tma(const __grid_constan
                                                             const unsigned char* __restrict__ ux,
                                                             const unsigned char* __restrict__ uy, int Nx, int Ny,
                                                             int tiles_x, int tiles_y, int ntiles, int64_t rhs_stride,
-                                                            float inv_h2, int* err) {
+                                                            float inv_h2, int* err, long long budget,
+                                                            int skip_first) {
   extern __shared__ __align__(128) unsigned char st_smem[];
   unsigned char* buf = (unsigned char*)(((uintptr_t)st_smem + 127) & ~(uintptr_t)127);
   __shared__ uint64_t full[ST_STAGES];
@@ -75,29 +76,26 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_tma(const __grid_constan
     tma_load_3d(dst, &tu, &full[s], 2 * (x0 - 2), y0 - 1, rhs);
     if (K2T) tma_load_3d(dst + ST_K2_OFF, &tk, &full[s], x0, y0, 0);
   };
-  int issued = 0;  // tiles whose box was requested (thread 0's count)
+  int fills[ST_STAGES] = {};  // boxes requested per stage (thread 0's count; the drain waits for the last)
   if (tid == 0)
     for (int s = 0; s < ST_STAGES; ++s) {
       const int t = blockIdx.x + s * gridDim.x;
-      if (t < ntiles) {
+      if (t < ntiles && !(skip_first && t == 0)) {  // injected fault: tile 0 of CTA 0 never arrives
         issue(t, s);
-        ++issued;
+        ++fills[s];
       }
     }
   const int c = tid & 31, rg = tid >> 5;  // point pair c of rows rg, rg + 8
-  int stage = 0, consumed = 0;
+  int stage = 0;
   uint32_t phase = 0;
-  bool ok = true;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    if (!mbar_wait(&full[stage], phase, abort_flag, err, 21)) {
-      ok = false;
-      break;
-    }
-    ++consumed;
+    // every thread observes the stage's barrier; the block leaves the loop together (below) when
+    // any thread gave up, so that no thread waits at a barrier the others have left
+    const bool got = mbar_wait(&full[stage], phase, abort_flag, err, 21, budget);
     const int rhs = tile_xy[stage][0], y0 = tile_xy[stage][1];
     const int x = tile_xy[stage][2] + 2 * c;
     const unsigned char* sb = buf + stage * ST_STAGE_STRIDE;
-    if (x < Nx) {
+    if (got && x < Nx) {
       const bool xunit = ux[x] && ux[x + 1];
       float2* yr = y + rhs * rhs_stride;
 #pragma unroll
@@ -148,13 +146,14 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_tma(const __grid_constan
         *(float4*)(yr + (int64_t)j * Nx + x) = make_float4(o0.x, o0.y, o1.x, o1.y);
       }
     }
-    __syncthreads();  // every thread is done with this stage's window
+    // every thread is done with this stage's window (or some thread gave up: stop issuing)
+    if (__syncthreads_or(!got)) break;
     if (tid == 0) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // order those reads before the refill
       const int tn = t + ST_STAGES * gridDim.x;
       if (tn < ntiles) {
         issue(tn, stage);
-        ++issued;
+        ++fills[stage];
       }
     }
     if (++stage == ST_STAGES) {
@@ -162,15 +161,10 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_tma(const __grid_constan
       phase ^= 1;
     }
   }
-  if (!ok && tid == 0) {
-    // let the boxes still in flight land before the CTA exits (bounded)
-    for (int k = consumed; k < issued; ++k) {
-      const int s = k % ST_STAGES;
-      long long t0 = clock64();
-      while (!mbar_try_wait(&full[s], (k / ST_STAGES) & 1) && clock64() - t0 < WAIT_CYCLES) {
-      }
-    }
-  }
+  // let every box requested land before the CTA exits (bounded; already done on the normal path)
+  if (tid == 0)
+#pragma unroll
+    for (int s = 0; s < ST_STAGES; ++s) mbar_drain(&full[s], fills[s]);
 }
 
 typedef CUresult (*EncodeTiledFnS)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -228,7 +222,8 @@ template <bool ADJ, bool K2T>
 static helm_status launch_stencil_tma(const CUtensorMap& mu, const CUtensorMap& mk, float2* y, const float* k2,
                                       const float2* px, const float2* py, const unsigned char* ux,
                                       const unsigned char* uy, int Nx, int Ny, int tiles_x, int tiles_y,
-                                      int ntiles, int64_t stride, float inv_h2, int* err, cudaStream_t st) {
+                                      int ntiles, int64_t stride, float inv_h2, int* err, long long budget,
+                                      int skip_first, cudaStream_t st) {
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   static int nsm = 148, per_sm = 1;
@@ -244,7 +239,7 @@ static helm_status launch_stencil_tma(const CUtensorMap& mu, const CUtensorMap& 
   HELM_CK(attr_err);
   const int grid = std::min(ntiles, nsm * per_sm);
   launch(k_stencil_tma<ADJ, K2T>, grid, ST_THREADS, ST_SMEM, st, mu, mk, y, k2, px, py, ux, uy, Nx, Ny, tiles_x,
-         tiles_y, ntiles, stride, inv_h2, err);
+         tiles_y, ntiles, stride, inv_h2, err, budget, skip_first);
   HELM_CK_LAUNCH();
   return HELM_OK;
 }
@@ -263,9 +258,11 @@ helm_status stencil_tma(const float2* x, float2* y, const float* k2, const float
   else
     mk = mu;
   const int64_t stride = (int64_t)Nx * Ny;
+  const long long budget = wait_budget();
+  const int skip = take_fault(HELM_FAULT_STENCIL_TILE) ? 1 : 0;
   auto go = [&](auto kern_adj, auto kern_k2) {
     return launch_stencil_tma<decltype(kern_adj)::value, decltype(kern_k2)::value>(
-        mu, mk, y, k2, px, py, ux, uy, Nx, Ny, tiles_x, tiles_y, ntiles, stride, inv_h2, err, st);
+        mu, mk, y, k2, px, py, ux, uy, Nx, Ny, tiles_x, tiles_y, ntiles, stride, inv_h2, err, budget, skip, st);
   };
   using T = std::true_type;
   using F = std::false_type;

@@ -29,21 +29,43 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Default budget of a pipeline wait, and the fixed budget of the waits that drain a CTA's own
+// copies in flight before it exits (those must end even after a pipeline wait gave up).
 constexpr long long WAIT_CYCLES = 2000000000LL;  // ~1 s at 2 GHz
 
-// Bounded wait for the phase of `parity`; false (and an error code) on timeout or abort.
+// Bounded wait for the phase of `parity`; false (and an error code) after `budget` clock64 cycles,
+// or when another thread of the CTA already gave up (abort_flag).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code) {
+                                          int code, long long budget) {
   long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > WAIT_CYCLES) {
+    if (clock64() - t0 > budget) {
       *abort_flag = 1;
       atomicExch(err, code);
       return false;
     }
   }
   return true;
+}
+
+// The same for a whole warp: every lane observes the barrier, and the warp goes on only if every
+// lane saw the phase complete, so that the warp-collective tcgen05 instructions that follow never
+// run with part of the warp gone.
+__device__ __forceinline__ bool mbar_wait_warp(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                               int code, long long budget) {
+  const bool ok = mbar_wait(bar, parity, abort_flag, err, code, budget);
+  return __all_sync(0xffffffffu, ok) != 0;
+}
+
+// Drain wait: the copy that completes phase (fills - 1) of `bar` (the last one issued into it) has
+// landed; bounded by WAIT_CYCLES whatever the pipeline budget.  fills = 0: nothing was issued.
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, int fills) {
+  if (fills <= 0) return;
+  const uint32_t parity = (uint32_t)(fills - 1) & 1u;
+  long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity) && clock64() - t0 < WAIT_CYCLES) {
+  }
 }
 
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2,

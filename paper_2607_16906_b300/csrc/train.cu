@@ -587,6 +587,7 @@ extern "C" helm_status helm_train_step(helm_ctx* ctx, helm_unet* net, const void
   double ss = 0;
   for (double v : h) ss += v;
   double gn = sqrt(ss);
+  HELM_TRY(conv_tc_check(net, st));  // a forward convolution gave up: no update from that gradient
   if (!std::isfinite(gn) || !std::isfinite(loss)) return fail(HELM_NAN, "helm_train_step: non-finite loss or gradient");
   double scale = (clip > 0 && gn > clip) ? clip / (gn + 1e-6) : 1.0;
   net->step += 1;
@@ -598,5 +599,34 @@ extern "C" helm_status helm_train_step(helm_ctx* ctx, helm_unet* net, const void
   HELM_TRY(unet_prepare(net, st));
   if (loss_host) *loss_host = loss;
   if (grad_norm_host) *grad_norm_host = gn;
+  return HELM_OK;
+}
+
+extern "C" helm_status helm_unet_get_adam(const helm_unet* net, double* m_host, double* v_host, int64_t* step_host) {
+  if (!net || !m_host || !v_host || !step_host) return fail(HELM_ERR_INVALID_ARG, "helm_unet_get_adam: NULL argument");
+  const int64_t P = net->L.total;
+  if (!net->adam_m) {  // no step taken yet: zero moments
+    for (int64_t i = 0; i < P; ++i) m_host[i] = v_host[i] = 0.0;
+    *step_host = 0;
+    return HELM_OK;
+  }
+  HELM_CK(cudaDeviceSynchronize());
+  HELM_CK(cudaMemcpy(m_host, net->adam_m, sizeof(double) * P, cudaMemcpyDeviceToHost));
+  HELM_CK(cudaMemcpy(v_host, net->adam_v, sizeof(double) * P, cudaMemcpyDeviceToHost));
+  *step_host = net->step;
+  return HELM_OK;
+}
+
+extern "C" helm_status helm_unet_set_adam(helm_unet* net, const double* m_host, const double* v_host, int64_t step) {
+  if (!net || !m_host || !v_host || step < 0) return fail(HELM_ERR_INVALID_ARG, "helm_unet_set_adam: bad argument");
+  const int64_t P = net->L.total;
+  if (!net->adam_m) {
+    HELM_CK(cudaMalloc(&net->adam_m, sizeof(double) * P));
+    HELM_CK(cudaMalloc(&net->adam_v, sizeof(double) * P));
+  }
+  HELM_CK(cudaDeviceSynchronize());
+  HELM_CK(cudaMemcpy(net->adam_m, m_host, sizeof(double) * P, cudaMemcpyHostToDevice));
+  HELM_CK(cudaMemcpy(net->adam_v, v_host, sizeof(double) * P, cudaMemcpyHostToDevice));
+  net->step = step;
   return HELM_OK;
 }

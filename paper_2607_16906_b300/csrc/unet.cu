@@ -543,8 +543,11 @@ helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, cons
   launch(k_set_io, 1, 1, 0, st, ub->io, (const void*)v, (void*)z, in_scale, out_scale);
   HELM_CK_LAUNCH();
   const UnetGraphKey key{net->id, sys, B, c_stride, ub->gen};
-  auto it = graphs_enabled() ? ub->graphs.find(key) : ub->graphs.end();
-  if (it == ub->graphs.end() && graphs_enabled() && ub->seen.count(key)) {
+  // a captured graph holds its kernels' arguments: while a test override (wait budget, injected
+  // fault) is active, the network runs eagerly so that the override reaches the kernels
+  const bool use_graphs = graphs_enabled() && !test_overrides_active();
+  auto it = use_graphs ? ub->graphs.find(key) : ub->graphs.end();
+  if (it == ub->graphs.end() && use_graphs && ub->seen.count(key)) {
     // second use of this key: capture the sequence on the library's own stream
     const uint64_t l0 = helm_launch_count();
     HELM_CK(cudaStreamBeginCapture(ub->gstream, cudaStreamCaptureModeThreadLocal));
@@ -573,7 +576,7 @@ helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, cons
     HELM_CK(cudaStreamWaitEvent(st, ub->ev_out, 0));
     return HELM_OK;
   }
-  if (graphs_enabled()) ub->seen.insert(key);
+  if (use_graphs) ub->seen.insert(key);
   return unet_sequence<R>(ctx, net, sys, v, z, B, in_scale, out_scale, st, c_stride, false, ub->io);
 }
 
@@ -692,7 +695,8 @@ extern "C" helm_status helm_unet_get_weights(const helm_unet* net, double* weigh
 
 extern "C" helm_status helm_precond_apply(helm_ctx* ctx, const helm_unet* net, const void* v, void* z,
                                           helm_dtype dtype, int nrhs, void* stream) {
-  if (!ctx || !net || !v || !z || nrhs <= 0) return fail(HELM_ERR_INVALID_ARG, "helm_precond_apply: bad argument");
+  if (!ctx || !net || !v || !z) return fail(HELM_ERR_INVALID_ARG, "helm_precond_apply: NULL argument");
+  HELM_TRY(check_columns(ctx, nrhs, "helm_precond_apply"));
   if (((uintptr_t)v | (uintptr_t)z) & 15) return fail(HELM_ERR_INVALID_ARG, "helm_precond_apply: pointers must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
   if (dtype == HELM_C64) return precond_entry<float>(ctx, net, (const float2*)v, (float2*)z, nrhs, st);

@@ -28,6 +28,9 @@ STATUS_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "OOM", 4: "NOT_CONVERGE
                 7: "TIMEOUT"}
 HELM_C64, HELM_C128 = 0, 1
 HELM_MAX_M = 4096
+HELM_MAX_COLUMNS = 65535
+HELM_LAYER_DEC1B_FINAL = 17
+HELM_FAULT_NONE, HELM_FAULT_STENCIL_TILE, HELM_FAULT_CONV_TILE, HELM_FAULT_ALLOC = 0, 1, 2, 3
 
 
 class helm_grid(ct.Structure):
@@ -71,6 +74,12 @@ _SIGS = {
                                    ct.POINTER(ct.c_double), _P]),
     "helm_loss_grad": (ct.c_int, [_P, _P, _P, ct.c_int, ct.POINTER(ct.c_double), _P, _P]),
     "helm_relres_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int, _P, _P]),
+    "helm_unet_layer_forward": (ct.c_int, [_P, ct.c_int, ct.c_int, _P, _P, _P, ct.c_int, ct.c_int, ct.c_int,
+                                           ct.POINTER(ct.c_int), _P]),
+    "helm_unet_get_adam": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
+    "helm_unet_set_adam": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_int64]),
+    "helm_set_wait_budget": (ct.c_int, [ct.c_int64]),
+    "helm_inject_fault": (ct.c_int, [ct.c_int, ct.c_int]),
     "helm_solve_history": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.c_int]),
     "helm_profile_enable": (ct.c_int, [_P, ct.c_int]),
     "helm_profile_read": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
@@ -109,6 +118,17 @@ def _dev_ptr(t: torch.Tensor):
     if not t.is_cuda or not t.is_contiguous():
         raise ValueError("expected a contiguous CUDA tensor")
     return ct.c_void_p(t.data_ptr())
+
+
+def _batch(t: torch.Tensor, ctx, nrhs, name, dtype=None):
+    """Check that t is a contiguous CUDA batch vector with (at least) ctx.npts * nrhs elements."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if t.numel() < ctx.npts * nrhs:
+        raise ValueError(f"{name} holds {t.numel()} values, fewer than npts * nrhs = {ctx.npts * nrhs}")
+    return _dev_ptr(t)
 
 
 def _dtype_code(t: torch.Tensor):
@@ -192,8 +212,10 @@ def helm_apply_adjoint(ctx, x, y, nrhs=1, stream=None):
 
 def helm_relres(ctx: Context, x: torch.Tensor, b: torch.Tensor, nrhs=1, stream=None) -> np.ndarray:
     ncol = len(ctx.systems) * nrhs
-    out = (ct.c_double * ncol)()
-    _check(_lib.helm_relres(ctx.handle, _dev_ptr(x), _dev_ptr(b), nrhs, out, _stream(stream)))
+    px = _batch(x, ctx, nrhs, "x", torch.complex128)
+    pb = _batch(b, ctx, nrhs, "b", torch.complex128)
+    out = (ct.c_double * max(ncol, 1))()
+    _check(_lib.helm_relres(ctx.handle, px, pb, nrhs, out, _stream(stream)))
     return np.array(out[:])
 
 
@@ -203,8 +225,34 @@ def helm_relres_noalloc(ctx: Context, x: torch.Tensor, b: torch.Tensor, out: tor
     ncol = len(ctx.systems) * nrhs
     if out.dtype != torch.float64 or out.numel() < ncol:
         raise ValueError("out must be a float64 CUDA tensor with nsys * nrhs entries")
-    _check(_lib.helm_relres_noalloc(ctx.handle, _dev_ptr(x), _dev_ptr(b), nrhs, _dev_ptr(out), _stream(stream)))
+    px = _batch(x, ctx, nrhs, "x", torch.complex128)
+    pb = _batch(b, ctx, nrhs, "b", torch.complex128)
+    _check(_lib.helm_relres_noalloc(ctx.handle, px, pb, nrhs, _dev_ptr(out), _stream(stream)))
     return out
+
+
+def helm_unet_layer_forward(net, layer, in0: torch.Tensor, out: torch.Tensor, B, H, W, in1=None, variant=0,
+                            stream=None):
+    """One layer of the BF16 network on NHWC bfloat16 CUDA tensors (helm_unet_layer_forward in
+    include/helm.h); returns the rows per tile of the row-tile kernel that ran (0: 9-box kernel)."""
+    for t in (in0, out) + ((in1,) if in1 is not None else ()):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("layer tensors must be contiguous CUDA tensors")
+    ry = ct.c_int()
+    _check(_lib.helm_unet_layer_forward(net.handle, layer, variant, _dev_ptr(in0),
+                                        _dev_ptr(in1) if in1 is not None else None, _dev_ptr(out), B, H, W,
+                                        ct.byref(ry), _stream(stream)))
+    return ry.value
+
+
+def helm_set_wait_budget(cycles: int):
+    """Pipeline-wait budget (clock64 cycles) of the TMA/tcgen05 kernels; <= 0 restores the default."""
+    _check(_lib.helm_set_wait_budget(int(cycles)))
+
+
+def helm_inject_fault(site: int, count: int = 1):
+    """Arm a host-side fault for the next `count` occurrences of `site` (HELM_FAULT_*)."""
+    _check(_lib.helm_inject_fault(int(site), int(count)))
 
 
 def helm_unet_param_count() -> int:
@@ -249,6 +297,22 @@ class UNet:
         out = np.zeros(self.nparams)
         _check(_lib.helm_unet_get_weights(self._h, out.ctypes.data_as(ct.POINTER(ct.c_double)), out.size))
         return out
+
+    def adam_state(self):
+        """(m, v, step) of the AdamW optimiser (helm_unet_get_adam)."""
+        m, v, st = np.zeros(self.nparams), np.zeros(self.nparams), ct.c_int64()
+        _check(_lib.helm_unet_get_adam(self._h, m.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                       v.ctypes.data_as(ct.POINTER(ct.c_double)), ct.byref(st)))
+        return m, v, st.value
+
+    def set_adam_state(self, m, v, step):
+        """Restore the AdamW moments and step count (helm_unet_set_adam)."""
+        m = np.ascontiguousarray(m, np.float64)
+        v = np.ascontiguousarray(v, np.float64)
+        if m.size != self.nparams or v.size != self.nparams:
+            raise ValueError("moments must have one value per parameter")
+        _check(_lib.helm_unet_set_adam(self._h, m.ctypes.data_as(ct.POINTER(ct.c_double)),
+                                       v.ctypes.data_as(ct.POINTER(ct.c_double)), int(step)))
 
     def set_weights(self, theta: torch.Tensor, stream=None):
         """helm_unet_set_weights: replace the weights from a CUDA float64 tensor of nparams values."""

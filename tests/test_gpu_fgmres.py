@@ -1,6 +1,8 @@
 """Parity of the CUDA FGMRES solver (a4-a8) against the oracle: one full cycle at a fixed
 iteration count (identity and U-Net preconditioners, FP64), converged solves against the sparse
 direct solution (plain FP64 and mixed paths, uneven batches), and status reporting."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -117,3 +119,91 @@ def test_status_reporting(helm):
     x.zero_()
     rc, info = helm.helm_fgmres_solve(ctx, None, z, x, 1, m=4, tol=1e-6)
     assert torch.count_nonzero(x).item() == 0
+
+
+# ---------------------------------------------------------------- the benchmarked configuration
+#
+# Mixed path as the benchmark runs it: FP32 Krylov basis and stencil, BF16 U-Net (trained
+# weights), FP64 Givens, FP64 true residual and iterative refinement (eq. 10), inner tolerance
+# 1e-5.  Target: true eta_b <= 1e-6 and a solution within 1e-5 of the sparse direct solution.
+
+TRAINED = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2607_16906_b300",
+                       "weights", "unet_trained.npy")
+
+
+@pytest.fixture(scope="module")
+def trained():
+    return np.load(TRAINED)
+
+
+@pytest.mark.parametrize("orth", ["dcgs2", "cgs2"])
+def test_benchmarked_path_converges_to_the_direct_solution(helm, trained, orth):
+    probs = small_problems(((40, 40, 12), (48, 32, 8), (33, 27, 6)), seed=35, nrhs=2)
+    ctx = make_ctx(probs)
+    net = helm.UNet(trained)
+    b = to_dev(_flat_b(probs), torch.complex128)
+    x = torch.zeros_like(b)
+    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 2, m=40, tol=1e-6, mixed=True, max_outer=20, inner_tol=1e-5,
+                                      orth=orth)
+    assert rc == helm.HELM_OK, info
+    got = split(x.cpu().numpy(), probs, 2)
+    k = 0
+    for p, xs in zip(probs, got):
+        A = hz.assemble(p.c, p.p, p.h, p.omega)
+        xd = hz.solve_direct(A, p.b.reshape(2, -1).T).T
+        for r in range(2):
+            rel = hz.relres(A, xs[r].ravel(), p.b[r].ravel())
+            assert rel <= 1e-6 and abs(rel - info[k]["relres_true"]) <= 1e-9 * max(rel, 1e-12)
+            assert np.linalg.norm(xs[r].ravel() - xd[r]) <= 1e-5 * np.linalg.norm(xd[r]), (k, rel)
+            k += 1
+
+
+def test_benchmarked_path_iterations_match_the_oracle(helm, trained):
+    """The CUDA mixed solve and the oracle's mixed emulation (refine with complex64 vectors and a
+    BF16-rounded network, same cycle length and tolerances) reach eta_b <= 1e-6 in iteration counts
+    within 25 % of each other (both use DCGS2)."""
+    probs = small_problems(((40, 40, 12),), seed=36)
+    p = probs[0]
+    ctx = make_ctx(probs)
+    net = helm.UNet(trained)
+    b = to_dev(_flat_b(probs), torch.complex128)
+    x = torch.zeros_like(b)
+    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=20, tol=1e-6, mixed=True, max_outer=30, inner_tol=1e-5,
+                                      orth="dcgs2")
+    assert rc == helm.HELM_OK
+    A = hz.assemble(p.c, p.p, p.h, p.omega)
+    Mb = lambda v: unet.precondition(trained, np.asarray(v, complex).reshape(1, p.Ny, p.Nx), p.c, p.h,
+                                     bf16=True)[0].ravel().astype(np.complex64)
+    _, oinfo = fg.refine(lambda u: A @ u, Mb, p.b[0].ravel(), m=20, tol=1e-6, inner_tol=1e-5, max_outer=30,
+                         orth="dcgs2")
+    assert oinfo.converged
+    assert abs(info[0]["iters"] - oinfo.iters) <= 0.25 * oinfo.iters, (info[0], oinfo.iters)
+
+
+@pytest.mark.parametrize("orth", ["dcgs2", "cgs2"])
+def test_mixed_cycle_estimates_follow_the_oracle(helm, trained, orth):
+    """One FP32 cycle with the BF16 network: the per-iteration Givens estimates equal the oracle's
+    complex64 / BF16-emulated cycle.  The network is nonlinear, so an FP32 summation-order
+    difference that flips one BF16 rounding (2^-8 relative) perturbs later iterates: the bound grows
+    from 2 % over the first iterations to 15 % (the oracle's own CGS2 and DCGS2 cycles, which differ
+    only in FP32 rounding, drift apart by up to 6 % over 16 iterations on this problem)."""
+    probs = small_problems(((40, 40, 12),), seed=33)
+    p = probs[0]
+    ctx = make_ctx(probs)
+    net = helm.UNet(trained)
+    b = to_dev(_flat_b(probs), torch.complex128)
+    x = torch.zeros_like(b)
+    m = 16
+    helm.helm_fgmres_solve(ctx, net, b, x, 1, m=m, tol=1e-300, mixed=True, max_outer=1, orth=orth)
+    hist = helm.helm_solve_history(ctx)
+    A = hz.assemble(p.c, p.p, p.h, p.omega)
+    Mb = lambda v: unet.precondition(trained, np.asarray(v, complex).reshape(1, p.Ny, p.Nx), p.c, p.h,
+                                     bf16=True)[0].ravel().astype(np.complex64)
+    A_lo = lambda u: (A @ np.asarray(u, complex)).astype(np.complex64)
+    bb = p.b[0].ravel()
+    res = fg.cycle(A_lo, Mb, (bb / np.linalg.norm(bb)).astype(np.complex64), m, 0.0, orth=orth, dtype=np.complex64)
+    ora = np.array(res.history)
+    assert hist.size == ora.size == m
+    rel = np.abs(hist - ora) / ora
+    assert (rel[:4] <= 2e-2).all() and (rel <= 0.15).all(), rel
+    assert ora[-1] < 0.1 * ora[0]                      # the cycle made progress worth comparing

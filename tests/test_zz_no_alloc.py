@@ -34,10 +34,11 @@ def test_noalloc_relres_matches_allocating_entry_point_twice():
 
 def test_noalloc_rejects_batches_beyond_the_fixed_scratch():
     from paper_2607_16906_b300 import helm
-    probs = small_problems(((20, 14, 5),), seed=42)
+    # Nx = 30, Ny = 80: 1 x 10 stencil blocks -> 20 scratch doubles per column; 2^20 doubles hold
+    # 52,428 columns, so 60,000 columns (within the launch limit of 65,535) exceed the fixed array
+    probs = small_problems(((20, 70, 5),), seed=42)
     ctx = make_ctx(probs)
-    # 1 x 3 blocks per column -> 6 doubles per column; 2^20 doubles allow 174762 columns
-    nrhs = 200000
+    nrhs = 60000
     x = torch.zeros(ctx.npts * nrhs, dtype=torch.complex128, device="cuda")
     out = torch.zeros(nrhs, dtype=torch.float64, device="cuda")
     with pytest.raises(helm.HelmError, match="fixed maximum"):
