@@ -356,7 +356,7 @@ def helm_fgmres_solve(ctx: Context, net, b: torch.Tensor, x: torch.Tensor, nrhs=
     info = (helm_solve_info * ncol)()
     rc = _lib.helm_fgmres_solve(ctx.handle, net.handle if net is not None else None, _dev_ptr(b), _dev_ptr(x),
                                 nrhs, ct.byref(opts), info, _stream(stream))
-    _check(rc, allow=() if raise_on else (HELM_NOT_CONVERGED, HELM_BREAKDOWN, HELM_NAN))
+    _check(rc, allow=() if raise_on else (HELM_NOT_CONVERGED, HELM_BREAKDOWN, HELM_NAN, HELM_TIMEOUT))
     cols = [dict(iters=i.iters, restarts=i.restarts, outer=i.outer, relres_true=i.relres_true,
                  relres_est=i.relres_est, status=STATUS_NAMES.get(i.status, i.status)) for i in info]
     return rc, cols

@@ -48,7 +48,7 @@ def _bf16_tensor(rng, shape):
     return x.cuda().contiguous(), x.float().numpy().astype(np.float64)
 
 
-def _variants(helm, net, layer, args):
+def _variants(helm, net, layer, args, in1=None):
     """Every kernel the layer has: row-tile variants 1..k (until the library says there are no
     more) and the 9-box kernel (-1); up-convs have one kernel."""
     kind = helm.helm_unet_layers()[min(layer, 16)][2]
@@ -58,7 +58,7 @@ def _variants(helm, net, layer, args):
     v = 1
     while True:
         try:
-            helm.helm_unet_layer_forward(net, layer, *args, variant=v)
+            helm.helm_unet_layer_forward(net, layer, *args, in1=in1, variant=v)
         except helm.HelmError:
             break
         out.append(v)
@@ -100,7 +100,7 @@ def test_layer_matches_oracle_convolution(helm, net_theta, layer):
         ref = ou.relu(ou.conv2d(xin, Wq, b, 1)).transpose(0, 2, 3, 1)
         out = torch.empty((B, H, Wd, co), dtype=torch.bfloat16, device="cuda")
     args = (in0, out, B, H, Wd)
-    variants = _variants(helm, net, layer, args) if kind != "up2" else [0]
+    variants = _variants(helm, net, layer, args, in1) if kind != "up2" else [0]
     if row_layer:
         assert len([v for v in variants if v > 0]) >= 2, variants   # the autotuner's candidates
     for v in variants:
