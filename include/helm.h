@@ -125,6 +125,11 @@ typedef struct {
 HELM_API helm_status helm_create(helm_ctx** out, int nsys, const helm_grid* grid, const helm_pml* pml,
                         const double* omega, const void* c_dev, int c_is_fp64, void* stream);
 HELM_API helm_status helm_destroy(helm_ctx* ctx);
+/* Replace the velocities of every system of ctx (grids, PMLs and frequencies unchanged), e.g. the next
+ * batch of a training set: k^2 and c / 1500 m/s are recomputed on `stream`.  c_dev as in helm_create;
+ * c must be > 0 and finite (HELM_ERR_INVALID_ARG; the previous values are then partly overwritten).
+ * Synchronises `stream`. */
+HELM_API helm_status helm_set_velocity(helm_ctx* ctx, const void* c_dev, int c_is_fp64, void* stream);
 /* Total points of one batch vector per right-hand side (sum of n_s), and the system count. */
 HELM_API int64_t helm_points(const helm_ctx* ctx);
 HELM_API int helm_num_systems(const helm_ctx* ctx);

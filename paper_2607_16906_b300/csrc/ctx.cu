@@ -319,6 +319,26 @@ extern "C" helm_status helm_create(helm_ctx** out, int nsys, const helm_grid* gr
   return HELM_OK;
 }
 
+extern "C" helm_status helm_set_velocity(helm_ctx* ctx, const void* c_dev, int c_is_fp64, void* stream) {
+  if (!ctx || !c_dev) return fail(HELM_ERR_INVALID_ARG, "helm_set_velocity: NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  HELM_CK(cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int), st));
+  for (auto& h : ctx->sys) {
+    const char* cb = (const char*)c_dev + h.off * (c_is_fp64 ? 8 : 4);
+    launch(k_wavenumbers, cdiv(h.n, 256), 256, 0, st, cb, c_is_fp64, h.n, h.omega, ctx->k2d + h.off, ctx->k2f + h.off,
+           ctx->chat + h.off, ctx->chat64 + h.off, ctx->flag_dev);
+  }
+  HELM_CK_LAUNCH();
+  int bad = 0;
+  HELM_CK(cudaMemcpyAsync(&bad, ctx->flag_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  HELM_CK(cudaStreamSynchronize(st));
+  if (bad) {
+    cudaMemsetAsync(ctx->flag_dev, 0, sizeof(int), st);
+    return fail(HELM_ERR_INVALID_ARG, "helm_set_velocity: c must be positive and finite everywhere");
+  }
+  return HELM_OK;
+}
+
 extern "C" helm_status helm_destroy(helm_ctx* ctx) {
   if (!ctx) return HELM_OK;
   cudaDeviceSynchronize();

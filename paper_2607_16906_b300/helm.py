@@ -56,6 +56,7 @@ _SIGS = {
     "helm_create": (ct.c_int, [ct.POINTER(_P), ct.c_int, ct.POINTER(helm_grid), ct.POINTER(helm_pml),
                                ct.POINTER(ct.c_double), _P, ct.c_int, _P]),
     "helm_destroy": (ct.c_int, [_P]),
+    "helm_set_velocity": (ct.c_int, [_P, _P, ct.c_int, _P]),
     "helm_points": (ct.c_int64, [_P]),
     "helm_num_systems": (ct.c_int, [_P]),
     "helm_apply": (ct.c_int, [_P, _P, _P, ct.c_int, ct.c_int, _P]),
@@ -181,6 +182,13 @@ class Context:
     @property
     def handle(self):
         return self._h
+
+    def set_velocity(self, c: torch.Tensor, stream=None):
+        """helm_set_velocity: new velocities (same grids) for every system, e.g. the next training batch."""
+        if c.dtype not in (torch.float64, torch.float32) or c.numel() != self.npts:
+            raise ValueError("c must hold sum(Nx*Ny) float32/float64 velocities")
+        c = c.contiguous()
+        _check(_lib.helm_set_velocity(self._h, _dev_ptr(c), int(c.dtype == torch.float64), _stream(stream)))
 
     def close(self):
         if self._h:

@@ -142,6 +142,142 @@ def gaussian_sources(nx, ny, p, rng) -> np.ndarray:
     return rng.standard_normal((Ny, Nx)) + 1j * rng.standard_normal((Ny, Nx))
 
 
+# ---------------------------------------------------------------- the paper's training distributions
+#
+# Sec. 3.2 draws velocities and sources independently from small menus and mixes them with fixed
+# probabilities (Tab. 4, datasets D0-D5).  The paper's c is normalised to [1, 2]; here c = 1500 m/s
+# times that value.  TruncIdealSkulls (cropped idealised skull images) is not available: the
+# skull ring above stands in for it.
+
+def uniform_velocity(nx: int, ny: int, p: int, rng: np.random.Generator) -> np.ndarray:
+    """U([1, 2]): every entry of c drawn independently, c = 1500 m/s x U[1, 2]."""
+    Nx, Ny = nx + 2 * p, ny + 2 * p
+    return C_WATER * rng.uniform(1.0, 2.0, (Ny, Nx))
+
+
+def constant_velocity(nx: int, ny: int, p: int, rng: np.random.Generator) -> np.ndarray:
+    """randConstant (Sec. 3.2) and gamma-constant (App. B): one value gamma ~ U[1, 2] everywhere."""
+    Nx, Ny = nx + 2 * p, ny + 2 * p
+    return np.full((Ny, Nx), C_WATER * rng.uniform(1.0, 2.0))
+
+
+def square_velocity(nx: int, ny: int, p: int, rng: np.random.Generator = None, frac=0.5) -> np.ndarray:
+    """square (Sec. 3.2): c = 2 (3000 m/s) on a centred square, 1 (1500 m/s) elsewhere; the square's
+    side is `frac` of the interior's smaller side (the paper does not give it)."""
+    Nx, Ny = nx + 2 * p, ny + 2 * p
+    c = np.full((Ny, Nx), C_WATER)
+    side = max(1, int(round(frac * min(nx, ny))))
+    y0, x0 = (Ny - side) // 2, (Nx - side) // 2
+    c[y0:y0 + side, x0:x0 + side] = 2.0 * C_WATER
+    return c
+
+
+def layered_velocity(nx: int, ny: int, p: int, rng: np.random.Generator, layers=4, faulted=False,
+                     alpha=1.0, beta=2.0) -> np.ndarray:
+    """4layered / 4faulted (App. B): `layers` horizontal layers, each of one speed 1500 m/s x
+    U[alpha, beta]; interfaces at sorted random interior rows.  Faulted: right of a random
+    vertical fault line every interface is shifted by one common random offset (a throw of 5-20 %
+    of the interior height, up or down), so the layers stay aligned but are discontinuous."""
+    Nx, Ny = nx + 2 * p, ny + 2 * p
+    speeds = C_WATER * rng.uniform(alpha, beta, layers)
+    cuts = np.sort(rng.choice(np.arange(p + 1, p + ny), layers - 1, replace=False))
+    rows = np.arange(Ny)[:, None] * np.ones((1, Nx))
+    shift = np.zeros((Ny, Nx))
+    if faulted:
+        xf = int(rng.integers(p + nx // 4, p + 3 * nx // 4))
+        throw = int(round(rng.uniform(0.05, 0.20) * ny)) * (1 if rng.uniform() < 0.5 else -1)
+        shift[:, xf:] = throw
+    layer = np.searchsorted(cuts, rows - shift, side="right")
+    return speeds[layer]
+
+
+def dirac_sources(nx: int, ny: int, p: int, rng: np.random.Generator, m=1, amplitude=None) -> np.ndarray:
+    """m dirac (App. B): m entries of b set to +-1 (random signs) at random interior nodes; with
+    `amplitude` (Sec. 3.2's dirac: 60) every entry gets that value instead."""
+    Nx, Ny = nx + 2 * p, ny + 2 * p
+    b = np.zeros((Ny, Nx), np.complex128)
+    for _ in range(m):
+        i = int(rng.integers(p, p + nx))
+        j = int(rng.integers(p, p + ny))
+        b[j, i] = amplitude if amplitude is not None else (1.0 if rng.uniform() < 0.5 else -1.0)
+    return b
+
+
+def dirac1_source(nx: int, ny: int, p: int, amplitude=60.0, at=None) -> np.ndarray:
+    """dirac1: one entry `amplitude` at `at` = (row, column), by default the grid centre (Sec. 3.2;
+    the tests of Sec. 4.2 put amplitude 1 at a fixed off-centre node)."""
+    Nx, Ny = nx + 2 * p, ny + 2 * p
+    b = np.zeros((Ny, Nx), np.complex128)
+    j, i = at if at is not None else (Ny // 2, Nx // 2)
+    b[j, i] = amplitude
+    return b
+
+
+def dirac4_source(nx: int, ny: int, p: int, amplitude=30.0) -> np.ndarray:
+    """dirac4 (Sec. 3.2): four entries `amplitude` at fixed nodes, here the interior's quarter points."""
+    Nx, Ny = nx + 2 * p, ny + 2 * p
+    b = np.zeros((Ny, Nx), np.complex128)
+    for fy in (0.25, 0.75):
+        for fx in (0.25, 0.75):
+            b[p + int(fy * ny), p + int(fx * nx)] = amplitude
+    return b
+
+
+def dirac1_smooth_source(nx: int, ny: int, p: int, at=None, sigma=2.0) -> np.ndarray:
+    """dirac1_smooth (Sec. 4.2): a Gaussian bump exp(-((x - c_x)^2 + (y - c_y)^2) / (2 sigma^2)) in
+    grid units, sigma = 2, centred at `at` = (c_y, c_x) (default: the node the paper's (60, 32) on a
+    64 x 64 grid maps to).  The printed formula repeats x in its second term; read as y."""
+    Nx, Ny = nx + 2 * p, ny + 2 * p
+    cy, cx = at if at is not None else (int(round(32 / 64 * (Ny - 1))), int(round(60 / 64 * (Nx - 1))))
+    yy, xx = np.mgrid[0:Ny, 0:Nx].astype(np.float64)
+    return np.exp(-((xx - cx) ** 2 + (yy - cy) ** 2) / (2.0 * sigma * sigma)).astype(np.complex128)
+
+
+# Tab. 4: source and velocity menus with their probabilities per dataset
+SOURCE_MENU = ("normal", "dirac", "dirac1", "dirac4")
+VELOCITY_MENU = ("uniform", "skull", "constant", "square")
+DATASETS = {
+    "D0": ((0.6, 0.3, 0.05, 0.05), (0.5, 0.5, 0.0, 0.0)),
+    "D1": ((1.0, 0.0, 0.0, 0.0), (0.5, 0.5, 0.0, 0.0)),
+    "D2": ((0.6, 0.3, 0.05, 0.05), (0.4, 0.4, 0.1, 0.1)),
+    "D3": ((1.0, 0.0, 0.0, 0.0), (0.4, 0.4, 0.1, 0.1)),
+    "D4": ((1.0, 0.0, 0.0, 0.0), (0.0, 1.0, 0.0, 0.0)),
+    "D5": ((1.0, 0.0, 0.0, 0.0), (1.0, 0.0, 0.0, 0.0)),
+}
+
+
+def dataset_sample(name: str, nx: int, p: int, rng: np.random.Generator):
+    """One (c, b, source kind, velocity kind) pair of dataset `name` (Tab. 4) on an nx^2 + p PML grid."""
+    sp, vp = DATASETS[name]
+    sk = SOURCE_MENU[int(rng.choice(4, p=sp))]
+    vk = VELOCITY_MENU[int(rng.choice(4, p=vp))]
+    c = {"uniform": uniform_velocity, "skull": skull_velocity, "constant": constant_velocity,
+         "square": square_velocity}[vk](nx, nx, p, rng)
+    if sk == "normal":
+        b = gaussian_sources(nx, nx, p, rng)
+    elif sk == "dirac":
+        b = dirac_sources(nx, nx, p, rng, 1, amplitude=60.0)
+    elif sk == "dirac1":
+        b = dirac1_source(nx, nx, p)
+    else:
+        b = dirac4_source(nx, nx, p)
+    return c, b, sk, vk
+
+
+def appendix_b_problem(kind: str, seed=6000, nx=128, p=16, ppw=10.0, nrhs=4, m=2) -> Problem:
+    """App. B test cases: velocity `kind` in {"gamma-constant", "4layered", "4faulted"}; sources
+    alternate between m dirac (+-1 at m random nodes) and dirac1_smooth."""
+    rng = rng_for(seed)
+    vel = {"gamma-constant": constant_velocity,
+           "4layered": lambda *a: layered_velocity(*a, layers=4),
+           "4faulted": lambda *a: layered_velocity(*a, layers=4, faulted=True)}[kind]
+    c = vel(nx, nx, p, rng)
+    b = np.stack([dirac_sources(nx, nx, p, rng, m) if k % 2 == 0 else dirac1_smooth_source(nx, nx, p)
+                  for k in range(nrhs)])
+    return Problem(nx, nx, p, grid_spacing(ppw), angular_frequency(), c, b,
+                   {"workload": f"App. B {kind}, {m} dirac / dirac1_smooth, {nx}^2+{p} PML", "seed": seed, "ppw": ppw})
+
+
 # ---------------------------------------------------------------- workloads
 
 def small_problem(seed=1000, nx=128, p=16, ppw=10.0) -> Problem:

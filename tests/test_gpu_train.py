@@ -142,3 +142,27 @@ def test_training_rejects_mixed_grid_sizes(helm):
     b = torch.ones(ctx.npts, dtype=torch.complex64, device="cuda")
     with pytest.raises(helm.HelmError):
         helm.helm_train_step(ctx, helm.UNet(synth.kaiming_uniform_params(ou.param_segments(), 1)), b)
+
+
+def test_epoch_training_loop_resumes_exactly(tmp_path):
+    """Epochs over a fixed sample set (Tab. 4 dataset D0), AdamW with the cosine schedule, validation
+    by solver iteration count, checkpoint with the AdamW state: stopping after one epoch and resuming
+    gives the same weights, bit for bit, as running both epochs at once."""
+    from paper_2607_16906_b300 import synth
+    from paper_2607_16906_b300 import train_precond as tp
+    prob = synth.small_problem(seed=1900, nx=32, p=8)
+    val = tp.Validator(prob, m=20, max_outer=10)
+    kw = dict(dataset="D0", samples=16, nx=24, p=4, batch=8, lr_max=1e-3, lr_min=1e-4, val_every=1,
+              validator=val, verbose=False)
+    net_a, st_a = tp.train_epochs(epochs=2, checkpoint=str(tmp_path / "a.npz"), out=str(tmp_path / "a.npy"), **kw)
+    assert len(st_a["history"]) == 2 and all("val" in r for r in st_a["history"])
+    assert st_a["step"] == 4 and st_a["best"] is not None
+    ck = str(tmp_path / "b.npz")
+    tp.train_epochs(epochs=1, checkpoint=ck, **kw)
+    _, (m1, v1, s1), st1 = tp.load_checkpoint(ck)
+    assert s1 == 2 and st1["epoch"] == 1 and np.abs(m1).sum() > 0
+    net_b, st_b = tp.train_epochs(epochs=2, checkpoint=ck, resume=True, **kw)
+    assert st_b["step"] == 4
+    assert np.array_equal(net_a.weights(), net_b.weights())
+    best = np.load(str(tmp_path / "a.npy"))
+    assert best.size == net_a.nparams

@@ -1,0 +1,73 @@
+"""The App. B workloads (spherical waves in a homogeneous medium, layered and faulted seismic media;
+m-dirac and dirac1_smooth sources) and samples of the Tab. 4 training distributions, solved by the
+CUDA path and checked against the oracle's sparse direct solution.
+
+Mixed path (FP32 basis, BF16 network with the trained weights, FP64 refinement) to eta_b <= 1e-6
+with the solution within 1e-5 of splu; plain FP64 path to 1e-10 with the solution within 1e-8.
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import helmholtz as hz
+from paper_2607_16906_b300 import synth
+
+from .gpu_util import make_ctx, split, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TRAINED = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2607_16906_b300",
+                       "weights", "unet_trained.npy")
+
+
+@pytest.fixture(scope="module")
+def helm():
+    from paper_2607_16906_b300 import helm as h
+    return h
+
+
+@pytest.fixture(scope="module")
+def net(helm):
+    return helm.UNet(np.load(TRAINED))
+
+
+def _check(helm, probs, x, nrhs, tol, err_tol):
+    got = split(x.cpu().numpy(), probs, nrhs)
+    for p, xs in zip(probs, got):
+        A = hz.assemble(p.c, p.p, p.h, p.omega)
+        xd = hz.solve_direct(A, p.b.reshape(nrhs, -1).T).T
+        for r in range(nrhs):
+            assert hz.relres(A, xs[r].ravel(), p.b[r].ravel()) <= tol
+            assert np.linalg.norm(xs[r].ravel() - xd[r]) <= err_tol * np.linalg.norm(xd[r])
+
+
+@pytest.mark.parametrize("mixed", [True, False])
+def test_appendix_b_workloads(helm, net, mixed):
+    probs = [synth.appendix_b_problem(k, seed=6100 + i, nx=48, p=8, nrhs=2, m=2)
+             for i, k in enumerate(("gamma-constant", "4layered", "4faulted"))]
+    ctx = make_ctx(probs)
+    b = to_dev(np.concatenate([p.b.ravel() for p in probs]), torch.complex128)
+    x = torch.zeros_like(b)
+    tol = 1e-6 if mixed else 1e-10
+    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 2, m=40, tol=tol, mixed=mixed, max_outer=30,
+                                      max_restarts=30, inner_tol=1e-5, orth="dcgs2")
+    assert rc == helm.HELM_OK, info
+    _check(helm, probs, x, 2, tol, 1e-5 if mixed else 1e-8)
+
+
+def test_training_distribution_samples(helm, net):
+    """One sample of each dataset D0-D5 (Tab. 4), every sample its own system of one batch."""
+    rng = synth.rng_for(6200)
+    probs = []
+    for name in synth.DATASETS:
+        c, bb, _, _ = synth.dataset_sample(name, 40, 8, rng)
+        probs.append(synth.Problem(40, 40, 8, synth.grid_spacing(10.0), synth.angular_frequency(), c, bb[None]))
+    ctx = make_ctx(probs)
+    b = to_dev(np.concatenate([p.b.ravel() for p in probs]), torch.complex128)
+    x = torch.zeros_like(b)
+    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=40, tol=1e-6, mixed=True, max_outer=40, inner_tol=1e-5,
+                                      orth="dcgs2")
+    assert rc == helm.HELM_OK, info
+    _check(helm, probs, x, 1, 1e-6, 1e-5)
