@@ -140,6 +140,15 @@ HELM_API int helm_num_systems(const helm_ctx* ctx);
 HELM_API helm_status helm_apply(helm_ctx* ctx, const void* x, void* y, helm_dtype dtype, int nrhs, void* stream);
 /* y = A^H x (= conj(A conj(x)) since A = A^T); used by the loss gradient (eq. 9). */
 HELM_API helm_status helm_apply_adjoint(helm_ctx* ctx, const void* x, void* y, helm_dtype dtype, int nrhs, void* stream);
+/* y = A_F x: the paper's own discretisation (Sec. 2.1, Tab. 1), Fourier differentiation on the
+ * periodic grid that includes the PML, with the stretched derivatives of the same PML (eq. 2):
+ *   A_F u = -[ (1/s_x) D_x((1/s_x) D_x u) + (1/s_y) D_y((1/s_y) D_y u) ] - k^2 u,
+ *   D u = IDFT(i kappa DFT(u)) along one axis, kappa_q = 2 pi q / (N h), the Nyquist mode set to zero,
+ * s = 1 + i sigma / omega at the grid nodes.  An alternative to helm_apply (the 5-point operator);
+ * the solver and the network use helm_apply's operator.  Every system's Nx and Ny must be powers of
+ * two in [16, 1024] (HELM_ERR_INVALID_ARG otherwise).  x, y: batch vectors that must not overlap. */
+HELM_API helm_status helm_apply_fourier(helm_ctx* ctx, const void* x, void* y, helm_dtype dtype, int nrhs,
+                                        void* stream);
 /* out_host[col] = ||b - A x|| / ||b|| in FP64 for every column (eq. 10); x, b are C128. Synchronises. */
 HELM_API helm_status helm_relres(helm_ctx* ctx, const void* x, const void* b, int nrhs, double* out_host, void* stream);
 

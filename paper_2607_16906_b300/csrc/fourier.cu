@@ -1,0 +1,246 @@
+// Fourier-differentiation Helmholtz operator with PML (the paper's discretisation, Sec. 2.1, Tab. 1):
+//
+//   y = A_F u = -[ (1/s_x) D_x((1/s_x) D_x u) + (1/s_y) D_y((1/s_y) D_y u) ] - k^2 u,
+//   D u = IDFT( i kappa DFT(u) ) along one axis, kappa_q = 2 pi q / (N h), the Nyquist mode zeroed,
+//
+// on the periodic N_x x N_y grid that includes the PML, with the node stretch factors s = 1 + i sigma /
+// omega of eq. 2 (the same nodes the 5-point operator uses).  Grid sides are powers of two, 16..1024.
+//
+// Two passes, each one read of its inputs and one write, with every FFT in shared memory:
+//   x pass: one block per grid row: DIF forward FFT (natural order in, bit-reversed out), multiply by
+//           i kappa / N at the bit-reversed position, DIT inverse FFT (bit-reversed in, natural out),
+//           scale by 1/s_x, the same again -> t_x, written to y;
+//   y pass: one block per 16 (FP32) or 8 (FP64) columns, the whole column height in shared memory
+//           (128-byte row segments, coalesced), the same derivative pair along y -> t_y; then
+//           y = -(t_x + t_y) - k^2 u.
+// Twiddle tables exp(-2 pi i t / N), t < N/2, are computed once per grid side on the host in FP64
+// and staged into shared memory by every block.  HBM traffic per point: x pass 16 B (FP32), y pass
+// 8 (u) + 8 (t_x) + 8 (u again) + 4 (k^2) + 8 (y) = 36 B: 52 B per point and right-hand side.
+#include <math.h>
+
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "helm_internal.cuh"
+
+namespace helm {
+
+constexpr int FX_THREADS = 256;
+constexpr int FY_THREADS = 256;
+template <typename R> struct FyCols;
+template <> struct FyCols<float> { static constexpr int v = 16; };
+template <> struct FyCols<double> { static constexpr int v = 8; };
+
+__device__ __forceinline__ int brev(int i, int logn) { return (int)(__brev((unsigned)i) >> (32 - logn)); }
+
+// In-place radix-2 transforms of `ncols` interleaved columns of length N (element (i, c) at
+// a[i * ncols + c]).  tw[t] = exp(-2 pi i t / N), t < N/2.
+// DIF forward: natural order in, bit-reversed order out.
+template <typename R>
+__device__ void fft_dif(C<R>* a, int N, int ncols, const C<R>* tw, int tid, int nt) {
+  for (int half = N >> 1, step = 1; half >= 1; half >>= 1, step <<= 1) {
+    const int nb = (N >> 1) * ncols;
+    for (int b = tid; b < nb; b += nt) {
+      const int c = b % ncols, bb = b / ncols;
+      const int k = bb & (half - 1), g = bb / half;
+      const int i0 = g * 2 * half + k, i1 = i0 + half;
+      const C<R> x0 = a[i0 * ncols + c], x1 = a[i1 * ncols + c];
+      a[i0 * ncols + c] = cadd(x0, x1);
+      a[i1 * ncols + c] = cmul(csub(x0, x1), tw[k * step]);
+    }
+    __syncthreads();
+  }
+}
+// DIT inverse (conjugate twiddles, no 1/N): bit-reversed order in, natural order out.
+template <typename R>
+__device__ void ifft_dit(C<R>* a, int N, int ncols, const C<R>* tw, int tid, int nt) {
+  for (int half = 1, step = N >> 1; half < N; half <<= 1, step >>= 1) {
+    const int nb = (N >> 1) * ncols;
+    for (int b = tid; b < nb; b += nt) {
+      const int c = b % ncols, bb = b / ncols;
+      const int k = bb & (half - 1), g = bb / half;
+      const int i0 = g * 2 * half + k, i1 = i0 + half;
+      const C<R> x0 = a[i0 * ncols + c], x1 = cmul(a[i1 * ncols + c], cconj(tw[k * step]));
+      a[i0 * ncols + c] = cadd(x0, x1);
+      a[i1 * ncols + c] = csub(x0, x1);
+    }
+    __syncthreads();
+  }
+}
+
+// i kappa_q / N for the spectrum entry at bit-reversed position `pos` (q = brev(pos)).
+template <typename R>
+__device__ __forceinline__ C<R> ikappa(int pos, int N, int logn, R two_pi_over_L) {
+  const int q = brev(pos, logn);
+  if (q == (N >> 1)) return mk<R>(0, 0);
+  const int qs = q < (N >> 1) ? q : q - N;
+  return mk<R>(0, (R)qs * two_pi_over_L / (R)N);
+}
+
+// t = (1/s) D((1/s) D t) along the column direction of a (spectral derivative pair), in place.
+// inv_s[i]: 1/s at node i.
+template <typename R>
+__device__ void derivative_pair(C<R>* a, int N, int logn, int ncols, const C<R>* tw, const C<R>* inv_s,
+                                R two_pi_over_L, int tid, int nt) {
+  for (int rep = 0; rep < 2; ++rep) {
+    fft_dif<R>(a, N, ncols, tw, tid, nt);
+    for (int e = tid; e < N * ncols; e += nt) a[e] = cmul(a[e], ikappa<R>(e / ncols, N, logn, two_pi_over_L));
+    __syncthreads();
+    ifft_dit<R>(a, N, ncols, tw, tid, nt);
+    for (int e = tid; e < N * ncols; e += nt) a[e] = cmul(a[e], inv_s[e / ncols]);
+    __syncthreads();
+  }
+}
+
+// x pass: one block per (row, rhs).  prof: the system's x profile (s at the Nx nodes first).
+template <typename R>
+__global__ void __launch_bounds__(FX_THREADS) k_fourier_x(const C<R>* __restrict__ u, C<R>* __restrict__ tx,
+                                                          const C<R>* __restrict__ prof, const C<R>* __restrict__ tw_g,
+                                                          int Nx, int logn, int Ny, int64_t rhs_stride,
+                                                          R two_pi_over_L) {
+  extern __shared__ __align__(16) unsigned char fx_smem[];
+  C<R>* a = (C<R>*)fx_smem;
+  C<R>* tw = a + Nx;
+  C<R>* inv_s = tw + Nx / 2;
+  const int row = blockIdx.x, rhs = blockIdx.y;
+  const int64_t base = rhs * rhs_stride + (int64_t)row * Nx;
+  for (int i = threadIdx.x; i < Nx; i += blockDim.x) {
+    a[i] = u[base + i];
+    const C<R> s = prof[i];
+    const R d = s.x * s.x + s.y * s.y;
+    inv_s[i] = mk<R>(s.x / d, -s.y / d);
+  }
+  for (int t = threadIdx.x; t < Nx / 2; t += blockDim.x) tw[t] = tw_g[t];
+  __syncthreads();
+  derivative_pair<R>(a, Nx, logn, 1, tw, inv_s, two_pi_over_L, threadIdx.x, blockDim.x);
+  for (int i = threadIdx.x; i < Nx; i += blockDim.x) tx[base + i] = a[i];
+}
+
+// y pass: one block per (column tile, rhs); y holds t_x on entry and A_F u on exit.
+template <typename R>
+__global__ void __launch_bounds__(FY_THREADS) k_fourier_y(const C<R>* __restrict__ u, C<R>* __restrict__ y,
+                                                          const R* __restrict__ k2, const C<R>* __restrict__ prof,
+                                                          const C<R>* __restrict__ tw_g, int Nx, int Ny, int logn,
+                                                          int64_t rhs_stride, R two_pi_over_L) {
+  constexpr int TC = FyCols<R>::v;
+  extern __shared__ __align__(16) unsigned char fy_smem[];
+  C<R>* a = (C<R>*)fy_smem;
+  C<R>* tw = a + (size_t)Ny * TC;
+  C<R>* inv_s = tw + Ny / 2;
+  const int x0 = blockIdx.x * TC, rhs = blockIdx.y;
+  const int64_t base = rhs * rhs_stride + x0;
+  for (int e = threadIdx.x; e < Ny * TC; e += blockDim.x) a[e] = u[base + (int64_t)(e / TC) * Nx + (e % TC)];
+  for (int j = threadIdx.x; j < Ny; j += blockDim.x) {
+    const C<R> s = prof[j];
+    const R d = s.x * s.x + s.y * s.y;
+    inv_s[j] = mk<R>(s.x / d, -s.y / d);
+  }
+  for (int t = threadIdx.x; t < Ny / 2; t += blockDim.x) tw[t] = tw_g[t];
+  __syncthreads();
+  derivative_pair<R>(a, Ny, logn, TC, tw, inv_s, two_pi_over_L, threadIdx.x, blockDim.x);
+  for (int e = threadIdx.x; e < Ny * TC; e += blockDim.x) {
+    const int64_t q = base + (int64_t)(e / TC) * Nx + (e % TC);
+    const int64_t pt = (int64_t)(e / TC) * Nx + x0 + (e % TC);
+    const C<R> uv = u[q];
+    const R kk = k2[pt];
+    const C<R> t = cadd(y[q], a[e]);
+    y[q] = mk<R>(-t.x - kk * uv.x, -t.y - kk * uv.y);
+  }
+}
+
+// ------------------------------------------------------------------ host side
+
+static int log2_exact(int n) {
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return (1 << l) == n ? l : -1;
+}
+
+bool fourier_supported(int Nx, int Ny) {
+  const int lx = log2_exact(Nx), ly = log2_exact(Ny);
+  return lx >= 4 && lx <= 10 && ly >= 4 && ly <= 10;
+}
+
+// Twiddle tables of one grid side, FP64 and FP32, cached per process and device.
+struct TwTables {
+  double2* d = nullptr;
+  float2* f = nullptr;
+};
+static std::map<std::pair<int, int>, TwTables> g_tw;
+static std::mutex g_tw_mu;
+
+static helm_status twiddles(int N, const double2** d, const float2** f) {
+  int dev = 0;
+  HELM_CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_tw_mu);
+  auto key = std::make_pair(dev, N);
+  auto it = g_tw.find(key);
+  if (it == g_tw.end()) {
+    std::vector<double2> hd(N / 2);
+    std::vector<float2> hf(N / 2);
+    for (int t = 0; t < N / 2; ++t) {
+      const double ang = -2.0 * M_PI * (double)t / (double)N;
+      hd[t] = make_double2(cos(ang), sin(ang));
+      hf[t] = make_float2((float)hd[t].x, (float)hd[t].y);
+    }
+    TwTables T;
+    HELM_CK(cudaMalloc(&T.d, sizeof(double2) * N / 2));
+    HELM_CK(cudaMalloc(&T.f, sizeof(float2) * N / 2));
+    HELM_CK(cudaMemcpy(T.d, hd.data(), sizeof(double2) * N / 2, cudaMemcpyHostToDevice));
+    HELM_CK(cudaMemcpy(T.f, hf.data(), sizeof(float2) * N / 2, cudaMemcpyHostToDevice));
+    it = g_tw.emplace(key, T).first;
+  }
+  *d = it->second.d;
+  *f = it->second.f;
+  return HELM_OK;
+}
+
+template <typename R>
+static helm_status fourier_op(helm_ctx* ctx, const C<R>* x, C<R>* y, int nrhs, cudaStream_t st) {
+  constexpr int TC = FyCols<R>::v;
+  for (auto& s : ctx->sys)
+    if (!fourier_supported(s.Nx, s.Ny))
+      return fail(HELM_ERR_INVALID_ARG, "helm_apply_fourier: grid sides (with the PML) must be powers of two in "
+                                        "[16, 1024]; got " + std::to_string(s.Nx) + " x " + std::to_string(s.Ny));
+  const bool fp64 = sizeof(R) == 8;
+  for (auto& s : ctx->sys) {
+    const double2* twd[2];
+    const float2* twf[2];
+    HELM_TRY(twiddles(s.Nx, &twd[0], &twf[0]));
+    HELM_TRY(twiddles(s.Ny, &twd[1], &twf[1]));
+    const C<R>* tw_x = fp64 ? (const C<R>*)twd[0] : (const C<R>*)twf[0];
+    const C<R>* tw_y = fp64 ? (const C<R>*)twd[1] : (const C<R>*)twf[1];
+    const C<R>* pr = fp64 ? (const C<R>*)ctx->prof_d : (const C<R>*)ctx->prof_f;
+    const R* k2 = fp64 ? (const R*)(ctx->k2d + s.off) : (const R*)(ctx->k2f + s.off);
+    const C<R>* xs = x + s.off * nrhs;
+    C<R>* ys = y + s.off * nrhs;
+    const size_t smx = sizeof(C<R>) * ((size_t)s.Nx + s.Nx / 2 + s.Nx);
+    const size_t smy = sizeof(C<R>) * ((size_t)s.Ny * TC + s.Ny / 2 + s.Ny);
+    if (smy > 48 * 1024) HELM_CK(cudaFuncSetAttribute(k_fourier_y<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy));
+    const R tpl_x = (R)(2.0 * M_PI / (s.Nx * s.h)), tpl_y = (R)(2.0 * M_PI / (s.Ny * s.h));
+    launch(k_fourier_x<R>, dim3(s.Ny, nrhs), std::min(FX_THREADS, s.Nx / 2), smx, st, xs, ys, pr + s.prof_x, tw_x,
+           s.Nx, log2_exact(s.Nx), s.Ny, (int64_t)s.n, tpl_x);
+    launch(k_fourier_y<R>, dim3(s.Nx / TC, nrhs), FY_THREADS, smy, st, xs, ys, k2, pr + s.prof_y, tw_y, s.Nx, s.Ny,
+           log2_exact(s.Ny), (int64_t)s.n, tpl_y);
+  }
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+}  // namespace helm
+
+using namespace helm;
+
+extern "C" helm_status helm_apply_fourier(helm_ctx* ctx, const void* x, void* y, helm_dtype dtype, int nrhs,
+                                          void* stream) {
+  if (!ctx || !x || !y) return fail(HELM_ERR_INVALID_ARG, "helm_apply_fourier: NULL argument");
+  HELM_TRY(check_columns(ctx, nrhs, "helm_apply_fourier"));
+  if (x == y) return fail(HELM_ERR_INVALID_ARG, "helm_apply_fourier: x and y must not alias");
+  if (((uintptr_t)x | (uintptr_t)y) & 15)
+    return fail(HELM_ERR_INVALID_ARG, "helm_apply_fourier: pointers must be 16-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (dtype == HELM_C64) return fourier_op<float>(ctx, (const float2*)x, (float2*)y, nrhs, st);
+  if (dtype == HELM_C128) return fourier_op<double>(ctx, (const double2*)x, (double2*)y, nrhs, st);
+  return fail(HELM_ERR_INVALID_ARG, "helm_apply_fourier: unknown dtype");
+}

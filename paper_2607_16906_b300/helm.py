@@ -61,6 +61,7 @@ _SIGS = {
     "helm_num_systems": (ct.c_int, [_P]),
     "helm_apply": (ct.c_int, [_P, _P, _P, ct.c_int, ct.c_int, _P]),
     "helm_apply_adjoint": (ct.c_int, [_P, _P, _P, ct.c_int, ct.c_int, _P]),
+    "helm_apply_fourier": (ct.c_int, [_P, _P, _P, ct.c_int, ct.c_int, _P]),
     "helm_relres": (ct.c_int, [_P, _P, _P, ct.c_int, ct.POINTER(ct.c_double), _P]),
     "helm_unet_param_count": (ct.c_size_t, []),
     "helm_unet_layer": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
@@ -211,6 +212,14 @@ def helm_apply(ctx: Context, x: torch.Tensor, y: torch.Tensor, nrhs=1, adjoint=F
         raise ValueError("x, y must be batch vectors of the same dtype and size npts * nrhs")
     f = _lib.helm_apply_adjoint if adjoint else _lib.helm_apply
     _check(f(ctx.handle, _dev_ptr(x), _dev_ptr(y), _dtype_code(x), nrhs, _stream(stream)))
+    return y
+
+
+def helm_apply_fourier(ctx: Context, x: torch.Tensor, y: torch.Tensor, nrhs=1, stream=None):
+    """y = A_F x, the Fourier-differentiation operator (helm_apply_fourier in include/helm.h)."""
+    if x.dtype != y.dtype or x.numel() != ctx.npts * nrhs or y.numel() != x.numel():
+        raise ValueError("x, y must be batch vectors of the same dtype and size npts * nrhs")
+    _check(_lib.helm_apply_fourier(ctx.handle, _dev_ptr(x), _dev_ptr(y), _dtype_code(x), nrhs, _stream(stream)))
     return y
 
 
