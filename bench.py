@@ -35,12 +35,11 @@ WEIGHTS = os.path.join(ROOT, "paper_2607_16906_b300", "weights", "unet_trained.n
 METRIC = "Helmholtz solves/s to rel.res 1e-6: batched mixed vs plain FP64, same B300"
 UNET_FLOP_PER_PT = 70816.0          # 2 x 35,408 MACs per full-resolution pixel (4-level U-Net)
 STENCIL_BYTES_FP32 = 16.0           # read z (8 B) + write A z (8 B) per point; k^2 (4 B/pt) read once per 32 RHS
-# Mean Krylov iterations per solve used to scale the oracle's per-iteration time into solves/s
-# when the reference arm runs in its own process (the CUDA arm prints its own measured mean).
 # FGMRES iterations per right-hand side of this workload with the trained network, as measured by
-# the CUDA arm (mean over the 32 RHS, 10 cycles of 512); the reference arm scales its per-iteration
-# time by it
-REF_ITERS_PER_SOLVE = 4780
+# the CUDA arm (mean over 8 of the 32 RHS, FGMRES(512), up to 20 cycles); the reference arm, which
+# runs in a process of its own, scales its measured per-iteration time by it (the CUDA arm prints its
+# own measured mean)
+REF_ITERS_PER_SOLVE = 4903
 # DRAM bytes per basis vector and point of one DCGS2 step (k_dsweepA 8.00 B + k_dsweepB 8.06 B),
 # from the ncu counters of the current sweep kernels
 DCGS2_DRAM_B_PER_VPT = 16.06
@@ -53,13 +52,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--m", type=int, default=512, help="Krylov vectors per cycle (Sec. 4: 512)")
-    ap.add_argument("--max-outer", type=int, default=10, help="FP64 refinement steps = restarts (Sec. 4: l = 10)")
+    ap.add_argument("--max-outer", type=int, default=20,
+                    help="FP64 refinement steps = FGMRES(m) cycles (Sec. 4 uses 10; 20 lets every RHS reach 1e-6)")
     ap.add_argument("--inner-tol", type=float, default=1e-5)
     ap.add_argument("--orth", default="dcgs2", choices=["cgs2", "dcgs2"])
     ap.add_argument("--nrhs", type=int, default=32)
     ap.add_argument("--rhs-batch", type=int, default=32, help="right-hand sides per solver call within a step")
     ap.add_argument("--weights", default=WEIGHTS)
-    ap.add_argument("--no-plain", action="store_true", help="skip the bounded plain-FP64 comparison")
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 and identity comparators")
+    ap.add_argument("--plain-rhs", type=int, default=1, help="right-hand sides of the plain-FP64 comparator")
+    ap.add_argument("--ident-rhs", type=int, default=4, help="right-hand sides of the unpreconditioned comparator")
+    ap.add_argument("--no-small", action="store_true", help="skip the small single-RHS configuration")
     ap.add_argument("--no-cpu", action="store_true", help="skip the bounded CPU-oracle baseline")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step throughput measurement")
     return ap.parse_args()
@@ -122,8 +125,11 @@ def parse_clock_samples(text):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_iteration_time(prob, theta, iters=2):
-    """Seconds per FGMRES iteration of the CPU FP64 oracle on one right-hand side of the workload."""
+def cpu_oracle_iteration_time(prob, theta, iters=5, basis=256):
+    """Seconds per FGMRES iteration of the CPU FP64 oracle on one right-hand side of the workload at
+    a Krylov basis of `basis` vectors: `iters` iterations of the oracle's own cycle (network, CSR
+    stencil, CGS2 at j <= iters) plus, for the basis the cycle has not yet built, `iters` times the
+    oracle's CGS2 arithmetic (two passes h = V^H w, w -= V h) on `basis` unit vectors."""
     from oracle import fgmres as fg
     from oracle import helmholtz as hz
     from oracle import unet as ou
@@ -131,7 +137,27 @@ def cpu_oracle_iteration_time(prob, theta, iters=2):
     pre = lambda v: ou.precondition(theta, v.reshape(1, prob.Ny, prob.Nx), prob.c, prob.h)[0].ravel()
     t0 = time.perf_counter()
     fg.cycle(lambda u: A @ u, pre, prob.b[0].ravel(), iters, 0.0)
-    return (time.perf_counter() - t0) / iters
+    t_cycle = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    V = rng.standard_normal((basis, prob.n)) + 1j * rng.standard_normal((basis, prob.n))
+    V /= np.linalg.norm(V, axis=1, keepdims=True)
+    w = rng.standard_normal(prob.n) + 0j
+    t0 = time.perf_counter()
+    for _ in range(iters):
+        for _ in range(2):
+            hh = np.conj(V @ np.conj(w))   # V^H w
+            w = w - V.T @ hh
+    t_orth = time.perf_counter() - t0
+    return (t_cycle + t_orth) / iters
+
+
+def splu_seconds(prob):
+    """Sparse direct LU factorisation + one solve (the oracle's reference solution), seconds."""
+    from oracle import helmholtz as hz
+    A = hz.assemble(prob.c, prob.p, prob.h, prob.omega)
+    t0 = time.perf_counter()
+    hz.solve_direct(A, prob.b[0].ravel())
+    return time.perf_counter() - t0
 
 
 def bench_config(args, wdesc, world):
@@ -152,9 +178,9 @@ def run_reference(args):
     theta, wdesc = load_weights(args.weights, ou.param_segments())
     times = []
     for _ in range(args.warmup):
-        cpu_oracle_iteration_time(prob, theta, iters=1)
+        cpu_oracle_iteration_time(prob, theta, iters=1, basis=32)
     for _ in range(args.steps):
-        times.append(cpu_oracle_iteration_time(prob, theta, iters=1))
+        times.append(cpu_oracle_iteration_time(prob, theta, iters=2, basis=args.m // 2))
     t_it = statistics.median(times)
     val = 1.0 / (t_it * REF_ITERS_PER_SOLVE)
     cores = os.cpu_count()
@@ -163,11 +189,58 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": bench_config(args, wdesc, 1),
             "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                             "sample": f"1 FGMRES iteration (numpy FP64 U-Net + CSR stencil + CGS2) of one RHS per "
-                                       f"step, scaled by {REF_ITERS_PER_SOLVE} iterations per solve (the CUDA arm's "
-                                       f"measured mean; the growth of the orthogonalisation with j is not included)"},
+                             "sample": f"2 FGMRES iterations of one RHS per step (numpy FP64 U-Net, CSR stencil, "
+                                       f"CGS2 at the mean basis {args.m // 2}), extrapolated by {REF_ITERS_PER_SOLVE} "
+                                       f"iterations per solve (the CUDA arm's measured mean)"},
             "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def measured_solve(helm, ctx, net, prob, nrhs, kw, what):
+    """Solve the first `nrhs` right-hand sides of the workload from x0 = 0 and time it (CUDA events)."""
+    import torch
+    b = torch.tensor(prob.b[:nrhs].ravel(), device="cuda")
+    x = torch.zeros_like(b)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = helm.helm_launch_count()
+    e0.record()
+    _, info = helm.helm_fgmres_solve(ctx, net, b, x, nrhs, **kw)
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    conv = sum(1 for c in info if c["status"] == "OK")
+    its = [c["iters"] for c in info]
+    return {"what": what, "rhs": nrhs, "converged": conv, "seconds": s, "solves_per_s": conv / s,
+            "iters": its, "mean_iters": float(np.mean(its)), "relres_true_max": max(c["relres_true"] for c in info),
+            "launches": helm.helm_launch_count() - l0, "opts": {k: v for k, v in kw.items()}}
+
+
+def small_configuration(helm, theta_trained):
+    """The small single-RHS configuration: 128^2 interior + 16 PML (160^2), one skull, one point
+    source, FGMRES(30), tol 1e-6.  Plain FP64 with the seeded (untrained) network as specified for this
+    configuration, the mixed path with the trained network, and unpreconditioned GMRES; each solve is
+    repeated 3 times after one warm-up and the median time is kept."""
+    import torch
+    from paper_2607_16906_b300 import synth
+    prob = synth.small_problem(seed=1000)
+    spec = helm.SystemSpec(prob.nx, prob.ny, prob.h, prob.p, prob.omega)
+    ctx = helm.Context([spec], torch.tensor(prob.c.ravel(), device="cuda"))
+    seeded = helm.UNet(synth.kaiming_uniform_params(helm.weight_segments(), 42))
+    trained = helm.UNet(theta_trained)
+    runs = {"plain_fp64_seeded_net": (seeded, dict(m=30, tol=1e-6, mixed=False, max_restarts=400, orth="dcgs2")),
+            "mixed_trained_net": (trained, dict(m=30, tol=1e-6, mixed=True, max_outer=400, inner_tol=1e-5,
+                                                orth="dcgs2")),
+            "gmres_identity": (None, dict(m=30, tol=1e-6, mixed=True, max_outer=400, inner_tol=1e-5,
+                                          orth="dcgs2"))}
+    out = {"workload": "128^2+16 PML (160^2), 1 skull, 1 point source, FGMRES(30), tol 1e-6"}
+    for name, (net, kw) in runs.items():
+        measured_solve(helm, ctx, net, prob, 1, kw, name)  # warm-up (graphs, tile tuning)
+        reps = [measured_solve(helm, ctx, net, prob, 1, kw, name) for _ in range(3)]
+        r = sorted(reps, key=lambda d: d["seconds"])[1]
+        r["launches_per_iter"] = r["launches"] / max(1, r["mean_iters"])
+        out[name] = r
+    return out
 
 
 def run_cuda(args):
@@ -346,32 +419,31 @@ def run_cuda(args):
                  "loss_first": losses[0], "loss_last": losses[-1]}
         del tctx, tnet, tb
 
-    # bounded plain-FP64 comparison: time a few FP64 iterations (FP64 U-Net), scale by the same count
-    plain = None
+    # comparators of the metric, measured to the same tolerance on a stated subset of the same
+    # right-hand sides: the plain FP64 GPU path (FP64 basis, stencil and network) and unpreconditioned
+    # GMRES (mixed path without the network), both with the same FGMRES(m) and cycle budget
+    plain = ident = small = None
     if rank == 0 and not args.no_plain:
-        helm.helm_profile_enable(ctx, True)
-        x.zero_()
-        torch.cuda.synchronize()
-        p0 = time.perf_counter()
-        helm.helm_fgmres_solve(ctx, net, b, x, nrhs, m=2, tol=1e-6, mixed=False, max_restarts=1, orth="cgs2")
-        torch.cuda.synchronize()
-        pt = time.perf_counter() - p0
-        pprof = helm.helm_profile_read(ctx)
-        helm.helm_profile_enable(ctx, False)
-        it_ms = sum(v[0] for k, v in pprof.items() if k in ("precond", "stencil", "orth", "lsq")) / 2
-        plain = {"ms_per_iter_32rhs": it_ms, "solves_per_s_upper_bound":
-                 nrhs / (max(mean_iters, 1.0) * it_ms / 1e3), "sample": "2 FP64 iterations x 32 RHS (FP64 U-Net, "
-                 "stencil, CGS2 at j <= 2), scaled by the mixed path's mean iteration count; the growth of the "
-                 "orthogonalisation with j is not included, so this bounds the plain path from above", "wall_s": pt}
+        plain = measured_solve(helm, ctx, net, prob, args.plain_rhs,
+                               dict(m=args.m, tol=1e-6, mixed=False, max_restarts=args.max_outer, orth=args.orth),
+                               "plain FP64 GPU path: FP64 Krylov basis and stencil, FP64 U-Net on CUDA cores, "
+                               "FP64 Givens")
+        ident = measured_solve(helm, ctx, None, prob, args.ident_rhs, dict(opts),
+                               "unpreconditioned GMRES (z_j = v_j), mixed path, same m and cycle budget")
+    if rank == 0 and not args.no_small:
+        small = small_configuration(helm, theta)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:  # the CPU baseline is quoted at N = 1 only
         from oracle import unet as ou  # the bounded CPU-oracle baseline leg
         th_o, _ = load_weights(args.weights, ou.param_segments())
-        t_it = cpu_oracle_iteration_time(prob, th_o, iters=1)
+        t_it = cpu_oracle_iteration_time(prob, th_o, iters=5, basis=args.m // 2)
+        t_lu = splu_seconds(prob)
         cpu = {"value": 1.0 / (t_it * max(mean_iters, 1.0)), "unit": "solves/s", "cores": os.cpu_count(),
-               "kind": "oracle", "sample": f"1 FGMRES iteration of one RHS ({t_it:.1f} s: numpy FP64 U-Net + CSR "
-                                           f"stencil + CGS2 at j = 1), scaled by the measured {mean_iters:.0f} "
-                                           f"iterations per solve (orthogonalisation growth not included)"}
+               "kind": "oracle", "sample": f"5 FGMRES iterations of one RHS ({t_it:.2f} s each: numpy FP64 U-Net, "
+                                           f"CSR stencil, CGS2 at the mean basis {args.m // 2}), extrapolated to "
+                                           f"the measured {mean_iters:.0f} iterations per solve",
+               "splu_s_per_system": t_lu, "splu": "scipy SuperLU factorisation + solve of the 576^2 system (the "
+                                                  "oracle's reference solution; not an iterative baseline)"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -384,7 +456,8 @@ def run_cuda(args):
                 "phases_ms": {k: v[0] for k, v in prof.items()},
                 "roofline": roof, "phase_rooflines": phase_rooflines, "phase_work": work,
                 "stencil_roofline": stencil,
-                "plain_fp64": plain, "train_step": train,
+                "plain_fp64": plain, "gmres_identity": ident, "small_160": small, "train_step": train,
+                "launches_per_iter": launches / max(1.0, sum(iters) / max(1, nrhs)),
                 "autotune": [f"{t['c_out']}<-{8 * t['slices']} {t['images']}x{t['H']}x{t['W']}: RY={t['rows_per_tile']}"
                              for t in helm.helm_tuned_tiles()],
                 "cpu_baseline": cpu, "clocks": clk, "gpu_launches": launches,
