@@ -145,28 +145,35 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 void uncount_launches(uint64_t n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
 
-void prof_begin(helm_ctx* ctx, int ph, cudaStream_t st) {
-  if (!ctx->prof_on) return;
-  cudaEventRecord(ctx->prof_ev[ph][0], st);
-}
-
-void prof_end(helm_ctx* ctx, int ph, cudaStream_t st) {
-  if (!ctx->prof_on) return;
-  cudaEventRecord(ctx->prof_ev[ph][1], st);
-  ctx->prof_pending[ph] = 1;
-}
+constexpr int PROF_SLOTS = 32;  // intervals per phase between two collections
 
 void prof_collect(helm_ctx* ctx) {
   if (!ctx->prof_on) return;
   for (int p = 0; p < NUM_PHASES; ++p) {
-    if (!ctx->prof_pending[p]) continue;
-    float ms = 0;
-    if (cudaEventElapsedTime(&ms, ctx->prof_ev[p][0], ctx->prof_ev[p][1]) == cudaSuccess) {
-      ctx->prof_ms[p] += ms;
-      ctx->prof_cnt[p] += 1;
+    for (int k = 0; k < ctx->prof_pending[p]; ++k) {
+      float ms = 0;
+      if (cudaEventElapsedTime(&ms, ctx->prof_ev[p][k][0], ctx->prof_ev[p][k][1]) == cudaSuccess) {
+        ctx->prof_ms[p] += ms;
+        ctx->prof_cnt[p] += 1;
+      }
     }
     ctx->prof_pending[p] = 0;
   }
+}
+
+void prof_begin(helm_ctx* ctx, int ph, cudaStream_t st) {
+  if (!ctx->prof_on) return;
+  if (ctx->prof_pending[ph] >= PROF_SLOTS) {  // ring full: wait for the recorded intervals and add them
+    cudaEventSynchronize(ctx->prof_ev[ph][PROF_SLOTS - 1][1]);
+    prof_collect(ctx);
+  }
+  cudaEventRecord(ctx->prof_ev[ph][ctx->prof_pending[ph]][0], st);
+}
+
+void prof_end(helm_ctx* ctx, int ph, cudaStream_t st) {
+  if (!ctx->prof_on) return;
+  cudaEventRecord(ctx->prof_ev[ph][ctx->prof_pending[ph]][1], st);
+  ctx->prof_pending[ph] += 1;
 }
 
 }  // namespace helm
@@ -175,9 +182,10 @@ extern "C" uint64_t helm_launch_count(void) { return helm::g_launches.load(); }
 
 extern "C" helm_status helm_profile_enable(helm_ctx* ctx, int on) {
   if (!ctx) return helm::fail(HELM_ERR_INVALID_ARG, "helm_profile_enable: NULL context");
-  if (on && !ctx->prof_ev[0][0]) {
+  if (on && !ctx->prof_ev[0][0][0]) {
     for (int p = 0; p < helm::NUM_PHASES; ++p)
-      for (int k = 0; k < 2; ++k) HELM_CK(cudaEventCreate(&ctx->prof_ev[p][k]));
+      for (auto& pair : ctx->prof_ev[p])
+        for (auto& e : pair) HELM_CK(cudaEventCreate(&e));
   }
   ctx->prof_on = on ? 1 : 0;
   for (int p = 0; p < helm::NUM_PHASES; ++p) {
@@ -354,8 +362,9 @@ extern "C" helm_status helm_destroy(helm_ctx* ctx) {
   cudaFree(ctx->flag_dev);
   if (ctx->pinned) cudaFreeHost(ctx->pinned);
   for (auto& pe : ctx->prof_ev)
-    for (auto& e : pe)
-      if (e) cudaEventDestroy(e);
+    for (auto& pair : pe)
+      for (auto& e : pair)
+        if (e) cudaEventDestroy(e);
   delete ctx;
   return HELM_OK;
 }

@@ -109,9 +109,9 @@ struct helm_ctx {
   size_t pinned_bytes = 0;
   // residual-estimate history of column 0 of the last solve (relative to ||b||), one entry per iteration
   std::vector<double> history;
-  // phase timers
+  // phase timers: per phase a ring of event pairs, collected after each host synchronisation
   int prof_on = 0;
-  cudaEvent_t prof_ev[8][2] = {};
+  cudaEvent_t prof_ev[8][32][2] = {};
   int prof_pending[8] = {};
   double prof_ms[8] = {};
   int64_t prof_cnt[8] = {};

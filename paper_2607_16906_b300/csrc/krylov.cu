@@ -22,6 +22,7 @@
 namespace helm {
 
 constexpr int RED_THREADS = 256;
+constexpr int CHECK_EVERY = 8;  // iterations between two host reads of the active-column count
 
 // ------------------------------------------------------------------ reductions
 
@@ -252,7 +253,8 @@ __global__ void k_givens(int j, int ncol, int m, const double* __restrict__ npar
                          const double2* __restrict__ hbuf, int ldp, double* __restrict__ vscale,
                          double2* __restrict__ Rm, double* __restrict__ cs, double2* __restrict__ sn,
                          double2* __restrict__ g, ColState* __restrict__ st, int* __restrict__ nactive,
-                         double* __restrict__ in_scale, const ColDesc* __restrict__ cols, double breakdown_eps) {
+                         double* __restrict__ in_scale, const ColDesc* __restrict__ cols, double breakdown_eps,
+                         double* __restrict__ hist0) {
   int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= ncol) return;
   ColState& S = st[col];
@@ -273,6 +275,7 @@ __global__ void k_givens(int j, int ncol, int m, const double* __restrict__ npar
   }
   givens_update(j, m, Rc, hn, colmax2, cs + (int64_t)col * m, sn + (int64_t)col * m, g + (int64_t)col * (m + 1), S,
                 breakdown_eps);
+  if (col == 0 && S.k == j + 1) hist0[j] = S.est;  // residual-estimate history of column 0
   double inv = hn > 0 ? 1.0 / hn : 0.0;
   vscale[(int64_t)col * (m + 1) + j + 1] = inv;
   in_scale[col] = S.active ? sqrt((double)cols[col].len) * inv : 0.0;
@@ -471,7 +474,8 @@ __global__ void __launch_bounds__(DC_THREADS) k_dcoef(int j, int nv, int has_u, 
                                                       double2* __restrict__ sn, double2* __restrict__ g,
                                                       ColState* __restrict__ st, C<R>* __restrict__ ca,
                                                       C<R>* __restrict__ cb, double2* __restrict__ sc,
-                                                      int* __restrict__ nactive, double breakdown_eps) {
+                                                      int* __restrict__ nactive, double breakdown_eps,
+                                                      double* __restrict__ hist0) {
   const int col = blockIdx.x;
   ColState& S = st[col];
   if (!S.active) return;
@@ -519,6 +523,7 @@ __global__ void __launch_bounds__(DC_THREADS) k_dcoef(int j, int nv, int has_u, 
       double rho = r2 > 0 ? sqrt(r2) : 0.0;
       s_rho = rho;
       givens_update(j - 1, m, sR, rho, colmax2, sC, sS, g + (int64_t)col * (m + 1), S, breakdown_eps);
+      if (col == 0 && S.k == j) hist0[j - 1] = S.est;  // residual-estimate history of column 0
       cs[(int64_t)col * m + j - 1] = sC[j - 1];
       sn[(int64_t)col * m + j - 1] = sS[j - 1];
       if (S.active && !has_w) {  // finalisation pass at the end of a cycle of m iterations
@@ -915,6 +920,7 @@ struct SolverWs {
   double* in_scale;
   double* out_scale;
   int* nactive;
+  double* hist0;  // Givens estimate of column 0 after each iteration of the cycle (m entries)
   // delayed-reorthogonalisation buffers
   double2* red;  // [ncol][2][ldq]
   C<R>* ca;      // [ncol][ldq]
@@ -958,6 +964,7 @@ static helm_status solver_ws(helm_ctx* ctx, int m, int ncol, int nch, int ndc, b
   size_t ois = take(sizeof(double) * ncol);
   size_t oos = take(sizeof(double) * ncol);
   size_t ona = take(sizeof(int) * 4);
+  size_t oh0 = take(sizeof(double) * (m + 1));
   HELM_TRY(ctx->ws_solver.reserve(off));
   char* b = (char*)ctx->ws_solver.ptr;
   W.V = (C<R>*)(b + oV);
@@ -979,6 +986,7 @@ static helm_status solver_ws(helm_ctx* ctx, int m, int ncol, int nch, int ndc, b
   W.in_scale = (double*)(b + ois);
   W.out_scale = (double*)(b + oos);
   W.nactive = (int*)(b + ona);
+  W.hist0 = (double*)(b + oh0);
   W.red = (double2*)(b + ored);
   W.ca = (C<R>*)(b + oca);
   W.cb = (C<R>*)(b + ocb);
@@ -1036,11 +1044,11 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
     if (db_smem > 48 * 1024)
       HELM_CK(cudaFuncSetAttribute(k_dsweepB<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)db_smem));
   }
-  HELM_TRY(ensure_pinned(ctx, sizeof(double) * 2 * ncol + sizeof(ColState) * (ncol + 1) + 64 + 64));
+  HELM_TRY(ensure_pinned(ctx, sizeof(double) * (2 * ncol + m) + sizeof(ColState) * ncol + 64 + 64));
   double* h_sums = (double*)ctx->pinned;
-  ColState* h_st = (ColState*)(h_sums + 2 * ncol);
-  ColState* h_c0 = h_st + ncol;  // column 0's state after each step (residual-estimate history)
-  int* h_nact = (int*)(h_c0 + 1);
+  double* h_hist = h_sums + 2 * ncol;                 // column 0's estimates of one cycle
+  ColState* h_st = (ColState*)(h_hist + m);
+  int* h_nact = (int*)(h_st + ncol);
   ctx->history.clear();
   const bool mixed = sizeof(R) == 4;
   const int max_cycles = mixed ? std::max(1, o.max_outer) : std::max(1, o.max_restarts);
@@ -1090,13 +1098,20 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
       break;
     }
     HELM_CK(cudaMemcpyAsync(W.st, h_st, sizeof(ColState) * ncol, cudaMemcpyHostToDevice, stream));
-    // history of column 0: one entry per new Hessenberg column rotated while the column is active
-    int last_k0 = 0;
-    auto record0 = [&](const ColState& c0) {
-      if (!done[0] && c0.k > last_k0) {
-        ctx->history.push_back(c0.est * rel[0]);
-        last_k0 = c0.k;
-      }
+    // The stopping test stays on the device: every kernel of an iteration skips the columns whose
+    // ColState is inactive, and k_givens / k_dcoef count the active ones.  The host reads that count
+    // only every `check` iterations, so most iterations are queued without a round trip; a batch whose
+    // columns all stopped runs at most check - 1 more iterations of early-exiting launches.
+    const int check = std::min(CHECK_EVERY, m);
+    bool stop = false;
+    auto poll = [&](int j) -> helm_status {
+      if ((j + 1) % check != 0 && j + 1 != m) return HELM_OK;
+      HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
+      HELM_CK(cudaStreamSynchronize(stream));
+      prof_collect(ctx);
+      nact = *h_nact;
+      stop = nact == 0;
+      return HELM_OK;
     };
     // g = e1 (the cycle runs on r / ||r||), vscale = 1, network scales for a unit-norm v1
     launch(k_cycle_setup, cdiv(ncol, 64), 64, 0, stream, ncol, m, ctx->cols_dev, W.g, W.vscale, W.in_scale,
@@ -1149,15 +1164,11 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         prof_begin(ctx, PH_LSQ, stream);
         HELM_CK(cudaMemsetAsync(W.nactive, 0, sizeof(int), stream));
         launch(k_givens<R>, cdiv(ncol, 64), 64, 0, stream, j, ncol, m, W.npartial, nch, W.hbuf, ldp, W.vscale, W.Rm,
-               W.cs, W.sn, W.g, W.st, W.nactive, W.in_scale, ctx->cols_dev, breakdown_eps);
+               W.cs, W.sn, W.g, W.st, W.nactive, W.in_scale, ctx->cols_dev, breakdown_eps, W.hist0);
         HELM_CK_LAUNCH();
-        HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
-        HELM_CK(cudaMemcpyAsync(h_c0, W.st, sizeof(ColState), cudaMemcpyDeviceToHost, stream));
         prof_end(ctx, PH_LSQ, stream);
-        HELM_CK(cudaStreamSynchronize(stream));
-        prof_collect(ctx);
-        record0(*h_c0);
-        if (*h_nact == 0) break;
+        HELM_TRY(poll(j));
+        if (stop) break;
       }
     } else {
       // CGS2 with delayed reorthogonalisation (kernels k_dsweepA / k_dcoef / k_dsweepB above)
@@ -1194,8 +1205,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         launch(k_dreduce, dim3(cdiv(2 * (nv + 1), 128), ncol), 128, 0, stream, (const double2*)W.partial, ndc, ldq,
                nv, W.st, W.red);
         launch(k_dcoef<R>, ncol, DC_THREADS, dc_smem(nv), stream, j, nv, has_u, 1, ncol, m, (const double2*)W.red, ldq,
-               W.Rm,
-               W.cs, W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps);
+               W.Rm, W.cs, W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps, W.hist0);
         launch(k_dsweepB<R>, vgrid, RED_THREADS, 2 * sizeof(C<R>) * nv, stream, (const C<R>*)W.V, vst, nv,
                has_u ? Uj : nullptr, (const C<R>*)W.w, W.V + (int64_t)(j + 1) * vst, (const C<R>*)W.ca,
                (const C<R>*)W.cb, (const double2*)W.sc, ldq, ctx->cols_dev, W.st, nch, W.npartial);
@@ -1203,15 +1213,8 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
                W.in_scale);
         HELM_CK_LAUNCH();
         prof_end(ctx, PH_ORTH, stream);
-        prof_begin(ctx, PH_LSQ, stream);
-        HELM_CK(cudaMemcpyAsync(h_nact, W.nactive, sizeof(int), cudaMemcpyDeviceToHost, stream));
-        HELM_CK(cudaMemcpyAsync(h_c0, W.st, sizeof(ColState), cudaMemcpyDeviceToHost, stream));
-        prof_end(ctx, PH_LSQ, stream);
-        HELM_CK(cudaStreamSynchronize(stream));
-        prof_collect(ctx);
-        record0(*h_c0);
-        nact = *h_nact;
-        if (*h_nact == 0) break;
+        HELM_TRY(poll(j));
+        if (stop) break;
       }
       // columns that ran all m iterations: finalise column m-1 (reorthogonalise the pending u_m)
       prof_begin(ctx, PH_ORTH, stream);
@@ -1221,8 +1224,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
       launch(k_dreduce, dim3(cdiv(2 * (m + 1), 128), ncol), 128, 0, stream, (const double2*)W.partial, ndc, ldq, m,
              W.st, W.red);
       launch(k_dcoef<R>, ncol, DC_THREADS, dc_smem(m), stream, m, m, 1, 0, ncol, m, (const double2*)W.red, ldq, W.Rm,
-             W.cs,
-             W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps);
+             W.cs, W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps, W.hist0);
       HELM_CK_LAUNCH();
       prof_end(ctx, PH_ORTH, stream);
     }
@@ -1246,10 +1248,12 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
            W.st, ctx->cols_dev, nch, x);
     HELM_CK_LAUNCH();
     HELM_CK(cudaMemcpyAsync(h_st, W.st, sizeof(ColState) * ncol, cudaMemcpyDeviceToHost, stream));
+    HELM_CK(cudaMemcpyAsync(h_hist, W.hist0, sizeof(double) * m, cudaMemcpyDeviceToHost, stream));
     prof_end(ctx, PH_UPDATE, stream);
     HELM_CK(cudaStreamSynchronize(stream));
     prof_collect(ctx);
-    record0(h_st[0]);  // DCGS2: the last column is rotated in the finalisation pass
+    if (!done[0])  // column 0's estimate after each of its iterations in this cycle
+      for (int i = 0; i < h_st[0].k; ++i) ctx->history.push_back(h_hist[i] * rel[0]);
     for (int c = 0; c < ncol; ++c) {
       if (done[c]) continue;
       inf[c].iters += h_st[c].k;
