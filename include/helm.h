@@ -165,6 +165,19 @@ HELM_API size_t helm_unet_param_count(void);
 /* Layer l (0..17): writes c_in, c_out, kind (0 = 3x3 conv, 1 = 2x2 up-conv, 2 = 1x1 conv). */
 HELM_API helm_status helm_unet_layer(int l, int* c_in, int* c_out, int* kind);
 HELM_API helm_status helm_unet_create(helm_unet** out, const double* weights_host, size_t nweights);
+/* Network kinds: 0 = the network above (helm_unet_create); 1 = the paper's own variant (Sec. 3.1, Tab. 2,
+ * read as): inputs (Re v, Im v, c / 1500 m/s, Re sigma_c, Im sigma_c) with the complex PML field
+ * sigma_c = s_x s_y - 1 (eq. 2); encoder of four 8x8 stride-2 pad-3 convolutions (5 -> 32 -> 32 -> 32
+ * -> 32 channels), decoder of four 8x8 stride-2 pad-3 transposed convolutions (32 -> 32, then 64 -> 32
+ * on [decoder, skip] concatenations), PReLU (one slope per layer) after each, batch normalisation folded
+ * into the convolutions, final 1x1 conv 32 -> 2; grid zero-padded to multiples of 16.
+ * Weights of kind 1 (665,930 doubles): per layer weight, bias, PReLU slope (none for the output layer);
+ * layers enc1 enc2 enc3 enc4 dec3 dec2 dec1 dec0 out; conv weights [Cout][Cin][8][8], transposed-conv
+ * weights [Cin][Cout][8][8], output weights [2][32].  Kind 1 serves helm_precond_apply and
+ * helm_fgmres_solve (BF16 on tcgen05 tensor cores, or FP64 on CUDA cores); its training is not built
+ * (helm_train_step / helm_loss_grad return HELM_ERR_INVALID_ARG). */
+HELM_API size_t helm_unet_param_count_kind(int kind);
+HELM_API helm_status helm_unet_create_kind(helm_unet** out, int kind, const double* weights_host, size_t nweights);
 HELM_API helm_status helm_unet_destroy(helm_unet* net);
 /* Copy the FP64 master weights back to the host (after training). */
 HELM_API helm_status helm_unet_get_weights(const helm_unet* net, double* weights_host, size_t nweights);

@@ -36,19 +36,20 @@ struct ConvTcArgs {
   int ntiles;
   const float* bias;      // [N]
   __nv_bfloat16* out;     // NHWC [B][H][W][N]
-  int relu;
+  int act;               // 0 none, 1 ReLU, 2 PReLU with `slope`
+  float slope;
   int* err;               // device error code (0 = ok)
   long long budget;       // clock64 cycles a pipeline wait may take before the kernel gives up
   int skip_first;         // failure injection: CTA 0 issues no loads for its first tile
 };
 
-template <int N, int CHUNK, int MODE>
+template <int N, int CHUNK, int MODE, int KS>
 struct TcCfg {
   static constexpr int A_BYTES = 128 * CHUNK * 2;
   static constexpr int B_BYTES = N * CHUNK * 2;
   // taps per pipeline stage: a whole kernel row (3 taps) for narrow chunks, so that one barrier
   // round trip carries three MMAs; one tap otherwise
-  static constexpr int TPS = (MODE == 0 && CHUNK <= 32) ? 3 : 1;
+  static constexpr int TPS = (MODE == 0 && KS == 3 && CHUNK <= 32) ? 3 : 1;
   static constexpr int STAGE_BYTES = TPS * (A_BYTES + B_BYTES);
   static constexpr int STAGES = (96 * 1024 / STAGE_BYTES) > 8 ? 8 : (96 * 1024 / STAGE_BYTES);
   static constexpr int TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
@@ -56,14 +57,16 @@ struct TcCfg {
   static constexpr int THREADS = 192;
 };
 
-// MODE 0: 3x3 conv, pad 1 (9 shifted taps per channel chunk), N = C_out, ReLU.
+// MODE 0: KS x KS conv, pad KS / 2 (KS^2 shifted taps per channel chunk), N = C_out.
+// MODE 2: the same taps with the MODE 1 epilogue (a stride-2 transposed conv written as a KS x KS conv
+//         with N = 4 C_out followed by depth-to-space).
 // MODE 1: 2x2 stride-2 transposed conv as one GEMM with N = 4 C_out (column n = tap C_out + co); the
 //         epilogue scatters column blocks to output pixel (2y + tap / 2, 2x + tap % 2); no activation.
-template <int N, int CHUNK, int MODE>
+template <int N, int CHUNK, int MODE, int KS>
 __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tA0,
                                                     const __grid_constant__ CUtensorMap tA1,
                                                     const __grid_constant__ CUtensorMap tW, ConvTcArgs a) {
-  using Cfg = TcCfg<N, CHUNK, MODE>;
+  using Cfg = TcCfg<N, CHUNK, MODE, KS>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
@@ -76,7 +79,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nk = a.nk0 + a.nk1;
-  constexpr int TAPS = MODE == 0 ? 9 : 1;
+  constexpr int TAPS = MODE == 1 ? 1 : KS * KS;
   constexpr int TPS = Cfg::TPS;
   const int ksteps = (TAPS / TPS) * nk;
 
@@ -138,8 +141,9 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
 #pragma unroll
             for (int t = 0; t < TPS; ++t) {
               const int tap = tg * TPS + t;
-              if (MODE == 0)
-                tma_load_4d(sa + t * Cfg::A_BYTES, src, &full[stage], c0, x0 + tap % 3 - 1, y0 + tap / 3 - 1, b);
+              if (MODE != 1)
+                tma_load_4d(sa + t * Cfg::A_BYTES, src, &full[stage], c0, x0 + tap % KS - KS / 2,
+                            y0 + tap / KS - KS / 2, b);
               else
                 tma_load_4d(sa + t * Cfg::A_BYTES, src, &full[stage], c0, x0, y0, b);
               tma_load_3d(sb + t * Cfg::B_BYTES, &tW, &full[stage], 0, 0, tap * nk + kc);
@@ -238,7 +242,8 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
 #pragma unroll
           for (int k = 0; k < 16; ++k) {
             float f = __uint_as_float(v[k]) + a.bias[co0 + k];
-            if (MODE == 0 && a.relu) f = fmaxf(f, 0.0f);
+            if (a.act == 1) f = fmaxf(f, 0.0f);
+            else if (a.act == 2) f = f > 0.0f ? f : a.slope * f;
             hv[k] = __float2bfloat16_rn(f);
           }
           uint4* dst = (uint4*)o;
@@ -431,16 +436,16 @@ static helm_status weight_map(CUtensorMap* m, const void* ptr, int N, int chunk,
   return HELM_OK;
 }
 
-template <int N, int CHUNK, int MODE>
+template <int N, int CHUNK, int MODE, int KS = 3>
 static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& w, const ConvTcArgs& args,
                              cudaStream_t st) {
-  using Cfg = TcCfg<N, CHUNK, MODE>;
+  using Cfg = TcCfg<N, CHUNK, MODE, KS>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   static int per_sm = 1, nsm = 148;
   std::call_once(once, [] {
     attr_err =
-        cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     int dev = 0, smem_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -448,11 +453,11 @@ static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const
     // resident CTAs per SM: shared memory (1 KB reserved per CTA), TMEM (512 columns), threads, and
     // the occupancy calculator (registers)
     if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE>, cudaFuncAttributePreferredSharedMemoryCarveout,
+      attr_err = cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE, KS>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       100);
     int by_regs = 8;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_conv_tc<N, CHUNK, MODE>) == cudaSuccess && fa.numRegs > 0)
+    if (cudaFuncGetAttributes(&fa, k_conv_tc<N, CHUNK, MODE, KS>) == cudaSuccess && fa.numRegs > 0)
       by_regs = 65536 / (((fa.numRegs + 7) / 8) * 8 * Cfg::THREADS);
     int by_smem = smem_sm / (Cfg::SMEM + 1024);
     per_sm = std::min(std::min(by_smem, 512 / Cfg::TMEM_COLS), std::min(2048 / Cfg::THREADS, by_regs));
@@ -460,7 +465,7 @@ static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const
   });
   HELM_CK(attr_err);
   int grid = std::min(args.ntiles, nsm * per_sm);
-  launch(k_conv_tc<N, CHUNK, MODE>, grid, Cfg::THREADS, Cfg::SMEM, st, a0, a1, w, args);
+  launch(k_conv_tc<N, CHUNK, MODE, KS>, grid, Cfg::THREADS, Cfg::SMEM, st, a0, a1, w, args);
   HELM_CK_LAUNCH();
   return HELM_OK;
 }
@@ -491,7 +496,8 @@ static helm_status conv_tc_box(const helm_unet* net, int l, const void* in0, int
   a.ntiles = B * a.tiles_x * a.tiles_y;
   a.bias = net->w32 + net->L.c_b[l];
   a.out = (__nv_bfloat16*)out;
-  a.relu = 1;
+  a.act = 1;
+  a.slope = 0.f;
   a.err = S.err;
   a.budget = wait_budget();
   a.skip_first = take_fault(HELM_FAULT_CONV_TILE) ? 1 : 0;
@@ -553,7 +559,8 @@ helm_status conv_tc_up(const helm_unet* net, int l, const void* in, void* out, i
   a.ntiles = B * a.tiles_x * a.tiles_y;
   a.bias = net->w32 + net->L.c_b[l];
   a.out = (__nv_bfloat16*)out;
-  a.relu = 0;
+  a.act = 0;
+  a.slope = 0.f;
   a.err = S.err;
   a.budget = wait_budget();
   a.skip_first = take_fault(HELM_FAULT_CONV_TILE) ? 1 : 0;
@@ -565,8 +572,49 @@ helm_status conv_tc_up(const helm_unet* net, int l, const void* in, void* out, i
   }
 }
 
+// A KS x KS convolution of another network kind on the same kernels (unet_paper.cu): weights in the
+// [tap][chunk][N][chunk] BF16 layout, N output columns (MODE 2: N = 4 C_out written depth-to-space to
+// the 2H x 2W grid), inputs NHWC BF16 from one or two sources, epilogue bias + activation `act`.
+helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* err, int ks, int mode, int N,
+                            int chunk, const void* in0, int C0, const void* in1, int C1, void* out, int B, int H,
+                            int W, int act, float slope, cudaStream_t st) {
+  if (C0 % chunk || C1 % chunk) return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: channels not a chunk multiple");
+  CUtensorMap m0, m1, mw;
+  HELM_TRY(act_map(&m0, in0, C0, B, H, W, chunk));
+  if (C1 > 0)
+    HELM_TRY(act_map(&m1, in1, C1, B, H, W, chunk));
+  else
+    m1 = m0;
+  const int nk = (C0 + C1) / chunk;
+  HELM_TRY(weight_map(&mw, w_tc, N, chunk, nk, ks * ks));
+  ConvTcArgs a;
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.nk0 = C0 / chunk;
+  a.nk1 = C1 / chunk;
+  a.tiles_x = (W + 15) / 16;
+  a.tiles_y = (H + 7) / 8;
+  a.ntiles = B * a.tiles_x * a.tiles_y;
+  a.bias = bias;
+  a.out = (__nv_bfloat16*)out;
+  a.act = act;
+  a.slope = slope;
+  a.err = err;
+  a.budget = wait_budget();
+  a.skip_first = take_fault(HELM_FAULT_CONV_TILE) ? 1 : 0;
+  const int key = ks * 1000000 + mode * 100000 + N * 100 + chunk;
+  switch (key) {
+    case 5000000 + 32 * 100 + 32: return launch_tc<32, 32, 0, 5>(m0, m1, mw, a, st);
+    case 5000000 + 32 * 100 + 64: return launch_tc<32, 64, 0, 5>(m0, m1, mw, a, st);
+    case 5200000 + 128 * 100 + 32: return launch_tc<128, 32, 2, 5>(m0, m1, mw, a, st);
+    default: return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: no kernel for this shape");
+  }
+}
+
 // Error code left by a timed-out tcgen05 kernel (0 if none); clears it.
 helm_status conv_tc_check(const helm_unet* net, cudaStream_t st) {
+  if (net->pn) return paper_check(net, st);
   if (!net->tc || !net->tc->err) return HELM_OK;
   int e = 0;
   HELM_CK(cudaMemcpyAsync(&e, net->tc->err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -593,6 +641,7 @@ extern "C" helm_status helm_unet_layer_forward(const helm_unet* net, int layer, 
     return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: bad image size");
   if (((uintptr_t)in0 | (uintptr_t)in1 | (uintptr_t)out) & 15)
     return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: pointers must be 16-byte aligned");
+  if (net->kind != 0) return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: network kind 0 only");
   if (!net->tc || !net->tc->ok)
     return fail(HELM_ERR_INVALID_ARG, "helm_unet_layer_forward: the tcgen05 path is not available on this device");
   cudaStream_t st = (cudaStream_t)stream;

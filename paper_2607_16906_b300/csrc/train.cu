@@ -546,6 +546,7 @@ using namespace helm;
 extern "C" helm_status helm_loss_grad(helm_ctx* ctx, const helm_unet* net, const void* b, helm_dtype dtype,
                                       double* loss_host, double* grad_dev, void* stream) {
   if (!ctx || !net || !b) return fail(HELM_ERR_INVALID_ARG, "helm_loss_grad: NULL argument");
+  if (net->kind != 0) return fail(HELM_ERR_INVALID_ARG, "helm_loss_grad: training of network kind 1 is not built");
   if ((uintptr_t)b & 15) return fail(HELM_ERR_INVALID_ARG, "helm_loss_grad: b must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
   helm_unet* n = const_cast<helm_unet*>(net);
@@ -563,6 +564,7 @@ extern "C" helm_status helm_loss_grad(helm_ctx* ctx, const helm_unet* net, const
 extern "C" helm_status helm_train_step(helm_ctx* ctx, helm_unet* net, const void* b, double lr, double wd,
                                        double clip, double* loss_host, double* grad_norm_host, void* stream) {
   if (!ctx || !net || !b) return fail(HELM_ERR_INVALID_ARG, "helm_train_step: NULL argument");
+  if (net->kind != 0) return fail(HELM_ERR_INVALID_ARG, "helm_train_step: training of network kind 1 is not built");
   if (!(lr >= 0) || !(wd >= 0)) return fail(HELM_ERR_INVALID_ARG, "helm_train_step: lr and wd must be >= 0");
   if ((uintptr_t)b & 15) return fail(HELM_ERR_INVALID_ARG, "helm_train_step: b must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;

@@ -526,6 +526,11 @@ template <typename R>
 helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
                               const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride,
                               bool keep_acts) {
+  if (net->kind == 1) {  // the paper's variant: its own launch sequence (no graph capture, no training)
+    if (keep_acts || c_stride != 0)
+      return fail(HELM_ERR_INVALID_ARG, "training of the paper's network variant is not built");
+    return paper_precondition<R>(ctx, net, sys, v, z, B, in_scale, out_scale, st);
+  }
   const SysHost& s = ctx->sys[sys];
   int Hp = (s.Ny + 7) / 8 * 8, Wp = (s.Nx + 7) / 8 * 8;
   UnetBuffers* ub;
@@ -662,9 +667,46 @@ extern "C" helm_status helm_unet_create(helm_unet** out, const double* weights_h
   return HELM_OK;
 }
 
+extern "C" size_t helm_unet_param_count_kind(int kind) {
+  return kind == 0 ? (size_t)make_layout().total : (kind == 1 ? (size_t)paper_param_count() : 0);
+}
+
+extern "C" helm_status helm_unet_create_kind(helm_unet** out, int kind, const double* weights_host,
+                                             size_t nweights) {
+  if (kind == 0) return helm_unet_create(out, weights_host, nweights);
+  if (kind != 1) return fail(HELM_ERR_INVALID_ARG, "helm_unet_create_kind: unknown network kind");
+  if (!out || !weights_host) return fail(HELM_ERR_INVALID_ARG, "helm_unet_create_kind: NULL argument");
+  *out = nullptr;
+  const int64_t total = paper_param_count();
+  if ((int64_t)nweights != total)
+    return fail(HELM_ERR_INVALID_ARG, "helm_unet_create_kind: expected " + std::to_string(total) + " weights, got " +
+                                          std::to_string(nweights));
+  for (size_t i = 0; i < nweights; ++i)
+    if (!std::isfinite(weights_host[i])) return fail(HELM_ERR_INVALID_ARG, "helm_unet_create_kind: non-finite weight");
+  static std::atomic<uint64_t> next_id{1u << 30};
+  helm_unet* net = new helm_unet();
+  net->id = next_id.fetch_add(1);
+  net->kind = 1;
+  net->L = NetLayout{};
+  net->L.total = total;
+  net->pn = new PaperNet();
+  helm_status rc = HELM_OK;
+  cudaError_t e = cudaMalloc(&net->master, sizeof(double) * total);
+  if (e == cudaSuccess) e = cudaMemcpy(net->master, weights_host, sizeof(double) * total, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) rc = cuda_fail(e, "helm_unet_create_kind: master weights", __FILE__, __LINE__);
+  if (rc == HELM_OK) rc = paper_prepare(net, 0);
+  if (rc != HELM_OK) {
+    helm_unet_destroy(net);
+    return rc;
+  }
+  *out = net;
+  return HELM_OK;
+}
+
 extern "C" helm_status helm_unet_destroy(helm_unet* net) {
   if (!net) return HELM_OK;
   cudaDeviceSynchronize();
+  paper_release(net);
   conv_tc_release(net);
   cudaFree(net->master);
   cudaFree(net->w64);
@@ -682,7 +724,7 @@ extern "C" helm_status helm_unet_set_weights(helm_unet* net, const double* weigh
     return fail(HELM_ERR_INVALID_ARG, "helm_unet_set_weights: bad argument");
   cudaStream_t st = (cudaStream_t)stream;
   HELM_CK(cudaMemcpyAsync(net->master, weights_dev, sizeof(double) * net->L.total, cudaMemcpyDeviceToDevice, st));
-  return unet_prepare(net, st);
+  return net->kind == 1 ? paper_prepare(net, st) : unet_prepare(net, st);
 }
 
 extern "C" helm_status helm_unet_get_weights(const helm_unet* net, double* weights_host, size_t nweights) {

@@ -132,10 +132,36 @@ __device__ __forceinline__ void store_act(float* p, float v) { *p = v; }
 template <typename T> const typename Acc<T>::A* cc_weights(const helm_unet* net);
 helm_status unet_prepare(helm_unet* net, cudaStream_t st);
 
+// The paper's U-Net variant (unet_paper.cu): network kind 1.
+constexpr int PAPER_LAYERS = 9;  // enc1..enc4, dec3..dec0, out
+struct PaperNet {
+  int64_t m_w[PAPER_LAYERS] = {}, m_b[PAPER_LAYERS] = {}, m_s[PAPER_LAYERS] = {};  // master offsets
+  double* w5[PAPER_LAYERS] = {};          // reformulated weights [tap][k][n], FP64
+  double* b5[PAPER_LAYERS] = {};          // per-column bias, FP64
+  __nv_bfloat16* wtc[PAPER_LAYERS] = {};  // tcgen05 layout [tap][kc][n][c], BF16
+  float* b32[PAPER_LAYERS] = {};
+  float* wout32 = nullptr;                // output layer, BF16-rounded weights in FP32 + 2 biases
+  double slope[PAPER_LAYERS] = {};        // PReLU slopes
+  int* err = nullptr;                     // tcgen05 pipeline error code
+  struct Set {
+    void* base = nullptr;
+    size_t cap = 0;
+  } act[2];  // activations: [0] BF16, [1] FP64
+};
+int64_t paper_param_count();
+helm_status paper_prepare(helm_unet* net, cudaStream_t st);
+void paper_release(helm_unet* net);
+template <typename R>
+helm_status paper_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
+                               const double* in_scale, const double* out_scale, cudaStream_t st);
+helm_status paper_check(const helm_unet* net, cudaStream_t st);
+
 }  // namespace helm
 
 struct helm_unet {
   uint64_t id = 0;  // unique per created network (keys of captured graphs)
+  int kind = 0;     // 0: the 16/32/64/128 U-Net; 1: the paper's variant (PaperNet)
+  helm::PaperNet* pn = nullptr;
   helm::NetLayout L;
   double* master = nullptr;  // FP64 master weights (PyTorch layouts)
   double* w64 = nullptr;     // CUDA-core layout, FP64

@@ -66,6 +66,8 @@ _SIGS = {
     "helm_unet_param_count": (ct.c_size_t, []),
     "helm_unet_layer": (ct.c_int, [ct.c_int, ct.POINTER(ct.c_int), ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]),
     "helm_unet_create": (ct.c_int, [ct.POINTER(_P), ct.POINTER(ct.c_double), ct.c_size_t]),
+    "helm_unet_create_kind": (ct.c_int, [ct.POINTER(_P), ct.c_int, ct.POINTER(ct.c_double), ct.c_size_t]),
+    "helm_unet_param_count_kind": (ct.c_size_t, [ct.c_int]),
     "helm_unet_destroy": (ct.c_int, [_P]),
     "helm_unet_get_weights": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.c_size_t]),
     "helm_unet_set_weights": (ct.c_int, [_P, _P, ct.c_size_t, _P]),
@@ -297,14 +299,32 @@ def weight_segments():
     return seg
 
 
-class UNet:
-    """helm_unet_create / helm_unet_destroy: network weights (FP64 master) and optimiser state."""
+def paper_weight_segments():
+    """(count, fan_in, kind) per parameter tensor of network kind 1 (the paper's variant, see
+    include/helm.h), for the seeded generator: 'w' weights, 'b' biases, 's' PReLU slopes."""
+    layers = (("down", 5, 32), ("down", 32, 32), ("down", 32, 32), ("down", 32, 32), ("up", 32, 32),
+              ("up", 64, 32), ("up", 64, 32), ("up", 64, 32), ("out", 32, 2))
+    seg = []
+    for kind, ci, co in layers:
+        fan = ci * (64 if kind != "out" else 1)
+        seg.append((ci * co * (64 if kind != "out" else 1), fan, "w"))
+        seg.append((co, fan, "b"))
+        if kind != "out":
+            seg.append((1, fan, "s"))
+    return seg
 
-    def __init__(self, weights: np.ndarray):
+
+class UNet:
+    """helm_unet_create(_kind) / helm_unet_destroy: network weights (FP64 master) and optimiser state.
+    kind 0: the 16/32/64/128 U-Net; kind 1: the paper's variant (include/helm.h)."""
+
+    def __init__(self, weights: np.ndarray, kind: int = 0):
         w = np.ascontiguousarray(weights, dtype=np.float64)
         self._h = _P()
-        _check(_lib.helm_unet_create(ct.byref(self._h), w.ctypes.data_as(ct.POINTER(ct.c_double)), w.size))
+        _check(_lib.helm_unet_create_kind(ct.byref(self._h), int(kind),
+                                          w.ctypes.data_as(ct.POINTER(ct.c_double)), w.size))
         self.nparams = w.size
+        self.kind = kind
 
     @property
     def handle(self):

@@ -343,13 +343,17 @@ def kaiming_uniform_params(segments, seed=42) -> np.ndarray:
     """Flat float64 parameter vector drawn from a seeded PCG64 stream.
 
     `segments` is a list of (count, fan_in, kind) with kind "w" (weights,
-    U(+-sqrt(6/fan_in)), i.e. Kaiming-uniform for ReLU) or "b" (bias,
-    U(+-1/sqrt(fan_in))).  The caller supplies the layout; seed 42 is the
-    paper's random seed (Tab. 3).
+    U(+-sqrt(6/fan_in)), i.e. Kaiming-uniform for ReLU), "b" (bias,
+    U(+-1/sqrt(fan_in))) or "s" (PReLU slopes: the usual initial value 0.25,
+    nothing drawn).  The caller supplies the layout; seed 42 is the paper's
+    random seed (Tab. 3).
     """
     rng = rng_for(seed)
     parts = []
     for count, fan_in, kind in segments:
+        if kind == "s":
+            parts.append(np.full(int(count), 0.25))
+            continue
         bound = np.sqrt(6.0 / fan_in) if kind == "w" else 1.0 / np.sqrt(fan_in)
         parts.append(rng.uniform(-bound, bound, int(count)))
     return np.concatenate(parts) if parts else np.zeros(0)

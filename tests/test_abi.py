@@ -63,3 +63,13 @@ def test_argument_errors_are_reported_without_a_gpu():
     assert lib.helm_apply(None, None, None, 0, 1, None) == helm.HELM_ERR_INVALID_ARG
     assert lib.helm_fgmres_solve(None, None, None, None, 1, None, None, None) == helm.HELM_ERR_INVALID_ARG
     assert lib.helm_tuned_tiles(None, 4) == 0
+
+
+def test_network_kinds_share_the_generator_layout():
+    """The binding's parameter layout of network kind 1 is the oracle's, and the library agrees on the count."""
+    from oracle import unet_paper as up
+    from paper_2607_16906_b300 import helm
+    assert helm.paper_weight_segments() == up.param_segments()
+    assert helm._lib.helm_unet_param_count_kind(1) == up.param_count() == 665930
+    assert helm._lib.helm_unet_param_count_kind(0) == 482050
+    assert helm._lib.helm_unet_param_count_kind(7) == 0
