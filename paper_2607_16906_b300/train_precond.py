@@ -128,7 +128,9 @@ def better(a, b):
 
 def train_epochs(dataset="D0", samples=10000, nx=128, p=16, ppw=10.0, batch=32, epochs=50, lr_max=1e-3,
                  lr_min=1e-5, wd=0.01, clip=1.0, seed=42, init=None, out=None, checkpoint=None, resume=False,
-                 val_every=5, validator=None, verbose=True, log_every=50):
+                 val_every=5, validator=None, verbose=True, log_every=50, stop_after=None):
+    """Epoch mode (module docstring).  `epochs` fixes the schedule; `stop_after` ends this invocation
+    after that many epochs in all (a later call with resume=True continues the same schedule)."""
     h, om = synth.grid_spacing(ppw), synth.angular_frequency()
     cs, bs, _ = make_sample_set(dataset, samples, nx, p, seed)
     c_dev = torch.tensor(cs, device="cuda")
@@ -146,7 +148,8 @@ def train_epochs(dataset="D0", samples=10000, nx=128, p=16, ppw=10.0, batch=32, 
     steps_per_epoch = samples // batch
     total = steps_per_epoch * epochs
     t0 = time.time()
-    while state["epoch"] < epochs:
+    last = epochs if stop_after is None else min(epochs, stop_after)
+    while state["epoch"] < last:
         ep = state["epoch"]
         losses = []
         for idx in batches(epoch_order(ep, samples, seed), batch):

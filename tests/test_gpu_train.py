@@ -158,7 +158,7 @@ def test_epoch_training_loop_resumes_exactly(tmp_path):
     assert len(st_a["history"]) == 2 and all("val" in r for r in st_a["history"])
     assert st_a["step"] == 4 and st_a["best"] is not None
     ck = str(tmp_path / "b.npz")
-    tp.train_epochs(epochs=1, checkpoint=ck, **kw)
+    tp.train_epochs(epochs=2, stop_after=1, checkpoint=ck, **kw)   # interrupted after the first epoch
     _, (m1, v1, s1), st1 = tp.load_checkpoint(ck)
     assert s1 == 2 and st1["epoch"] == 1 and np.abs(m1).sum() > 0
     net_b, st_b = tp.train_epochs(epochs=2, checkpoint=ck, resume=True, **kw)
