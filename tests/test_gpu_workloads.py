@@ -58,7 +58,9 @@ def test_appendix_b_workloads(helm, net, mixed):
 
 
 def test_training_distribution_samples(helm, net):
-    """One sample of each dataset D0-D5 (Tab. 4), every sample its own system of one batch."""
+    """One sample of each dataset D0-D5 (Tab. 4), every sample its own system of one batch.  These
+    include white-noise velocities (U([1, 2]) per node) whose conditioning lets the solution error
+    reach about 20 eta_b, so the residual is driven to 1e-7 to show the 1e-5 error target."""
     rng = synth.rng_for(6200)
     probs = []
     for name in synth.DATASETS:
@@ -67,7 +69,7 @@ def test_training_distribution_samples(helm, net):
     ctx = make_ctx(probs)
     b = to_dev(np.concatenate([p.b.ravel() for p in probs]), torch.complex128)
     x = torch.zeros_like(b)
-    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=40, tol=1e-6, mixed=True, max_outer=40, inner_tol=1e-5,
+    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=40, tol=1e-7, mixed=True, max_outer=40, inner_tol=1e-5,
                                       orth="dcgs2")
     assert rc == helm.HELM_OK, info
-    _check(helm, probs, x, 1, 1e-6, 1e-5)
+    _check(helm, probs, x, 1, 1e-7, 1e-5)
