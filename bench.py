@@ -63,6 +63,14 @@ def parse():
     ap.add_argument("--plain-rhs", type=int, default=1, help="right-hand sides of the plain-FP64 comparator")
     ap.add_argument("--ident-rhs", type=int, default=4, help="right-hand sides of the unpreconditioned comparator")
     ap.add_argument("--no-small", action="store_true", help="skip the small single-RHS configuration")
+    ap.add_argument("--large", action="store_true",
+                    help="also solve the large configuration (2176^2, line arrays, FP64 refinement to 1e-8)")
+    ap.add_argument("--large-rhs", type=int, default=2)
+    ap.add_argument("--large-m", type=int, default=1024)
+    ap.add_argument("--uneven", action="store_true", help="also solve the uneven 64-system batch in one call")
+    ap.add_argument("--uneven-m", type=int, default=256)
+    ap.add_argument("--only-extra", action="store_true",
+                    help="skip the timed main workload: run only the legs asked for with --large / --uneven")
     ap.add_argument("--no-cpu", action="store_true", help="skip the bounded CPU-oracle baseline")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step throughput measurement")
     return ap.parse_args()
@@ -248,6 +256,88 @@ def small_configuration(helm, theta_trained):
     return out
 
 
+def large_configuration(helm, theta, nrhs, m):
+    """The large configuration: 2048^2 interior + 64 PML (2176^2, 4.7 M unknowns), 12 points per
+    wavelength, thin skull ring, line-array sources; mixed path with FP64 refinement to eta_b <= 1e-8.
+    FGMRES(m) with m = `m` (the restarted FGMRES(50) of the configuration stalls with this network:
+    restart lengths of 128 and 256 already fail on the 576^2 workload); `nrhs` of the 8 right-hand
+    sides, as the Krylov basis of 2 x (m + 1) vectors per RHS has to fit in HBM.  The plain FP64 path
+    is timed over 3 iterations and extrapolated to the mixed path's count (labelled)."""
+    import torch
+    from paper_2607_16906_b300 import synth
+    prob = synth.large_problem(seed=5000, nrhs=nrhs)
+    spec = helm.SystemSpec(prob.nx, prob.ny, prob.h, prob.p, prob.omega)
+    ctx = helm.Context([spec], torch.tensor(prob.c.ravel(), device="cuda"))
+    net = helm.UNet(theta)
+    measured_solve(helm, ctx, net, prob, nrhs, dict(m=4, tol=1e-300, mixed=True, max_outer=1), "warm-up")
+    helm.helm_profile_enable(ctx, True)
+    r = measured_solve(helm, ctx, net, prob, nrhs, dict(m=m, tol=1e-8, mixed=True, max_outer=60, inner_tol=1e-5,
+                                                        orth="dcgs2"),
+                       "mixed path, FP64 refinement to 1e-8")
+    prof = helm.helm_profile_read(ctx)
+    work = helm.helm_profile_work(ctx)
+    helm.helm_profile_enable(ctx, False)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    r["phases_ms"] = {k: v[0] for k, v in prof.items()}
+    if prof["orth"][0] > 0:
+        gbs = work["orth"] / (prof["orth"][0] / 1e3) / 1e9
+        r["orth_roofline"] = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
+    if prof["stencil"][0] > 0:
+        gbs = work["stencil"] / (prof["stencil"][0] / 1e3) / 1e9
+        r["stencil_roofline"] = {"achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm}
+    p = measured_solve(helm, ctx, net, prob, nrhs, dict(m=3, tol=1e-300, mixed=False, max_restarts=1, orth="dcgs2"),
+                       "plain FP64, 3 iterations")
+    per_it = p["seconds"] / 3
+    r["plain_fp64_extrapolated"] = {"s_per_iter": per_it, "solves_per_s": nrhs / (per_it * max(1.0, r["mean_iters"])),
+                                    "sample": "3 FP64 iterations of all RHS (FP64 U-Net on CUDA cores) x the mixed "
+                                              "path's mean iteration count (extrapolated)"}
+    r["workload"] = f"2048^2+64 PML (2176^2), PPW 12, thin skull ring, {nrhs} of 8 line-array RHS, FGMRES({m})"
+    return r
+
+
+def uneven_configuration(helm, theta, m):
+    """The uneven batch: 64 systems with sides drawn from {256..1024} + PML 16..32 and 8-12 points per
+    wavelength, one point source each, all in one context and one solver call (mixed path, FGMRES(m),
+    up to 40 cycles, tol 1e-6).  Reports converged systems, iterations and launches per iteration."""
+    import torch
+    from paper_2607_16906_b300 import synth
+    probs = synth.uneven_problems()
+    specs = [helm.SystemSpec(p.nx, p.ny, p.h, p.p, p.omega) for p in probs]
+    ctx = helm.Context(specs, torch.tensor(np.concatenate([p.c.ravel() for p in probs]), device="cuda"))
+    net = helm.UNet(theta)
+    b = torch.tensor(np.concatenate([p.b.ravel() for p in probs]), device="cuda")
+    x = torch.zeros_like(b)
+    helm.helm_fgmres_solve(ctx, net, b, x, 1, m=4, tol=1e-300, mixed=True, max_outer=1)  # warm-up
+    x.zero_()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = helm.helm_launch_count()
+    e0.record()
+    _, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=m, tol=1e-6, mixed=True, max_outer=40, inner_tol=1e-5,
+                                     orth="dcgs2")
+    e1.record()
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3
+    conv = [c["status"] == "OK" for c in info]
+    its = [c["iters"] for c in info]
+    by_side = {}
+    for p, c, it in zip(probs, conv, its):
+        d = by_side.setdefault(p.nx, {"systems": 0, "converged": 0, "iters": []})
+        d["systems"] += 1
+        d["converged"] += int(c)
+        d["iters"].append(it)
+    for d in by_side.values():
+        d["mean_iters"] = float(np.mean(d.pop("iters")))
+    launches = helm.helm_launch_count() - l0
+    return {"workload": "64 systems, sides {256..1024} + PML 16..32, PPW 8-12, 1 point source each, one call",
+            "m": m, "converged": int(sum(conv)), "systems": len(probs), "seconds": s, "solves_per_s": sum(conv) / s,
+            "mean_iters": float(np.mean(its)), "max_iters": int(max(its)), "launches": launches,
+            "launches_per_iter": launches / max(1, max(its)), "by_side": by_side,
+            "points": int(sum(p.n for p in probs))}
+
+
 def run_cuda(args):
     import torch
     from paper_2607_16906_b300 import helm, replicas, synth
@@ -259,6 +349,18 @@ def run_cuda(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if args.only_extra:  # the large / uneven configurations alone (rank 0), no timed main workload
+        if rank == 0:
+            theta, wdesc = load_weights(args.weights, helm.weight_segments())
+            out = {"metric": METRIC, "extra_legs_only": True, "weights": wdesc}
+            if args.large:
+                out["large_2176"] = large_configuration(helm, theta, args.large_rhs, args.large_m)
+            if args.uneven:
+                out["uneven_64"] = uneven_configuration(helm, theta, args.uneven_m)
+            print(json.dumps(out), flush=True)
+        if dist:
+            dist.destroy_process_group()
+        return
     prob = workload(args.nrhs, seed_offset=rank)
     nrhs = args.nrhs
     spec = helm.SystemSpec(prob.nx, prob.ny, prob.h, prob.p, prob.omega)
@@ -437,6 +539,8 @@ def run_cuda(args):
                                "unpreconditioned GMRES (z_j = v_j), mixed path, same m and cycle budget")
     if rank == 0 and not args.no_small:
         small = small_configuration(helm, theta)
+    large = large_configuration(helm, theta, args.large_rhs, args.large_m) if rank == 0 and args.large else None
+    uneven = uneven_configuration(helm, theta, args.uneven_m) if rank == 0 and args.uneven else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:  # the CPU baseline is quoted at N = 1 only
         from oracle import unet as ou  # the bounded CPU-oracle baseline leg
@@ -462,6 +566,7 @@ def run_cuda(args):
                 "roofline": roof, "phase_rooflines": phase_rooflines, "phase_work": work,
                 "stencil_roofline": stencil,
                 "plain_fp64": plain, "gmres_identity": ident, "small_160": small, "train_step": train,
+                "large_2176": large, "uneven_64": uneven,
                 "launches_per_iter": launches / max(1.0, sum(iters) / max(1, nrhs)),
                 "autotune": [f"{t['c_out']}<-{8 * t['slices']} {t['images']}x{t['H']}x{t['W']}: RY={t['rows_per_tile']}"
                              for t in helm.helm_tuned_tiles()],
