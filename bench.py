@@ -271,7 +271,7 @@ def large_configuration(helm, theta, nrhs, m):
     net = helm.UNet(theta)
     measured_solve(helm, ctx, net, prob, nrhs, dict(m=4, tol=1e-300, mixed=True, max_outer=1), "warm-up")
     helm.helm_profile_enable(ctx, True)
-    r = measured_solve(helm, ctx, net, prob, nrhs, dict(m=m, tol=1e-8, mixed=True, max_outer=60, inner_tol=1e-5,
+    r = measured_solve(helm, ctx, net, prob, nrhs, dict(m=m, tol=1e-8, mixed=True, max_outer=30, inner_tol=1e-5,
                                                         orth="dcgs2"),
                        "mixed path, FP64 refinement to 1e-8")
     prof = helm.helm_profile_read(ctx)
