@@ -37,7 +37,8 @@
  *  - Environment switches: HELM_DISABLE_GRAPHS=1 runs the
  *    BF16 network eagerly instead of replaying captured CUDA graphs;
  *    HELM_AUTOTUNE=0 keeps the first rows-per-tile variant of every row-tile
- *    convolution instead of timing the variants on first use; HELM_DISABLE_TC=1
+ *    convolution and the first tile shape of the FP32 stencil instead of timing
+ *    the variants on first use; HELM_DISABLE_TC=1
  *    runs the BF16 convolutions on CUDA cores, HELM_DISABLE_ROW=1 the narrow
  *    layers on the 9-box tcgen05 kernels (comparison and testing aids).  The first
  *    two are read once per process, the last two when a network is created.  None
@@ -321,6 +322,16 @@ HELM_API helm_status helm_set_wait_budget(int64_t cycles);
 /* Arm `site` for its next `count` occurrences (launches, or workspace reservations); site
  * HELM_FAULT_NONE or count <= 0 disarms.  HELM_ERR_INVALID_ARG for an unknown site. */
 HELM_API helm_status helm_inject_fault(int site, int count);
+
+/* Tile shapes the autotuner chose so far for the FP32 TMA stencil (no counterpart in the paper: the
+ * first call for a grid shape times a few tile heights and pipeline depths with CUDA events, which
+ * synchronises the caller's stream that one time; every candidate gives bit-identical results).
+ * Writes up to max_entries records of 6 ints {Nx, Ny, nrhs, adjoint, rows per tile, stages} and
+ * returns how many it wrote. */
+HELM_API int helm_tuned_stencil(int* out, int max_entries);
+/* Test aid: run every later FP32 stencil launch with tile candidate `variant` (1: 32 rows x 2 stages,
+ * 2: 16 x 4, 3: 32 x 3, 4: 64 x 2) instead of the tuned one; 0 restores tuning.  Process-wide. */
+HELM_API helm_status helm_set_stencil_variant(int variant);
 
 /* Thread-local message for the last non-OK status returned on this thread. */
 HELM_API const char* helm_last_error(void);

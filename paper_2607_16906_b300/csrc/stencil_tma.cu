@@ -1,19 +1,23 @@
 // TMA-tiled FP32 stencil (a2, eq. 3): the complex 5-point operator with PML stretching on tiles
 // staged in shared memory by the tensor-memory accelerator.
 //
-// A persistent CTA walks tiles of ST_TH rows x ST_TW points of one right-hand side.  One 3-D TMA box
-// per tile brings the (ST_TH + 2) x (ST_TW + 4) halo window of u (FP32 complex viewed as floats,
+// A persistent CTA walks tiles of TH rows x ST_TW points of one right-hand side.  One 3-D TMA box
+// per tile brings the (TH + 2) x (ST_TW + 4) halo window of u (FP32 complex viewed as floats,
 // starting two points left of the tile so that the copy starts on a 16-byte boundary) into shared
 // memory; out-of-range rows and columns arrive as zeros, which are exactly the homogeneous
-// Dirichlet ghost values.  ST_STAGES boxes are in flight per CTA, so the loads of later tiles
+// Dirichlet ghost values.  STAGES boxes are in flight per CTA, so the loads of later tiles
 // overlap the arithmetic of the current one.  Each thread owns two adjacent points of a row (16-byte
-// shared-memory reads, one 16-byte global store) and ST_TH / 8 rows.  Per point the kernel moves the
+// shared-memory reads, one 16-byte global store) and TH / 8 rows.  Per point the kernel moves the
 // algorithmic 8 + 8 + 4 B of HBM traffic (u, A u, k^2); the halo re-reads come from L2.
 #include <cuda.h>
 
 #include <algorithm>
+#include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <type_traits>
+#include <vector>
 
 #include "helm_internal.cuh"
 #include "stencil_point.cuh"
@@ -21,24 +25,28 @@
 
 namespace helm {
 
-constexpr int ST_TW = 64;                       // output points per tile row
-constexpr int ST_TH = 32;                       // output rows per tile
+constexpr int ST_TW = 64;                       // output points per tile row (32 lanes x 2 points)
 constexpr int ST_BW = ST_TW + 4;                // loaded points per row (x0 - 2 .. x0 + ST_TW + 1)
-constexpr int ST_BH = ST_TH + 2;                // loaded rows (y0 - 1 .. y0 + ST_TH)
-constexpr int ST_STAGE_BYTES = ST_BW * ST_BH * 8;                    // one u box
-constexpr int ST_K2_BYTES = ST_TW * ST_TH * 4;                       // one k^2 box
-constexpr int ST_K2_OFF = (ST_STAGE_BYTES + 127) / 128 * 128;        // k^2 box after the u box
-constexpr int ST_STAGE_STRIDE = ST_K2_OFF + ST_K2_BYTES;             // stages start 128-byte aligned
-constexpr int ST_STAGES = 2;
 constexpr int ST_THREADS = 256;
-constexpr int ST_SMEM = ST_STAGES * ST_STAGE_STRIDE + 128;
+
+// Tile height TH (rows; a multiple of 8: each of the 8 warps owns TH / 8 rows) and pipeline depth.
+template <int TH, int STAGES>
+struct StCfg {
+  static constexpr int BH = TH + 2;                                  // loaded rows (y0 - 1 .. y0 + TH)
+  static constexpr int STAGE_BYTES = ST_BW * BH * 8;                 // one u box
+  static constexpr int K2_BYTES = ST_TW * TH * 4;                    // one k^2 box
+  static constexpr int K2_OFF = (STAGE_BYTES + 127) / 128 * 128;     // k^2 box after the u box
+  static constexpr int STAGE_STRIDE = K2_OFF + K2_BYTES;             // stages start 128-byte aligned
+  static constexpr int SMEM = STAGES * STAGE_STRIDE + 128;
+  static_assert(TH % 8 == 0, "tile height");
+};
 
 __device__ __forceinline__ float4 conj4(float4 v) { return make_float4(v.x, -v.y, v.z, -v.w); }
 __device__ __forceinline__ float2 conj2(float2 v) { return make_float2(v.x, -v.y); }
 
 // K2T: the k^2 tile comes with the u window (second box of the stage) instead of from global loads.
 // ux / uy: per-node flags, 1 where all FP32 stretch factors of that column / row are exactly 1.
-template <bool ADJ, bool K2T>
+template <bool ADJ, bool K2T, int TH, int ST_STAGES>
 __global__ void __launch_bounds__(ST_THREADS) k_stencil_tma(const __grid_constant__ CUtensorMap tu,
                                                             const __grid_constant__ CUtensorMap tk,
                                                             float2* __restrict__ y, const float* __restrict__ k2,
@@ -49,6 +57,10 @@ __global__ void __launch_bounds__(ST_THREADS) k_stencil_tma(const __grid_constan
                                                             int tiles_x, int tiles_y, int ntiles, int64_t rhs_stride,
                                                             float inv_h2, int* err, long long budget,
                                                             int skip_first) {
+  using Cfg = StCfg<TH, ST_STAGES>;
+  constexpr int ST_TH = TH;
+  constexpr int ST_STAGE_BYTES = Cfg::STAGE_BYTES, ST_K2_BYTES = Cfg::K2_BYTES, ST_K2_OFF = Cfg::K2_OFF;
+  constexpr int ST_STAGE_STRIDE = Cfg::STAGE_STRIDE;
   extern __shared__ __align__(128) unsigned char st_smem[];
   unsigned char* buf = (unsigned char*)(((uintptr_t)st_smem + 127) & ~(uintptr_t)127);
   __shared__ uint64_t full[ST_STAGES];
@@ -184,13 +196,13 @@ static EncodeTiledFnS encode_fn() {
   return fn;
 }
 
-static helm_status stencil_map(CUtensorMap* m, const void* ptr, int Nx, int Ny, int nrhs) {
+static helm_status stencil_map(CUtensorMap* m, const void* ptr, int Nx, int Ny, int nrhs, int th) {
   EncodeTiledFnS fn = encode_fn();
   if (!fn) return fail(HELM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   // FP32 complex viewed as floats: [nrhs][Ny][2 Nx]
   cuuint64_t dims[3] = {(cuuint64_t)2 * Nx, (cuuint64_t)Ny, (cuuint64_t)nrhs};
   cuuint64_t strides[2] = {(cuuint64_t)Nx * 8, (cuuint64_t)Nx * Ny * 8};
-  cuuint32_t box[3] = {2 * ST_BW, ST_BH, 1};
+  cuuint32_t box[3] = {2 * ST_BW, (cuuint32_t)(th + 2), 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(ptr), dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -200,12 +212,12 @@ static helm_status stencil_map(CUtensorMap* m, const void* ptr, int Nx, int Ny, 
 }
 
 // k^2 of one system as a [1][Ny][Nx] float tensor (row stride 4 Nx bytes: needs Nx % 4 == 0)
-static helm_status k2_map(CUtensorMap* m, const float* k2, int Nx, int Ny) {
+static helm_status k2_map(CUtensorMap* m, const float* k2, int Nx, int Ny, int th) {
   EncodeTiledFnS fn = encode_fn();
   if (!fn) return fail(HELM_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
   cuuint64_t dims[3] = {(cuuint64_t)Nx, (cuuint64_t)Ny, 1};
   cuuint64_t strides[2] = {(cuuint64_t)Nx * 4, (cuuint64_t)Nx * Ny * 4};
-  cuuint32_t box[3] = {ST_TW, ST_TH, 1};
+  cuuint32_t box[3] = {ST_TW, (cuuint32_t)th, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(k2), dims, strides, box, es,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -218,56 +230,165 @@ bool stencil_tma_supported(int Nx, int Ny, const void* x, const void* y) {
   return Nx >= 2 && Ny >= 1 && (Nx & 1) == 0 && (((uintptr_t)x | (uintptr_t)y) & 15) == 0;
 }
 
-template <bool ADJ, bool K2T>
-static helm_status launch_stencil_tma(const CUtensorMap& mu, const CUtensorMap& mk, float2* y, const float* k2,
-                                      const float2* px, const float2* py, const unsigned char* ux,
-                                      const unsigned char* uy, int Nx, int Ny, int tiles_x, int tiles_y,
-                                      int ntiles, int64_t stride, float inv_h2, int* err, long long budget,
-                                      int skip_first, cudaStream_t st) {
+// One tile shape: maps, occupancy, launch.
+template <bool ADJ, bool K2T, int TH, int STAGES>
+static helm_status launch_stencil_tma(const float2* x, float2* y, const float* k2, const float2* px,
+                                      const float2* py, const unsigned char* ux, const unsigned char* uy, int Nx,
+                                      int Ny, int nrhs, float inv_h2, int* err, long long budget, int skip_first,
+                                      cudaStream_t st) {
+  using Cfg = StCfg<TH, STAGES>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   static int nsm = 148, per_sm = 1;
   std::call_once(once, [] {
-    attr_err = cudaFuncSetAttribute(k_stencil_tma<ADJ, K2T>, cudaFuncAttributeMaxDynamicSharedMemorySize, ST_SMEM);
+    attr_err = cudaFuncSetAttribute(k_stencil_tma<ADJ, K2T, TH, STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    Cfg::SMEM);
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     int a = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stencil_tma<ADJ, K2T>, ST_THREADS, ST_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_stencil_tma<ADJ, K2T, TH, STAGES>, ST_THREADS, Cfg::SMEM);
     per_sm = std::max(1, a);
   });
   HELM_CK(attr_err);
+  const int tiles_x = (Nx + ST_TW - 1) / ST_TW, tiles_y = (Ny + TH - 1) / TH;
+  const int ntiles = tiles_x * tiles_y * nrhs;
+  if (ntiles == 0) return HELM_OK;
+  CUtensorMap mu, mk;
+  HELM_TRY(stencil_map(&mu, x, Nx, Ny, nrhs, TH));
+  if (K2T)
+    HELM_TRY(k2_map(&mk, k2, Nx, Ny, TH));
+  else
+    mk = mu;
   const int grid = std::min(ntiles, nsm * per_sm);
-  launch(k_stencil_tma<ADJ, K2T>, grid, ST_THREADS, ST_SMEM, st, mu, mk, y, k2, px, py, ux, uy, Nx, Ny, tiles_x,
-         tiles_y, ntiles, stride, inv_h2, err, budget, skip_first);
+  launch(k_stencil_tma<ADJ, K2T, TH, STAGES>, grid, ST_THREADS, Cfg::SMEM, st, mu, mk, y, k2, px, py, ux, uy, Nx, Ny,
+         tiles_x, tiles_y, ntiles, (int64_t)Nx * Ny, inv_h2, err, budget, skip_first);
   HELM_CK_LAUNCH();
   return HELM_OK;
+}
+
+// ------------------------------------------------------------------ tile autotuner
+//
+// The tile height trades halo re-reads ((TH + 2) / TH rows loaded per row) against the number of
+// tiles in flight per SM (shared memory per stage).  On the first call for a grid shape (Nx, Ny,
+// nrhs, adjoint, k^2 staged) every candidate runs once untimed and once timed with CUDA events on the
+// caller's stream, and the fastest is kept.  Every candidate computes each point with the same
+// arithmetic, so the choice never changes a result.  HELM_AUTOTUNE=0 keeps the first candidate, as do
+// calls during a stream capture.
+
+typedef helm_status (*StLaunchFn)(const float2*, float2*, const float*, const float2*, const float2*,
+                                  const unsigned char*, const unsigned char*, int, int, int, float, int*, long long,
+                                  int, cudaStream_t);
+struct StCand {
+  int th, stages;
+  StLaunchFn fn;
+};
+
+template <bool ADJ, bool K2T>
+static const std::vector<StCand>& st_candidates() {
+  static const std::vector<StCand> c = {{32, 2, launch_stencil_tma<ADJ, K2T, 32, 2>},
+                                        {16, 4, launch_stencil_tma<ADJ, K2T, 16, 4>},
+                                        {32, 3, launch_stencil_tma<ADJ, K2T, 32, 3>},
+                                        {64, 2, launch_stencil_tma<ADJ, K2T, 64, 2>}};
+  return c;
+}
+
+struct StKey {
+  int Nx, Ny, nrhs, adj, k2t;
+  bool operator<(const StKey& o) const {
+    return std::tie(Nx, Ny, nrhs, adj, k2t) < std::tie(o.Nx, o.Ny, o.nrhs, o.adj, o.k2t);
+  }
+};
+static std::mutex g_st_mu;
+static std::map<StKey, int> g_st_choice;
+static std::atomic<int> g_st_forced{0};  // helm_set_stencil_variant: 0 = tuned, k = candidate k
+
+static bool st_autotune_enabled() {
+  static const bool on = [] {
+    const char* e = getenv("HELM_AUTOTUNE");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+
+template <bool ADJ, bool K2T>
+static helm_status stencil_tuned(const float2* x, float2* y, const float* k2, const float2* px, const float2* py,
+                                 const unsigned char* ux, const unsigned char* uy, int Nx, int Ny, int nrhs,
+                                 float inv_h2, int* err, long long budget, int skip, cudaStream_t st) {
+  const auto& cands = st_candidates<ADJ, K2T>();
+  const int forced = g_st_forced.load();
+  if (forced > 0)
+    return cands[std::min<size_t>(forced, cands.size()) - 1].fn(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err,
+                                                                 budget, skip, st);
+  const StKey key{Nx, Ny, nrhs, ADJ ? 1 : 0, K2T ? 1 : 0};
+  {
+    std::lock_guard<std::mutex> lk(g_st_mu);
+    auto it = g_st_choice.find(key);
+    if (it != g_st_choice.end())
+      return cands[it->second].fn(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, skip, st);
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  HELM_CK(cudaStreamIsCapturing(st, &cap));
+  if (!st_autotune_enabled() || cap != cudaStreamCaptureStatusNone || skip)
+    return cands[0].fn(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, skip, st);
+  cudaEvent_t e0, e1;
+  HELM_CK(cudaEventCreate(&e0));
+  HELM_CK(cudaEventCreate(&e1));
+  int best = 0;
+  float best_ms = 0.f;
+  helm_status rc = HELM_OK;
+  for (size_t i = 0; i < cands.size() && rc == HELM_OK; ++i) {
+    rc = cands[i].fn(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, 0, st);  // set-up, warm-up
+    if (rc != HELM_OK) break;
+    cudaEventRecord(e0, st);
+    rc = cands[i].fn(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, 0, st);
+    cudaEventRecord(e1, st);
+    float ms = 0.f;
+    if (rc == HELM_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+        (i == 0 || ms < best_ms)) {
+      best = (int)i;
+      best_ms = ms;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != HELM_OK) return rc;
+  std::lock_guard<std::mutex> lk(g_st_mu);
+  g_st_choice[key] = best;
+  return HELM_OK;
+}
+
+// Tile heights chosen so far: out[k] = {Nx, Ny, nrhs, adjoint, rows per tile, stages}.
+int stencil_tuned_tiles(int (*out)[6], int max) {
+  std::lock_guard<std::mutex> lk(g_st_mu);
+  int k = 0;
+  for (auto& kv : g_st_choice) {
+    if (k >= max) break;
+    const StKey& r = kv.first;
+    const auto& c = (r.adj ? (r.k2t ? st_candidates<true, true>() : st_candidates<true, false>())
+                           : (r.k2t ? st_candidates<false, true>() : st_candidates<false, false>()))[kv.second];
+    out[k][0] = r.Nx;
+    out[k][1] = r.Ny;
+    out[k][2] = r.nrhs;
+    out[k][3] = r.adj;
+    out[k][4] = c.th;
+    out[k][5] = c.stages;
+    ++k;
+  }
+  return k;
 }
 
 helm_status stencil_tma(const float2* x, float2* y, const float* k2, const float2* px, const float2* py,
                         const unsigned char* ux, const unsigned char* uy, int Nx, int Ny, int nrhs, float inv_h2,
                         bool adjoint, int* err, cudaStream_t st) {
-  const int tiles_x = (Nx + ST_TW - 1) / ST_TW, tiles_y = (Ny + ST_TH - 1) / ST_TH;
-  const int ntiles = tiles_x * tiles_y * nrhs;
-  if (ntiles == 0) return HELM_OK;
-  CUtensorMap mu, mk;
-  HELM_TRY(stencil_map(&mu, x, Nx, Ny, nrhs));
   const bool k2t = (Nx & 3) == 0 && ((uintptr_t)k2 & 15) == 0;
-  if (k2t)
-    HELM_TRY(k2_map(&mk, k2, Nx, Ny));
-  else
-    mk = mu;
-  const int64_t stride = (int64_t)Nx * Ny;
   const long long budget = wait_budget();
   const int skip = take_fault(HELM_FAULT_STENCIL_TILE) ? 1 : 0;
-  auto go = [&](auto kern_adj, auto kern_k2) {
-    return launch_stencil_tma<decltype(kern_adj)::value, decltype(kern_k2)::value>(
-        mu, mk, y, k2, px, py, ux, uy, Nx, Ny, tiles_x, tiles_y, ntiles, stride, inv_h2, err, budget, skip, st);
-  };
-  using T = std::true_type;
-  using F = std::false_type;
-  if (adjoint) return k2t ? go(T{}, T{}) : go(T{}, F{});
-  return k2t ? go(F{}, T{}) : go(F{}, F{});
+  if (adjoint)
+    return k2t ? stencil_tuned<true, true>(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, skip, st)
+               : stencil_tuned<true, false>(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, skip, st);
+  return k2t ? stencil_tuned<false, true>(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, skip, st)
+             : stencil_tuned<false, false>(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, skip, st);
 }
 
 helm_status stencil_check(helm_ctx* ctx, cudaStream_t st) {
@@ -282,3 +403,14 @@ helm_status stencil_check(helm_ctx* ctx, cudaStream_t st) {
 }
 
 }  // namespace helm
+
+extern "C" int helm_tuned_stencil(int* out, int max_entries) {
+  if (!out || max_entries <= 0) return 0;
+  return helm::stencil_tuned_tiles(reinterpret_cast<int (*)[6]>(out), max_entries);
+}
+
+extern "C" helm_status helm_set_stencil_variant(int variant) {
+  if (variant < 0 || variant > 4) return helm::fail(HELM_ERR_INVALID_ARG, "helm_set_stencil_variant: 0..4");
+  helm::g_st_forced.store(variant);
+  return HELM_OK;
+}

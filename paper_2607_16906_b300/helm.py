@@ -90,6 +90,8 @@ _SIGS = {
     "helm_profile_work": (ct.c_int, [_P, ct.POINTER(ct.c_double)]),
     "helm_launch_count": (ct.c_uint64, []),
     "helm_tuned_tiles": (ct.c_int, [ct.POINTER(ct.c_int), ct.c_int]),
+    "helm_tuned_stencil": (ct.c_int, [ct.POINTER(ct.c_int), ct.c_int]),
+    "helm_set_stencil_variant": (ct.c_int, [ct.c_int]),
     "helm_last_error": (ct.c_char_p, []),
 }
 PHASES = ("precond", "stencil", "orth", "lsq", "residual", "update")
@@ -474,6 +476,19 @@ def helm_tuned_tiles():
     buf = (ct.c_int * (6 * 256))()
     n = _lib.helm_tuned_tiles(buf, 256)
     keys = ("c_out", "slices", "images", "H", "W", "rows_per_tile")
+    return [dict(zip(keys, buf[6 * k: 6 * k + 6])) for k in range(n)]
+
+
+def helm_set_stencil_variant(variant: int):
+    """Force FP32 stencil tile candidate `variant` (1..4) for later launches; 0 restores tuning."""
+    _check(_lib.helm_set_stencil_variant(int(variant)))
+
+
+def helm_tuned_stencil():
+    """Tile shape the autotuner chose per FP32 stencil grid shape: list of dicts."""
+    buf = (ct.c_int * (6 * 256))()
+    n = _lib.helm_tuned_stencil(buf, 256)
+    keys = ("Nx", "Ny", "nrhs", "adjoint", "rows_per_tile", "stages")
     return [dict(zip(keys, buf[6 * k: 6 * k + 6])) for k in range(n)]
 
 

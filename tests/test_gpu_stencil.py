@@ -55,19 +55,25 @@ def test_fp32_stencil_matches_oracle(helm):
             assert np.abs(g[k] - r[k]).max() <= 2e-6 * np.abs(r[k]).max()
 
 
+@pytest.mark.parametrize("variant", [1, 2, 3, 4])
 @pytest.mark.parametrize("adjoint", [False, True])
-def test_fp32_stencil_segments_and_fallback(helm, adjoint):
+def test_fp32_stencil_segments_and_fallback(helm, adjoint, variant):
     """FP32 stencil and adjoint: even-width systems take the TMA-tiled kernel (ragged last tile in x
     and y, a width of exactly one tile, zero-filled halo at every edge), with the k^2 tile staged by
     TMA (widths 64 and 100 at 16-byte aligned offsets) or read from global memory (width 114, 30);
-    the odd-width system takes the one-point-per-thread kernel."""
+    the odd-width system takes the one-point-per-thread kernel.  Every tile candidate of the
+    autotuner (16, 32 or 64 rows, 2-4 stages) is run."""
     probs = small_problems(((60, 5, 2), (80, 30, 10), (100, 37, 7), (20, 14, 5), (13, 9, 3)), seed=23)
     nrhs = 3
     ctx = make_ctx(probs)
     per, flat = random_batch(probs, nrhs, 31, np.complex64)
     x = to_dev(flat, torch.complex64)
     y = torch.empty_like(x)
-    helm.helm_apply(ctx, x, y, nrhs, adjoint=adjoint)
+    helm.helm_set_stencil_variant(variant)
+    try:
+        helm.helm_apply(ctx, x, y, nrhs, adjoint=adjoint)
+    finally:
+        helm.helm_set_stencil_variant(0)
     got = split(y.cpu().numpy().astype(np.complex128), probs, nrhs)
     ref = _oracle_apply(probs, [a.astype(np.complex128) for a in per], adjoint)
     for g, r in zip(got, ref):
