@@ -499,7 +499,68 @@ def run_cuda(args):
     hbm = peaks.get("hbm_gbs", 6400.0)
     stencil = {"bound": "hbm", "achieved": st_gbs, "peak": hbm, "unit": "GB/s", "frac": st_gbs / hbm,
                "ms": st_ms, "bytes_per_launch": st_bytes, "kernel": "k_stencil_tma<float> (FP32, 32 RHS)",
-               "l2": "flushed before each launch (write 256 MB, read 256 MB)"}
+               "l2": "flushed before each launch (write 256 MB, read 256 MB)",
+               "tile": [t for t in helm.helm_tuned_stencil() if t["nrhs"] == nrhs]}
+
+    def timed(fn, reps=10):
+        """Mean CUDA-event time (ms) of fn over `reps` launches, each after an L2 flush."""
+        tot = 0.0
+        for it in range(reps + 3):
+            flush.fill_(it)
+            flush_r.sum()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            fn()
+            a1.record()
+            torch.cuda.synchronize()
+            if it >= 3:
+                tot += a0.elapsed_time(a1)
+        return tot / reps
+
+    # the paper's discretisation: the Fourier-differentiation operator (FP32) on 1024^2 grids (the
+    # largest power-of-two side) x 8 RHS; algorithmic traffic 52 B per point (row pass 16 B, column
+    # pass 36 B)
+    fourier = None
+    if rank == 0:
+        from paper_2607_16906_b300 import synth as sy
+        fprob = sy.Problem(1008, 1008, 8, prob.h, prob.omega, sy.skull_velocity(1008, 1008, 8, sy.rng_for(77)),
+                           np.zeros((1, 1024, 1024), complex))
+        fctx = helm.Context([helm.SystemSpec(1008, 1008, prob.h, 8, prob.omega)],
+                            torch.tensor(fprob.c.ravel(), device="cuda"))
+        fx = torch.randn(fctx.npts * 8, dtype=torch.complex64, device="cuda")
+        fy = torch.empty_like(fx)
+        f_ms = timed(lambda: helm.helm_apply_fourier(fctx, fx, fy, 8))
+        f_bytes = 52.0 * fctx.npts * 8
+        fourier = {"bound": "hbm", "achieved": f_bytes / (f_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+                   "frac": f_bytes / (f_ms / 1e3) / 1e9 / hbm, "ms": f_ms, "bytes_per_launch": f_bytes,
+                   "kernels": "k_fourier_x + k_fourier_y (FP32, 1024^2 x 8 RHS)",
+                   "l2": "flushed before each launch"}
+        del fctx, fx, fy
+
+    # the paper's U-Net variant (network kind 1, seeded weights): one BF16 application to the 32
+    # right-hand sides of the workload; the flops per full-resolution pixel are those the tensor
+    # cores execute after the 5x5 reformulation (82,464 MAC, structural zeros included; the 8x8
+    # layers themselves need 51,264)
+    paper_net = None
+    if rank == 0:
+        pn = helm.UNet(synth.kaiming_uniform_params(helm.paper_weight_segments(), 42), kind=1)
+        pv = torch.randn(ctx.npts * nrhs, dtype=torch.complex64, device="cuda")
+        pz = torch.empty_like(pv)
+        helm.helm_precond_apply(ctx, pn, pv, pz, nrhs)
+        p_ms = timed(lambda: helm.helm_precond_apply(ctx, pn, pv, pz, nrhs), reps=5)
+        # GEMM MACs per full-resolution pixel: down layers 25 taps x K x 32 at 1/4, 1/16, 1/64, 1/256
+        # of the pixels (K = 32, 128, 128, 128); up layers 25 x K x 128 at 1/256, 1/64, 1/16, 1/4
+        # (K = 32, 64, 64, 64); output 32 x 2
+        macs = (25 * 32 * 32 / 4 + 25 * 128 * 32 * (1 / 16 + 1 / 64 + 1 / 256) +
+                25 * 128 * (32 / 256 + 64 / 64 + 64 / 16 + 64 / 4) + 64)
+        p_flops = 2.0 * macs * ctx.npts * nrhs
+        pk = peaks.get("bf16_tflops", 1800.0)
+        paper_net = {"bound": "tensor", "achieved": p_flops / (p_ms / 1e3) / 1e12, "peak": pk, "unit": "TFLOP/s",
+                     "frac": p_flops / (p_ms / 1e3) / 1e12 / pk, "ms": p_ms, "flop_per_pixel": 2.0 * macs,
+                     "what": "network kind 1 (the paper's variant), BF16 on tcgen05, 32 RHS of 576^2, "
+                             "GEMM flops of the 5x5 reformulation (36 % structural zeros included)",
+                     "peak_source": "measured burst bf16 (MEASURED_PEAKS.json)"}
+        del pn, pv, pz
 
     # training-step throughput on the training configuration (64 x (128^2 + 16 PML), mixed skull / GRF
     # velocities, point-source and line-array sources): helm_train_step = BF16 forward, adjoint
@@ -564,7 +625,7 @@ def run_cuda(args):
                 "relres_true_max": max(c["relres_true"] for c in infos) if infos else None,
                 "phases_ms": {k: v[0] for k, v in prof.items()},
                 "roofline": roof, "phase_rooflines": phase_rooflines, "phase_work": work,
-                "stencil_roofline": stencil,
+                "stencil_roofline": stencil, "fourier_roofline": fourier, "paper_unet": paper_net,
                 "plain_fp64": plain, "gmres_identity": ident, "small_160": small, "train_step": train,
                 "large_2176": large, "uneven_64": uneven,
                 "launches_per_iter": launches / max(1.0, sum(iters) / max(1, nrhs)),
