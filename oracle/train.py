@@ -25,12 +25,14 @@ import numpy as np
 
 from . import helmholtz as hz
 from . import unet
+from . import unet_paper
 
 
-def loss_and_grad(theta, b, c, p, h, omega, bf16=False, want_grad=True):
+def loss_and_grad(theta, b, c, p, h, omega, bf16=False, want_grad=True, kind=0):
     """Mean over the batch of eq. 9, and its gradient w.r.t. theta.
 
-    b: complex [B][Ny][Nx]; c: [B][Ny][Nx] velocity per sample.
+    b: complex [B][Ny][Nx]; c: [B][Ny][Nx] velocity per sample.  kind 0: oracle.unet; kind 1: the
+    paper's variant (oracle.unet_paper), whose input also carries the PML field.
     Returns (loss, grad or None, per-sample losses).
     """
     b = np.asarray(b, np.complex128)
@@ -39,8 +41,12 @@ def loss_and_grad(theta, b, c, p, h, omega, bf16=False, want_grad=True):
     nb = np.sqrt((np.abs(b) ** 2).reshape(B, -1).sum(1))
     alpha = np.sqrt(n) / nb
     bt = b * alpha[:, None, None]                       # unit-RMS source, ||bt||^2 = n
-    x = unet.network_input(bt, c)
-    y, act = unet.forward(theta, x, bf16=bf16, keep=True)
+    if kind == 0:
+        x = unet.network_input(bt, c)
+        y, act = unet.forward(theta, x, bf16=bf16, keep=True)
+    else:
+        x = np.concatenate([unet_paper.network_input(bt[s:s + 1], c[s], p, h, omega) for s in range(B)])
+        y, act = unet_paper.forward(theta, x, bf16=bf16, keep=True)
     u = (y[:, 0, :Ny, :Nx] + 1j * y[:, 1, :Ny, :Nx]) * h * h
     losses = np.zeros(B)
     gy = np.zeros_like(y)
@@ -53,7 +59,7 @@ def loss_and_grad(theta, b, c, p, h, omega, bf16=False, want_grad=True):
             gy[s, 1, :Ny, :Nx] = g.imag
     if not want_grad:
         return losses.mean(), None, losses
-    gtheta, _ = unet.backward(theta, act, gy)
+    gtheta = unet.backward(theta, act, gy)[0] if kind == 0 else unet_paper.backward(theta, act, gy)
     return losses.mean(), gtheta, losses
 
 

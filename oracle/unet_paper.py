@@ -20,8 +20,9 @@ Parameter vector (flat float64): per layer weight, bias, PReLU slope (no slope f
 layer); conv weights [C_out][C_in][8][8], transposed-conv weights [C_in][C_out][8][8]; layers
 enc1 enc2 enc3 enc4 dec3 dec2 dec1 dec0 out.
 
-Every convolution is the plain definition (sums over taps of a matmul); pinned against
-torch.nn.functional in tests/test_oracle_unet_paper.py.
+Every convolution is the plain definition (sums over taps of a matmul); the forward is pinned
+against torch.nn.functional and the backward (gradients of every weight, bias and PReLU slope)
+against torch autograd and central differences in tests/test_oracle_unet_paper.py.
 """
 from __future__ import annotations
 
@@ -125,20 +126,60 @@ def prelu(x, a):
     return np.where(x > 0, x, a * x)
 
 
-def forward(theta, x, bf16=False):
+def conv_down_backward(x, W, g):
+    """Gradients of conv_down w.r.t. x, W, b given g = dL/dy."""
+    N, C, H, Wd = x.shape
+    Ho, Wo = g.shape[2], g.shape[3]
+    xp = np.zeros((N, C, H + 2 * P + 1, Wd + 2 * P + 1))
+    xp[:, :, P:P + H, P:P + Wd] = x
+    gxp = np.zeros_like(xp)
+    gW = np.zeros_like(W)
+    for ky in range(K):
+        for kx in range(K):
+            patch = xp[:, :, ky:ky + S * Ho:S, kx:kx + S * Wo:S]
+            gW[:, :, ky, kx] = np.einsum("nohw,nchw->oc", g, patch, optimize=True)
+            gxp[:, :, ky:ky + S * Ho:S, kx:kx + S * Wo:S] += np.einsum("oc,nohw->nchw", W[:, :, ky, kx], g,
+                                                                      optimize=True)
+    return gxp[:, :, P:P + H, P:P + Wd], gW, g.sum(axis=(0, 2, 3))
+
+
+def conv_up_backward(x, W, g):
+    """Gradients of conv_up w.r.t. x, W, b given g = dL/dy (y of size 2H x 2W)."""
+    N, C, H, Wd = x.shape
+    O = W.shape[1]
+    gp = np.zeros((N, O, g.shape[2] + 2 * P + 1, g.shape[3] + 2 * P + 1))
+    gp[:, :, P:P + g.shape[2], P:P + g.shape[3]] = g
+    gx = np.zeros_like(x)
+    gW = np.zeros_like(W)
+    for ky in range(K):
+        for kx in range(K):
+            gs = gp[:, :, ky:ky + S * H:S, kx:kx + S * Wd:S]          # dL/d contrib[n,o,i,j]
+            gW[:, :, ky, kx] = np.einsum("nchw,nohw->co", x, gs, optimize=True)
+            gx += np.einsum("co,nohw->nchw", W[:, :, ky, kx], gs, optimize=True)
+    return gx, gW, g.sum(axis=(0, 2, 3))
+
+
+def forward(theta, x, bf16=False, keep=False):
     """x [N, 5, H, W] (H, W multiples of 16) -> [N, 2, H, W].  bf16: conv inputs and weights rounded
-    to bfloat16 (FP64 accumulation), as the mixed path does."""
+    to bfloat16 (FP64 accumulation), as the mixed path does.  keep: also return what backward needs."""
     Pm = unpack(theta)
     q = bf16_round if bf16 else (lambda a: a)
+    act = {}
 
     def layer(name, inp):
         W, b, a = Pm[name]
         kind = dict((n, k) for n, k, _, _ in LAYERS)[name]
+        xin = q(inp)
         if kind == "down":
-            return prelu(conv_down(q(inp), q(W), b), a)
-        if kind == "up":
-            return prelu(conv_up(q(inp), q(W), b), a)
-        return np.einsum("oc,nchw->nohw", q(W)[:, :, 0, 0], q(inp)) + b[None, :, None, None]
+            pre = conv_down(xin, q(W), b)
+        elif kind == "up":
+            pre = conv_up(xin, q(W), b)
+        else:
+            y = np.einsum("oc,nchw->nohw", q(W)[:, :, 0, 0], xin) + b[None, :, None, None]
+            act[name] = (xin, None)
+            return y
+        act[name] = (xin, pre)
+        return prelu(pre, a)
 
     e1 = layer("enc1", x)
     e2 = layer("enc2", e1)
@@ -148,7 +189,52 @@ def forward(theta, x, bf16=False):
     d2 = layer("dec2", np.concatenate([d3, e3], axis=1))
     d1 = layer("dec1", np.concatenate([d2, e2], axis=1))
     d0 = layer("dec0", np.concatenate([d1, e1], axis=1))
-    return layer("out", d0)
+    y = layer("out", d0)
+    return (y, act) if keep else y
+
+
+def backward(theta, act, gy):
+    """Flat gradient (weights, biases, PReLU slopes in the parameter order) given gy = dL/dy and the
+    activations saved by forward(keep=True)."""
+    Pm = unpack(theta)
+    grads = {}
+
+    def layer_b(name, g):
+        W, b, a = Pm[name]
+        kind = dict((n, k) for n, k, _, _ in LAYERS)[name]
+        xin, pre = act[name]
+        if kind == "conv1":
+            gW = np.einsum("nohw,nchw->oc", g, xin)[:, :, None, None]
+            grads[name] = (gW, g.sum(axis=(0, 2, 3)), None)
+            return np.einsum("oc,nohw->nchw", W[:, :, 0, 0], g)
+        ga = float(np.sum(g * np.where(pre > 0, 0.0, pre)))
+        g = g * np.where(pre > 0, 1.0, a)
+        if kind == "down":
+            gx, gW, gb = conv_down_backward(xin, W, g)
+        else:
+            gx, gW, gb = conv_up_backward(xin, W, g)
+        grads[name] = (gW, gb, ga)
+        return gx
+
+    g = layer_b("out", gy)
+    g = layer_b("dec0", g)
+    gd1, ge1 = g[:, :WIDTH], g[:, WIDTH:]
+    g = layer_b("dec1", gd1)
+    gd2, ge2 = g[:, :WIDTH], g[:, WIDTH:]
+    g = layer_b("dec2", gd2)
+    gd3, ge3 = g[:, :WIDTH], g[:, WIDTH:]
+    ge4 = layer_b("dec3", gd3)
+    ge3 = ge3 + layer_b("enc4", ge4)
+    ge2 = ge2 + layer_b("enc3", ge3)
+    ge1 = ge1 + layer_b("enc2", ge2)
+    layer_b("enc1", ge1)
+    parts = []
+    for name, kind, _, _ in LAYERS:
+        gW, gb, ga = grads[name]
+        parts += [gW.ravel(), gb.ravel()]
+        if kind != "conv1":
+            parts.append(np.array([ga]))
+    return np.concatenate(parts)
 
 
 def network_input(v, c, p, h, omega, sigma_max=None):

@@ -113,3 +113,21 @@ def test_clip_matches_torch():
     tn = torch.nn.utils.clip_grad_norm_([p], 1.0)
     assert abs(n - tn.item()) <= 1e-5 * n
     assert np.abs(gc - p.grad.double().numpy()).max() <= 1e-6
+
+
+def test_loss_gradient_of_the_paper_network_matches_central_differences():
+    """Eq. 9 through network kind 1 (oracle.unet_paper): the gradient matches a central difference."""
+    from oracle import unet_paper as upn
+    rng = synth.rng_for(21)
+    nx, p = 20, 6
+    h, om = synth.grid_spacing(10.0), synth.angular_frequency()
+    c = np.stack([synth.skull_velocity(nx, nx, p, rng, thickness=(2, 3)) for _ in range(2)])
+    b = np.stack([synth.point_sources(nx, nx, p, rng, 2) for _ in range(2)])
+    theta = upn.init_params(synth.kaiming_uniform_params(upn.param_segments(), 3))
+    L, g, _ = train.loss_and_grad(theta, b, c, p, h, om, kind=1)
+    d = rng.standard_normal(theta.size)
+    d /= np.linalg.norm(d)
+    eps = 1e-7
+    Lp, _, _ = train.loss_and_grad(theta + eps * d, b, c, p, h, om, want_grad=False, kind=1)
+    Lm, _, _ = train.loss_and_grad(theta - eps * d, b, c, p, h, om, want_grad=False, kind=1)
+    assert abs((Lp - Lm) / (2 * eps) - g @ d) <= 1e-5 * abs(g @ d) + 1e-12

@@ -80,3 +80,52 @@ def test_network_input_channels():
     assert np.allclose(x[0, 3] + 1j * x[0, 4], np.outer(sy, sx) - 1)
     assert (x[0, 3:, p:p + nx, p:p + nx] == 0).all()          # no PML field in the interior
     assert np.allclose(x[0, 2], c / 1500.0)
+
+
+def test_backward_equals_torch_autograd_and_central_differences():
+    theta = _theta(9)
+    rng = synth.rng_for(10)
+    x = rng.standard_normal((2, 5, 32, 32))
+    gy = rng.standard_normal((2, 2, 32, 32))
+    y, act = up.forward(theta, x, keep=True)
+    g = up.backward(theta, act, gy)
+    # torch autograd on the same composition
+    th = torch.tensor(theta, requires_grad=True)
+    off, P = 0, {}
+    for name, kind, ci, co in up.LAYERS:
+        shp = up._wshape(kind, ci, co)
+        nw = int(np.prod(shp))
+        W = th[off:off + nw].reshape(shp)
+        off += nw
+        b = th[off:off + co]
+        off += co
+        a = None
+        if kind != "conv1":
+            a = th[off:off + 1]
+            off += 1
+        P[name] = (W, b, a)
+    t = torch.tensor(x)
+    e = []
+    h = t
+    for n in ("enc1", "enc2", "enc3", "enc4"):
+        W, b, a = P[n]
+        h = F.prelu(F.conv2d(h, W, b, stride=2, padding=3), a)
+        e.append(h)
+    W, b, a = P["dec3"]
+    h = F.prelu(F.conv_transpose2d(e[3], W, b, stride=2, padding=3), a)
+    for n, skip in (("dec2", e[2]), ("dec1", e[1]), ("dec0", e[0])):
+        W, b, a = P[n]
+        h = F.prelu(F.conv_transpose2d(torch.cat([h, skip], 1), W, b, stride=2, padding=3), a)
+    W, b, _ = P["out"]
+    out = F.conv2d(h, W, b)
+    (out * torch.tensor(gy)).sum().backward()
+    ref = th.grad.numpy()
+    assert np.abs(g - ref).max() <= 1e-10 * np.abs(ref).max()
+    # central differences along a random unit direction (a short step, so that no pre-activation
+    # crosses the PReLU kink between the two evaluations)
+    d = rng.standard_normal(theta.size)
+    d /= np.linalg.norm(d)
+    eps = 1e-7
+    fp = (up.forward(theta + eps * d, x) * gy).sum()
+    fm = (up.forward(theta - eps * d, x) * gy).sum()
+    assert abs((fp - fm) / (2 * eps) - g @ d) <= 1e-5 * abs(g @ d)
