@@ -488,6 +488,7 @@ __global__ void k_alpha_b(const double* __restrict__ norm2, int B, int64_t n, do
 // R = double: FP64 network.
 template <typename R>
 static helm_status loss_grad_impl(helm_ctx* ctx, helm_unet* net, const C<R>* b, double* loss_host, cudaStream_t st) {
+  if (net->kind == 1) return paper_loss_grad<R>(ctx, net, b, loss_host, st);
   using T = typename std::conditional<sizeof(R) == 8, double, __nv_bfloat16>::type;
   using G = typename std::conditional<sizeof(R) == 8, double, float>::type;
   const SysHost& s0 = ctx->sys[0];
@@ -546,7 +547,6 @@ using namespace helm;
 extern "C" helm_status helm_loss_grad(helm_ctx* ctx, const helm_unet* net, const void* b, helm_dtype dtype,
                                       double* loss_host, double* grad_dev, void* stream) {
   if (!ctx || !net || !b) return fail(HELM_ERR_INVALID_ARG, "helm_loss_grad: NULL argument");
-  if (net->kind != 0) return fail(HELM_ERR_INVALID_ARG, "helm_loss_grad: training of network kind 1 is not built");
   if ((uintptr_t)b & 15) return fail(HELM_ERR_INVALID_ARG, "helm_loss_grad: b must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
   helm_unet* n = const_cast<helm_unet*>(net);
@@ -564,7 +564,6 @@ extern "C" helm_status helm_loss_grad(helm_ctx* ctx, const helm_unet* net, const
 extern "C" helm_status helm_train_step(helm_ctx* ctx, helm_unet* net, const void* b, double lr, double wd,
                                        double clip, double* loss_host, double* grad_norm_host, void* stream) {
   if (!ctx || !net || !b) return fail(HELM_ERR_INVALID_ARG, "helm_train_step: NULL argument");
-  if (net->kind != 0) return fail(HELM_ERR_INVALID_ARG, "helm_train_step: training of network kind 1 is not built");
   if (!(lr >= 0) || !(wd >= 0)) return fail(HELM_ERR_INVALID_ARG, "helm_train_step: lr and wd must be >= 0");
   if ((uintptr_t)b & 15) return fail(HELM_ERR_INVALID_ARG, "helm_train_step: b must be 16-byte aligned");
   cudaStream_t st = (cudaStream_t)stream;
@@ -598,7 +597,7 @@ extern "C" helm_status helm_train_step(helm_ctx* ctx, helm_unet* net, const void
   launch(k_adamw, cdiv(P, 256), 256, 0, st, net->master, (const double*)net->grad, net->adam_m, net->adam_v, P, lr,
          wd, b1, b2, eps, c1, c2, scale);
   HELM_CK_LAUNCH();
-  HELM_TRY(unet_prepare(net, st));
+  HELM_TRY(net->kind == 1 ? paper_prepare(net, st) : unet_prepare(net, st));
   if (loss_host) *loss_host = loss;
   if (grad_norm_host) *grad_norm_host = gn;
   return HELM_OK;

@@ -526,9 +526,9 @@ template <typename R>
 helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
                               const double* in_scale, const double* out_scale, cudaStream_t st, int64_t c_stride,
                               bool keep_acts) {
-  if (net->kind == 1) {  // the paper's variant: its own launch sequence (no graph capture, no training)
+  if (net->kind == 1) {  // the paper's variant: its own launch sequence (no graph capture)
     if (keep_acts || c_stride != 0)
-      return fail(HELM_ERR_INVALID_ARG, "training of the paper's network variant is not built");
+      return fail(HELM_ERR_INVALID_ARG, "network kind 1 is trained through paper_loss_grad");
     return paper_precondition<R>(ctx, net, sys, v, z, B, in_scale, out_scale, st);
   }
   const SysHost& s = ctx->sys[sys];

@@ -123,6 +123,7 @@ helm_status unet_precondition(helm_ctx* ctx, const helm_unet* net, int sys, cons
 template <typename T> struct Acc;
 template <> struct Acc<double> { using A = double; };
 template <> struct Acc<__nv_bfloat16> { using A = float; };
+template <> struct Acc<float> { using A = float; };
 __device__ __forceinline__ float to_acc(__nv_bfloat16 v) { return __bfloat162float(v); }
 __device__ __forceinline__ double to_acc(double v) { return v; }
 __device__ __forceinline__ float to_acc(float v) { return v; }
@@ -155,6 +156,10 @@ template <typename R>
 helm_status paper_precondition(helm_ctx* ctx, const helm_unet* net, int sys, const C<R>* v, C<R>* z, int B,
                                const double* in_scale, const double* out_scale, cudaStream_t st);
 helm_status paper_check(const helm_unet* net, cudaStream_t st);
+// Loss (eq. 9, batch mean) and its gradient into net->grad (master layout) for network kind 1:
+// forward and backward on CUDA cores in FP32 (R = float, the training path) or FP64 (R = double).
+template <typename R>
+helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* b, double* loss_host, cudaStream_t st);
 
 }  // namespace helm
 

@@ -17,10 +17,12 @@
 //                      y + d through tap t = q + 3 - 2 d; the kernel's epilogue writes column block q to
 //                      output phase q (no separate depth-to-space pass).
 // Mixed path: BF16 activations, tcgen05 GEMMs with FP32 accumulation, PReLU in the epilogue.  Plain
-// path: FP64 on CUDA cores with the same reformulated weights.  Training of this kind is not built.
+// path: FP64 on CUDA cores with the same reformulated weights.  Training (the end of this file): FP32
+// on CUDA cores, forward with the pre-activations kept, backward through the same reformulation.
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "helm_internal.cuh"
 #include "unet.cuh"
@@ -172,7 +174,7 @@ void paper_release(helm_unet* net) {
 // Input channels (Re s v, Im s v, c / 1500, Re sigma_c, Im sigma_c, 0, 0, 0) on the 16-padded grid.
 template <typename T, typename R>
 __global__ void k_paper_pack(const C<R>* __restrict__ v, int64_t col_stride, const double* __restrict__ in_scale,
-                             const double* __restrict__ chat, const double2* __restrict__ px,
+                             const double* __restrict__ chat, int64_t c_stride, const double2* __restrict__ px,
                              const double2* __restrict__ py, int Nx, int Ny, int Hp, int Wp, int B,
                              T* __restrict__ x0) {
   const int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -187,7 +189,7 @@ __global__ void k_paper_pack(const C<R>* __restrict__ v, int64_t col_stride, con
     const double s = in_scale[b];
     ch[0] = (double)val.x * s;
     ch[1] = (double)val.y * s;
-    ch[2] = chat[q];
+    ch[2] = chat[b * c_stride + q];
     const double2 sx = px[x], sy = py[y];
     ch[3] = sx.x * sy.x - sx.y * sy.y - 1.0;
     ch[4] = sx.x * sy.y + sx.y * sy.x;
@@ -320,8 +322,8 @@ helm_status paper_precondition(helm_ctx* ctx, const helm_unet* net, int sys, con
   HELM_TRY(paper_buffers(P, B, Hp, Wp, fp64, a));
   const int64_t npix = (int64_t)B * Hp * Wp;
   launch(k_paper_pack<T, R>, cdiv(npix, 256), 256, 0, st, v, s.n, in_scale, (const double*)(ctx->chat64 + s.off),
-         (const double2*)(ctx->prof_d + s.prof_x), (const double2*)(ctx->prof_d + s.prof_y), s.Nx, s.Ny, Hp, Wp, B,
-         (T*)a[PA_X0]);
+         (int64_t)0, (const double2*)(ctx->prof_d + s.prof_x), (const double2*)(ctx->prof_d + s.prof_y), s.Nx, s.Ny,
+         Hp, Wp, B, (T*)a[PA_X0]);
   HELM_CK_LAUNCH();
   auto s2d = [&](int src, int dst, int C, int H, int W) -> helm_status {  // H, W: source grid
     const int64_t n = (int64_t)B * (H / 2) * (W / 2) * 4 * C;
@@ -389,5 +391,505 @@ helm_status paper_check(const helm_unet* net, cudaStream_t st) {
   }
   return HELM_OK;
 }
+
+
+// ================================================================== training (eqs. 8-9) of kind 1
+//
+// Forward on CUDA cores in E (FP32 for training, FP64 for gradient checks) keeping every layer's
+// input and pre-activation; backward in reverse through the same reformulated layers:
+//   PReLU:  g_pre = g_post (pre > 0 ? 1 : a),  dL/da = sum g_post (pre > 0 ? 0 : pre);
+//   up layer: the pre-activation gradient on the 2H x 2W grid is rearranged space-to-depth into the
+//     GEMM's 4 C_out columns (column q C_out + co = output phase q), the inverse of the forward's
+//     depth-to-space;
+//   5x5 GEMM layer: dW[tap][k][n] = sum_px in[px + tap][k] g[px][n] (split over pixels, FP64
+//     partials summed in a fixed order), db[n] = sum_px g[px][n], d in[q][k] = sum_{tap,n}
+//     W[tap][k][n] g[q - tap][n];
+//   down layer: the input gradient is on the space-to-depth tensor; depth-to-space returns it to the
+//     previous activation.  Concatenated inputs split into the decoder and skip gradients.
+// Each master weight of an 8x8 layer appears exactly once among the 5x5 taps, so its gradient is read
+// back from there (the structural zeros' gradients are dropped).
+
+constexpr int PW_THREADS = 256;  // weight-gradient tile: 16 k x 16 n outputs, 32 pixels per stage
+
+// Forward GEMM layer on CUDA cores with the pre-activation kept (up: both written depth-to-space).
+template <typename E>
+__global__ void __launch_bounds__(PC_THREADS) k_pconv_keep(const E* __restrict__ in0, int C0, const E* __restrict__ in1,
+                                                           int C1, const double* __restrict__ w5,
+                                                           const double* __restrict__ b5, E* __restrict__ pre,
+                                                           E* __restrict__ post, int N, int cout, int up, int B,
+                                                           int H, int W, int ks, double slope) {
+  const int64_t pix = blockIdx.x * (int64_t)PC_THREADS + threadIdx.x;
+  if (pix >= (int64_t)B * H * W) return;
+  const int n0 = blockIdx.y * 16;
+  const int x = (int)(pix % W);
+  const int y = (int)((pix / W) % H);
+  const int64_t b = pix / ((int64_t)W * H);
+  const int K = C0 + C1, r = ks / 2;
+  E acc[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc[k] = (E)b5[n0 + k];
+  for (int tap = 0; tap < ks * ks; ++tap) {
+    const int yy = y + tap / ks - r, xx = x + tap % ks - r;
+    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+    const int64_t q = (b * H + yy) * W + xx;
+    const double* wt = w5 + (int64_t)tap * K * N + n0;
+    for (int c = 0; c < K; ++c) {
+      const E v = c < C0 ? in0[q * C0 + c] : in1[q * C1 + (c - C0)];
+      const double* wr = wt + (int64_t)c * N;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc[k] += v * (E)wr[k];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int n = n0 + k;
+    int64_t o;
+    if (!up) {
+      o = pix * N + n;
+    } else {
+      const int q = n / cout, co = n % cout;
+      o = ((b * 2 * H + 2 * y + (q >> 1)) * (2 * W) + 2 * x + (q & 1)) * cout + co;
+    }
+    if (pre) pre[o] = acc[k];
+    if (post) post[o] = acc[k] > E(0) ? acc[k] : (E)slope * acc[k];
+  }
+}
+
+// Depth-to-space (inverse of k_s2d): out[b][2Y + py][2X + px][c] = in[b][Y][X][(py * 2 + px) C + c].
+template <typename E>
+__global__ void k_d2s(const E* __restrict__ in, E* __restrict__ out, int C, int B, int Hi, int Wi, int accumulate) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t total = (int64_t)B * Hi * Wi * 4 * C;
+  if (e >= total) return;
+  const int k = (int)(e % (4 * C));
+  const int64_t pix = e / (4 * C);
+  const int X = (int)(pix % Wi);
+  const int Y = (int)((pix / Wi) % Hi);
+  const int64_t b = pix / ((int64_t)Wi * Hi);
+  const int ph = k / C, c = k % C;
+  const int64_t o = ((b * 2 * Hi + 2 * Y + (ph >> 1)) * (2 * Wi) + 2 * X + (ph & 1)) * C + c;
+  out[o] = accumulate ? out[o] + in[e] : in[e];
+}
+
+// PReLU backward in place on g (g_post -> g_pre); per-block partial sums of dL/da.
+template <typename E>
+__global__ void k_prelu_bwd(E* __restrict__ g, const E* __restrict__ pre, int64_t n, double slope,
+                            double* __restrict__ partial) {
+  __shared__ double red[256 / 32];
+  double s = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const E p = pre[i], gv = g[i];
+    if (p > E(0)) {
+      g[i] = gv;
+    } else {
+      s += (double)gv * (double)p;
+      g[i] = gv * (E)slope;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    partial[blockIdx.x] = t;
+  }
+}
+
+// Weight gradient of a KS x KS GEMM layer: partial[split][tap][k][n] = sum over the split's pixels of
+// in[px + tap][k] g[px][n]; one block per (split, 16 x 16 (k, n) tile, tap).  With tap == ks * ks
+// (an extra grid slice) the block sums g for the bias instead (k tile 0 only).
+template <typename E>
+__global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const E* __restrict__ in0, int C0, const E* __restrict__ in1,
+                                                       int C1, const E* __restrict__ g, int N, int B, int H, int W,
+                                                       int ks, int nsplit, double* __restrict__ partial,
+                                                       double* __restrict__ bpartial) {
+  const int K = C0 + C1, r = ks / 2;
+  const int split = blockIdx.x, tap = blockIdx.z;
+  const int nkt = (K + 15) / 16;
+  const int k0 = (blockIdx.y % nkt) * 16, n0 = (blockIdx.y / nkt) * 16;
+  const int tk = threadIdx.x & 15, tn = threadIdx.x >> 4;
+  const int64_t P = (int64_t)B * H * W;
+  const int64_t pb = P * split / nsplit, pe = P * (split + 1) / nsplit;
+  __shared__ double xs[32][17];
+  __shared__ double gs[32][17];
+  const bool bias = tap == ks * ks;
+  if (bias && k0 != 0) return;
+  const int dy = bias ? 0 : tap / ks - r, dx = bias ? 0 : tap % ks - r;
+  double acc = 0;
+  for (int64_t p0 = pb; p0 < pe; p0 += 32) {
+    for (int e = threadIdx.x; e < 512; e += PW_THREADS) {
+      const int p = e >> 4, c = e & 15;
+      const int64_t px = p0 + p;
+      double xv = 0, gv = 0;
+      if (px < pe) {
+        const int x = (int)(px % W);
+        const int y = (int)((px / W) % H);
+        const int64_t b = px / ((int64_t)W * H);
+        if (n0 + c < N) gv = (double)g[px * N + n0 + c];
+        const int k = k0 + c;
+        if (bias) {
+          xv = 1.0;
+        } else if (k < K) {
+          const int yy = y + dy, xx = x + dx;
+          if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+            const int64_t q = (b * H + yy) * W + xx;
+            xv = (double)(k < C0 ? in0[q * C0 + k] : in1[q * C1 + (k - C0)]);
+          }
+        }
+      }
+      xs[p][c] = xv;
+      gs[p][c] = gv;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int p = 0; p < 32; ++p) acc += xs[p][tk] * gs[p][tn];
+    __syncthreads();
+  }
+  const int k = k0 + tk, n = n0 + tn;
+  if (n >= N) return;
+  if (bias) {
+    if (tk == 0) bpartial[(int64_t)split * N + n] = acc;
+  } else if (k < K) {
+    partial[(((int64_t)split * ks * ks + tap) * K + k) * N + n] = acc;
+  }
+}
+
+// Sum the split partials in a fixed order: gw[tap][k][n], gb[n].
+__global__ void k_pwgrad_reduce(const double* __restrict__ partial, const double* __restrict__ bpartial, int nsplit,
+                                int64_t nw, int N, double* __restrict__ gw, double* __restrict__ gb) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < nw) {
+    double s = 0;
+    for (int sp = 0; sp < nsplit; ++sp) s += partial[(int64_t)sp * nw + e];
+    gw[e] = s;
+  }
+  if (e < N) {
+    double s = 0;
+    for (int sp = 0; sp < nsplit; ++sp) s += bpartial[(int64_t)sp * N + e];
+    gb[e] = s;
+  }
+}
+
+// Input gradient of a KS x KS GEMM layer: gin[q][k] = sum_{tap, n} W[tap][k][n] g[q - tap][n]; channels
+// k < C0 go to gin0 (C0 per pixel), the rest to gin1.  One thread per (pixel, 16 channels).
+template <typename E>
+__global__ void __launch_bounds__(PC_THREADS) k_pdgrad(const E* __restrict__ g, int N, const double* __restrict__ w5,
+                                                       E* __restrict__ gin0, int C0, E* __restrict__ gin1, int C1,
+                                                       int B, int H, int W, int ks) {
+  const int64_t pix = blockIdx.x * (int64_t)PC_THREADS + threadIdx.x;
+  if (pix >= (int64_t)B * H * W) return;
+  const int k0 = blockIdx.y * 16;
+  const int K = C0 + C1, r = ks / 2;
+  const int x = (int)(pix % W);
+  const int y = (int)((pix / W) % H);
+  const int64_t b = pix / ((int64_t)W * H);
+  E acc[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) acc[k] = 0;
+  for (int tap = 0; tap < ks * ks; ++tap) {
+    const int yy = y - (tap / ks - r), xx = x - (tap % ks - r);  // output pixel that read this one at `tap`
+    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
+    const E* gp = g + ((b * H + yy) * W + xx) * N;
+    const double* wt = w5 + (int64_t)tap * K * N;
+    for (int n = 0; n < N; ++n) {
+      const E gv = gp[n];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) acc[k] += gv * (E)wt[(int64_t)(k0 + k) * N + n];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int kk = k0 + k;
+    if (kk < C0)
+      gin0[pix * C0 + kk] = acc[k];
+    else if (kk < K)
+      gin1[pix * C1 + (kk - C0)] = acc[k];
+  }
+}
+
+// Gradient of the network output from the loss: g[b][y][x][0..1] = coef[b] (Re, Im)(A^H r) on the
+// physical grid, 0 on the padding; coef = -2 out_scale / (B ||b||^2).
+template <typename R, typename E>
+__global__ void k_ploss_out(const C<R>* __restrict__ ahr, const double* __restrict__ sums,
+                            const double* __restrict__ out_scale, int Nx, int Ny, int Hp, int Wp, int B,
+                            E* __restrict__ gy) {
+  const int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (pix >= (int64_t)B * Hp * Wp) return;
+  const int x = (int)(pix % Wp);
+  const int y = (int)((pix / Wp) % Hp);
+  const int b = (int)(pix / ((int64_t)Wp * Hp));
+  E g0 = 0, g1 = 0;
+  if (x < Nx && y < Ny) {
+    const double bb = sums[2 * b + 1];
+    const double c = bb > 0 ? -2.0 * out_scale[b] / (B * bb) : 0.0;
+    const C<R> a = ahr[(int64_t)b * Nx * Ny + (int64_t)y * Nx + x];
+    g0 = (E)(c * a.x);
+    g1 = (E)(c * a.y);
+  }
+  gy[pix * 2] = g0;
+  gy[pix * 2 + 1] = g1;
+}
+
+__global__ void k_palpha(const double* __restrict__ nb2, int B, int64_t n, double h2, double* __restrict__ in_s,
+                         double* __restrict__ out_s) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  const double nv = sqrt(nb2[b]);
+  const double a = nv > 0 ? sqrt((double)n) / nv : 0.0;
+  in_s[b] = a;
+  out_s[b] = a > 0 ? h2 / a : 0.0;
+}
+
+// Master-layout gradient of one layer from its reformulated weight gradient (see k_paper_reform).
+__global__ void k_pgather(const double* __restrict__ gw5, const double* __restrict__ gb5,
+                          const double* __restrict__ slope_parts, int nparts, int kind, int cin, int cpad, int cout,
+                          int K, int N, int64_t m_w, int64_t m_b, int64_t m_s, double* __restrict__ grad) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nw = (int64_t)cin * cout * (kind == P_OUT ? 1 : 64);
+  if (e < nw) {
+    double v;
+    if (kind == P_OUT) {
+      const int co = (int)(e / cin), ci = (int)(e % cin);
+      v = gw5[(int64_t)ci * N + co];
+    } else {
+      const int tx = (int)(e % 8), ty = (int)((e / 8) % 8);
+      const int a = (int)((e / 64) % (kind == P_DOWN ? cin : cout));
+      const int z = (int)(e / (64 * (int64_t)(kind == P_DOWN ? cin : cout)));
+      if (kind == P_DOWN) {  // master [co = z][ci = a][ty][tx]
+        const int py = (ty - 3) & 1, px = (tx - 3) & 1;
+        const int dy = (ty - 3 - py) / 2, dx = (tx - 3 - px) / 2;
+        const int tap = (dy + 2) * 5 + dx + 2, k = (py * 2 + px) * cpad + a;
+        v = gw5[((int64_t)tap * K + k) * N + z];
+      } else {  // master [ci = z][co = a][ty][tx]
+        const int qy = (ty - 3) & 1, qx = (tx - 3) & 1;
+        const int dy = (qy - (ty - 3)) / 2, dx = (qx - (tx - 3)) / 2;
+        const int tap = (dy + 2) * 5 + dx + 2, n = (qy * 2 + qx) * cout + a;
+        v = gw5[((int64_t)tap * K + z) * N + n];
+      }
+    }
+    grad[m_w + e] = v;
+  }
+  if (e < cout) {
+    double v = gb5[e];
+    if (kind == P_UP) v = gb5[e] + gb5[cout + e] + gb5[2 * cout + e] + gb5[3 * cout + e];
+    grad[m_b + e] = v;
+  }
+  if (e == 0 && kind != P_OUT) {
+    double t = 0;
+    for (int i = 0; i < nparts; ++i) t += slope_parts[i];  // fixed order
+    grad[m_s] = t;
+  }
+}
+
+template <typename E>
+static helm_status pwgrad(const E* in0, int C0, const E* in1, int C1, const E* g, int N, int B, int H, int W, int ks,
+                          double* partial, double* bpartial, int nsplit, double* gw, double* gb, cudaStream_t st) {
+  const int K = C0 + C1;
+  dim3 grid(nsplit, ((K + 15) / 16) * ((N + 15) / 16), ks * ks + 1);
+  launch(k_pwgrad<E>, grid, PW_THREADS, 0, st, in0, C0, in1, C1, g, N, B, H, W, ks, nsplit, partial, bpartial);
+  const int64_t nw = (int64_t)ks * ks * K * N;
+  launch(k_pwgrad_reduce, cdiv(std::max<int64_t>(nw, N), 256), 256, 0, st, (const double*)partial,
+         (const double*)bpartial, nsplit, nw, N, gw, gb);
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+
+// Output layer for training: z = out_scale (y0 + i y1), y = D0 Wout + bout with unrounded weights.
+template <typename E, typename R>
+__global__ void k_pfinal(const E* __restrict__ in, const double* __restrict__ w5, const double* __restrict__ b5,
+                         const double* __restrict__ out_scale, int Nx, int Ny, int Hp, int Wp, int B,
+                         C<R>* __restrict__ z, int64_t col_stride) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)B * Ny * Nx) return;
+  const int x = (int)(e % Nx);
+  const int y = (int)((e / Nx) % Ny);
+  const int b = (int)(e / ((int64_t)Nx * Ny));
+  const E* ip = in + (((int64_t)b * Hp + y) * Wp + x) * 32;
+  E y0 = (E)b5[0], y1 = (E)b5[1];
+  for (int c = 0; c < 32; ++c) {
+    y0 += ip[c] * (E)w5[c * 2 + 0];
+    y1 += ip[c] * (E)w5[c * 2 + 1];
+  }
+  const double sc = out_scale[b];
+  z[b * col_stride + (int64_t)y * Nx + x] = mk<R>((R)(y0 * sc), (R)(y1 * sc));
+}
+
+template <typename R>
+helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, double* loss_host, cudaStream_t st) {
+  using E = R;  // FP32 (training) or FP64 (checks)
+  PaperNet& P = *net->pn;
+  const SysHost& s0 = ctx->sys[0];
+  for (auto& s : ctx->sys)
+    if (s.Nx != s0.Nx || s.Ny != s0.Ny || s.h != s0.h || s.p != s0.p)
+      return fail(HELM_ERR_INVALID_ARG, "training batches need systems of one grid size, spacing and PML");
+  const int B = ctx->nsys;
+  const int Hp = (s0.Ny + 15) / 16 * 16, Wp = (s0.Nx + 15) / 16 * 16;
+  const int64_t full = (int64_t)Hp * Wp, npx = B * full;
+  HELM_TRY(ensure_cols(ctx, 1));
+  if (!net->grad) HELM_CK(cudaMalloc(&net->grad, sizeof(double) * net->L.total));
+  // ---- workspace: activations and pre-activations (E), gradients (E), FP64 partials
+  const int64_t el_act[13] = {8 * full, 32 * full / 4, 32 * full / 4, 128 * full / 16, 32 * full / 16,
+                              128 * full / 64, 32 * full / 64, 128 * full / 256, 32 * full / 256, 32 * full / 64,
+                              32 * full / 16, 32 * full / 4, 32 * full};
+  const int64_t el_pre[8] = {32 * full / 4, 32 * full / 16, 32 * full / 64, 32 * full / 256,
+                             32 * full / 64, 32 * full / 16, 32 * full / 4, 32 * full};
+  constexpr int NSPLIT = 64, NPP = 1024;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) / 256 * 256;
+    return o;
+  };
+  size_t o_act[13], o_pre[8];
+  for (int k = 0; k < 13; ++k) o_act[k] = take(sizeof(E) * el_act[k] * B);
+  for (int k = 0; k < 8; ++k) o_pre[k] = take(sizeof(E) * el_pre[k] * B);
+  const size_t o_z = take(sizeof(C<R>) * ctx->npts), o_r = take(sizeof(C<R>) * ctx->npts),
+               o_ahr = take(sizeof(C<R>) * ctx->npts);
+  const size_t o_gy = take(sizeof(E) * 2 * npx);
+  const size_t o_ga = take(sizeof(E) * 32 * npx), o_gb = take(sizeof(E) * 32 * npx), o_gc = take(sizeof(E) * 8 * npx);
+  const size_t o_ge[4] = {take(sizeof(E) * 32 * npx / 4), take(sizeof(E) * 32 * npx / 16),
+                          take(sizeof(E) * 32 * npx / 64), take(sizeof(E) * 32 * npx / 256)};
+  const size_t o_part = take(sizeof(double) * (size_t)NSPLIT * 25 * 64 * 128),
+               o_bpart = take(sizeof(double) * NSPLIT * 128), o_gw = take(sizeof(double) * 25 * 64 * 128),
+               o_gbias = take(sizeof(double) * 128), o_pp = take(sizeof(double) * NPP),
+               o_sc = take(sizeof(double) * 5 * B);
+  HELM_TRY(ctx->ws_train.reserve(off));
+  char* base = (char*)ctx->ws_train.ptr;
+  E* a[13];
+  E* pre[8];
+  for (int k = 0; k < 13; ++k) a[k] = (E*)(base + o_act[k]);
+  for (int k = 0; k < 8; ++k) pre[k] = (E*)(base + o_pre[k]);
+  C<R>* z = (C<R>*)(base + o_z);
+  C<R>* rres = (C<R>*)(base + o_r);
+  C<R>* ahr = (C<R>*)(base + o_ahr);
+  E* gy = (E*)(base + o_gy);
+  E* gA = (E*)(base + o_ga);
+  E* gB = (E*)(base + o_gb);
+  E* gC = (E*)(base + o_gc);
+  E* gE[4];
+  for (int k = 0; k < 4; ++k) gE[k] = (E*)(base + o_ge[k]);
+  double* part = (double*)(base + o_part);
+  double* bpart = (double*)(base + o_bpart);
+  double* gw = (double*)(base + o_gw);
+  double* gbias = (double*)(base + o_gbias);
+  double* pp = (double*)(base + o_pp);
+  double* nb2 = (double*)(base + o_sc);
+  double* in_s = nb2 + B;
+  double* out_s = in_s + B;
+  double* sums = out_s + B;  // 2 B entries: ||r||^2, ||b||^2 per sample
+  const int H = Hp, W = Wp;
+
+  // ---- forward, keeping every layer's input and pre-activation
+  HELM_TRY(col_norm2<R>(ctx, bvec, 1, nb2, st));
+  launch(k_palpha, cdiv(B, 64), 64, 0, st, (const double*)nb2, B, s0.n, s0.h * s0.h, in_s, out_s);
+  launch(k_paper_pack<E, R>, cdiv(npx, 256), 256, 0, st, bvec, s0.n, (const double*)in_s,
+         (const double*)(ctx->chat64), s0.n, (const double2*)(ctx->prof_d + s0.prof_x),
+         (const double2*)(ctx->prof_d + s0.prof_y), s0.Nx, s0.Ny, Hp, Wp, B, a[PA_X0]);
+  auto s2d = [&](const E* src, E* dst, int C, int h, int w) {  // h, w: source grid
+    const int64_t n = (int64_t)B * (h / 2) * (w / 2) * 4 * C;
+    launch(k_s2d<E>, cdiv(n, 256), 256, 0, st, src, dst, C, B, h / 2, w / 2);
+  };
+  auto fwd = [&](int l, const E* i0, int C0, const E* i1, int C1, int h, int w) {
+    const PaperLayer& L = kP[l];
+    dim3 grid(cdiv((int64_t)B * h * w, PC_THREADS), L.N / 16);
+    E* post = a[l < 4 ? PA_E1 + 2 * l : PA_D3 + (l - 4)];
+    launch(k_pconv_keep<E>, grid, PC_THREADS, 0, st, i0, C0, i1, C1, (const double*)P.w5[l], (const double*)P.b5[l],
+           pre[l], post, L.N, L.cout, L.kind == P_UP ? 1 : 0, B, h, w, 5, P.slope[l]);
+  };
+  s2d(a[PA_X0], a[PA_S0], 8, H, W);
+  fwd(0, a[PA_S0], 32, nullptr, 0, H / 2, W / 2);
+  s2d(a[PA_E1], a[PA_S1], 32, H / 2, W / 2);
+  fwd(1, a[PA_S1], 128, nullptr, 0, H / 4, W / 4);
+  s2d(a[PA_E2], a[PA_S2], 32, H / 4, W / 4);
+  fwd(2, a[PA_S2], 128, nullptr, 0, H / 8, W / 8);
+  s2d(a[PA_E3], a[PA_S3], 32, H / 8, W / 8);
+  fwd(3, a[PA_S3], 128, nullptr, 0, H / 16, W / 16);
+  fwd(4, a[PA_E4], 32, nullptr, 0, H / 16, W / 16);
+  fwd(5, a[PA_D3], 32, a[PA_E3], 32, H / 8, W / 8);
+  fwd(6, a[PA_D2], 32, a[PA_E2], 32, H / 4, W / 4);
+  fwd(7, a[PA_D1], 32, a[PA_E1], 32, H / 2, W / 2);
+  launch(k_pfinal<E, R>, cdiv((int64_t)B * s0.n, 256), 256, 0, st, (const E*)a[PA_D0],
+         (const double*)P.w5[PAPER_LAYERS - 1], (const double*)P.b5[PAPER_LAYERS - 1], (const double*)out_s, s0.Nx,
+         s0.Ny, Hp, Wp, B, z, s0.n);
+  HELM_CK_LAUNCH();
+  // ---- loss (eq. 9) and the gradient of the network output
+  HELM_TRY(residual_op<R>(ctx, z, bvec, rres, 1, sums, st));
+  HELM_TRY(apply_op<R>(ctx, rres, ahr, 1, true, st));
+  launch(k_ploss_out<R, E>, cdiv(npx, 256), 256, 0, st, (const C<R>*)ahr, (const double*)sums, (const double*)out_s,
+         s0.Nx, s0.Ny, Hp, Wp, B, gy);
+  HELM_CK_LAUNCH();
+
+  // ---- backward
+  auto gather = [&](int l, int nparts) {
+    const PaperLayer& L = kP[l];
+    const int64_t nw = (int64_t)L.cin * L.cout * (L.kind == P_OUT ? 1 : 64);
+    launch(k_pgather, cdiv(std::max<int64_t>(nw, L.cout), 256), 256, 0, st, (const double*)gw, (const double*)gbias,
+           (const double*)pp, nparts, L.kind, L.cin, l == 0 ? P_X0_CH : L.cin, L.cout, L.K, L.N, P.m_w[l], P.m_b[l],
+           P.m_s[l], net->grad);
+  };
+  auto prelu_bwd = [&](int l, E* g, int64_t n) {
+    const int nb = (int)std::min<int64_t>(NPP, cdiv(n, 256));
+    launch(k_prelu_bwd<E>, nb, 256, 0, st, g, (const E*)pre[l], n, P.slope[l], pp);
+    return nb;
+  };
+  auto dgrad = [&](const E* g, int N, int l, E* gin0, int C0, E* gin1, int C1, int h, int w, int ks) {
+    dim3 grid(cdiv((int64_t)B * h * w, PC_THREADS), (C0 + C1 + 15) / 16);
+    launch(k_pdgrad<E>, grid, PC_THREADS, 0, st, g, N, (const double*)P.w5[l], gin0, C0, gin1, C1, B, h, w, ks);
+  };
+  auto d2s_acc = [&](const E* gs, E* gprev, int C, int hi, int wi) {  // gs on the half grid hi x wi
+    const int64_t n = (int64_t)B * hi * wi * 4 * C;
+    launch(k_d2s<E>, cdiv(n, 256), 256, 0, st, gs, gprev, C, B, hi, wi, 1);
+  };
+  // output layer (1 x 1, N = 2): weights, bias, input gradient
+  HELM_TRY(pwgrad<E>(a[PA_D0], 32, (const E*)nullptr, 0, gy, 2, B, H, W, 1, part, bpart, NSPLIT, gw, gbias, st));
+  gather(PAPER_LAYERS - 1, 0);
+  dgrad(gy, 2, PAPER_LAYERS - 1, gA, 32, nullptr, 0, H, W, 1);  // gD0 -> gA
+  // decoder: l = 7 (d0) .. 4 (d3); the post-activation gradient in gA is on the layer's output grid
+  const int dec_h[4] = {H / 2, H / 4, H / 8, H / 16};  // GEMM grids of l = 7, 6, 5, 4
+  for (int i = 0; i < 4; ++i) {
+    const int l = 7 - i, h = dec_h[i], w = W * h / H;
+    const int64_t nout = (int64_t)B * (2 * h) * (2 * w) * 32;
+    const int nparts = prelu_bwd(l, gA, nout);                       // gA: g_pre on the 2h x 2w grid
+    s2d(gA, gB, 32, 2 * h, 2 * w);                                   // gB: GEMM columns on h x w (128)
+    const E* in0 = a[l == 4 ? PA_E4 : PA_D3 + (l - 4) - 1];          // decoder input of this layer
+    const E* in1 = l == 4 ? nullptr : a[PA_E4 - 2 * (l - 4)];        // skip (e_3, e_2, e_1 for l = 5, 6, 7)
+    const int C1 = l == 4 ? 0 : 32;
+    HELM_TRY(pwgrad<E>(in0, 32, in1, C1, gB, 128, B, h, w, 5, part, bpart, NSPLIT, gw, gbias, st));
+    gather(l, nparts);
+    E* ge = gE[7 - l];                                               // e_1 (l = 7) .. e_4 (l = 4) grad
+    if (l == 4)
+      dgrad(gB, 128, l, ge, 32, nullptr, 0, h, w, 5);                // g e_4
+    else
+      dgrad(gB, 128, l, gA, 32, ge, 32, h, w, 5);                    // g d_{next} -> gA, g skip -> ge
+  }
+  // encoder: l = 3 (e4) .. 0 (e1); gE[l] holds the post-activation gradient of e_{l+1}
+  for (int l = 3; l >= 0; --l) {
+    const int h = H >> (l + 1), w = W >> (l + 1);
+    const int64_t nout = (int64_t)B * h * w * 32;
+    const int nparts = prelu_bwd(l, gE[l], nout);
+    const E* in = a[PA_S0 + 2 * l];                                   // S0, S1, S2, S3
+    const int K = l == 0 ? 32 : 128;
+    HELM_TRY(pwgrad<E>(in, K, (const E*)nullptr, 0, gE[l], 32, B, h, w, 5, part, bpart, NSPLIT, gw, gbias, st));
+    gather(l, nparts);
+    if (l > 0) {
+      dgrad(gE[l], 32, l, gC, 128, nullptr, 0, h, w, 5);             // gradient on S_l (128 channels)
+      d2s_acc(gC, gE[l - 1], 32, h, w);                              // back to e_l, added to its skip part
+    }
+  }
+  HELM_CK_LAUNCH();
+  if (loss_host) {
+    std::vector<double> hs(2 * B);
+    HELM_CK(cudaMemcpyAsync(hs.data(), sums, sizeof(double) * 2 * B, cudaMemcpyDeviceToHost, st));
+    HELM_CK(cudaStreamSynchronize(st));
+    double L = 0;
+    for (int k = 0; k < B; ++k) L += hs[2 * k + 1] > 0 ? hs[2 * k] / hs[2 * k + 1] : 0.0;
+    *loss_host = L / B;
+  }
+  return HELM_OK;
+}
+
+template helm_status paper_loss_grad<float>(helm_ctx*, helm_unet*, const float2*, double*, cudaStream_t);
+template helm_status paper_loss_grad<double>(helm_ctx*, helm_unet*, const double2*, double*, cudaStream_t);
 
 }  // namespace helm

@@ -166,3 +166,41 @@ def test_epoch_training_loop_resumes_exactly(tmp_path):
     assert np.array_equal(net_a.weights(), net_b.weights())
     best = np.load(str(tmp_path / "a.npy"))
     assert best.size == net_a.nparams
+
+
+# ---------------------------------------------------------------- network kind 1 (the paper's variant)
+
+def _theta_paper(helm, seed=42):
+    return synth.kaiming_uniform_params(helm.paper_weight_segments(), seed)
+
+
+def test_paper_network_fp64_loss_and_gradient_match_oracle(helm):
+    """Eq. 9 through network kind 1: the FP64 loss and gradient (CUDA cores, through the 5x5
+    reformulation and its gather back to the 8x8 weights) equal the oracle's plain strided
+    convolutions, including the PReLU slope gradients."""
+    c, b, nx, p, h, om = _batch(B=3, nx=20, p=6, seed=63)
+    theta = _theta_paper(helm)
+    ctx = _ctx(helm, c, nx, p, h, om)
+    net = helm.UNet(theta, kind=1)
+    L, g = helm.helm_loss_grad(ctx, net, torch.tensor(b.ravel(), device="cuda"))
+    Lr, gr, _ = ot.loss_and_grad(theta, b, c, p, h, om, kind=1)
+    assert abs(L - Lr) <= 1e-11 * Lr
+    g = g.cpu().numpy()
+    assert np.abs(g - gr).max() <= 1e-9 * np.abs(gr).max()
+
+
+def test_paper_network_fp32_gradient_and_training(helm):
+    """The FP32 training path of kind 1 gives the oracle's FP64 gradient to FP32 accuracy, and a few
+    AdamW steps lower the batch loss."""
+    c, b, nx, p, h, om = _batch(B=4, nx=28, p=6, seed=64)
+    theta = _theta_paper(helm, 44)
+    ctx = _ctx(helm, c, nx, p, h, om)
+    net = helm.UNet(theta, kind=1)
+    b32 = torch.tensor(b.ravel().astype(np.complex64), device="cuda")
+    L, g = helm.helm_loss_grad(ctx, net, b32)
+    Lr, gr, _ = ot.loss_and_grad(theta, b.astype(np.complex64).astype(complex), c, p, h, om, kind=1)
+    g = g.cpu().numpy()
+    assert abs(L - Lr) <= 1e-4 * Lr
+    assert np.linalg.norm(g - gr) <= 1e-3 * np.linalg.norm(gr)
+    losses = [helm.helm_train_step(ctx, net, b32, lr=1e-3, wd=0.0, clip=1.0)[0] for _ in range(12)]
+    assert losses[-1] < 0.9 * losses[0], losses
