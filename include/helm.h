@@ -175,8 +175,8 @@ HELM_API helm_status helm_unet_create(helm_unet** out, const double* weights_hos
  * Weights of kind 1 (665,930 doubles): per layer weight, bias, PReLU slope (none for the output layer);
  * layers enc1 enc2 enc3 enc4 dec3 dec2 dec1 dec0 out; conv weights [Cout][Cin][8][8], transposed-conv
  * weights [Cin][Cout][8][8], output weights [2][32].  Kind 1 serves helm_precond_apply and
- * helm_fgmres_solve (BF16 on tcgen05 tensor cores, or FP64 on CUDA cores); its training is not built
- * (helm_train_step / helm_loss_grad return HELM_ERR_INVALID_ARG). */
+ * helm_fgmres_solve (BF16 on tcgen05 tensor cores, or FP64 on CUDA cores) and helm_train_step /
+ * helm_loss_grad (forward and backward on CUDA cores: FP32 for C64 batches, FP64 for C128). */
 HELM_API size_t helm_unet_param_count_kind(int kind);
 HELM_API helm_status helm_unet_create_kind(helm_unet** out, int kind, const double* weights_host, size_t nweights);
 HELM_API helm_status helm_unet_destroy(helm_unet* net);

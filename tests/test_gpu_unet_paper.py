@@ -94,12 +94,3 @@ def test_paper_network_mixed_cycle_is_consistent(helm, theta):
     p = probs[0]
     A = hz.assemble(p.c, p.p, p.h, p.omega)
     assert abs(hz.relres(A, x.cpu().numpy(), p.b[0].ravel()) - c["relres_true"]) <= 1e-9 * c["relres_true"]
-
-
-def test_paper_network_training_is_refused(helm, theta):
-    probs = small_problems(((20, 14, 5),), seed=95)
-    ctx = make_ctx(probs)
-    net = helm.UNet(theta, kind=1)
-    b = to_dev(probs[0].b.ravel(), torch.complex64)
-    with pytest.raises(helm.HelmError, match="not built"):
-        helm.helm_train_step(ctx, net, b)
