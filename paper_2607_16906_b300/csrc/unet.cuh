@@ -138,6 +138,7 @@ constexpr int PAPER_LAYERS = 9;  // enc1..enc4, dec3..dec0, out
 struct PaperNet {
   int64_t m_w[PAPER_LAYERS] = {}, m_b[PAPER_LAYERS] = {}, m_s[PAPER_LAYERS] = {};  // master offsets
   double* w5[PAPER_LAYERS] = {};          // reformulated weights [tap][k][n], FP64
+  float* w5f[PAPER_LAYERS] = {};          // the same in FP32 (training path)
   double* b5[PAPER_LAYERS] = {};          // per-column bias, FP64
   __nv_bfloat16* wtc[PAPER_LAYERS] = {};  // tcgen05 layout [tap][kc][n][c], BF16
   float* b32[PAPER_LAYERS] = {};

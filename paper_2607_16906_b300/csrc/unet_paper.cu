@@ -100,6 +100,11 @@ __global__ void k_paper_tc(const double* __restrict__ w5, const double* __restri
   wtc[e] = __float2bfloat16_rn((float)w5[((int64_t)tap * K + kc * chunk + c) * N + n]);
 }
 
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < n) b[e] = (float)a[e];
+}
+
 // Output layer for the BF16 path: 32 x 2 weights rounded to BF16 (held in FP32), then 2 biases.
 __global__ void k_paper_out32(const double* __restrict__ w5, const double* __restrict__ b5, float* __restrict__ o) {
   const int e = threadIdx.x;
@@ -122,6 +127,7 @@ helm_status paper_prepare(helm_unet* net, cudaStream_t st) {
     const int64_t n5 = (int64_t)taps * L.K * L.N;
     if (!P.w5[l]) {
       HELM_CK(cudaMalloc(&P.w5[l], sizeof(double) * n5));
+      HELM_CK(cudaMalloc(&P.w5f[l], sizeof(float) * n5));
       HELM_CK(cudaMalloc(&P.b5[l], sizeof(double) * L.N));
       if (L.kind != P_OUT) {
         HELM_CK(cudaMalloc(&P.wtc[l], sizeof(__nv_bfloat16) * n5));
@@ -131,6 +137,7 @@ helm_status paper_prepare(helm_unet* net, cudaStream_t st) {
     const int cpad = l == 0 ? P_X0_CH : L.cin;
     launch(k_paper_reform, cdiv(std::max<int64_t>(n5, L.N), 256), 256, 0, st, (const double*)net->master, P.m_w[l],
            P.m_b[l], L.kind, L.cin, cpad, L.cout, L.K, L.N, P.w5[l], P.b5[l]);
+    launch(k_to_f32, cdiv(n5, 256), 256, 0, st, (const double*)P.w5[l], P.w5f[l], n5);
     if (L.kind != P_OUT)
       launch(k_paper_tc, cdiv(std::max<int64_t>(n5, L.N), 256), 256, 0, st, (const double*)P.w5[l],
              (const double*)P.b5[l], L.K, L.N, L.chunk, P.wtc[l], P.b32[l]);
@@ -157,6 +164,7 @@ void paper_release(helm_unet* net) {
   PaperNet& P = *net->pn;
   for (int l = 0; l < PAPER_LAYERS; ++l) {
     cudaFree(P.w5[l]);
+    cudaFree(P.w5f[l]);
     cudaFree(P.b5[l]);
     cudaFree(P.wtc[l]);
     cudaFree(P.b32[l]);
@@ -414,7 +422,7 @@ constexpr int PW_THREADS = 256;  // weight-gradient tile: 16 k x 16 n outputs, 3
 // Forward GEMM layer on CUDA cores with the pre-activation kept (up: both written depth-to-space).
 template <typename E>
 __global__ void __launch_bounds__(PC_THREADS) k_pconv_keep(const E* __restrict__ in0, int C0, const E* __restrict__ in1,
-                                                           int C1, const double* __restrict__ w5,
+                                                           int C1, const E* __restrict__ w5,
                                                            const double* __restrict__ b5, E* __restrict__ pre,
                                                            E* __restrict__ post, int N, int cout, int up, int B,
                                                            int H, int W, int ks, double slope) {
@@ -432,12 +440,12 @@ __global__ void __launch_bounds__(PC_THREADS) k_pconv_keep(const E* __restrict__
     const int yy = y + tap / ks - r, xx = x + tap % ks - r;
     if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
     const int64_t q = (b * H + yy) * W + xx;
-    const double* wt = w5 + (int64_t)tap * K * N + n0;
+    const E* wt = w5 + (int64_t)tap * K * N + n0;
     for (int c = 0; c < K; ++c) {
       const E v = c < C0 ? in0[q * C0 + c] : in1[q * C1 + (c - C0)];
-      const double* wr = wt + (int64_t)c * N;
+      const E* wr = wt + (int64_t)c * N;
 #pragma unroll
-      for (int k = 0; k < 16; ++k) acc[k] += v * (E)wr[k];
+      for (int k = 0; k < 16; ++k) acc[k] += v * wr[k];
     }
   }
 #pragma unroll
@@ -574,7 +582,7 @@ __global__ void k_pwgrad_reduce(const double* __restrict__ partial, const double
 // Input gradient of a KS x KS GEMM layer: gin[q][k] = sum_{tap, n} W[tap][k][n] g[q - tap][n]; channels
 // k < C0 go to gin0 (C0 per pixel), the rest to gin1.  One thread per (pixel, 16 channels).
 template <typename E>
-__global__ void __launch_bounds__(PC_THREADS) k_pdgrad(const E* __restrict__ g, int N, const double* __restrict__ w5,
+__global__ void __launch_bounds__(PC_THREADS) k_pdgrad(const E* __restrict__ g, int N, const E* __restrict__ w5,
                                                        E* __restrict__ gin0, int C0, E* __restrict__ gin1, int C1,
                                                        int B, int H, int W, int ks) {
   const int64_t pix = blockIdx.x * (int64_t)PC_THREADS + threadIdx.x;
@@ -591,11 +599,11 @@ __global__ void __launch_bounds__(PC_THREADS) k_pdgrad(const E* __restrict__ g, 
     const int yy = y - (tap / ks - r), xx = x - (tap % ks - r);  // output pixel that read this one at `tap`
     if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
     const E* gp = g + ((b * H + yy) * W + xx) * N;
-    const double* wt = w5 + (int64_t)tap * K * N;
+    const E* wt = w5 + (int64_t)tap * K * N;
     for (int n = 0; n < N; ++n) {
       const E gv = gp[n];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) acc[k] += gv * (E)wt[(int64_t)(k0 + k) * N + n];
+      for (int k = 0; k < 16; ++k) acc[k] += gv * wt[(int64_t)(k0 + k) * N + n];
     }
   }
 #pragma unroll
@@ -728,6 +736,12 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
   const int64_t full = (int64_t)Hp * Wp, npx = B * full;
   HELM_TRY(ensure_cols(ctx, 1));
   if (!net->grad) HELM_CK(cudaMalloc(&net->grad, sizeof(double) * net->L.total));
+  auto wts = [&](int l) -> const E* {  // reformulated weights in the arithmetic type
+    if constexpr (sizeof(E) == 8)
+      return P.w5[l];
+    else
+      return P.w5f[l];
+  };
   // ---- workspace: activations and pre-activations (E), gradients (E), FP64 partials
   const int64_t el_act[13] = {8 * full, 32 * full / 4, 32 * full / 4, 128 * full / 16, 32 * full / 16,
                               128 * full / 64, 32 * full / 64, 128 * full / 256, 32 * full / 256, 32 * full / 64,
@@ -794,8 +808,8 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
     const PaperLayer& L = kP[l];
     dim3 grid(cdiv((int64_t)B * h * w, PC_THREADS), L.N / 16);
     E* post = a[l < 4 ? PA_E1 + 2 * l : PA_D3 + (l - 4)];
-    launch(k_pconv_keep<E>, grid, PC_THREADS, 0, st, i0, C0, i1, C1, (const double*)P.w5[l], (const double*)P.b5[l],
-           pre[l], post, L.N, L.cout, L.kind == P_UP ? 1 : 0, B, h, w, 5, P.slope[l]);
+    launch(k_pconv_keep<E>, grid, PC_THREADS, 0, st, i0, C0, i1, C1, wts(l), (const double*)P.b5[l], pre[l], post,
+           L.N, L.cout, L.kind == P_UP ? 1 : 0, B, h, w, 5, P.slope[l]);
   };
   s2d(a[PA_X0], a[PA_S0], 8, H, W);
   fwd(0, a[PA_S0], 32, nullptr, 0, H / 2, W / 2);
@@ -835,7 +849,7 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
   };
   auto dgrad = [&](const E* g, int N, int l, E* gin0, int C0, E* gin1, int C1, int h, int w, int ks) {
     dim3 grid(cdiv((int64_t)B * h * w, PC_THREADS), (C0 + C1 + 15) / 16);
-    launch(k_pdgrad<E>, grid, PC_THREADS, 0, st, g, N, (const double*)P.w5[l], gin0, C0, gin1, C1, B, h, w, ks);
+    launch(k_pdgrad<E>, grid, PC_THREADS, 0, st, g, N, wts(l), gin0, C0, gin1, C1, B, h, w, ks);
   };
   auto d2s_acc = [&](const E* gs, E* gprev, int C, int hi, int wi) {  // gs on the half grid hi x wi
     const int64_t n = (int64_t)B * hi * wi * 4 * C;
