@@ -70,7 +70,12 @@ def parse():
     ap.add_argument("--uneven", action="store_true", help="also solve the uneven 64-system batch in one call")
     ap.add_argument("--uneven-m", type=int, default=256)
     ap.add_argument("--only-extra", action="store_true",
-                    help="skip the timed main workload: run only the legs asked for with --large / --uneven")
+                    help="skip the timed main workload: run only the legs asked for with --large / --uneven / "
+                         "--fourier / --paper-net")
+    ap.add_argument("--fourier", action="store_true", help="with --only-extra: the Fourier operator leg")
+    ap.add_argument("--paper-net", action="store_true", help="with --only-extra: the kind-1 network leg")
+    ap.add_argument("--extra-rhs", type=int, default=8, help="right-hand sides of the --fourier / --paper-net legs")
+    ap.add_argument("--reps", type=int, default=10, help="timed repetitions of the --fourier / --paper-net legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the bounded CPU-oracle baseline")
     ap.add_argument("--no-train", action="store_true", help="skip the training-step throughput measurement")
     return ap.parse_args()
@@ -256,6 +261,70 @@ def small_configuration(helm, theta_trained):
     return out
 
 
+def timed_flushed(fn, reps=10):
+    """Mean CUDA-event time (ms) of fn over `reps` launches after 3 untimed ones, each preceded by an
+    L2 flush (a 256 MB write, then a 256 MB read of another buffer)."""
+    import torch
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    flush_r = torch.ones(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tot = 0.0
+    for it in range(reps + 3):
+        flush.fill_(it)
+        flush_r.sum()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        fn()
+        a1.record()
+        torch.cuda.synchronize()
+        if it >= 3:
+            tot += a0.elapsed_time(a1)
+    return tot / max(1, reps)
+
+
+def fourier_leg(helm, h, omega, peaks, nrhs=8, reps=10):
+    """The paper's discretisation: the Fourier-differentiation operator (FP32) on a 1024^2 grid (the
+    largest power-of-two side, 1008^2 + 8 PML) x `nrhs` RHS against its algorithmic 52 B per point
+    (row pass 16 B, column pass 36 B)."""
+    import torch
+    from paper_2607_16906_b300 import synth as sy
+    c = sy.skull_velocity(1008, 1008, 8, sy.rng_for(77))
+    fctx = helm.Context([helm.SystemSpec(1008, 1008, h, 8, omega)], torch.tensor(c.ravel(), device="cuda"))
+    fx = torch.randn(fctx.npts * nrhs, dtype=torch.complex64, device="cuda")
+    fy = torch.empty_like(fx)
+    f_ms = timed_flushed(lambda: helm.helm_apply_fourier(fctx, fx, fy, nrhs), reps)
+    f_bytes = 52.0 * fctx.npts * nrhs
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    return {"bound": "hbm", "achieved": f_bytes / (f_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
+            "frac": f_bytes / (f_ms / 1e3) / 1e9 / hbm, "ms": f_ms, "bytes_per_launch": f_bytes,
+            "kernels": f"k_fourier_x + k_fourier_y (FP32, 1024^2 x {nrhs} RHS)", "l2": "flushed before each launch"}
+
+
+def paper_net_leg(helm, ctx, nrhs, peaks, reps=5):
+    """The paper's U-Net variant (network kind 1, seeded weights): one BF16 application to `nrhs`
+    right-hand sides of the context; the flops per full-resolution pixel are those the tensor cores
+    execute after the 5x5 reformulation (82,464 MAC, structural zeros included; the 8x8 layers
+    themselves need 51,264)."""
+    import torch
+    from paper_2607_16906_b300 import synth as sy
+    pn = helm.UNet(sy.kaiming_uniform_params(helm.paper_weight_segments(), 42), kind=1)
+    pv = torch.randn(ctx.npts * nrhs, dtype=torch.complex64, device="cuda")
+    pz = torch.empty_like(pv)
+    helm.helm_precond_apply(ctx, pn, pv, pz, nrhs)
+    p_ms = timed_flushed(lambda: helm.helm_precond_apply(ctx, pn, pv, pz, nrhs), reps)
+    # GEMM MACs per full-resolution pixel: down layers 25 taps x K x 32 at 1/4, 1/16, 1/64, 1/256 of
+    # the pixels (K = 32, 128, 128, 128); up layers 25 x K x 128 at 1/256, 1/64, 1/16, 1/4 (K = 32,
+    # 64, 64, 64); output 32 x 2
+    macs = (25 * 32 * 32 / 4 + 25 * 128 * 32 * (1 / 16 + 1 / 64 + 1 / 256) +
+            25 * 128 * (32 / 256 + 64 / 64 + 64 / 16 + 64 / 4) + 64)
+    p_flops = 2.0 * macs * ctx.npts * nrhs
+    pk = peaks.get("bf16_tflops", 1800.0)
+    return {"bound": "tensor", "achieved": p_flops / (p_ms / 1e3) / 1e12, "peak": pk, "unit": "TFLOP/s",
+            "frac": p_flops / (p_ms / 1e3) / 1e12 / pk, "ms": p_ms, "flop_per_pixel": 2.0 * macs,
+            "what": f"network kind 1 (the paper's variant), BF16 on tcgen05, {nrhs} RHS, GEMM flops of the 5x5 "
+                    "reformulation (36 % structural zeros included)",
+            "peak_source": "measured burst bf16 (MEASURED_PEAKS.json)"}
+
+
 def large_configuration(helm, theta, nrhs, m):
     """The large configuration: 2048^2 interior + 64 PML (2176^2, 4.7 M unknowns), 12 points per
     wavelength, thin skull ring, line-array sources; mixed path with FP64 refinement to eta_b <= 1e-8.
@@ -357,6 +426,16 @@ def run_cuda(args):
                 out["large_2176"] = large_configuration(helm, theta, args.large_rhs, args.large_m)
             if args.uneven:
                 out["uneven_64"] = uneven_configuration(helm, theta, args.uneven_m)
+            peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+                os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+            if args.fourier or args.paper_net:
+                fp = workload(1)
+                if args.fourier:
+                    out["fourier_roofline"] = fourier_leg(helm, fp.h, fp.omega, peaks, args.extra_rhs, args.reps)
+                if args.paper_net:
+                    fspec = helm.SystemSpec(fp.nx, fp.ny, fp.h, fp.p, fp.omega)
+                    fctx = helm.Context([fspec], torch.tensor(fp.c.ravel(), device="cuda"))
+                    out["paper_unet"] = paper_net_leg(helm, fctx, args.extra_rhs, peaks, args.reps)
             print(json.dumps(out), flush=True)
         if dist:
             dist.destroy_process_group()
@@ -502,65 +581,8 @@ def run_cuda(args):
                "l2": "flushed before each launch (write 256 MB, read 256 MB)",
                "tile": [t for t in helm.helm_tuned_stencil() if t["nrhs"] == nrhs]}
 
-    def timed(fn, reps=10):
-        """Mean CUDA-event time (ms) of fn over `reps` launches, each after an L2 flush."""
-        tot = 0.0
-        for it in range(reps + 3):
-            flush.fill_(it)
-            flush_r.sum()
-            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a0.record()
-            fn()
-            a1.record()
-            torch.cuda.synchronize()
-            if it >= 3:
-                tot += a0.elapsed_time(a1)
-        return tot / reps
-
-    # the paper's discretisation: the Fourier-differentiation operator (FP32) on 1024^2 grids (the
-    # largest power-of-two side) x 8 RHS; algorithmic traffic 52 B per point (row pass 16 B, column
-    # pass 36 B)
-    fourier = None
-    if rank == 0:
-        from paper_2607_16906_b300 import synth as sy
-        fprob = sy.Problem(1008, 1008, 8, prob.h, prob.omega, sy.skull_velocity(1008, 1008, 8, sy.rng_for(77)),
-                           np.zeros((1, 1024, 1024), complex))
-        fctx = helm.Context([helm.SystemSpec(1008, 1008, prob.h, 8, prob.omega)],
-                            torch.tensor(fprob.c.ravel(), device="cuda"))
-        fx = torch.randn(fctx.npts * 8, dtype=torch.complex64, device="cuda")
-        fy = torch.empty_like(fx)
-        f_ms = timed(lambda: helm.helm_apply_fourier(fctx, fx, fy, 8))
-        f_bytes = 52.0 * fctx.npts * 8
-        fourier = {"bound": "hbm", "achieved": f_bytes / (f_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                   "frac": f_bytes / (f_ms / 1e3) / 1e9 / hbm, "ms": f_ms, "bytes_per_launch": f_bytes,
-                   "kernels": "k_fourier_x + k_fourier_y (FP32, 1024^2 x 8 RHS)",
-                   "l2": "flushed before each launch"}
-        del fctx, fx, fy
-
-    # the paper's U-Net variant (network kind 1, seeded weights): one BF16 application to the 32
-    # right-hand sides of the workload; the flops per full-resolution pixel are those the tensor
-    # cores execute after the 5x5 reformulation (82,464 MAC, structural zeros included; the 8x8
-    # layers themselves need 51,264)
-    paper_net = None
-    if rank == 0:
-        pn = helm.UNet(synth.kaiming_uniform_params(helm.paper_weight_segments(), 42), kind=1)
-        pv = torch.randn(ctx.npts * nrhs, dtype=torch.complex64, device="cuda")
-        pz = torch.empty_like(pv)
-        helm.helm_precond_apply(ctx, pn, pv, pz, nrhs)
-        p_ms = timed(lambda: helm.helm_precond_apply(ctx, pn, pv, pz, nrhs), reps=5)
-        # GEMM MACs per full-resolution pixel: down layers 25 taps x K x 32 at 1/4, 1/16, 1/64, 1/256
-        # of the pixels (K = 32, 128, 128, 128); up layers 25 x K x 128 at 1/256, 1/64, 1/16, 1/4
-        # (K = 32, 64, 64, 64); output 32 x 2
-        macs = (25 * 32 * 32 / 4 + 25 * 128 * 32 * (1 / 16 + 1 / 64 + 1 / 256) +
-                25 * 128 * (32 / 256 + 64 / 64 + 64 / 16 + 64 / 4) + 64)
-        p_flops = 2.0 * macs * ctx.npts * nrhs
-        pk = peaks.get("bf16_tflops", 1800.0)
-        paper_net = {"bound": "tensor", "achieved": p_flops / (p_ms / 1e3) / 1e12, "peak": pk, "unit": "TFLOP/s",
-                     "frac": p_flops / (p_ms / 1e3) / 1e12 / pk, "ms": p_ms, "flop_per_pixel": 2.0 * macs,
-                     "what": "network kind 1 (the paper's variant), BF16 on tcgen05, 32 RHS of 576^2, "
-                             "GEMM flops of the 5x5 reformulation (36 % structural zeros included)",
-                     "peak_source": "measured burst bf16 (MEASURED_PEAKS.json)"}
-        del pn, pv, pz
+    fourier = fourier_leg(helm, prob.h, prob.omega, peaks) if rank == 0 else None
+    paper_net = paper_net_leg(helm, ctx, nrhs, peaks) if rank == 0 else None
 
     # training-step throughput on the training configuration (64 x (128^2 + 16 PML), mixed skull / GRF
     # velocities, point-source and line-array sources): helm_train_step = BF16 forward, adjoint
