@@ -128,23 +128,25 @@ def better(a, b):
 
 def train_epochs(dataset="D0", samples=10000, nx=128, p=16, ppw=10.0, batch=32, epochs=50, lr_max=1e-3,
                  lr_min=1e-5, wd=0.01, clip=1.0, seed=42, init=None, out=None, checkpoint=None, resume=False,
-                 val_every=5, validator=None, verbose=True, log_every=50, stop_after=None):
+                 val_every=5, validator=None, verbose=True, log_every=50, stop_after=None, kind=0):
     """Epoch mode (module docstring).  `epochs` fixes the schedule; `stop_after` ends this invocation
-    after that many epochs in all (a later call with resume=True continues the same schedule)."""
+    after that many epochs in all (a later call with resume=True continues the same schedule).
+    kind: network kind (0: the 16/32/64/128 U-Net, 1: the paper's variant)."""
     h, om = synth.grid_spacing(ppw), synth.angular_frequency()
     cs, bs, _ = make_sample_set(dataset, samples, nx, p, seed)
     c_dev = torch.tensor(cs, device="cuda")
     b_dev = torch.tensor(bs, device="cuda")
     ctx = helm.Context([helm.SystemSpec(nx, nx, h, p, om) for _ in range(batch)], c_dev[:batch].reshape(-1))
     state = {"epoch": 0, "step": 0, "best": None, "history": [], "dataset": dataset, "samples": samples,
-             "batch": batch, "epochs": epochs, "seed": seed}
+             "batch": batch, "epochs": epochs, "seed": seed, "kind": kind}
     if resume and checkpoint and os.path.exists(checkpoint):
         w, (m, v, st), state = load_checkpoint(checkpoint)
-        net = helm.UNet(w)
+        net = helm.UNet(w, kind=kind)
         net.set_adam_state(m, v, st)
     else:
-        theta = init if init is not None else synth.kaiming_uniform_params(helm.weight_segments(), seed)
-        net = helm.UNet(theta)
+        segs = helm.weight_segments() if kind == 0 else helm.paper_weight_segments()
+        theta = init if init is not None else synth.kaiming_uniform_params(segs, seed)
+        net = helm.UNet(theta, kind=kind)
     steps_per_epoch = samples // batch
     total = steps_per_epoch * epochs
     t0 = time.time()
@@ -253,6 +255,7 @@ def main():
     ap.add_argument("--val-every", type=int, default=5)
     ap.add_argument("--val-rhs", type=int, default=4, help="held-out right-hand sides of the fine-grid workload")
     ap.add_argument("--no-val", action="store_true")
+    ap.add_argument("--kind", type=int, default=0, help="network kind: 0 (16/32/64/128 U-Net) or 1 (the paper's)")
     # streaming mode
     ap.add_argument("--steps", type=int, default=3000)
     ap.add_argument("--grids", default="128x64", help="comma list of <interior side>x<batch>")
@@ -267,7 +270,8 @@ def main():
         val = None if a.no_val else Validator(synth.fine_multi_rhs_problem(seed=3900, nrhs=a.val_rhs))
         _, state = train_epochs(dataset=a.dataset, samples=a.samples, nx=a.grid, p=a.pml, batch=a.batch,
                                 epochs=a.epochs, lr_max=a.lr, lr_min=a.lr_min, init=init, out=a.out,
-                                checkpoint=a.checkpoint, resume=a.resume, val_every=a.val_every, validator=val)
+                                checkpoint=a.checkpoint, resume=a.resume, val_every=a.val_every, validator=val,
+                                kind=a.kind)
         if a.log:
             with open(a.log, "w") as f:
                 json.dump(state, f)
