@@ -506,7 +506,8 @@ __global__ void k_prelu_bwd(E* __restrict__ g, const E* __restrict__ pre, int64_
 
 // Weight gradient of a KS x KS GEMM layer: partial[split][tap][k][n] = sum over the split's pixels of
 // in[px + tap][k] g[px][n]; one block per (split, 16 x 16 (k, n) tile, tap).  With tap == ks * ks
-// (an extra grid slice) the block sums g for the bias instead (k tile 0 only).
+// (an extra grid slice) the block sums g for the bias instead (k tile 0 only).  Each block
+// accumulates its split in E (FP32 on the training path); the splits are summed in FP64.
 template <typename E>
 __global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const E* __restrict__ in0, int C0, const E* __restrict__ in1,
                                                        int C1, const E* __restrict__ g, int N, int B, int H, int W,
@@ -519,30 +520,30 @@ __global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const E* __restrict__ in0
   const int tk = threadIdx.x & 15, tn = threadIdx.x >> 4;
   const int64_t P = (int64_t)B * H * W;
   const int64_t pb = P * split / nsplit, pe = P * (split + 1) / nsplit;
-  __shared__ double xs[32][17];
-  __shared__ double gs[32][17];
+  __shared__ E xs[32][17];
+  __shared__ E gs[32][17];
   const bool bias = tap == ks * ks;
   if (bias && k0 != 0) return;
   const int dy = bias ? 0 : tap / ks - r, dx = bias ? 0 : tap % ks - r;
-  double acc = 0;
+  E acc = 0;
   for (int64_t p0 = pb; p0 < pe; p0 += 32) {
     for (int e = threadIdx.x; e < 512; e += PW_THREADS) {
       const int p = e >> 4, c = e & 15;
       const int64_t px = p0 + p;
-      double xv = 0, gv = 0;
+      E xv = 0, gv = 0;
       if (px < pe) {
         const int x = (int)(px % W);
         const int y = (int)((px / W) % H);
         const int64_t b = px / ((int64_t)W * H);
-        if (n0 + c < N) gv = (double)g[px * N + n0 + c];
+        if (n0 + c < N) gv = g[px * N + n0 + c];
         const int k = k0 + c;
         if (bias) {
-          xv = 1.0;
+          xv = E(1);
         } else if (k < K) {
           const int yy = y + dy, xx = x + dx;
           if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
             const int64_t q = (b * H + yy) * W + xx;
-            xv = (double)(k < C0 ? in0[q * C0 + k] : in1[q * C1 + (k - C0)]);
+            xv = k < C0 ? in0[q * C0 + k] : in1[q * C1 + (k - C0)];
           }
         }
       }
@@ -557,9 +558,9 @@ __global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const E* __restrict__ in0
   const int k = k0 + tk, n = n0 + tn;
   if (n >= N) return;
   if (bias) {
-    if (tk == 0) bpartial[(int64_t)split * N + n] = acc;
+    if (tk == 0) bpartial[(int64_t)split * N + n] = (double)acc;
   } else if (k < K) {
-    partial[(((int64_t)split * ks * ks + tap) * K + k) * N + n] = acc;
+    partial[(((int64_t)split * ks * ks + tap) * K + k) * N + n] = (double)acc;
   }
 }
 
