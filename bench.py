@@ -88,6 +88,23 @@ def load_weights(path, segments):
     return synth.kaiming_uniform_params(segments, 42), "seeded Kaiming-uniform (untrained)"
 
 
+def network_name(kind):
+    """The network kind, named."""
+    if kind == 1:
+        return "kind 1: the paper's U-Net (5 inputs incl. PML sigma, 32 channels, 8x8 stride-2 convs, PReLU)"
+    return "kind 0: 3-input 16/32/64/128 U-Net (3x3 convs, ReLU)"
+
+
+def oracle_precond(theta, prob):
+    """The oracle's FP64 network application z = M(v) for one right-hand side of `prob`."""
+    from oracle import unet as ou
+    from oracle import unet_paper as oup
+    if theta.size == oup.param_count():
+        return lambda v: oup.precondition(theta, v.reshape(1, prob.Ny, prob.Nx), prob.c, prob.p, prob.h,
+                                          prob.omega)[0].ravel()
+    return lambda v: ou.precondition(theta, v.reshape(1, prob.Ny, prob.Nx), prob.c, prob.h)[0].ravel()
+
+
 def workload(nrhs, seed_offset=0):
     from paper_2607_16906_b300 import synth
     return synth.fine_multi_rhs_problem(seed=3000 + seed_offset, nrhs=nrhs)
@@ -145,9 +162,8 @@ def cpu_oracle_iteration_time(prob, theta, iters=5, basis=256):
     oracle's CGS2 arithmetic (two passes h = V^H w, w -= V h) on `basis` unit vectors."""
     from oracle import fgmres as fg
     from oracle import helmholtz as hz
-    from oracle import unet as ou
     A = hz.assemble(prob.c, prob.p, prob.h, prob.omega)
-    pre = lambda v: ou.precondition(theta, v.reshape(1, prob.Ny, prob.Nx), prob.c, prob.h)[0].ravel()
+    pre = oracle_precond(theta, prob)
     t0 = time.perf_counter()
     fg.cycle(lambda u: A @ u, pre, prob.b[0].ravel(), iters, 0.0)
     t_cycle = time.perf_counter() - t0
@@ -173,12 +189,13 @@ def splu_seconds(prob):
     return time.perf_counter() - t0
 
 
-def bench_config(args, wdesc, world):
+def bench_config(args, wdesc, world, kind):
     """The workload description both arms print."""
     return {"workload": "fine-grid multi-RHS: 512^2+32 PML (576^2), 32 point-source RHS, skull ring",
             "nrhs": args.nrhs, "rhs_per_call": max(1, min(args.rhs_batch, args.nrhs)), "m": args.m,
             "max_outer": args.max_outer, "orth": args.orth, "tol": 1e-6, "inner_tol": args.inner_tol, "ppw": 10,
-            "weights": wdesc, "l2": "inputs and Krylov basis (GBs) larger than L2",
+            "weights": wdesc, "network": network_name(kind),
+            "l2": "inputs and Krylov basis (GBs) larger than L2",
             "parallelism": f"replicas x{world}"}
 
 
@@ -187,6 +204,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import unet as ou
+    from oracle import unet_paper as oup
     prob = workload(args.nrhs)
     theta, wdesc = load_weights(args.weights, ou.param_segments())
     times = []
@@ -200,7 +218,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_it * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": bench_config(args, wdesc, 1),
+            "config": bench_config(args, wdesc, 1, 1 if theta.size == oup.param_count() else 0),
             "cpu_baseline": {"value": val, "unit": "solves/s", "cores": cores, "kind": "oracle",
                              "sample": f"2 FGMRES iterations of one RHS per step (numpy FP64 U-Net, CSR stencil, "
                                        f"CGS2 at the mean basis {args.m // 2}), extrapolated by {REF_ITERS_PER_SOLVE} "
@@ -239,8 +257,9 @@ def small_configuration(helm, theta_trained):
     prob = synth.small_problem(seed=1000)
     spec = helm.SystemSpec(prob.nx, prob.ny, prob.h, prob.p, prob.omega)
     ctx = helm.Context([spec], torch.tensor(prob.c.ravel(), device="cuda"))
-    seeded = helm.UNet(synth.kaiming_uniform_params(helm.weight_segments(), 42))
     trained = helm.UNet(theta_trained)
+    segs = helm.weight_segments() if trained.kind == 0 else helm.paper_weight_segments()
+    seeded = helm.UNet(synth.kaiming_uniform_params(segs, 42), kind=trained.kind)
     # (network, options, timed repetitions): the slow FP64 runs once (after a short warm-up solve)
     runs = {"plain_fp64_seeded_net": (seeded, dict(m=30, tol=1e-6, mixed=False, max_restarts=100, orth="dcgs2"), 1),
             "plain_fp64_trained_net": (trained, dict(m=30, tol=1e-6, mixed=False, max_restarts=100, orth="dcgs2"), 1),
@@ -641,7 +660,7 @@ def run_cuda(args):
         line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "c64/bf16 (f64 refinement)", "data": "synthetic",
-                "config": bench_config(args, wdesc, world),
+                "config": bench_config(args, wdesc, world, net.kind),
                 "converged": converged, "columns": args.steps * nrhs * world,
                 "mean_iters_per_solve": mean_iters,
                 "relres_true_max": max(c["relres_true"] for c in infos) if infos else None,

@@ -280,6 +280,15 @@ def helm_unet_param_count() -> int:
     return int(_lib.helm_unet_param_count())
 
 
+def network_kind(nparams: int) -> int:
+    """The network kind whose parameter count is `nparams` (helm_unet_param_count_kind: the two
+    kinds differ in size); ValueError if neither matches."""
+    for kind in (0, 1):
+        if int(_lib.helm_unet_param_count_kind(kind)) == int(nparams):
+            return kind
+    raise ValueError(f"{nparams} parameters match no network kind")
+
+
 def helm_unet_layers():
     """[(c_in, c_out, kind)] with kind 0 = 3x3 conv, 1 = 2x2 up-conv, 2 = 1x1 conv, in parameter order."""
     out = []
@@ -320,8 +329,11 @@ class UNet:
     """helm_unet_create(_kind) / helm_unet_destroy: network weights (FP64 master) and optimiser state.
     kind 0: the 16/32/64/128 U-Net; kind 1: the paper's variant (include/helm.h)."""
 
-    def __init__(self, weights: np.ndarray, kind: int = 0):
+    def __init__(self, weights: np.ndarray, kind=None):
+        """kind None: taken from the number of weights (network_kind)."""
         w = np.ascontiguousarray(weights, dtype=np.float64)
+        if kind is None:
+            kind = network_kind(w.size)
         self._h = _P()
         _check(_lib.helm_unet_create_kind(ct.byref(self._h), int(kind),
                                           w.ctypes.data_as(ct.POINTER(ct.c_double)), w.size))
