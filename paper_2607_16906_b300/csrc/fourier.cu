@@ -6,13 +6,17 @@
 // on the periodic N_x x N_y grid that includes the PML, with the node stretch factors s = 1 + i sigma /
 // omega of eq. 2 (the same nodes the 5-point operator uses).  Grid sides are powers of two, 16..1024.
 //
-// Two passes, each one read of its inputs and one write, with every FFT in shared memory:
-//   x pass: one block per grid row: DIF forward FFT (natural order in, bit-reversed out), multiply by
+// Two passes, each one read of its inputs and one write:
+//   x pass: DIF forward FFT of a grid row (natural order in, bit-reversed out), multiply by
 //           i kappa / N at the bit-reversed position, DIT inverse FFT (bit-reversed in, natural out),
 //           scale by 1/s_x, the same again -> t_x, written to y;
-//   y pass: one block per 16 (FP32) or 8 (FP64) columns, the whole column height in shared memory
-//           (128-byte row segments, coalesced), the same derivative pair along y -> t_y; then
-//           y = -(t_x + t_y) - k^2 u.
+//   y pass: the same derivative pair along the columns -> t_y; then y = -(t_x + t_y) - k^2 u.
+// FP32 with sides of 32 or more: one warp transforms one line held in registers (lane l, register r
+// hold element l + 32 r): an in-register E-point FFT over r (E = N / 32), the twiddles of the
+// N = 32 E split, and a 32-point FFT across the lanes by shuffles; the x pass reads its rows straight
+// into registers, the y pass stages 8 columns of the whole height in shared memory (64-byte row
+// segments, a padded pitch so the column reads are free of bank conflicts).  FP64 and sides of 16:
+// block-wide radix-2 FFTs in shared memory (one block per row; 16 (FP32) or 8 (FP64) columns).
 // Twiddle tables exp(-2 pi i t / N), t < N/2, are computed once per grid side on the host in FP64
 // and staged into shared memory by every block.  HBM traffic per point: x pass 16 B (FP32), y pass
 // 8 (u) + 8 (t_x) + 8 (u again) + 4 (k^2) + 8 (y) = 36 B: 52 B per point and right-hand side.
@@ -149,6 +153,225 @@ __global__ void __launch_bounds__(FY_THREADS) k_fourier_y(const C<R>* __restrict
   }
 }
 
+// ------------------------------------------------------------------ warp-register FFTs (FP32)
+
+// W_N^t for 0 <= t < N from the half table tw (W_N^(t + N/2) = -W_N^t).
+template <int N>
+__device__ __forceinline__ float2 tw_full(const float2* tw, int t) {
+  const float2 w = tw[t & (N / 2 - 1)];
+  return t & (N / 2) ? make_float2(-w.x, -w.y) : w;
+}
+
+template <int E>
+__device__ __forceinline__ int brev_e(int r) {
+  int o = 0;
+#pragma unroll
+  for (int b = 1, c = E >> 1; b < E; b <<= 1, c >>= 1)
+    if (r & b) o |= c;
+  return o;
+}
+
+__device__ __forceinline__ float2 shfl_x(float2 v, int h) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, h), __shfl_xor_sync(0xffffffffu, v.y, h));
+}
+
+// Forward DFT of the N = 32 E points a (lane l, register r: point l + 32 r) without scaling; on exit
+// position n holds X[brev_L(n)], L = log2 N.  tw: W_N^t, t < N/2.
+template <int E>
+__device__ __forceinline__ void warp_fft_fwd(float2 (&a)[E], const float2* tw, int lane) {
+  constexpr int N = 32 * E;
+  // E-point DIF over the registers (W_E^m = W_N^(32 m)): register r ends with frequency brev_e(r)
+#pragma unroll
+  for (int half = E / 2; half >= 1; half >>= 1) {
+#pragma unroll
+    for (int i = 0; i < E / 2; ++i) {
+      const int k = i % half, i0 = (i / half) * 2 * half + k, i1 = i0 + half;
+      const float2 x0 = a[i0], x1 = a[i1];
+      a[i0] = cadd(x0, x1);
+      a[i1] = k == 0 ? csub(x0, x1) : cmul(csub(x0, x1), tw[32 * k * (E / (2 * half))]);
+    }
+  }
+  // twiddles of the split: W_N^(lane k1)
+#pragma unroll
+  for (int r = 1; r < E; ++r) a[r] = cmul(a[r], tw_full<N>(tw, lane * brev_e<E>(r)));
+  // 32-point DIF across the lanes (W_32^m = W_N^(E m)): lane l ends with frequency brev_5(l)
+#pragma unroll
+  for (int h = 16; h >= 1; h >>= 1) {
+    const bool upper = lane & h;
+    const float2 w = tw[(lane & (h - 1)) * (16 / h) * E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const float2 p = shfl_x(a[r], h);
+      a[r] = upper ? cmul(csub(p, a[r]), w) : cadd(a[r], p);
+    }
+  }
+}
+
+// Inverse of warp_fft_fwd (conjugate twiddles, no 1/N): position n holds the spectrum at brev_L(n) on
+// entry, point n in natural order on exit.
+template <int E>
+__device__ __forceinline__ void warp_fft_inv(float2 (&a)[E], const float2* tw, int lane) {
+  constexpr int N = 32 * E;
+#pragma unroll
+  for (int h = 1; h <= 16; h <<= 1) {
+    const bool upper = lane & h;
+    const float2 w = cconj(tw[(lane & (h - 1)) * (16 / h) * E]);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const float2 t = upper ? cmul(a[r], w) : a[r];
+      const float2 p = shfl_x(t, h);
+      a[r] = upper ? csub(p, t) : cadd(t, p);
+    }
+  }
+#pragma unroll
+  for (int r = 1; r < E; ++r) a[r] = cmul(a[r], cconj(tw_full<N>(tw, lane * brev_e<E>(r))));
+#pragma unroll
+  for (int half = 1; half < E; half <<= 1) {
+#pragma unroll
+    for (int i = 0; i < E / 2; ++i) {
+      const int k = i % half, i0 = (i / half) * 2 * half + k, i1 = i0 + half;
+      const float2 x0 = a[i0];
+      const float2 x1 = k == 0 ? a[i1] : cmul(a[i1], cconj(tw[32 * k * (E / (2 * half))]));
+      a[i0] = cadd(x0, x1);
+      a[i1] = csub(x0, x1);
+    }
+  }
+}
+
+// t = (1/s) D((1/s) D t) on one line held by the warp; inv_s[n] = 1/s at point n.
+template <int E>
+__device__ __forceinline__ void warp_derivative_pair(float2 (&a)[E], const float2* tw, const float2* inv_s,
+                                                     float two_pi_over_L, int lane) {
+  constexpr int N = 32 * E;
+  constexpr int LOGN = 5 + (E >= 2) + (E >= 4) + (E >= 8) + (E >= 16) + (E >= 32);
+#pragma unroll
+  for (int rep = 0; rep < 2; ++rep) {
+    warp_fft_fwd<E>(a, tw, lane);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+      const int q = (int)(__brev((unsigned)(lane + 32 * r)) >> (32 - LOGN));
+      const float c = q == N / 2 ? 0.0f : (float)(q < N / 2 ? q : q - N) * two_pi_over_L / (float)N;
+      a[r] = make_float2(-c * a[r].y, c * a[r].x);
+    }
+    warp_fft_inv<E>(a, tw, lane);
+#pragma unroll
+    for (int r = 0; r < E; ++r) a[r] = cmul(a[r], inv_s[lane + 32 * r]);
+  }
+}
+
+constexpr int FW_WARPS = 8;  // lines per block
+
+// x pass, FP32, Nx = 32 E: warp w of block b transforms line b * 8 + w of the (rhs, row) lines.
+template <int E>
+__global__ void __launch_bounds__(FW_WARPS * 32) k_fourier_xw(const float2* __restrict__ u, float2* __restrict__ tx,
+                                                             const float2* __restrict__ prof,
+                                                             const float2* __restrict__ tw_g, int Ny, int nlines,
+                                                             int64_t rhs_stride, float two_pi_over_L) {
+  constexpr int N = 32 * E;
+  __shared__ float2 tw[N / 2];
+  __shared__ float2 inv_s[N];
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float2 s = prof[i];
+    const float d = s.x * s.x + s.y * s.y;
+    inv_s[i] = make_float2(s.x / d, -s.y / d);
+    if (i < N / 2) tw[i] = tw_g[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int line = blockIdx.x * FW_WARPS + (threadIdx.x >> 5);
+  if (line >= nlines) return;  // whole warps leave; no block-wide barrier follows
+  const int rhs = line / Ny, row = line % Ny;
+  const int64_t base = rhs * rhs_stride + (int64_t)row * N;
+  float2 a[E];
+#pragma unroll
+  for (int r = 0; r < E; ++r) a[r] = u[base + lane + 32 * r];
+  warp_derivative_pair<E>(a, tw, inv_s, two_pi_over_L, lane);
+#pragma unroll
+  for (int r = 0; r < E; ++r) tx[base + lane + 32 * r] = a[r];
+}
+
+constexpr int FYW_COLS = 8;                 // columns per block (one warp each)
+constexpr int FYW_PITCH = FYW_COLS + 1;     // padded row pitch of the shared column slab
+
+// y pass, FP32, Ny = 32 E: one block per (8 columns, rhs); y holds t_x on entry and A_F u on exit.
+template <int E>
+__global__ void __launch_bounds__(FYW_COLS * 32, E >= 32 ? 1 : 2) k_fourier_yw(const float2* __restrict__ u, float2* __restrict__ y,
+                                                                const float* __restrict__ k2,
+                                                                const float2* __restrict__ prof,
+                                                                const float2* __restrict__ tw_g, int Nx,
+                                                                int64_t rhs_stride, float two_pi_over_L) {
+  constexpr int N = 32 * E;
+  extern __shared__ __align__(16) unsigned char fyw_smem[];
+  float2* slab = (float2*)fyw_smem;       // [N][FYW_PITCH]
+  float2* tw = slab + N * FYW_PITCH;       // [N / 2]
+  float2* inv_s = tw + N / 2;              // [N]
+  const int x0 = blockIdx.x * FYW_COLS, rhs = blockIdx.y;
+  const int64_t base = rhs * rhs_stride + x0;
+  const int cols = min(FYW_COLS, Nx - x0);
+  for (int e = threadIdx.x; e < N * FYW_COLS; e += blockDim.x) {
+    const int j = e / FYW_COLS, c = e % FYW_COLS;
+    if (c < cols) slab[j * FYW_PITCH + c] = u[base + (int64_t)j * Nx + c];
+  }
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const float2 s = prof[i];
+    const float d = s.x * s.x + s.y * s.y;
+    inv_s[i] = make_float2(s.x / d, -s.y / d);
+    if (i < N / 2) tw[i] = tw_g[i];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
+  if (c < cols) {
+    float2 a[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) a[r] = slab[(lane + 32 * r) * FYW_PITCH + c];
+    warp_derivative_pair<E>(a, tw, inv_s, two_pi_over_L, lane);
+#pragma unroll
+    for (int r = 0; r < E; ++r) slab[(lane + 32 * r) * FYW_PITCH + c] = a[r];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < N * FYW_COLS; e += blockDim.x) {
+    const int j = e / FYW_COLS, cc = e % FYW_COLS;
+    if (cc >= cols) continue;
+    const int64_t q = base + (int64_t)j * Nx + cc;
+    const int64_t pt = (int64_t)j * Nx + x0 + cc;
+    const float2 uv = u[q];
+    const float kk = k2[pt];
+    const float2 t = cadd(y[q], slab[j * FYW_PITCH + cc]);
+    y[q] = make_float2(-t.x - kk * uv.x, -t.y - kk * uv.y);
+  }
+}
+
+template <int E>
+static void launch_fourier_w(int axis, const float2* x, float2* y, const float* k2, const float2* pr,
+                             const float2* tw, int Nx, int Ny, int nrhs, int64_t n, float tpl, cudaStream_t st) {
+  constexpr int N = 32 * E;
+  if (axis == 0) {
+    const int nlines = Ny * nrhs;
+    launch(k_fourier_xw<E>, (nlines + FW_WARPS - 1) / FW_WARPS, FW_WARPS * 32, 0, st, x, y, pr, tw, Ny, nlines, n,
+           tpl);
+  } else {
+    const size_t sm = sizeof(float2) * ((size_t)N * FYW_PITCH + N / 2 + N);
+    cudaFuncSetAttribute(k_fourier_yw<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    launch(k_fourier_yw<E>, dim3((Nx + FYW_COLS - 1) / FYW_COLS, nrhs), FYW_COLS * 32, sm, st, x, y, k2, pr, tw, Nx,
+           n, tpl);
+  }
+}
+
+// FP32 warp-register pass along one axis (0: x, 1: y) for a side of 32..1024; false if the side is
+// outside that range (the block-wide kernels serve it).
+static bool fourier_warp_pass(int axis, int side, const float2* x, float2* y, const float* k2, const float2* pr,
+                              const float2* tw, int Nx, int Ny, int nrhs, int64_t n, float tpl, cudaStream_t st) {
+  switch (side) {
+    case 32: launch_fourier_w<1>(axis, x, y, k2, pr, tw, Nx, Ny, nrhs, n, tpl, st); return true;
+    case 64: launch_fourier_w<2>(axis, x, y, k2, pr, tw, Nx, Ny, nrhs, n, tpl, st); return true;
+    case 128: launch_fourier_w<4>(axis, x, y, k2, pr, tw, Nx, Ny, nrhs, n, tpl, st); return true;
+    case 256: launch_fourier_w<8>(axis, x, y, k2, pr, tw, Nx, Ny, nrhs, n, tpl, st); return true;
+    case 512: launch_fourier_w<16>(axis, x, y, k2, pr, tw, Nx, Ny, nrhs, n, tpl, st); return true;
+    case 1024: launch_fourier_w<32>(axis, x, y, k2, pr, tw, Nx, Ny, nrhs, n, tpl, st); return true;
+    default: return false;
+  }
+}
+
 // ------------------------------------------------------------------ host side
 
 static int log2_exact(int n) {
@@ -196,6 +419,8 @@ static helm_status twiddles(int N, const double2** d, const float2** f) {
   return HELM_OK;
 }
 
+template <typename R> struct fp64_t { static constexpr bool v = sizeof(R) == 8; };
+
 template <typename R>
 static helm_status fourier_op(helm_ctx* ctx, const C<R>* x, C<R>* y, int nrhs, cudaStream_t st) {
   constexpr int TC = FyCols<R>::v;
@@ -219,10 +444,19 @@ static helm_status fourier_op(helm_ctx* ctx, const C<R>* x, C<R>* y, int nrhs, c
     const size_t smy = sizeof(C<R>) * ((size_t)s.Ny * TC + s.Ny / 2 + s.Ny);
     if (smy > 48 * 1024) HELM_CK(cudaFuncSetAttribute(k_fourier_y<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smy));
     const R tpl_x = (R)(2.0 * M_PI / (s.Nx * s.h)), tpl_y = (R)(2.0 * M_PI / (s.Ny * s.h));
-    launch(k_fourier_x<R>, dim3(s.Ny, nrhs), std::min(FX_THREADS, s.Nx / 2), smx, st, xs, ys, pr + s.prof_x, tw_x,
-           s.Nx, log2_exact(s.Nx), s.Ny, (int64_t)s.n, tpl_x);
-    launch(k_fourier_y<R>, dim3(s.Nx / TC, nrhs), FY_THREADS, smy, st, xs, ys, k2, pr + s.prof_y, tw_y, s.Nx, s.Ny,
-           log2_exact(s.Ny), (int64_t)s.n, tpl_y);
+    bool wx = false, wy = false;
+    if constexpr (!fp64_t<R>::v) {
+      wx = fourier_warp_pass(0, s.Nx, xs, ys, k2, pr + s.prof_x, tw_x, s.Nx, s.Ny, nrhs, (int64_t)s.n, tpl_x, st);
+    }
+    if (!wx)
+      launch(k_fourier_x<R>, dim3(s.Ny, nrhs), std::min(FX_THREADS, s.Nx / 2), smx, st, xs, ys, pr + s.prof_x, tw_x,
+             s.Nx, log2_exact(s.Nx), s.Ny, (int64_t)s.n, tpl_x);
+    if constexpr (!fp64_t<R>::v) {
+      wy = fourier_warp_pass(1, s.Ny, xs, ys, k2, pr + s.prof_y, tw_y, s.Nx, s.Ny, nrhs, (int64_t)s.n, tpl_y, st);
+    }
+    if (!wy)
+      launch(k_fourier_y<R>, dim3(s.Nx / TC, nrhs), FY_THREADS, smy, st, xs, ys, k2, pr + s.prof_y, tw_y, s.Nx, s.Ny,
+             log2_exact(s.Ny), (int64_t)s.n, tpl_y);
   }
   HELM_CK_LAUNCH();
   return HELM_OK;
