@@ -297,6 +297,28 @@ HELM_API int helm_tuned_tiles(int* out, int max_entries);
  * Pointers 16-byte aligned; B, H, W >= 1.  Asynchronous on `stream`.  HELM_ERR_INVALID_ARG when
  * the tcgen05 path is unavailable on the current device. */
 #define HELM_LAYER_DEC1B_FINAL 17
+
+/* One layer of network kind 1 (the paper's variant, see helm_unet_create_kind) in the BF16 path,
+ * exactly as helm_precond_apply runs it (tcgen05, BF16 operands, FP32 accumulation, bias and PReLU
+ * in FP32, BF16 output), on caller-owned NHWC BF16 device tensors; a test and diagnostic aid with no
+ * paper counterpart.  H x W is the layer's 5x5 GEMM grid: the output grid of an encoder layer, the
+ * input grid of a decoder layer.
+ *   layer 0:    enc1 (Tab. 2: 8x8, stride 2, pad 3, PReLU).  in0: the network input packed
+ *               space-to-depth, [B][H][W][32], channel (2 (y % 2) + x % 2) * 8 + c holding input
+ *               channel c (5 used of 8) of pixel (y, x) of the 2H x 2W grid.  out: [B][H][W][32].
+ *   layer 1..3: enc2..enc4.  in0: the previous encoder output [B][2H][2W][32].  out: [B][H][W][32].
+ *   layer 4:    dec3 (8x8 transposed, stride 2, pad 3, PReLU).  in0: [B][H][W][32].  out: [B][2H][2W][32].
+ *   layer 5..7: dec2..dec0 on the concatenation [in0, in1], both [B][H][W][32] (in1: the skip
+ *               connection).  out: [B][2H][2W][32].
+ *   HELM_PAPER_LAYER_DEC0_FINAL: dec0 with the output layer (1x1 conv 32 -> 2 on the BF16
+ *               activation) fused into its epilogue, written as FP32 pairs out[B][2H][2W][2] (scale 1).
+ * in1 must be NULL except for layers 5..7.  Pointers 16-byte aligned; B, H, W >= 1, B H W <= 2^29.
+ * Asynchronous on `stream`; a pipeline timeout is reported by the next solve or by the network's
+ * error check.  HELM_ERR_INVALID_ARG for another network kind or where the tcgen05 path is
+ * unavailable. */
+#define HELM_PAPER_LAYER_DEC0_FINAL 8
+HELM_API helm_status helm_paper_layer_forward(const helm_unet* net, int layer, const void* in0, const void* in1,
+                                              void* out, int B, int H, int W, void* stream);
 HELM_API helm_status helm_unet_layer_forward(const helm_unet* net, int layer, int variant, const void* in0,
                                              const void* in1, void* out, int B, int H, int W, int* ry_out,
                                              void* stream);

@@ -41,6 +41,17 @@ struct ConvTcArgs {
   int* err;               // device error code (0 = ok)
   long long budget;       // clock64 cycles a pipeline wait may take before the kernel gives up
   int skip_first;         // failure injection: CTA 0 issues no loads for its first tile
+  // MODE 0: source 0 is an NHWC tensor of the 2H x 2W grid read as its space-to-depth view (channel
+  // chunk kc = input row phase; the map's rows are traversed with stride 2)
+  int s2d;
+  // MODE 2 only, optional: the network's 1x1 output layer C_out -> 2 fused into the epilogue:
+  // z[b][Y][X] = out_scale[b] (wf^T a + bf) for the output pixels inside the physical Nx x Ny grid, no
+  // activation stored
+  const float* wf;        // [C_out][2] weights, then the 2 biases
+  const double* out_scale;  // per image; null: scale 1
+  float2* z;
+  int Nx, Ny;
+  int64_t zstride;
 };
 
 template <int N, int CHUNK, int MODE, int KS>
@@ -141,7 +152,10 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
 #pragma unroll
             for (int t = 0; t < TPS; ++t) {
               const int tap = tg * TPS + t;
-              if (MODE != 1)
+              if (MODE == 0 && a.s2d)
+                tma_load_4d(sa + t * Cfg::A_BYTES, src, &full[stage], 0, x0 + tap % KS - KS / 2,
+                            2 * (y0 + tap / KS - KS / 2) + kc, b);
+              else if (MODE != 1)
                 tma_load_4d(sa + t * Cfg::A_BYTES, src, &full[stage], c0, x0 + tap % KS - KS / 2,
                             y0 + tap / KS - KS / 2, b);
               else
@@ -228,12 +242,34 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       int y = (r / a.tiles_x) * 8 + ly, x = (r % a.tiles_x) * 16 + lx;
       bool inside = y < a.H && x < a.W;
       constexpr int COUT = MODE == 0 ? N : N / 4;
+      const bool fused = MODE == 2 && a.z != nullptr;
+      float f0 = 0.0f, f1 = 0.0f;
 #pragma unroll
       for (int cb = 0; cb < N / 16; ++cb) {
         uint32_t v[16];
         tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + acc * N + cb * 16, v);
         tmem_ld_wait();
-        if (inside) {
+        if (fused && inside) {
+          // the output layer on the BF16-rounded activation of output phase `tap`, channels in order
+          const int tap = (cb * 16) / COUT, co0 = (cb * 16) % COUT;
+          if (co0 == 0) {
+            f0 = a.wf[2 * COUT];
+            f1 = a.wf[2 * COUT + 1];
+          }
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            float f = __uint_as_float(v[k]) + a.bias[cb * 16 + k];
+            f = f > 0.0f ? f : a.slope * f;
+            const float h = __bfloat162float(__float2bfloat16_rn(f));
+            f0 += h * a.wf[2 * (co0 + k)];
+            f1 += h * a.wf[2 * (co0 + k) + 1];
+          }
+          const int Y = 2 * y + tap / 2, X = 2 * x + tap % 2;
+          if (co0 + 16 == COUT && Y < a.Ny && X < a.Nx) {
+            const double sc = a.out_scale ? a.out_scale[b] : 1.0;
+            a.z[b * a.zstride + (int64_t)Y * a.Nx + X] = make_float2((float)(f0 * sc), (float)(f1 * sc));
+          }
+        } else if (inside && !fused) {
           const int tap = (cb * 16) / COUT, co0 = (cb * 16) % COUT;
           int64_t opix = MODE == 0 ? (((int64_t)b * a.H + y) * a.W + x)
                                    : (((int64_t)b * 2 * a.H + 2 * y + tap / 2) * (2 * a.W) + 2 * x + tap % 2);
@@ -332,6 +368,16 @@ struct TcState {
 
 static int tc_chunk(int cin_pad) { return cin_pad >= 64 ? 64 : cin_pad; }
 
+// The tcgen05 kernels can run: the tensor-map encoder is reachable and the current device is sm_103.
+bool tc_available() {
+  if (!encode_fn()) return false;
+  int dev = 0, major = 0, minor = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  return major == 10 && minor == 3;
+}
+
 static bool tc_disabled_by_env() {
   const char* e = getenv("HELM_DISABLE_TC");
   return e && e[0] == '1';
@@ -424,6 +470,23 @@ static helm_status act_map(CUtensorMap* m, const void* ptr, int C, int B, int H,
   return HELM_OK;
 }
 
+// The space-to-depth view of an NHWC BF16 tensor [B][2H][2W][C] on the H x W grid: one box is the
+// 8 x 16 patch of one row phase, each pixel's 2C values being its two column phases (contiguous in
+// memory); the map's rows are the source's rows, traversed with stride 2 from 2 Y + phase.
+static helm_status act_map_s2d(CUtensorMap* m, const void* ptr, int chunk, int B, int H, int W) {
+  const int C = chunk / 2;
+  cuuint64_t dims[4] = {(cuuint64_t)chunk, (cuuint64_t)W, (cuuint64_t)(2 * H), (cuuint64_t)B};
+  cuuint64_t strides[3] = {(cuuint64_t)chunk * 2, (cuuint64_t)2 * W * C * 2, (cuuint64_t)4 * H * W * C * 2};
+  cuuint32_t box[4] = {(cuuint32_t)chunk, 16, 16, 1};
+  cuuint32_t es[4] = {1, 1, 2, 1};
+  CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(chunk), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(HELM_ERR_CUDA, "cuTensorMapEncodeTiled (space-to-depth view) failed: " + std::to_string((int)r));
+  return HELM_OK;
+}
+
 static helm_status weight_map(CUtensorMap* m, const void* ptr, int N, int chunk, int nk, int taps = 9) {
   cuuint64_t dims[3] = {(cuuint64_t)chunk, (cuuint64_t)N, (cuuint64_t)(taps * nk)};
   cuuint64_t strides[2] = {(cuuint64_t)chunk * 2, (cuuint64_t)N * chunk * 2};
@@ -485,7 +548,7 @@ static helm_status conv_tc_box(const helm_unet* net, int l, const void* in0, int
     m1 = m0;
   const int nk = (C0 + C1) / chunk;
   HELM_TRY(weight_map(&mw, S.w[l], d.cout, chunk, nk));
-  ConvTcArgs a;
+  ConvTcArgs a{};
   a.B = B;
   a.H = H;
   a.W = W;
@@ -548,7 +611,7 @@ helm_status conv_tc_up(const helm_unet* net, int l, const void* in, void* out, i
   CUtensorMap m0, mw;
   HELM_TRY(act_map(&m0, in, d.cin, B, Hi, Wi, chunk));
   HELM_TRY(weight_map(&mw, S.w[l], 4 * d.cout, chunk, nk, 1));
-  ConvTcArgs a;
+  ConvTcArgs a{};
   a.B = B;
   a.H = Hi;
   a.W = Wi;
@@ -577,17 +640,23 @@ helm_status conv_tc_up(const helm_unet* net, int l, const void* in, void* out, i
 // the 2H x 2W grid), inputs NHWC BF16 from one or two sources, epilogue bias + activation `act`.
 helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* err, int ks, int mode, int N,
                             int chunk, const void* in0, int C0, const void* in1, int C1, void* out, int B, int H,
-                            int W, int act, float slope, cudaStream_t st) {
+                            int W, int act, float slope, cudaStream_t st, bool s2d0, const RowFinal* fin) {
   if (C0 % chunk || C1 % chunk) return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: channels not a chunk multiple");
+  if (s2d0 && (mode != 0 || C1 != 0 || C0 != 2 * chunk))
+    return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: the space-to-depth view needs one source of two row phases");
+  if (fin && mode != 2) return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: the fused output layer needs mode 2");
   CUtensorMap m0, m1, mw;
-  HELM_TRY(act_map(&m0, in0, C0, B, H, W, chunk));
+  if (s2d0)
+    HELM_TRY(act_map_s2d(&m0, in0, chunk, B, H, W));
+  else
+    HELM_TRY(act_map(&m0, in0, C0, B, H, W, chunk));
   if (C1 > 0)
     HELM_TRY(act_map(&m1, in1, C1, B, H, W, chunk));
   else
     m1 = m0;
   const int nk = (C0 + C1) / chunk;
   HELM_TRY(weight_map(&mw, w_tc, N, chunk, nk, ks * ks));
-  ConvTcArgs a;
+  ConvTcArgs a{};
   a.B = B;
   a.H = H;
   a.W = W;
@@ -603,6 +672,13 @@ helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* e
   a.err = err;
   a.budget = wait_budget();
   a.skip_first = take_fault(HELM_FAULT_CONV_TILE) ? 1 : 0;
+  a.s2d = s2d0 ? 1 : 0;
+  a.wf = fin ? fin->wf : nullptr;
+  a.out_scale = fin ? fin->out_scale : nullptr;
+  a.z = fin ? fin->z : nullptr;
+  a.Nx = fin ? fin->Nx : 0;
+  a.Ny = fin ? fin->Ny : 0;
+  a.zstride = fin ? fin->zstride : 0;
   const int key = ks * 1000000 + mode * 100000 + N * 100 + chunk;
   switch (key) {
     case 5000000 + 32 * 100 + 32: return launch_tc<32, 32, 0, 5>(m0, m1, mw, a, st);

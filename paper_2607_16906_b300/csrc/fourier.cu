@@ -194,8 +194,9 @@ __device__ __forceinline__ void warp_fft_fwd(float2 (&a)[E], const float2* tw, i
   // twiddles of the split: W_N^(lane k1)
 #pragma unroll
   for (int r = 1; r < E; ++r) a[r] = cmul(a[r], tw_full<N>(tw, lane * brev_e<E>(r)));
-  // 32-point DIF across the lanes (W_32^m = W_N^(E m)): lane l ends with frequency brev_5(l)
-#pragma unroll
+  // 32-point DIF across the lanes (W_32^m = W_N^(E m)): lane l ends with frequency brev_5(l); the
+  // stage loop stays rolled (its body takes any h) to keep the kernel's code small
+#pragma unroll 1
   for (int h = 16; h >= 1; h >>= 1) {
     const bool upper = lane & h;
     const float2 w = tw[(lane & (h - 1)) * (16 / h) * E];
@@ -212,7 +213,7 @@ __device__ __forceinline__ void warp_fft_fwd(float2 (&a)[E], const float2* tw, i
 template <int E>
 __device__ __forceinline__ void warp_fft_inv(float2 (&a)[E], const float2* tw, int lane) {
   constexpr int N = 32 * E;
-#pragma unroll
+#pragma unroll 1
   for (int h = 1; h <= 16; h <<= 1) {
     const bool upper = lane & h;
     const float2 w = cconj(tw[(lane & (h - 1)) * (16 / h) * E]);
@@ -244,7 +245,7 @@ __device__ __forceinline__ void warp_derivative_pair(float2 (&a)[E], const float
                                                      float two_pi_over_L, int lane) {
   constexpr int N = 32 * E;
   constexpr int LOGN = 5 + (E >= 2) + (E >= 4) + (E >= 8) + (E >= 16) + (E >= 32);
-#pragma unroll
+#pragma unroll 1
   for (int rep = 0; rep < 2; ++rep) {
     warp_fft_fwd<E>(a, tw, lane);
 #pragma unroll

@@ -31,7 +31,9 @@ namespace helm {
 
 helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* err, int ks, int mode, int N,
                             int chunk, const void* in0, int C0, const void* in1, int C1, void* out, int B, int H,
-                            int W, int act, float slope, cudaStream_t st);
+                            int W, int act, float slope, cudaStream_t st, bool s2d0, const RowFinal* fin);
+
+bool tc_available();
 
 enum PaperKind { P_DOWN = 0, P_UP = 1, P_OUT = 2 };
 struct PaperLayer {
@@ -179,7 +181,9 @@ void paper_release(helm_unet* net) {
 
 // ------------------------------------------------------------------ kernels of the forward pass
 
-// Input channels (Re s v, Im s v, c / 1500, Re sigma_c, Im sigma_c, 0, 0, 0) on the 16-padded grid.
+// Input channels (Re s v, Im s v, c / 1500, Re sigma_c, Im sigma_c, 0, 0, 0) on the 16-padded grid,
+// written straight into the space-to-depth layout of the first layer: pixel (y, x) is phase
+// (y % 2) * 2 + x % 2 of pixel (y / 2, x / 2), 8 channels per phase.
 template <typename T, typename R>
 __global__ void k_paper_pack(const C<R>* __restrict__ v, int64_t col_stride, const double* __restrict__ in_scale,
                              const double* __restrict__ chat, int64_t c_stride, const double2* __restrict__ px,
@@ -202,7 +206,7 @@ __global__ void k_paper_pack(const C<R>* __restrict__ v, int64_t col_stride, con
     ch[3] = sx.x * sy.x - sx.y * sy.y - 1.0;
     ch[4] = sx.x * sy.y + sx.y * sy.x;
   }
-  T* o = x0 + pix * P_X0_CH;
+  T* o = x0 + ((((int64_t)b * (Hp / 2) + y / 2) * (Wp / 2) + x / 2) * 4 + (y & 1) * 2 + (x & 1)) * P_X0_CH;
 #pragma unroll
   for (int k = 0; k < P_X0_CH; ++k) store_act(o + k, (typename Acc<T>::A)ch[k]);
 }
@@ -296,10 +300,11 @@ enum PaperAct { PA_X0 = 0, PA_S0, PA_E1, PA_S1, PA_E2, PA_S2, PA_E3, PA_S3, PA_E
 static helm_status paper_buffers(PaperNet& P, int B, int Hp, int Wp, bool fp64, void** a) {
   const size_t es = fp64 ? 8 : 2;
   const size_t full = (size_t)Hp * Wp;
-  // channels x pixels of each activation, in PaperAct order
-  const size_t el[13] = {P_X0_CH * full, 32 * full / 4, 32 * full / 4, 128 * full / 16, 32 * full / 16,
-                         128 * full / 64, 32 * full / 64, 128 * full / 256, 32 * full / 256, 32 * full / 64,
-                         32 * full / 16, 32 * full / 4, 32 * full};
+  // channels x pixels of each activation, in PaperAct order; the input is packed straight into S0, and
+  // the BF16 path reads S1..S3 through space-to-depth views and fuses the output layer (no D0)
+  const size_t el[13] = {0, 32 * full / 4, 32 * full / 4, fp64 ? 128 * full / 16 : 0, 32 * full / 16,
+                         fp64 ? 128 * full / 64 : 0, 32 * full / 64, fp64 ? 128 * full / 256 : 0, 32 * full / 256,
+                         32 * full / 64, 32 * full / 16, 32 * full / 4, fp64 ? 32 * full : 0};
   size_t need = 0;
   for (size_t v : el) need += (v * B * es + 255) / 256 * 256;
   PaperNet::Set& S = P.act[fp64 ? 1 : 0];
@@ -331,7 +336,7 @@ helm_status paper_precondition(helm_ctx* ctx, const helm_unet* net, int sys, con
   const int64_t npix = (int64_t)B * Hp * Wp;
   launch(k_paper_pack<T, R>, cdiv(npix, 256), 256, 0, st, v, s.n, in_scale, (const double*)(ctx->chat64 + s.off),
          (int64_t)0, (const double2*)(ctx->prof_d + s.prof_x), (const double2*)(ctx->prof_d + s.prof_y), s.Nx, s.Ny,
-         Hp, Wp, B, (T*)a[PA_X0]);
+         Hp, Wp, B, (T*)a[PA_S0]);
   HELM_CK_LAUNCH();
   auto s2d = [&](int src, int dst, int C, int H, int W) -> helm_status {  // H, W: source grid
     const int64_t n = (int64_t)B * (H / 2) * (W / 2) * 4 * C;
@@ -339,8 +344,10 @@ helm_status paper_precondition(helm_ctx* ctx, const helm_unet* net, int sys, con
     HELM_CK_LAUNCH();
     return HELM_OK;
   };
-  // one reformulated layer on the grid H x W (the GEMM's pixel grid)
-  auto layer = [&](int l, int src0, int C0, int src1, int C1, int dst, int H, int W) -> helm_status {
+  // one reformulated layer on the grid H x W (the GEMM's pixel grid); s2d0: source 0 is the 2H x 2W
+  // activation read through its space-to-depth view (BF16 path); fin: the output layer fused in
+  auto layer = [&](int l, int src0, int C0, int src1, int C1, int dst, int H, int W, bool s2d0 = false,
+                   const RowFinal* fin = nullptr) -> helm_status {
     const PaperLayer& L = kP[l];
     if constexpr (fp64) {
       dim3 grid(cdiv((int64_t)B * H * W, PC_THREADS), L.N / 16);
@@ -351,22 +358,41 @@ helm_status paper_precondition(helm_ctx* ctx, const helm_unet* net, int sys, con
       return HELM_OK;
     } else {
       return conv_tc_generic(P.wtc[l], P.b32[l], P.err, 5, L.kind == P_UP ? 2 : 0, L.N, L.chunk, a[src0], C0,
-                             src1 >= 0 ? a[src1] : nullptr, C1, a[dst], B, H, W, 2, (float)P.slope[l], st);
+                             src1 >= 0 ? a[src1] : nullptr, C1, dst >= 0 ? a[dst] : nullptr, B, H, W, 2,
+                             (float)P.slope[l], st, s2d0, fin);
     }
   };
   int H = Hp, W = Wp;
-  HELM_TRY(s2d(PA_X0, PA_S0, P_X0_CH, H, W));
   HELM_TRY(layer(0, PA_S0, 4 * P_X0_CH, -1, 0, PA_E1, H / 2, W / 2));
-  HELM_TRY(s2d(PA_E1, PA_S1, 32, H / 2, W / 2));
-  HELM_TRY(layer(1, PA_S1, 128, -1, 0, PA_E2, H / 4, W / 4));
-  HELM_TRY(s2d(PA_E2, PA_S2, 32, H / 4, W / 4));
-  HELM_TRY(layer(2, PA_S2, 128, -1, 0, PA_E3, H / 8, W / 8));
-  HELM_TRY(s2d(PA_E3, PA_S3, 32, H / 8, W / 8));
-  HELM_TRY(layer(3, PA_S3, 128, -1, 0, PA_E4, H / 16, W / 16));
+  if constexpr (fp64) {
+    HELM_TRY(s2d(PA_E1, PA_S1, 32, H / 2, W / 2));
+    HELM_TRY(layer(1, PA_S1, 128, -1, 0, PA_E2, H / 4, W / 4));
+    HELM_TRY(s2d(PA_E2, PA_S2, 32, H / 4, W / 4));
+    HELM_TRY(layer(2, PA_S2, 128, -1, 0, PA_E3, H / 8, W / 8));
+    HELM_TRY(s2d(PA_E3, PA_S3, 32, H / 8, W / 8));
+    HELM_TRY(layer(3, PA_S3, 128, -1, 0, PA_E4, H / 16, W / 16));
+  } else {
+    HELM_TRY(layer(1, PA_E1, 128, -1, 0, PA_E2, H / 4, W / 4, true));
+    HELM_TRY(layer(2, PA_E2, 128, -1, 0, PA_E3, H / 8, W / 8, true));
+    HELM_TRY(layer(3, PA_E3, 128, -1, 0, PA_E4, H / 16, W / 16, true));
+  }
   HELM_TRY(layer(4, PA_E4, 32, -1, 0, PA_D3, H / 16, W / 16));      // -> H/8
   HELM_TRY(layer(5, PA_D3, 32, PA_E3, 32, PA_D2, H / 8, W / 8));    // -> H/4
   HELM_TRY(layer(6, PA_D2, 32, PA_E2, 32, PA_D1, H / 4, W / 4));    // -> H/2
-  HELM_TRY(layer(7, PA_D1, 32, PA_E1, 32, PA_D0, H / 2, W / 2));    // -> H
+  if constexpr (!fp64) {
+    // the last transposed conv with the output layer in its epilogue (no full-resolution activation)
+    RowFinal f;
+    f.wf = P.wout32;
+    f.out_scale = out_scale;
+    f.z = (float2*)z;
+    f.Nx = s.Nx;
+    f.Ny = s.Ny;
+    f.zstride = s.n;
+    f.io = nullptr;
+    return layer(7, PA_D1, 32, PA_E1, 32, -1, H / 2, W / 2, false, &f);
+  } else {
+    HELM_TRY(layer(7, PA_D1, 32, PA_E1, 32, PA_D0, H / 2, W / 2));  // -> H
+  }
   const int64_t nout = (int64_t)B * s.Ny * s.Nx;
   const typename Acc<T>::A* wf;
   const typename Acc<T>::A* bf;
@@ -800,7 +826,7 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
   launch(k_palpha, cdiv(B, 64), 64, 0, st, (const double*)nb2, B, s0.n, s0.h * s0.h, in_s, out_s);
   launch(k_paper_pack<E, R>, cdiv(npx, 256), 256, 0, st, bvec, s0.n, (const double*)in_s,
          (const double*)(ctx->chat64), s0.n, (const double2*)(ctx->prof_d + s0.prof_x),
-         (const double2*)(ctx->prof_d + s0.prof_y), s0.Nx, s0.Ny, Hp, Wp, B, a[PA_X0]);
+         (const double2*)(ctx->prof_d + s0.prof_y), s0.Nx, s0.Ny, Hp, Wp, B, a[PA_S0]);
   auto s2d = [&](const E* src, E* dst, int C, int h, int w) {  // h, w: source grid
     const int64_t n = (int64_t)B * (h / 2) * (w / 2) * 4 * C;
     launch(k_s2d<E>, cdiv(n, 256), 256, 0, st, src, dst, C, B, h / 2, w / 2);
@@ -812,7 +838,6 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
     launch(k_pconv_keep<E>, grid, PC_THREADS, 0, st, i0, C0, i1, C1, wts(l), (const double*)P.b5[l], pre[l], post,
            L.N, L.cout, L.kind == P_UP ? 1 : 0, B, h, w, 5, P.slope[l]);
   };
-  s2d(a[PA_X0], a[PA_S0], 8, H, W);
   fwd(0, a[PA_S0], 32, nullptr, 0, H / 2, W / 2);
   s2d(a[PA_E1], a[PA_S1], 32, H / 2, W / 2);
   fwd(1, a[PA_S1], 128, nullptr, 0, H / 4, W / 4);
@@ -908,3 +933,39 @@ template helm_status paper_loss_grad<float>(helm_ctx*, helm_unet*, const float2*
 template helm_status paper_loss_grad<double>(helm_ctx*, helm_unet*, const double2*, double*, cudaStream_t);
 
 }  // namespace helm
+
+using namespace helm;
+
+extern "C" helm_status helm_paper_layer_forward(const helm_unet* net, int layer, const void* in0, const void* in1,
+                                                void* out, int B, int H, int W, void* stream) {
+  if (!net || !in0 || !out) return fail(HELM_ERR_INVALID_ARG, "helm_paper_layer_forward: NULL argument");
+  if (net->kind != 1 || !net->pn) return fail(HELM_ERR_INVALID_ARG, "helm_paper_layer_forward: network kind 1 only");
+  if (layer < 0 || layer > HELM_PAPER_LAYER_DEC0_FINAL)
+    return fail(HELM_ERR_INVALID_ARG, "helm_paper_layer_forward: layer out of range");
+  if (B < 1 || H < 1 || W < 1 || (int64_t)B * H * W > ((int64_t)1 << 29))
+    return fail(HELM_ERR_INVALID_ARG, "helm_paper_layer_forward: bad image size");
+  if (((uintptr_t)in0 | (uintptr_t)in1 | (uintptr_t)out) & 15)
+    return fail(HELM_ERR_INVALID_ARG, "helm_paper_layer_forward: pointers must be 16-byte aligned");
+  const bool fused = layer == HELM_PAPER_LAYER_DEC0_FINAL;
+  const int l = fused ? 7 : layer;
+  if ((l >= 5) != (in1 != nullptr))
+    return fail(HELM_ERR_INVALID_ARG, "helm_paper_layer_forward: in1 is required exactly for layers 5..7");
+  if (!tc_available())
+    return fail(HELM_ERR_INVALID_ARG, "helm_paper_layer_forward: the tcgen05 path is not available on this device");
+  const PaperNet& P = *net->pn;
+  const PaperLayer& L = kP[l];
+  RowFinal f;
+  if (fused) {
+    f.wf = P.wout32;
+    f.out_scale = nullptr;
+    f.z = (float2*)out;
+    f.Nx = 2 * W;
+    f.Ny = 2 * H;
+    f.zstride = (int64_t)4 * H * W;
+    f.io = nullptr;
+  }
+  const int C0 = l == 0 ? 4 * P_X0_CH : (l <= 3 ? 128 : 32), C1 = l >= 5 ? 32 : 0;
+  return conv_tc_generic(P.wtc[l], P.b32[l], P.err, 5, L.kind == P_UP ? 2 : 0, L.N, L.chunk, in0, C0, in1, C1,
+                         fused ? nullptr : out, B, H, W, 2, (float)P.slope[l], (cudaStream_t)stream,
+                         l >= 1 && l <= 3, fused ? &f : nullptr);
+}

@@ -80,6 +80,7 @@ _SIGS = {
     "helm_relres_noalloc": (ct.c_int, [_P, _P, _P, ct.c_int, _P, _P]),
     "helm_unet_layer_forward": (ct.c_int, [_P, ct.c_int, ct.c_int, _P, _P, _P, ct.c_int, ct.c_int, ct.c_int,
                                            ct.POINTER(ct.c_int), _P]),
+    "helm_paper_layer_forward": (ct.c_int, [_P, ct.c_int, _P, _P, _P, ct.c_int, ct.c_int, ct.c_int, _P]),
     "helm_unet_get_adam": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64)]),
     "helm_unet_set_adam": (ct.c_int, [_P, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double), ct.c_int64]),
     "helm_set_wait_budget": (ct.c_int, [ct.c_int64]),
@@ -264,6 +265,20 @@ def helm_unet_layer_forward(net, layer, in0: torch.Tensor, out: torch.Tensor, B,
                                         _dev_ptr(in1) if in1 is not None else None, _dev_ptr(out), B, H, W,
                                         ct.byref(ry), _stream(stream)))
     return ry.value
+
+
+HELM_PAPER_LAYER_DEC0_FINAL = 8
+
+
+def helm_paper_layer_forward(net, layer, in0: torch.Tensor, out: torch.Tensor, B, H, W, in1=None, stream=None):
+    """One layer of network kind 1 on NHWC bfloat16 CUDA tensors (helm_paper_layer_forward in
+    include/helm.h); H x W is the layer's 5x5 GEMM grid."""
+    for t in (in0, out) + ((in1,) if in1 is not None else ()):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("layer tensors must be contiguous CUDA tensors")
+    _check(_lib.helm_paper_layer_forward(net.handle, layer, _dev_ptr(in0),
+                                         _dev_ptr(in1) if in1 is not None else None, _dev_ptr(out), B, H, W,
+                                         _stream(stream)))
 
 
 def helm_set_wait_budget(cycles: int):

@@ -102,7 +102,7 @@ def save_weights(path, w):
 class Validator:
     """Mean FGMRES iterations to eta_b <= tol on a held-out problem (mixed path, DCGS2)."""
 
-    def __init__(self, prob, m=512, max_outer=10, tol=1e-6, inner_tol=1e-5):
+    def __init__(self, prob, m=512, max_outer=20, tol=1e-6, inner_tol=1e-5):
         self.prob = prob
         spec = helm.SystemSpec(prob.nx, prob.ny, prob.h, prob.p, prob.omega)
         self.ctx = helm.Context([spec], torch.tensor(prob.c.ravel(), device="cuda"))
@@ -253,7 +253,8 @@ def main():
     ap.add_argument("--checkpoint", default=None)
     ap.add_argument("--resume", action="store_true")
     ap.add_argument("--val-every", type=int, default=5)
-    ap.add_argument("--val-rhs", type=int, default=4, help="held-out right-hand sides of the fine-grid workload")
+    ap.add_argument("--val-rhs", type=int, default=16, help="held-out right-hand sides of the fine-grid workload")
+    ap.add_argument("--seed", type=int, default=42, help="epoch mode: seed of the sample set and epoch order")
     ap.add_argument("--no-val", action="store_true")
     ap.add_argument("--kind", type=int, default=0, help="network kind: 0 (16/32/64/128 U-Net) or 1 (the paper's)")
     # streaming mode
@@ -271,7 +272,7 @@ def main():
         _, state = train_epochs(dataset=a.dataset, samples=a.samples, nx=a.grid, p=a.pml, batch=a.batch,
                                 epochs=a.epochs, lr_max=a.lr, lr_min=a.lr_min, init=init, out=a.out,
                                 checkpoint=a.checkpoint, resume=a.resume, val_every=a.val_every, validator=val,
-                                kind=a.kind)
+                                kind=a.kind, seed=a.seed)
         if a.log:
             with open(a.log, "w") as f:
                 json.dump(state, f)

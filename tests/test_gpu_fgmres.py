@@ -10,6 +10,7 @@ import torch
 from oracle import fgmres as fg
 from oracle import helmholtz as hz
 from oracle import unet
+from oracle import unet_paper
 from paper_2607_16906_b300 import synth
 
 from .gpu_util import make_ctx, small_problems, split, to_dev
@@ -127,23 +128,39 @@ def test_status_reporting(helm):
 # weights), FP64 Givens, FP64 true residual and iterative refinement (eq. 10), inner tolerance
 # 1e-5.  Target: true eta_b <= 1e-6 and a solution within 1e-5 of the sparse direct solution.
 
-TRAINED = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2607_16906_b300",
-                       "weights", "unet_trained.npy")
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2607_16906_b300",
+                       "weights")
+# the shipped trained networks: kind 0 (16/32/64/128 U-Net) and kind 1 (the paper's variant)
+SHIPPED = {"kind0": "unet_trained.npy", "kind1": "unet_paper_trained.npy"}
 
 
-@pytest.fixture(scope="module")
-def trained():
-    return np.load(TRAINED)
+@pytest.fixture(scope="module", params=sorted(SHIPPED))
+def trained(request):
+    return np.load(os.path.join(WEIGHTS, SHIPPED[request.param]))
+
+
+def _oracle_bf16_net(theta, p):
+    """The oracle's BF16-emulated network of the weights' kind, z = M(v) in complex64."""
+    if theta.size == unet_paper.param_count():
+        return lambda v: unet_paper.precondition(theta, np.asarray(v, complex).reshape(1, p.Ny, p.Nx), p.c, p.p, p.h,
+                                                 p.omega, bf16=True)[0].ravel().astype(np.complex64)
+    return lambda v: unet.precondition(theta, np.asarray(v, complex).reshape(1, p.Ny, p.Nx), p.c, p.h,
+                                       bf16=True)[0].ravel().astype(np.complex64)
 
 
 @pytest.mark.parametrize("orth", ["dcgs2", "cgs2"])
 def test_benchmarked_path_converges_to_the_direct_solution(helm, trained, orth):
+    """Both accuracy targets of the mixed path: true eta_b <= 1e-6 and a solution within 1e-5 of the
+    sparse direct solution.  The error of an iterate is up to cond(A)-times its residual; on these
+    systems the ratio reaches about 10 (10.2 for one column of the 33 x 27 grid), so a solve stopped
+    just below eta_b = 1e-6 can miss the error target by a hair: the solve is run to eta_b <= 5e-7,
+    which meets both."""
     probs = small_problems(((40, 40, 12), (48, 32, 8), (33, 27, 6)), seed=35, nrhs=2)
     ctx = make_ctx(probs)
     net = helm.UNet(trained)
     b = to_dev(_flat_b(probs), torch.complex128)
     x = torch.zeros_like(b)
-    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 2, m=40, tol=1e-6, mixed=True, max_outer=20, inner_tol=1e-5,
+    rc, info = helm.helm_fgmres_solve(ctx, net, b, x, 2, m=40, tol=5e-7, mixed=True, max_outer=20, inner_tol=1e-5,
                                       orth=orth)
     assert rc == helm.HELM_OK, info
     got = split(x.cpu().numpy(), probs, 2)
@@ -153,7 +170,7 @@ def test_benchmarked_path_converges_to_the_direct_solution(helm, trained, orth):
         xd = hz.solve_direct(A, p.b.reshape(2, -1).T).T
         for r in range(2):
             rel = hz.relres(A, xs[r].ravel(), p.b[r].ravel())
-            assert rel <= 1e-6 and abs(rel - info[k]["relres_true"]) <= 1e-9 * max(rel, 1e-12)
+            assert rel <= 5e-7 and abs(rel - info[k]["relres_true"]) <= 1e-9 * max(rel, 1e-12)
             assert np.linalg.norm(xs[r].ravel() - xd[r]) <= 1e-5 * np.linalg.norm(xd[r]), (k, rel)
             k += 1
 
@@ -172,8 +189,7 @@ def test_benchmarked_path_iterations_match_the_oracle(helm, trained):
                                       orth="dcgs2")
     assert rc == helm.HELM_OK
     A = hz.assemble(p.c, p.p, p.h, p.omega)
-    Mb = lambda v: unet.precondition(trained, np.asarray(v, complex).reshape(1, p.Ny, p.Nx), p.c, p.h,
-                                     bf16=True)[0].ravel().astype(np.complex64)
+    Mb = _oracle_bf16_net(trained, p)
     _, oinfo = fg.refine(lambda u: A @ u, Mb, p.b[0].ravel(), m=20, tol=1e-6, inner_tol=1e-5, max_outer=30,
                          orth="dcgs2")
     assert oinfo.converged
@@ -197,8 +213,7 @@ def test_mixed_cycle_estimates_follow_the_oracle(helm, trained, orth):
     helm.helm_fgmres_solve(ctx, net, b, x, 1, m=m, tol=1e-300, mixed=True, max_outer=1, orth=orth)
     hist = helm.helm_solve_history(ctx)
     A = hz.assemble(p.c, p.p, p.h, p.omega)
-    Mb = lambda v: unet.precondition(trained, np.asarray(v, complex).reshape(1, p.Ny, p.Nx), p.c, p.h,
-                                     bf16=True)[0].ravel().astype(np.complex64)
+    Mb = _oracle_bf16_net(trained, p)
     A_lo = lambda u: (A @ np.asarray(u, complex)).astype(np.complex64)
     bb = p.b[0].ravel()
     res = fg.cycle(A_lo, Mb, (bb / np.linalg.norm(bb)).astype(np.complex64), m, 0.0, orth=orth, dtype=np.complex64)
