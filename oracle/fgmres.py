@@ -275,7 +275,8 @@ def refine(apply_A, precond_lo, b, m=30, tol=1e-6, inner_tol=1e-4, max_outer=20,
 
     Outer (FP64): r = b - A x, stop when ||r|| / ||b|| <= tol.  Inner: FGMRES on
     A d = r / ||r|| with vectors stored in `inner_dtype`, until the estimate
-    drops by `inner_tol` relative to ||r / ||r|||| = 1 or m iterations; then
+    drops below max(inner_tol, tol ||b|| / ||r||) relative to ||r / ||r|||| = 1 (the
+    inner solve need not go further than the outer target) or m iterations; then
     x += ||r|| d.
     """
     b = np.asarray(b, np.complex128)
@@ -297,13 +298,14 @@ def refine(apply_A, precond_lo, b, m=30, tol=1e-6, inner_tol=1e-4, max_outer=20,
         rhat = (r / nr).astype(inner_dtype)
         d = np.zeros(b.size, np.complex128)
         rr = rhat.astype(np.complex128)
+        target = max(inner_tol, tol * nb / nr)
         for _ in range(max_cycles_inner):
-            res = cycle(A_lo, precond_lo, rr.astype(inner_dtype), m, inner_tol, orth, dtype=inner_dtype)
+            res = cycle(A_lo, precond_lo, rr.astype(inner_dtype), m, target, orth, dtype=inner_dtype)
             d = d + res.x
             info.iters += res.iters
             info.cycles += 1
             rr = rhat.astype(np.complex128) - apply_A(d)
-            if np.linalg.norm(rr) <= inner_tol:
+            if np.linalg.norm(rr) <= target:
                 break
         x = x + nr * d
     else:

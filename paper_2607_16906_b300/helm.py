@@ -297,11 +297,11 @@ def helm_unet_param_count() -> int:
 
 def network_kind(nparams: int) -> int:
     """The network kind whose parameter count is `nparams` (helm_unet_param_count_kind: the two
-    kinds differ in size); ValueError if neither matches."""
+    kinds differ in size); 0 if neither matches (helm_unet_create then rejects the count)."""
     for kind in (0, 1):
         if int(_lib.helm_unet_param_count_kind(kind)) == int(nparams):
             return kind
-    raise ValueError(f"{nparams} parameters match no network kind")
+    return 0
 
 
 def helm_unet_layers():
