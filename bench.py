@@ -31,15 +31,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-WEIGHTS = os.path.join(ROOT, "paper_2607_16906_b300", "weights", "unet_trained.npy")
+WEIGHTS = os.path.join(ROOT, "paper_2607_16906_b300", "weights", "unet_paper_trained.npy")
 METRIC = "Helmholtz solves/s to rel.res 1e-6: batched mixed vs plain FP64, same B300"
-UNET_FLOP_PER_PT = 70816.0          # 2 x 35,408 MACs per full-resolution pixel (4-level U-Net)
 STENCIL_BYTES_FP32 = 16.0           # read z (8 B) + write A z (8 B) per point; k^2 (4 B/pt) read once per 32 RHS
 # FGMRES iterations per right-hand side of this workload with the trained network, as measured by
 # the CUDA arm (mean over the 32 RHS, FGMRES(512), up to 20 cycles); the reference arm, which
 # runs in a process of its own, scales its measured per-iteration time by it (the CUDA arm prints its
 # own measured mean)
-REF_ITERS_PER_SOLVE = 4857
+REF_ITERS_PER_SOLVE = 3580
 # DRAM bytes per basis vector and point of one DCGS2 step (k_dsweepA 8.00 B + k_dsweepB 8.06 B),
 # from the ncu counters of the current sweep kernels
 DCGS2_DRAM_B_PER_VPT = 16.06

@@ -1126,7 +1126,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         // z_j = N_theta(v_j)
         prof_begin(ctx, PH_PRECOND, stream);
         if (ctx->prof_on) {
-          ctx->prof_work[PH_PRECOND] += net ? 70816.0 * ctx->npts * nrhs : 0.0;
+          ctx->prof_work[PH_PRECOND] += net ? unet_flop_per_point(net->kind) * ctx->npts * nrhs : 0.0;
           ctx->prof_work[PH_STENCIL] += 16.0 * ctx->npts * nrhs + 4.0 * ctx->npts;
           ctx->prof_work[PH_ORTH] += (32.0 * (j + 1) + 48.0) * ctx->npts * nrhs * (double)nact / ncol;
         }
@@ -1177,7 +1177,7 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         C<R>* Zj = W.Z + (int64_t)j * vst;
         prof_begin(ctx, PH_PRECOND, stream);
         if (ctx->prof_on) {
-          ctx->prof_work[PH_PRECOND] += net ? 70816.0 * ctx->npts * nrhs : 0.0;
+          ctx->prof_work[PH_PRECOND] += net ? unet_flop_per_point(net->kind) * ctx->npts * nrhs : 0.0;
           ctx->prof_work[PH_STENCIL] += 16.0 * ctx->npts * nrhs + 4.0 * ctx->npts;
           ctx->prof_work[PH_ORTH] += (16.0 * (j > 0 ? j : 1) + 48.0) * ctx->npts * nrhs * (double)nact / ncol;
         }

@@ -151,6 +151,10 @@ struct PaperNet {
   } act[2];  // activations: [0] BF16, [1] FP64
 };
 int64_t paper_param_count();
+// Algorithmic flops of one network application per full-resolution pixel: kind 0, its 3x3 / 2x2 /
+// 1x1 layers (2 x 35,408 MACs); kind 1, the 8x8 strided and transposed layers and the output layer
+// (2 x 51,264 MACs; the 5x5 reformulation executes 82,464 MACs, structural zeros included).
+inline double unet_flop_per_point(int kind) { return kind == 1 ? 102528.0 : 70816.0; }
 helm_status paper_prepare(helm_unet* net, cudaStream_t st);
 void paper_release(helm_unet* net);
 template <typename R>
