@@ -56,16 +56,26 @@ struct ConvTcArgs {
 
 template <int N, int CHUNK, int MODE, int KS>
 struct TcCfg {
-  static constexpr int A_BYTES = 128 * CHUNK * 2;
+  // KS = 5 (the reformulated stride-2 layers): one stage is one (input-channel chunk, kernel column
+  // dx): the 12-row patch rows y0 - 2 .. y0 + 9 of the column-shifted window and the KS weight tiles of
+  // that column.  The A operand of kernel row dy is the same patch 16 dy pixels further on (a whole
+  // number of 8-row swizzle atoms), so every input pixel is loaded 12 / 8 times per chunk instead of
+  // 25 times.  KS = 3: one stage is one or three taps, each with its own patch and weight tile.
+  static constexpr bool RR = KS == 5;
+  static constexpr int A_ROWS = RR ? 8 + KS - 1 : 8;
+  static constexpr int A_BYTES = A_ROWS * 16 * CHUNK * 2;
   static constexpr int B_BYTES = N * CHUNK * 2;
   // taps per pipeline stage: a whole kernel row (3 taps) for narrow chunks, so that one barrier
   // round trip carries three MMAs; one tap otherwise
-  static constexpr int TPS = (MODE == 0 && KS == 3 && CHUNK <= 32) ? 3 : 1;
-  static constexpr int STAGE_BYTES = TPS * (A_BYTES + B_BYTES);
-  static constexpr int STAGES = (96 * 1024 / STAGE_BYTES) > 8 ? 8 : (96 * 1024 / STAGE_BYTES);
+  static constexpr int TPS = RR ? KS : ((MODE == 0 && KS == 3 && CHUNK <= 32) ? 3 : 1);
+  static constexpr int STAGE_BYTES = RR ? A_BYTES + KS * B_BYTES : TPS * (A_BYTES + B_BYTES);
+  static constexpr int BUDGET = RR ? 200 * 1024 : 96 * 1024;
+  static constexpr int STAGES = (BUDGET / STAGE_BYTES) > 8 ? 8 : (BUDGET / STAGE_BYTES);
   static constexpr int TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
   static constexpr int THREADS = 192;
+  static_assert(STAGES >= 2, "pipeline depth");
+  static_assert(!RR || (A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0), "swizzle-atom alignment of the stage buffers");
 };
 
 // MODE 0: KS x KS conv, pad KS / 2 (KS^2 shifted taps per channel chunk), N = C_out.
@@ -92,6 +102,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
   const int nk = a.nk0 + a.nk1;
   constexpr int TAPS = MODE == 1 ? 1 : KS * KS;
   constexpr int TPS = Cfg::TPS;
+  // stages per tile: KS = 5, one per (chunk, kernel column); otherwise one per (chunk, tap group)
   const int ksteps = (TAPS / TPS) * nk;
 
   if (threadIdx.x == 0) {
@@ -147,8 +158,24 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
             }
             ++fills[stage];
             unsigned char* sa = smem + stage * Cfg::STAGE_BYTES;
-            unsigned char* sb = sa + TPS * Cfg::A_BYTES;
             mbar_expect_tx(&full[stage], Cfg::STAGE_BYTES);
+            if constexpr (Cfg::RR) {
+              // kernel column dx = tg: the (8 + KS - 1)-row patch and the KS weight tiles (dy, dx)
+              unsigned char* sb = sa + Cfg::A_BYTES;
+              if (MODE == 0 && a.s2d)
+                tma_load_4d(sa, src, &full[stage], 0, x0 + tg - KS / 2, 2 * (y0 - KS / 2) + kc, b);
+              else
+                tma_load_4d(sa, src, &full[stage], c0, x0 + tg - KS / 2, y0 - KS / 2, b);
+#pragma unroll
+              for (int dy = 0; dy < KS; ++dy)
+                tma_load_3d(sb + dy * Cfg::B_BYTES, &tW, &full[stage], 0, 0, (dy * KS + tg) * nk + kc);
+              if (++stage == Cfg::STAGES) {
+                stage = 0;
+                phase ^= 1;
+              }
+              continue;
+            }
+            unsigned char* sb = sa + TPS * Cfg::A_BYTES;
 #pragma unroll
             for (int t = 0; t < TPS; ++t) {
               const int tap = tg * TPS + t;
@@ -194,7 +221,21 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
           break;
         }
         tc_fence_after();
-        if (lane == 0) {
+        if (lane == 0 && Cfg::RR) {
+          // kernel rows dy of this column: A = the patch from pixel row dy, B = weight tile dy
+          const uint32_t sa = smem_u32(smem + stage * Cfg::STAGE_BYTES);
+          const uint32_t sb = sa + Cfg::A_BYTES;
+#pragma unroll
+          for (int dy = 0; dy < KS; ++dy) {
+            const uint64_t ad = smem_desc(sa + dy * 16 * CHUNK * 2, CHUNK * 2);
+            const uint64_t bd = smem_desc(sb + dy * Cfg::B_BYTES, CHUNK * 2);
+#pragma unroll
+            for (int k = 0; k < CHUNK / 16; ++k)
+              umma_bf16(d_tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), IDESC,
+                        (ks > 0 || dy > 0 || k > 0) ? 1u : 0u);
+          }
+          umma_commit(&empty[stage]);
+        } else if (lane == 0) {
           uint32_t sa = smem_u32(smem + stage * Cfg::STAGE_BYTES);
           uint32_t sb = sa + TPS * Cfg::A_BYTES;
 #pragma unroll
@@ -458,10 +499,10 @@ static CUtensorMapSwizzle swizzle_for(int chunk) {
   return chunk == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (chunk == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
-static helm_status act_map(CUtensorMap* m, const void* ptr, int C, int B, int H, int W, int chunk) {
+static helm_status act_map(CUtensorMap* m, const void* ptr, int C, int B, int H, int W, int chunk, int rows = 8) {
   cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
   cuuint64_t strides[3] = {(cuuint64_t)C * 2, (cuuint64_t)W * C * 2, (cuuint64_t)H * W * C * 2};
-  cuuint32_t box[4] = {(cuuint32_t)chunk, 16, 8, 1};
+  cuuint32_t box[4] = {(cuuint32_t)chunk, 16, (cuuint32_t)rows, 1};
   cuuint32_t es[4] = {1, 1, 1, 1};
   CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, strides, box, es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(chunk), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -473,11 +514,11 @@ static helm_status act_map(CUtensorMap* m, const void* ptr, int C, int B, int H,
 // The space-to-depth view of an NHWC BF16 tensor [B][2H][2W][C] on the H x W grid: one box is the
 // 8 x 16 patch of one row phase, each pixel's 2C values being its two column phases (contiguous in
 // memory); the map's rows are the source's rows, traversed with stride 2 from 2 Y + phase.
-static helm_status act_map_s2d(CUtensorMap* m, const void* ptr, int chunk, int B, int H, int W) {
+static helm_status act_map_s2d(CUtensorMap* m, const void* ptr, int chunk, int B, int H, int W, int rows) {
   const int C = chunk / 2;
   cuuint64_t dims[4] = {(cuuint64_t)chunk, (cuuint64_t)W, (cuuint64_t)(2 * H), (cuuint64_t)B};
   cuuint64_t strides[3] = {(cuuint64_t)chunk * 2, (cuuint64_t)2 * W * C * 2, (cuuint64_t)4 * H * W * C * 2};
-  cuuint32_t box[4] = {(cuuint32_t)chunk, 16, 16, 1};
+  cuuint32_t box[4] = {(cuuint32_t)chunk, 16, (cuuint32_t)(2 * rows), 1};
   cuuint32_t es[4] = {1, 1, 2, 1};
   CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, strides, box, es,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_for(chunk), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -646,12 +687,13 @@ helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* e
     return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: the space-to-depth view needs one source of two row phases");
   if (fin && mode != 2) return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: the fused output layer needs mode 2");
   CUtensorMap m0, m1, mw;
+  const int rows = ks == 5 ? 12 : 8;  // patch rows of one stage (TcCfg::A_ROWS)
   if (s2d0)
-    HELM_TRY(act_map_s2d(&m0, in0, chunk, B, H, W));
+    HELM_TRY(act_map_s2d(&m0, in0, chunk, B, H, W, rows));
   else
-    HELM_TRY(act_map(&m0, in0, C0, B, H, W, chunk));
+    HELM_TRY(act_map(&m0, in0, C0, B, H, W, chunk, rows));
   if (C1 > 0)
-    HELM_TRY(act_map(&m1, in1, C1, B, H, W, chunk));
+    HELM_TRY(act_map(&m1, in1, C1, B, H, W, chunk, rows));
   else
     m1 = m0;
   const int nk = (C0 + C1) / chunk;
