@@ -54,15 +54,18 @@ struct ConvTcArgs {
   int64_t zstride;
 };
 
-template <int N, int CHUNK, int MODE, int KS>
+template <int N, int CHUNK, int MODE, int KS, int RB = 1>
 struct TcCfg {
-  // KS = 5 (the reformulated stride-2 layers): one stage is one (input-channel chunk, kernel column
-  // dx): the 12-row patch rows y0 - 2 .. y0 + 9 of the column-shifted window and the KS weight tiles of
-  // that column.  The A operand of kernel row dy is the same patch 16 dy pixels further on (a whole
-  // number of 8-row swizzle atoms), so every input pixel is loaded 12 / 8 times per chunk instead of
-  // 25 times.  KS = 3: one stage is one or three taps, each with its own patch and weight tile.
+  // KS = 5 (the reformulated stride-2 layers): a tile is RB row blocks of 8 x 16 pixels stacked
+  // vertically (RB MMA accumulators of 128 x N); one stage is one (input-channel chunk, kernel
+  // column dx): the (8 RB + 4)-row patch of the column-shifted window and the KS weight tiles of that
+  // column.  The A operand of row block rb and kernel row dy is the same patch 16 (8 rb + dy) pixels
+  // further on (a whole number of 8-row swizzle atoms), so every input pixel is loaded
+  // (8 RB + 4) / (8 RB) times per chunk instead of 25 times, and every weight tile serves RB blocks.
+  // KS = 3: one stage is one or three taps, each with its own patch and weight tile (RB = 1).
   static constexpr bool RR = KS == 5;
-  static constexpr int A_ROWS = RR ? 8 + KS - 1 : 8;
+  static_assert(RR || RB == 1, "row blocks are a 5x5-layer feature");
+  static constexpr int A_ROWS = RR ? 8 * RB + KS - 1 : 8;
   static constexpr int A_BYTES = A_ROWS * 16 * CHUNK * 2;
   static constexpr int B_BYTES = N * CHUNK * 2;
   // taps per pipeline stage: a whole kernel row (3 taps) for narrow chunks, so that one barrier
@@ -71,10 +74,12 @@ struct TcCfg {
   static constexpr int STAGE_BYTES = RR ? A_BYTES + KS * B_BYTES : TPS * (A_BYTES + B_BYTES);
   static constexpr int BUDGET = RR ? 200 * 1024 : 96 * 1024;
   static constexpr int STAGES = (BUDGET / STAGE_BYTES) > 8 ? 8 : (BUDGET / STAGE_BYTES);
-  static constexpr int TMEM_COLS = 2 * N < 32 ? 32 : 2 * N;
+  static constexpr int ACC_COLS = RB * N;  // one tile's accumulators
+  static constexpr int TMEM_COLS = 2 * ACC_COLS < 32 ? 32 : 2 * ACC_COLS;
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
   static constexpr int THREADS = 192;
   static_assert(STAGES >= 2, "pipeline depth");
+  static_assert(TMEM_COLS <= 512 && (TMEM_COLS & (TMEM_COLS - 1)) == 0, "TMEM allocation");
   static_assert(!RR || (A_BYTES % 1024 == 0 && B_BYTES % 1024 == 0), "swizzle-atom alignment of the stage buffers");
 };
 
@@ -83,11 +88,11 @@ struct TcCfg {
 //         with N = 4 C_out followed by depth-to-space).
 // MODE 1: 2x2 stride-2 transposed conv as one GEMM with N = 4 C_out (column n = tap C_out + co); the
 //         epilogue scatters column blocks to output pixel (2y + tap / 2, 2x + tap % 2); no activation.
-template <int N, int CHUNK, int MODE, int KS>
+template <int N, int CHUNK, int MODE, int KS, int RB = 1>
 __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUtensorMap tA0,
                                                     const __grid_constant__ CUtensorMap tA1,
                                                     const __grid_constant__ CUtensorMap tW, ConvTcArgs a) {
-  using Cfg = TcCfg<N, CHUNK, MODE, KS>;
+  using Cfg = TcCfg<N, CHUNK, MODE, KS, RB>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + Cfg::STAGES * Cfg::STAGE_BYTES);
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         int b = t / (a.tiles_x * a.tiles_y);
         int r = t % (a.tiles_x * a.tiles_y);
-        int y0 = (r / a.tiles_x) * 8, x0 = (r % a.tiles_x) * 16;
+        int y0 = (r / a.tiles_x) * 8 * RB, x0 = (r % a.tiles_x) * 16;
         for (int kc = 0; kc < nk && ok; ++kc) {
           const CUtensorMap* src = kc < a.nk0 ? &tA0 : &tA1;
           int c0 = (kc < a.nk0 ? kc : kc - a.nk0) * CHUNK;
@@ -214,7 +219,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
         break;
       }
       tc_fence_after();
-      const uint32_t d_tmem = tmem_base + acc * N;
+      const uint32_t d_tmem = tmem_base + acc * Cfg::ACC_COLS;
       for (int ks = 0; ks < ksteps; ++ks) {
         if (!mbar_wait_warp(&full[stage], phase, abort_flag, a.err, 3, a.budget)) {
           ok = false;
@@ -227,12 +232,15 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
           const uint32_t sb = sa + Cfg::A_BYTES;
 #pragma unroll
           for (int dy = 0; dy < KS; ++dy) {
-            const uint64_t ad = smem_desc(sa + dy * 16 * CHUNK * 2, CHUNK * 2);
             const uint64_t bd = smem_desc(sb + dy * Cfg::B_BYTES, CHUNK * 2);
 #pragma unroll
-            for (int k = 0; k < CHUNK / 16; ++k)
-              umma_bf16(d_tmem, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), IDESC,
-                        (ks > 0 || dy > 0 || k > 0) ? 1u : 0u);
+            for (int rb = 0; rb < RB; ++rb) {
+              const uint64_t ad = smem_desc(sa + (8 * rb + dy) * 16 * CHUNK * 2, CHUNK * 2);
+#pragma unroll
+              for (int k = 0; k < CHUNK / 16; ++k)
+                umma_bf16(d_tmem + rb * N, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), IDESC,
+                          (ks > 0 || dy > 0 || k > 0) ? 1u : 0u);
+            }
           }
           umma_commit(&empty[stage]);
         } else if (lane == 0) {
@@ -280,52 +288,65 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       tc_fence_after();
       int b = t / (a.tiles_x * a.tiles_y);
       int r = t % (a.tiles_x * a.tiles_y);
-      int y = (r / a.tiles_x) * 8 + ly, x = (r % a.tiles_x) * 16 + lx;
-      bool inside = y < a.H && x < a.W;
       constexpr int COUT = MODE == 0 ? N : N / 4;
       const bool fused = MODE == 2 && a.z != nullptr;
-      float f0 = 0.0f, f1 = 0.0f;
+#pragma unroll 1
+      for (int rb = 0; rb < RB; ++rb) {
+        const int y = (r / a.tiles_x) * 8 * RB + rb * 8 + ly, x = (r % a.tiles_x) * 16 + lx;
+        const bool inside = y < a.H && x < a.W;
+        float f0 = 0.0f, f1 = 0.0f;
+        float2 zr[2];  // the fused output of phases (qy, 0) and (qy, 1): one 16-byte store per row
 #pragma unroll
-      for (int cb = 0; cb < N / 16; ++cb) {
-        uint32_t v[16];
-        tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + acc * N + cb * 16, v);
-        tmem_ld_wait();
-        if (fused && inside) {
-          // the output layer on the BF16-rounded activation of output phase `tap`, channels in order
-          const int tap = (cb * 16) / COUT, co0 = (cb * 16) % COUT;
-          if (co0 == 0) {
-            f0 = a.wf[2 * COUT];
-            f1 = a.wf[2 * COUT + 1];
-          }
+        for (int cb = 0; cb < N / 16; ++cb) {
+          uint32_t v[16];
+          tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + acc * Cfg::ACC_COLS + rb * N + cb * 16, v);
+          tmem_ld_wait();
+          if (fused && inside) {
+            // the output layer on the BF16-rounded activation of output phase `tap`, channels in order
+            const int tap = (cb * 16) / COUT, co0 = (cb * 16) % COUT;
+            if (co0 == 0) {
+              f0 = a.wf[2 * COUT];
+              f1 = a.wf[2 * COUT + 1];
+            }
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            float f = __uint_as_float(v[k]) + a.bias[cb * 16 + k];
-            f = f > 0.0f ? f : a.slope * f;
-            const float h = __bfloat162float(__float2bfloat16_rn(f));
-            f0 += h * a.wf[2 * (co0 + k)];
-            f1 += h * a.wf[2 * (co0 + k) + 1];
-          }
-          const int Y = 2 * y + tap / 2, X = 2 * x + tap % 2;
-          if (co0 + 16 == COUT && Y < a.Ny && X < a.Nx) {
-            const double sc = a.out_scale ? a.out_scale[b] : 1.0;
-            a.z[b * a.zstride + (int64_t)Y * a.Nx + X] = make_float2((float)(f0 * sc), (float)(f1 * sc));
-          }
-        } else if (inside && !fused) {
-          const int tap = (cb * 16) / COUT, co0 = (cb * 16) % COUT;
-          int64_t opix = MODE == 0 ? (((int64_t)b * a.H + y) * a.W + x)
-                                   : (((int64_t)b * 2 * a.H + 2 * y + tap / 2) * (2 * a.W) + 2 * x + tap % 2);
-          __nv_bfloat16* o = a.out + opix * COUT + co0;
-          __align__(16) __nv_bfloat16 hv[16];
+            for (int k = 0; k < 16; ++k) {
+              float f = __uint_as_float(v[k]) + a.bias[cb * 16 + k];
+              f = f > 0.0f ? f : a.slope * f;
+              const float h = __bfloat162float(__float2bfloat16_rn(f));
+              f0 += h * a.wf[2 * (co0 + k)];
+              f1 += h * a.wf[2 * (co0 + k) + 1];
+            }
+            if (co0 + 16 == COUT) {
+              const double sc = a.out_scale ? a.out_scale[b] : 1.0;
+              zr[tap & 1] = make_float2((float)(f0 * sc), (float)(f1 * sc));
+              const int Y = 2 * y + tap / 2, X = 2 * x;
+              if ((tap & 1) && Y < a.Ny && X < a.Nx) {
+                float2* zp = a.z + b * a.zstride + (int64_t)Y * a.Nx + X;
+                if (X + 1 < a.Nx && ((((uintptr_t)zp) & 15) == 0)) {
+                  *(float4*)zp = make_float4(zr[0].x, zr[0].y, zr[1].x, zr[1].y);
+                } else {
+                  zp[0] = zr[0];
+                  if (X + 1 < a.Nx) zp[1] = zr[1];
+                }
+              }
+            }
+          } else if (inside && !fused) {
+            const int tap = (cb * 16) / COUT, co0 = (cb * 16) % COUT;
+            int64_t opix = MODE == 0 ? (((int64_t)b * a.H + y) * a.W + x)
+                                     : (((int64_t)b * 2 * a.H + 2 * y + tap / 2) * (2 * a.W) + 2 * x + tap % 2);
+            __nv_bfloat16* o = a.out + opix * COUT + co0;
+            __align__(16) __nv_bfloat16 hv[16];
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            float f = __uint_as_float(v[k]) + a.bias[co0 + k];
-            if (a.act == 1) f = fmaxf(f, 0.0f);
-            else if (a.act == 2) f = f > 0.0f ? f : a.slope * f;
-            hv[k] = __float2bfloat16_rn(f);
+            for (int k = 0; k < 16; ++k) {
+              float f = __uint_as_float(v[k]) + a.bias[co0 + k];
+              if (a.act == 1) f = fmaxf(f, 0.0f);
+              else if (a.act == 2) f = f > 0.0f ? f : a.slope * f;
+              hv[k] = __float2bfloat16_rn(f);
+            }
+            uint4* dst = (uint4*)o;
+            dst[0] = ((const uint4*)hv)[0];
+            dst[1] = ((const uint4*)hv)[1];
           }
-          uint4* dst = (uint4*)o;
-          dst[0] = ((const uint4*)hv)[0];
-          dst[1] = ((const uint4*)hv)[1];
         }
       }
       tc_fence_before();
@@ -540,16 +561,16 @@ static helm_status weight_map(CUtensorMap* m, const void* ptr, int N, int chunk,
   return HELM_OK;
 }
 
-template <int N, int CHUNK, int MODE, int KS = 3>
+template <int N, int CHUNK, int MODE, int KS = 3, int RB = 1>
 static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const CUtensorMap& w, const ConvTcArgs& args,
                              cudaStream_t st) {
-  using Cfg = TcCfg<N, CHUNK, MODE, KS>;
+  using Cfg = TcCfg<N, CHUNK, MODE, KS, RB>;
   static std::once_flag once;
   static cudaError_t attr_err = cudaSuccess;
   static int per_sm = 1, nsm = 148;
   std::call_once(once, [] {
     attr_err =
-        cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE, KS>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
+        cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE, KS, RB>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::SMEM);
     int dev = 0, smem_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -557,11 +578,11 @@ static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const
     // resident CTAs per SM: shared memory (1 KB reserved per CTA), TMEM (512 columns), threads, and
     // the occupancy calculator (registers)
     if (attr_err == cudaSuccess)
-      attr_err = cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE, KS>, cudaFuncAttributePreferredSharedMemoryCarveout,
+      attr_err = cudaFuncSetAttribute(k_conv_tc<N, CHUNK, MODE, KS, RB>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       100);
     int by_regs = 8;
     cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, k_conv_tc<N, CHUNK, MODE, KS>) == cudaSuccess && fa.numRegs > 0)
+    if (cudaFuncGetAttributes(&fa, k_conv_tc<N, CHUNK, MODE, KS, RB>) == cudaSuccess && fa.numRegs > 0)
       by_regs = 65536 / (((fa.numRegs + 7) / 8) * 8 * Cfg::THREADS);
     int by_smem = smem_sm / (Cfg::SMEM + 1024);
     per_sm = std::min(std::min(by_smem, 512 / Cfg::TMEM_COLS), std::min(2048 / Cfg::THREADS, by_regs));
@@ -569,7 +590,7 @@ static helm_status launch_tc(const CUtensorMap& a0, const CUtensorMap& a1, const
   });
   HELM_CK(attr_err);
   int grid = std::min(args.ntiles, nsm * per_sm);
-  launch(k_conv_tc<N, CHUNK, MODE, KS>, grid, Cfg::THREADS, Cfg::SMEM, st, a0, a1, w, args);
+  launch(k_conv_tc<N, CHUNK, MODE, KS, RB>, grid, Cfg::THREADS, Cfg::SMEM, st, a0, a1, w, args);
   HELM_CK_LAUNCH();
   return HELM_OK;
 }
@@ -687,7 +708,18 @@ helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* e
     return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: the space-to-depth view needs one source of two row phases");
   if (fin && mode != 2) return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: the fused output layer needs mode 2");
   CUtensorMap m0, m1, mw;
-  const int rows = ks == 5 ? 12 : 8;  // patch rows of one stage (TcCfg::A_ROWS)
+  // row blocks per tile (5x5 layers): 4 (narrow chunks of N = 32) or 2, the most whose last tile row
+  // wastes at most an eighth of the grid's rows, else 1
+  int rb = 1;
+  if (ks == 5)
+    for (int c : {(N == 32 && chunk == 32) ? 4 : 2, 2}) {
+      const int tile_rows = 8 * c;
+      if ((H + tile_rows - 1) / tile_rows * tile_rows - H <= H / 8) {
+        rb = c;
+        break;
+      }
+    }
+  const int rows = ks == 5 ? 8 * rb + 4 : 8;  // patch rows of one stage (TcCfg::A_ROWS)
   if (s2d0)
     HELM_TRY(act_map_s2d(&m0, in0, chunk, B, H, W, rows));
   else
@@ -705,7 +737,7 @@ helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* e
   a.nk0 = C0 / chunk;
   a.nk1 = C1 / chunk;
   a.tiles_x = (W + 15) / 16;
-  a.tiles_y = (H + 7) / 8;
+  a.tiles_y = (H + 8 * rb - 1) / (8 * rb);
   a.ntiles = B * a.tiles_x * a.tiles_y;
   a.bias = bias;
   a.out = (__nv_bfloat16*)out;
@@ -721,11 +753,15 @@ helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* e
   a.Nx = fin ? fin->Nx : 0;
   a.Ny = fin ? fin->Ny : 0;
   a.zstride = fin ? fin->zstride : 0;
-  const int key = ks * 1000000 + mode * 100000 + N * 100 + chunk;
+  const int key = rb * 10000000 + ks * 1000000 + mode * 100000 + N * 100 + chunk;
   switch (key) {
-    case 5000000 + 32 * 100 + 32: return launch_tc<32, 32, 0, 5>(m0, m1, mw, a, st);
-    case 5000000 + 32 * 100 + 64: return launch_tc<32, 64, 0, 5>(m0, m1, mw, a, st);
-    case 5200000 + 128 * 100 + 32: return launch_tc<128, 32, 2, 5>(m0, m1, mw, a, st);
+    case 15000000 + 32 * 100 + 32: return launch_tc<32, 32, 0, 5, 1>(m0, m1, mw, a, st);
+    case 25000000 + 32 * 100 + 32: return launch_tc<32, 32, 0, 5, 2>(m0, m1, mw, a, st);
+    case 45000000 + 32 * 100 + 32: return launch_tc<32, 32, 0, 5, 4>(m0, m1, mw, a, st);
+    case 15000000 + 32 * 100 + 64: return launch_tc<32, 64, 0, 5, 1>(m0, m1, mw, a, st);
+    case 25000000 + 32 * 100 + 64: return launch_tc<32, 64, 0, 5, 2>(m0, m1, mw, a, st);
+    case 15200000 + 128 * 100 + 32: return launch_tc<128, 32, 2, 5, 1>(m0, m1, mw, a, st);
+    case 25200000 + 128 * 100 + 32: return launch_tc<128, 32, 2, 5, 2>(m0, m1, mw, a, st);
     default: return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: no kernel for this shape");
   }
 }
