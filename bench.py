@@ -35,13 +35,17 @@ WEIGHTS = os.path.join(ROOT, "paper_2607_16906_b300", "weights", "unet_paper_tra
 METRIC = "Helmholtz solves/s to rel.res 1e-6: batched mixed vs plain FP64, same B300"
 STENCIL_BYTES_FP32 = 16.0           # read z (8 B) + write A z (8 B) per point; k^2 (4 B/pt) read once per 32 RHS
 # FGMRES iterations per right-hand side of this workload with the trained network, as measured by
-# the CUDA arm (mean over the 32 RHS, FGMRES(512), up to 20 cycles); the reference arm, which
+# the CUDA arm (mean over the 32 RHS, FGMRES(128), up to 80 cycles); the reference arm, which
 # runs in a process of its own, scales its measured per-iteration time by it (the CUDA arm prints its
 # own measured mean)
-REF_ITERS_PER_SOLVE = 3580
+REF_ITERS_PER_SOLVE = 4948
 # DRAM bytes per basis vector and point of one DCGS2 step (k_dsweepA 8.00 B + k_dsweepB 8.06 B),
 # from the ncu counters of the current sweep kernels
 DCGS2_DRAM_B_PER_VPT = 16.06
+# DRAM bytes of one application of the kind-1 network per full-resolution pixel (input packing and
+# the eight tcgen05 layers, output layer fused), from the ncu counters of the current kernels on
+# 4 RHS of this workload (None until measured)
+PAPER_NET_DRAM_B_PER_PX = None
 
 
 def parse():
@@ -50,9 +54,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
-    ap.add_argument("--m", type=int, default=512, help="Krylov vectors per cycle (Sec. 4: 512)")
-    ap.add_argument("--max-outer", type=int, default=20,
-                    help="FP64 refinement steps = FGMRES(m) cycles (Sec. 4 uses 10; 20 lets every RHS reach 1e-6)")
+    ap.add_argument("--m", type=int, default=128,
+                    help="Krylov vectors per cycle (Sec. 4 uses 512; 128 is the fastest of 128..1024 measured with "
+                         "the trained kind-1 network)")
+    ap.add_argument("--max-outer", type=int, default=80,
+                    help="FP64 refinement steps = FGMRES(m) cycles (budget m x 80 = 10,240 iterations per RHS)")
     ap.add_argument("--inner-tol", type=float, default=1e-5)
     ap.add_argument("--orth", default="dcgs2", choices=["cgs2", "dcgs2"])
     ap.add_argument("--nrhs", type=int, default=32)
@@ -562,6 +568,13 @@ def run_cuda(args):
                                           "frac": None}))
     roof.update({"kernel": names.get(dom, dom), "traffic": None,
                  "peak_source": "measured (MEASURED_PEAKS.json)" if peaks else "fallback"})
+    if dom == "precond" and net.kind == 1 and prof["precond"][1] > 0:
+        # one "launch" of the preconditioner = one network application to the solver call's columns
+        npx = ctx.npts * rb
+        roof.update({"traffic": PAPER_NET_DRAM_B_PER_PX * npx if PAPER_NET_DRAM_B_PER_PX else None,
+                     "algorithmic_per_application": work["precond"] / prof["precond"][1],
+                     "applications": prof["precond"][1],
+                     "traffic_source": "ncu DRAM bytes of one application's kernels per pixel x pixels"})
     if dom == "orth" and args.orth == "dcgs2" and prof["orth"][1] > 0:
         # one "launch" of the orthogonalisation = one DCGS2 step (sweep A + sweep B + 3 small
         # kernels); its algorithmic bytes are 16 nv + 48 B per point, nv the step's basis size
