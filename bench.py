@@ -71,9 +71,11 @@ def parse():
     ap.add_argument("--large", action="store_true",
                     help="also solve the large configuration (2176^2, line arrays, FP64 refinement to 1e-8)")
     ap.add_argument("--large-rhs", type=int, default=2)
-    ap.add_argument("--large-m", type=int, default=1024)
+    ap.add_argument("--large-m", type=int, default=256)
+    ap.add_argument("--large-outer", type=int, default=60, help="refinement steps (cycles) of the large solve")
     ap.add_argument("--uneven", action="store_true", help="also solve the uneven 64-system batch in one call")
-    ap.add_argument("--uneven-m", type=int, default=256)
+    ap.add_argument("--uneven-m", type=int, default=128)
+    ap.add_argument("--uneven-outer", type=int, default=80, help="refinement steps (cycles) of the uneven solve")
     ap.add_argument("--only-extra", action="store_true",
                     help="skip the timed main workload: run only the legs asked for with --large / --uneven / "
                          "--fourier / --paper-net")
@@ -349,13 +351,13 @@ def paper_net_leg(helm, ctx, nrhs, peaks, reps=5):
             "peak_source": "measured burst bf16 (MEASURED_PEAKS.json)"}
 
 
-def large_configuration(helm, theta, nrhs, m):
+def large_configuration(helm, theta, nrhs, m, max_outer=60):
     """The large configuration: 2048^2 interior + 64 PML (2176^2, 4.7 M unknowns), 12 points per
     wavelength, thin skull ring, line-array sources; mixed path with FP64 refinement to eta_b <= 1e-8.
-    FGMRES(m) with m = `m` (the restarted FGMRES(50) of the configuration stalls with this network:
-    restart lengths of 128 and 256 already fail on the 576^2 workload); `nrhs` of the 8 right-hand
-    sides, as the Krylov basis of 2 x (m + 1) vectors per RHS has to fit in HBM.  The plain FP64 path
-    is timed over 3 iterations and extrapolated to the mixed path's count (labelled)."""
+    FGMRES(m) with m = `m` and up to `max_outer` cycles (the configuration names FGMRES(50); the kind-0
+    network stalls with restarts of 256 or less, the kind-1 network does not on the 576^2 workload);
+    `nrhs` of the 8 right-hand sides.  The plain FP64 path is timed over 3 iterations and
+    extrapolated to the mixed path's count (labelled)."""
     import torch
     from paper_2607_16906_b300 import synth
     prob = synth.large_problem(seed=5000, nrhs=nrhs)
@@ -364,7 +366,7 @@ def large_configuration(helm, theta, nrhs, m):
     net = helm.UNet(theta)
     measured_solve(helm, ctx, net, prob, nrhs, dict(m=4, tol=1e-300, mixed=True, max_outer=1), "warm-up")
     helm.helm_profile_enable(ctx, True)
-    r = measured_solve(helm, ctx, net, prob, nrhs, dict(m=m, tol=1e-8, mixed=True, max_outer=30, inner_tol=1e-5,
+    r = measured_solve(helm, ctx, net, prob, nrhs, dict(m=m, tol=1e-8, mixed=True, max_outer=max_outer, inner_tol=1e-5,
                                                         orth="dcgs2"),
                        "mixed path, FP64 refinement to 1e-8")
     prof = helm.helm_profile_read(ctx)
@@ -390,10 +392,11 @@ def large_configuration(helm, theta, nrhs, m):
     return r
 
 
-def uneven_configuration(helm, theta, m):
+def uneven_configuration(helm, theta, m, max_outer=80):
     """The uneven batch: 64 systems with sides drawn from {256..1024} + PML 16..32 and 8-12 points per
     wavelength, one point source each, all in one context and one solver call (mixed path, FGMRES(m),
-    up to 40 cycles, tol 1e-6).  Reports converged systems, iterations and launches per iteration."""
+    up to `max_outer` cycles, tol 1e-6).  Reports converged systems, iterations and launches per
+    iteration."""
     import torch
     from paper_2607_16906_b300 import synth
     probs = synth.uneven_problems()
@@ -408,7 +411,7 @@ def uneven_configuration(helm, theta, m):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = helm.helm_launch_count()
     e0.record()
-    _, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=m, tol=1e-6, mixed=True, max_outer=40, inner_tol=1e-5,
+    _, info = helm.helm_fgmres_solve(ctx, net, b, x, 1, m=m, tol=1e-6, mixed=True, max_outer=max_outer, inner_tol=1e-5,
                                      orth="dcgs2")
     e1.record()
     torch.cuda.synchronize()
@@ -447,9 +450,9 @@ def run_cuda(args):
             theta, wdesc = load_weights(args.weights, helm.weight_segments())
             out = {"metric": METRIC, "extra_legs_only": True, "weights": wdesc}
             if args.large:
-                out["large_2176"] = large_configuration(helm, theta, args.large_rhs, args.large_m)
+                out["large_2176"] = large_configuration(helm, theta, args.large_rhs, args.large_m, args.large_outer)
             if args.uneven:
-                out["uneven_64"] = uneven_configuration(helm, theta, args.uneven_m)
+                out["uneven_64"] = uneven_configuration(helm, theta, args.uneven_m, args.uneven_outer)
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
                 os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
             if args.fourier or args.paper_net:
@@ -653,8 +656,8 @@ def run_cuda(args):
                                "unpreconditioned GMRES (z_j = v_j), mixed path, same m and cycle budget")
     if rank == 0 and not args.no_small:
         small = small_configuration(helm, theta)
-    large = large_configuration(helm, theta, args.large_rhs, args.large_m) if rank == 0 and args.large else None
-    uneven = uneven_configuration(helm, theta, args.uneven_m) if rank == 0 and args.uneven else None
+    large = large_configuration(helm, theta, args.large_rhs, args.large_m, args.large_outer) if rank == 0 and args.large else None
+    uneven = uneven_configuration(helm, theta, args.uneven_m, args.uneven_outer) if rank == 0 and args.uneven else None
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:  # the CPU baseline is quoted at N = 1 only
         from oracle import unet as ou  # the bounded CPU-oracle baseline leg
