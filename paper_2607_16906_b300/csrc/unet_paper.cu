@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <vector>
 
 #include "helm_internal.cuh"
@@ -183,32 +184,60 @@ void paper_release(helm_unet* net) {
 
 // Input channels (Re s v, Im s v, c / 1500, Re sigma_c, Im sigma_c, 0, 0, 0) on the 16-padded grid,
 // written straight into the space-to-depth layout of the first layer: pixel (y, x) is phase
-// (y % 2) * 2 + x % 2 of pixel (y / 2, x / 2), 8 channels per phase.
+// (y % 2) * 2 + x % 2 of pixel (y / 2, x / 2), 8 channels per phase.  One thread per pixel of the
+// grid (Wp / PACK_THREADS, Hp), looping over the B images: the PML channels (FP64) are formed once per
+// pixel, c / 1500 once unless it differs per image (c_stride > 0); the BF16 path scales v in FP32
+// (its result is rounded to BF16) and stores each pixel's 8 channels as one 16-byte vector.
+constexpr int PACK_THREADS = 128;
 template <typename T, typename R>
-__global__ void k_paper_pack(const C<R>* __restrict__ v, int64_t col_stride, const double* __restrict__ in_scale,
-                             const double* __restrict__ chat, int64_t c_stride, const double2* __restrict__ px,
-                             const double2* __restrict__ py, int Nx, int Ny, int Hp, int Wp, int B,
-                             T* __restrict__ x0) {
-  const int64_t pix = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (pix >= (int64_t)B * Hp * Wp) return;
-  const int x = (int)(pix % Wp);
-  const int y = (int)((pix / Wp) % Hp);
-  const int b = (int)(pix / ((int64_t)Wp * Hp));
-  double ch[P_X0_CH] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (x < Nx && y < Ny) {
-    const int64_t q = (int64_t)y * Nx + x;
-    const C<R> val = v[b * col_stride + q];
-    const double s = in_scale[b];
-    ch[0] = (double)val.x * s;
-    ch[1] = (double)val.y * s;
-    ch[2] = chat[b * c_stride + q];
+__global__ void __launch_bounds__(PACK_THREADS) k_paper_pack(const C<R>* __restrict__ v, int64_t col_stride,
+                                                             const double* __restrict__ in_scale,
+                                                             const double* __restrict__ chat, int64_t c_stride,
+                                                             const double2* __restrict__ px,
+                                                             const double2* __restrict__ py, int Nx, int Ny, int Hp,
+                                                             int Wp, int B, T* __restrict__ x0) {
+  constexpr bool bf16 = std::is_same<T, __nv_bfloat16>::value;
+  const int x = blockIdx.x * PACK_THREADS + threadIdx.x;
+  const int y = blockIdx.y;
+  if (x >= Wp) return;
+  const bool in = x < Nx && y < Ny;
+  const int64_t q = (int64_t)y * Nx + x;
+  double sig_re = 0, sig_im = 0, c0 = 0;
+  if (in) {
     const double2 sx = px[x], sy = py[y];
-    ch[3] = sx.x * sy.x - sx.y * sy.y - 1.0;
-    ch[4] = sx.x * sy.y + sx.y * sy.x;
+    sig_re = sx.x * sy.x - sx.y * sy.y - 1.0;
+    sig_im = sx.x * sy.y + sx.y * sy.x;
+    c0 = chat[q];
   }
-  T* o = x0 + ((((int64_t)b * (Hp / 2) + y / 2) * (Wp / 2) + x / 2) * 4 + (y & 1) * 2 + (x & 1)) * P_X0_CH;
+  const int64_t plane = (int64_t)(Hp / 2) * (Wp / 2) * 4 * P_X0_CH;  // elements of one image
+  T* o = x0 + (((int64_t)(y / 2) * (Wp / 2) + x / 2) * 4 + (y & 1) * 2 + (x & 1)) * P_X0_CH;
+  for (int b = 0; b < B; ++b, o += plane) {
+    double ch[P_X0_CH] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (in) {
+      const C<R> val = v[b * col_stride + q];
+      if constexpr (bf16) {
+        const float s = (float)in_scale[b];
+        ch[0] = (float)val.x * s;
+        ch[1] = (float)val.y * s;
+      } else {
+        const double s = in_scale[b];
+        ch[0] = (double)val.x * s;
+        ch[1] = (double)val.y * s;
+      }
+      ch[2] = c_stride ? chat[b * c_stride + q] : c0;
+      ch[3] = sig_re;
+      ch[4] = sig_im;
+    }
+    if constexpr (bf16) {
+      __align__(16) __nv_bfloat16 hv[P_X0_CH];
 #pragma unroll
-  for (int k = 0; k < P_X0_CH; ++k) store_act(o + k, (typename Acc<T>::A)ch[k]);
+      for (int k = 0; k < P_X0_CH; ++k) hv[k] = __float2bfloat16_rn((float)ch[k]);
+      *(uint4*)o = *(const uint4*)hv;
+    } else {
+#pragma unroll
+      for (int k = 0; k < P_X0_CH; ++k) store_act(o + k, (typename Acc<T>::A)ch[k]);
+    }
+  }
 }
 
 // Space-to-depth: out[b][Y][X][(py * 2 + px) C + c] = in[b][2Y + py][2X + px][c]  (Ho = H / 2).
@@ -333,8 +362,7 @@ helm_status paper_precondition(helm_ctx* ctx, const helm_unet* net, int sys, con
   const int Hp = (s.Ny + 15) / 16 * 16, Wp = (s.Nx + 15) / 16 * 16;
   void* a[13];
   HELM_TRY(paper_buffers(P, B, Hp, Wp, fp64, a));
-  const int64_t npix = (int64_t)B * Hp * Wp;
-  launch(k_paper_pack<T, R>, cdiv(npix, 256), 256, 0, st, v, s.n, in_scale, (const double*)(ctx->chat64 + s.off),
+  launch(k_paper_pack<T, R>, dim3(cdiv(Wp, PACK_THREADS), Hp), PACK_THREADS, 0, st, v, s.n, in_scale, (const double*)(ctx->chat64 + s.off),
          (int64_t)0, (const double2*)(ctx->prof_d + s.prof_x), (const double2*)(ctx->prof_d + s.prof_y), s.Nx, s.Ny,
          Hp, Wp, B, (T*)a[PA_S0]);
   HELM_CK_LAUNCH();
@@ -824,7 +852,7 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
   // ---- forward, keeping every layer's input and pre-activation
   HELM_TRY(col_norm2<R>(ctx, bvec, 1, nb2, st));
   launch(k_palpha, cdiv(B, 64), 64, 0, st, (const double*)nb2, B, s0.n, s0.h * s0.h, in_s, out_s);
-  launch(k_paper_pack<E, R>, cdiv(npx, 256), 256, 0, st, bvec, s0.n, (const double*)in_s,
+  launch(k_paper_pack<E, R>, dim3(cdiv(Wp, PACK_THREADS), Hp), PACK_THREADS, 0, st, bvec, s0.n, (const double*)in_s,
          (const double*)(ctx->chat64), s0.n, (const double2*)(ctx->prof_d + s0.prof_x),
          (const double2*)(ctx->prof_d + s0.prof_y), s0.Nx, s0.Ny, Hp, Wp, B, a[PA_S0]);
   auto s2d = [&](const E* src, E* dst, int C, int h, int w) {  // h, w: source grid
