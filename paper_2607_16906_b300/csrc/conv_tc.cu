@@ -44,6 +44,9 @@ struct ConvTcArgs {
   // MODE 0: source 0 is an NHWC tensor of the 2H x 2W grid read as its space-to-depth view (channel
   // chunk kc = input row phase; the map's rows are traversed with stride 2)
   int s2d;
+  // optional, per image: an image whose scale is 0 (a converged column of the solver, whose network
+  // input scale is zero) is skipped by every role; with the fused output layer its output is zeroed
+  const double* img_scale;
   // MODE 2 only, optional: the network's 1x1 output layer C_out -> 2 fused into the epilogue:
   // z[b][Y][X] = out_scale[b] (wf^T a + bf) for the output pixels inside the physical Nx x Ny grid, no
   // activation stored
@@ -144,6 +147,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
       for (int s = 0; s < Cfg::STAGES; ++s) fills[s] = 0;
       for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         int b = t / (a.tiles_x * a.tiles_y);
+        if (a.img_scale && a.img_scale[b] == 0.0) continue;
         int r = t % (a.tiles_x * a.tiles_y);
         int y0 = (r / a.tiles_x) * 8 * RB, x0 = (r % a.tiles_x) * 16;
         for (int kc = 0; kc < nk && ok; ++kc) {
@@ -214,6 +218,7 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     uint32_t acc_phase = 0;
     bool ok = true;
     for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+      if (a.img_scale && a.img_scale[t / (a.tiles_x * a.tiles_y)] == 0.0) continue;
       if (!mbar_wait_warp(&tempty[acc], acc_phase ^ 1, abort_flag, a.err, 2, a.budget)) {
         ok = false;
         break;
@@ -284,12 +289,28 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
     int acc = 0;
     uint32_t acc_phase = 0;
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-      if (!mbar_wait_warp(&tfull[acc], acc_phase, abort_flag, a.err, 4, a.budget)) break;
-      tc_fence_after();
       int b = t / (a.tiles_x * a.tiles_y);
       int r = t % (a.tiles_x * a.tiles_y);
       constexpr int COUT = MODE == 0 ? N : N / 4;
       const bool fused = MODE == 2 && a.z != nullptr;
+      if (a.img_scale && a.img_scale[b] == 0.0) {
+        // skipped image: no accumulator was filled; the fused output layer writes its zeros
+        if (fused)
+          for (int rb = 0; rb < RB; ++rb) {
+            const int y = (r / a.tiles_x) * 8 * RB + rb * 8 + ly, x = (r % a.tiles_x) * 16 + lx;
+            if (y >= a.H || x >= a.W) continue;
+            for (int qy = 0; qy < 2; ++qy) {
+              const int Y = 2 * y + qy, X = 2 * x;
+              if (Y >= a.Ny || X >= a.Nx) continue;
+              float2* zp = a.z + b * a.zstride + (int64_t)Y * a.Nx + X;
+              zp[0] = make_float2(0.0f, 0.0f);
+              if (X + 1 < a.Nx) zp[1] = make_float2(0.0f, 0.0f);
+            }
+          }
+        continue;
+      }
+      if (!mbar_wait_warp(&tfull[acc], acc_phase, abort_flag, a.err, 4, a.budget)) break;
+      tc_fence_after();
 #pragma unroll 1
       for (int rb = 0; rb < RB; ++rb) {
         const int y = (r / a.tiles_x) * 8 * RB + rb * 8 + ly, x = (r % a.tiles_x) * 16 + lx;
@@ -702,7 +723,8 @@ helm_status conv_tc_up(const helm_unet* net, int l, const void* in, void* out, i
 // the 2H x 2W grid), inputs NHWC BF16 from one or two sources, epilogue bias + activation `act`.
 helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* err, int ks, int mode, int N,
                             int chunk, const void* in0, int C0, const void* in1, int C1, void* out, int B, int H,
-                            int W, int act, float slope, cudaStream_t st, bool s2d0, const RowFinal* fin) {
+                            int W, int act, float slope, cudaStream_t st, bool s2d0, const RowFinal* fin,
+                            const double* img_scale) {
   if (C0 % chunk || C1 % chunk) return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: channels not a chunk multiple");
   if (s2d0 && (mode != 0 || C1 != 0 || C0 != 2 * chunk))
     return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: the space-to-depth view needs one source of two row phases");
@@ -747,6 +769,7 @@ helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* e
   a.budget = wait_budget();
   a.skip_first = take_fault(HELM_FAULT_CONV_TILE) ? 1 : 0;
   a.s2d = s2d0 ? 1 : 0;
+  a.img_scale = img_scale;
   a.wf = fin ? fin->wf : nullptr;
   a.out_scale = fin ? fin->out_scale : nullptr;
   a.z = fin ? fin->z : nullptr;

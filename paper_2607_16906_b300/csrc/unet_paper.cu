@@ -32,7 +32,8 @@ namespace helm {
 
 helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* err, int ks, int mode, int N,
                             int chunk, const void* in0, int C0, const void* in1, int C1, void* out, int B, int H,
-                            int W, int act, float slope, cudaStream_t st, bool s2d0, const RowFinal* fin);
+                            int W, int act, float slope, cudaStream_t st, bool s2d0, const RowFinal* fin,
+                            const double* img_scale);
 
 bool tc_available();
 
@@ -387,7 +388,7 @@ helm_status paper_precondition(helm_ctx* ctx, const helm_unet* net, int sys, con
     } else {
       return conv_tc_generic(P.wtc[l], P.b32[l], P.err, 5, L.kind == P_UP ? 2 : 0, L.N, L.chunk, a[src0], C0,
                              src1 >= 0 ? a[src1] : nullptr, C1, dst >= 0 ? a[dst] : nullptr, B, H, W, 2,
-                             (float)P.slope[l], st, s2d0, fin);
+                             (float)P.slope[l], st, s2d0, fin, in_scale);
     }
   };
   int H = Hp, W = Wp;
@@ -995,5 +996,5 @@ extern "C" helm_status helm_paper_layer_forward(const helm_unet* net, int layer,
   const int C0 = l == 0 ? 4 * P_X0_CH : (l <= 3 ? 128 : 32), C1 = l >= 5 ? 32 : 0;
   return conv_tc_generic(P.wtc[l], P.b32[l], P.err, 5, L.kind == P_UP ? 2 : 0, L.N, L.chunk, in0, C0, in1, C1,
                          fused ? nullptr : out, B, H, W, 2, (float)P.slope[l], (cudaStream_t)stream,
-                         l >= 1 && l <= 3, fused ? &f : nullptr);
+                         l >= 1 && l <= 3, fused ? &f : nullptr, nullptr);
 }

@@ -94,3 +94,26 @@ def test_paper_network_mixed_cycle_is_consistent(helm, theta):
     p = probs[0]
     A = hz.assemble(p.c, p.p, p.h, p.omega)
     assert abs(hz.relres(A, x.cpu().numpy(), p.b[0].ravel()) - c["relres_true"]) <= 1e-9 * c["relres_true"]
+
+
+def test_paper_network_skips_zero_columns(helm, theta):
+    """Columns whose input scale is zero (a zero vector here; a converged column inside the solver)
+    are skipped by every tcgen05 layer: their output is exactly zero and the other columns are
+    bit-identical to a run in which every column is live."""
+    probs = small_problems(((40, 40, 12),), seed=95)
+    ctx = make_ctx(probs)
+    net = helm.UNet(theta, kind=1)
+    nrhs = 4
+    _, flat = random_batch(probs, nrhs, 96, np.complex64)
+    v = to_dev(flat, torch.complex64)
+    n = probs[0].n
+    z_all = torch.empty_like(v)
+    helm.helm_precond_apply(ctx, net, v, z_all, nrhs)
+    v0 = v.clone()
+    v0[n:2 * n] = 0
+    v0[3 * n:4 * n] = 0
+    z0 = torch.full_like(v, float("nan"))
+    helm.helm_precond_apply(ctx, net, v0, z0, nrhs)
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(z0[n:2 * n]).item() == 0 and torch.count_nonzero(z0[3 * n:]).item() == 0
+    assert torch.equal(z0[:n], z_all[:n]) and torch.equal(z0[2 * n:3 * n], z_all[2 * n:3 * n])
