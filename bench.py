@@ -81,6 +81,8 @@ def parse():
                          "--fourier / --paper-net")
     ap.add_argument("--fourier", action="store_true", help="with --only-extra: the Fourier operator leg")
     ap.add_argument("--paper-net", action="store_true", help="with --only-extra: the kind-1 network leg")
+    ap.add_argument("--train-leg", action="store_true", help="with --only-extra: the training-step leg")
+    ap.add_argument("--train-steps", type=int, default=10, help="timed steps of the training-step leg")
     ap.add_argument("--extra-rhs", type=int, default=8, help="right-hand sides of the --fourier / --paper-net legs")
     ap.add_argument("--reps", type=int, default=10, help="timed repetitions of the --fourier / --paper-net legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the bounded CPU-oracle baseline")
@@ -351,6 +353,34 @@ def paper_net_leg(helm, ctx, nrhs, peaks, reps=5):
             "peak_source": "measured burst bf16 (MEASURED_PEAKS.json)"}
 
 
+def train_leg(helm, theta, steps=10):
+    """Training-step throughput on the training configuration (64 x (128^2 + 16 PML), mixed skull /
+    GRF velocities, point-source and line-array sources): helm_train_step = network forward, adjoint
+    stencil, conv backward, AdamW (eqs. 8-9) for the weights' network kind; 3 warm-up and `steps`
+    timed steps on a copy of the weights."""
+    import torch
+    from paper_2607_16906_b300 import synth
+    cs, bs, th, om = synth.training_batch()
+    nb, nt = cs.shape[0], cs.shape[1] - 32
+    tctx = helm.Context([helm.SystemSpec(nt, nt, th, 16, om) for _ in range(nb)],
+                        torch.tensor(cs.ravel(), device="cuda"))
+    tnet = helm.UNet(theta)
+    tb = torch.tensor(bs.ravel().astype(np.complex64), device="cuda")
+    for _ in range(3):
+        helm.helm_train_step(tctx, tnet, tb, lr=1e-5)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record()
+    losses = [helm.helm_train_step(tctx, tnet, tb, lr=1e-5)[0] for _ in range(steps)]
+    t1.record()
+    torch.cuda.synchronize()
+    tms = t0.elapsed_time(t1) / steps
+    return {"steps_per_s": 1e3 / tms, "ms_per_step": tms, "samples_per_s": nb * 1e3 / tms,
+            "network_kind": tnet.kind,
+            "batch": f"{nb} x {nt}^2 + 16 PML (skull / GRF velocities, point / line-array sources)",
+            "loss_first": losses[0], "loss_last": losses[-1]}
+
+
 def large_configuration(helm, theta, nrhs, m, max_outer=60):
     """The large configuration: 2048^2 interior + 64 PML (2176^2, 4.7 M unknowns), 12 points per
     wavelength, thin skull ring, line-array sources; mixed path with FP64 refinement to eta_b <= 1e-8.
@@ -453,6 +483,8 @@ def run_cuda(args):
                 out["large_2176"] = large_configuration(helm, theta, args.large_rhs, args.large_m, args.large_outer)
             if args.uneven:
                 out["uneven_64"] = uneven_configuration(helm, theta, args.uneven_m, args.uneven_outer)
+            if args.train_leg:
+                out["train_step"] = train_leg(helm, theta, args.train_steps)
             peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
                 os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
             if args.fourier or args.paper_net:
@@ -618,30 +650,7 @@ def run_cuda(args):
     fourier = fourier_leg(helm, prob.h, prob.omega, peaks) if rank == 0 else None
     paper_net = paper_net_leg(helm, ctx, nrhs, peaks) if rank == 0 else None
 
-    # training-step throughput on the training configuration (64 x (128^2 + 16 PML), mixed skull / GRF
-    # velocities, point-source and line-array sources): helm_train_step = BF16 forward, adjoint
-    # stencil, conv backward, AdamW (eqs. 8-9); 3 warm-up and 10 timed steps on a copy of the weights
-    train = None
-    if rank == 0 and not args.no_train:
-        cs, bs, th, om = synth.training_batch()
-        nb, nt = cs.shape[0], cs.shape[1] - 32
-        tctx = helm.Context([helm.SystemSpec(nt, nt, th, 16, om) for _ in range(nb)],
-                            torch.tensor(cs.ravel(), device="cuda"))
-        tnet = helm.UNet(theta)
-        tb = torch.tensor(bs.ravel().astype(np.complex64), device="cuda")
-        for _ in range(3):
-            helm.helm_train_step(tctx, tnet, tb, lr=1e-5)
-        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        t0.record()
-        losses = [helm.helm_train_step(tctx, tnet, tb, lr=1e-5)[0] for _ in range(10)]
-        t1.record()
-        torch.cuda.synchronize()
-        tms = t0.elapsed_time(t1) / 10
-        train = {"steps_per_s": 1e3 / tms, "ms_per_step": tms, "samples_per_s": nb * 1e3 / tms,
-                 "batch": f"{nb} x {nt}^2 + 16 PML (skull / GRF velocities, point / line-array sources)",
-                 "loss_first": losses[0], "loss_last": losses[-1]}
-        del tctx, tnet, tb
+    train = train_leg(helm, theta, args.train_steps) if rank == 0 and not args.no_train else None
 
     # comparators of the metric, measured to the same tolerance on a stated subset of the same
     # right-hand sides: the plain FP64 GPU path (FP64 basis, stencil and network) and unpreconditioned
