@@ -47,6 +47,8 @@ struct ConvTcArgs {
   // optional, per image: an image whose scale is 0 (a converged column of the solver, whose network
   // input scale is zero) is skipped by every role; with the fused output layer its output is zeroed
   const double* img_scale;
+  // optional (training): the BF16 pre-activation is stored here too, at the output's index
+  __nv_bfloat16* pre_out;
   // MODE 2 only, optional: the network's 1x1 output layer C_out -> 2 fused into the epilogue:
   // z[b][Y][X] = out_scale[b] (wf^T a + bf) for the output pixels inside the physical Nx x Ny grid, no
   // activation stored
@@ -357,9 +359,11 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
                                      : (((int64_t)b * 2 * a.H + 2 * y + tap / 2) * (2 * a.W) + 2 * x + tap % 2);
             __nv_bfloat16* o = a.out + opix * COUT + co0;
             __align__(16) __nv_bfloat16 hv[16];
+            __align__(16) __nv_bfloat16 hp[16];
 #pragma unroll
             for (int k = 0; k < 16; ++k) {
               float f = __uint_as_float(v[k]) + a.bias[co0 + k];
+              hp[k] = __float2bfloat16_rn(f);
               if (a.act == 1) f = fmaxf(f, 0.0f);
               else if (a.act == 2) f = f > 0.0f ? f : a.slope * f;
               hv[k] = __float2bfloat16_rn(f);
@@ -367,6 +371,11 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
             uint4* dst = (uint4*)o;
             dst[0] = ((const uint4*)hv)[0];
             dst[1] = ((const uint4*)hv)[1];
+            if (a.pre_out) {
+              uint4* dp = (uint4*)(a.pre_out + opix * COUT + co0);
+              dp[0] = ((const uint4*)hp)[0];
+              dp[1] = ((const uint4*)hp)[1];
+            }
           }
         }
       }
@@ -724,7 +733,7 @@ helm_status conv_tc_up(const helm_unet* net, int l, const void* in, void* out, i
 helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* err, int ks, int mode, int N,
                             int chunk, const void* in0, int C0, const void* in1, int C1, void* out, int B, int H,
                             int W, int act, float slope, cudaStream_t st, bool s2d0, const RowFinal* fin,
-                            const double* img_scale) {
+                            const double* img_scale, void* pre_out) {
   if (C0 % chunk || C1 % chunk) return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: channels not a chunk multiple");
   if (s2d0 && (mode != 0 || C1 != 0 || C0 != 2 * chunk))
     return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: the space-to-depth view needs one source of two row phases");
@@ -770,6 +779,7 @@ helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* e
   a.skip_first = take_fault(HELM_FAULT_CONV_TILE) ? 1 : 0;
   a.s2d = s2d0 ? 1 : 0;
   a.img_scale = img_scale;
+  a.pre_out = (__nv_bfloat16*)pre_out;
   a.wf = fin ? fin->wf : nullptr;
   a.out_scale = fin ? fin->out_scale : nullptr;
   a.z = fin ? fin->z : nullptr;

@@ -33,7 +33,7 @@ namespace helm {
 helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* err, int ks, int mode, int N,
                             int chunk, const void* in0, int C0, const void* in1, int C1, void* out, int B, int H,
                             int W, int act, float slope, cudaStream_t st, bool s2d0, const RowFinal* fin,
-                            const double* img_scale);
+                            const double* img_scale, void* pre_out = nullptr);
 
 bool tc_available();
 
@@ -458,8 +458,11 @@ helm_status paper_check(const helm_unet* net, cudaStream_t st) {
 
 // ================================================================== training (eqs. 8-9) of kind 1
 //
-// Forward on CUDA cores in E (FP32 for training, FP64 for gradient checks) keeping every layer's
-// input and pre-activation; backward in reverse through the same reformulated layers:
+// Forward keeping every layer's input and pre-activation: on the mixed path (R = FP32) the tcgen05
+// layers of the preconditioner in BF16 with FP32 accumulation (activations and pre-activations
+// stored in BF16, the encoder inputs rearranged space-to-depth for the weight gradients), on the
+// FP64 path (gradient checks) CUDA cores in FP64.  Backward on CUDA cores, gradients in E = R,
+// in reverse through the same reformulated layers:
 //   PReLU:  g_pre = g_post (pre > 0 ? 1 : a),  dL/da = sum g_post (pre > 0 ? 0 : pre);
 //   up layer: the pre-activation gradient on the 2H x 2W grid is rearranged space-to-depth into the
 //     GEMM's 4 C_out columns (column q C_out + co = output phase q), the inverse of the forward's
@@ -534,14 +537,15 @@ __global__ void k_d2s(const E* __restrict__ in, E* __restrict__ out, int C, int 
   out[o] = accumulate ? out[o] + in[e] : in[e];
 }
 
-// PReLU backward in place on g (g_post -> g_pre); per-block partial sums of dL/da.
-template <typename E>
-__global__ void k_prelu_bwd(E* __restrict__ g, const E* __restrict__ pre, int64_t n, double slope,
+// PReLU backward in place on g (g_post -> g_pre); per-block partial sums of dL/da.  pre: the kept
+// pre-activation (E, or BF16 on the mixed path).
+template <typename E, typename T>
+__global__ void k_prelu_bwd(E* __restrict__ g, const T* __restrict__ pre, int64_t n, double slope,
                             double* __restrict__ partial) {
   __shared__ double red[256 / 32];
   double s = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    const E p = pre[i], gv = g[i];
+    const E p = (E)to_acc(pre[i]), gv = g[i];
     if (p > E(0)) {
       g[i] = gv;
     } else {
@@ -562,9 +566,10 @@ __global__ void k_prelu_bwd(E* __restrict__ g, const E* __restrict__ pre, int64_
 // Weight gradient of a KS x KS GEMM layer: partial[split][tap][k][n] = sum over the split's pixels of
 // in[px + tap][k] g[px][n]; one block per (split, 16 x 16 (k, n) tile, tap).  With tap == ks * ks
 // (an extra grid slice) the block sums g for the bias instead (k tile 0 only).  Each block
-// accumulates its split in E (FP32 on the training path); the splits are summed in FP64.
-template <typename E>
-__global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const E* __restrict__ in0, int C0, const E* __restrict__ in1,
+// accumulates its split in E (FP32 on the training path); the splits are summed in FP64.  The
+// activations are of type T (E, or BF16 on the mixed path).
+template <typename E, typename T>
+__global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const T* __restrict__ in0, int C0, const T* __restrict__ in1,
                                                        int C1, const E* __restrict__ g, int N, int B, int H, int W,
                                                        int ks, int nsplit, double* __restrict__ partial,
                                                        double* __restrict__ bpartial) {
@@ -598,7 +603,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const E* __restrict__ in0
           const int yy = y + dy, xx = x + dx;
           if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
             const int64_t q = (b * H + yy) * W + xx;
-            xv = k < C0 ? in0[q * C0 + k] : in1[q * C1 + (k - C0)];
+            xv = (E)to_acc(k < C0 ? in0[q * C0 + k] : in1[q * C1 + (k - C0)]);
           }
         }
       }
@@ -746,12 +751,12 @@ __global__ void k_pgather(const double* __restrict__ gw5, const double* __restri
   }
 }
 
-template <typename E>
-static helm_status pwgrad(const E* in0, int C0, const E* in1, int C1, const E* g, int N, int B, int H, int W, int ks,
+template <typename E, typename T>
+static helm_status pwgrad(const T* in0, int C0, const T* in1, int C1, const E* g, int N, int B, int H, int W, int ks,
                           double* partial, double* bpartial, int nsplit, double* gw, double* gb, cudaStream_t st) {
   const int K = C0 + C1;
   dim3 grid(nsplit, ((K + 15) / 16) * ((N + 15) / 16), ks * ks + 1);
-  launch(k_pwgrad<E>, grid, PW_THREADS, 0, st, in0, C0, in1, C1, g, N, B, H, W, ks, nsplit, partial, bpartial);
+  launch(k_pwgrad<E, T>, grid, PW_THREADS, 0, st, in0, C0, in1, C1, g, N, B, H, W, ks, nsplit, partial, bpartial);
   const int64_t nw = (int64_t)ks * ks * K * N;
   launch(k_pwgrad_reduce, cdiv(std::max<int64_t>(nw, N), 256), 256, 0, st, (const double*)partial,
          (const double*)bpartial, nsplit, nw, N, gw, gb);
@@ -781,7 +786,9 @@ __global__ void k_pfinal(const E* __restrict__ in, const double* __restrict__ w5
 
 template <typename R>
 helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, double* loss_host, cudaStream_t st) {
-  using E = R;  // FP32 (training) or FP64 (checks)
+  using E = R;  // gradients: FP32 (training) or FP64 (checks)
+  constexpr bool mixed = sizeof(R) == 4;
+  using T = typename std::conditional<mixed, __nv_bfloat16, double>::type;  // activations
   PaperNet& P = *net->pn;
   const SysHost& s0 = ctx->sys[0];
   for (auto& s : ctx->sys)
@@ -812,8 +819,8 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
     return o;
   };
   size_t o_act[13], o_pre[8];
-  for (int k = 0; k < 13; ++k) o_act[k] = take(sizeof(E) * el_act[k] * B);
-  for (int k = 0; k < 8; ++k) o_pre[k] = take(sizeof(E) * el_pre[k] * B);
+  for (int k = 0; k < 13; ++k) o_act[k] = take(sizeof(T) * el_act[k] * B);
+  for (int k = 0; k < 8; ++k) o_pre[k] = take(sizeof(T) * el_pre[k] * B);
   const size_t o_z = take(sizeof(C<R>) * ctx->npts), o_r = take(sizeof(C<R>) * ctx->npts),
                o_ahr = take(sizeof(C<R>) * ctx->npts);
   const size_t o_gy = take(sizeof(E) * 2 * npx);
@@ -826,10 +833,10 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
                o_sc = take(sizeof(double) * 5 * B);
   HELM_TRY(ctx->ws_train.reserve(off));
   char* base = (char*)ctx->ws_train.ptr;
-  E* a[13];
-  E* pre[8];
-  for (int k = 0; k < 13; ++k) a[k] = (E*)(base + o_act[k]);
-  for (int k = 0; k < 8; ++k) pre[k] = (E*)(base + o_pre[k]);
+  T* a[13];
+  T* pre[8];
+  for (int k = 0; k < 13; ++k) a[k] = (T*)(base + o_act[k]);
+  for (int k = 0; k < 8; ++k) pre[k] = (T*)(base + o_pre[k]);
   C<R>* z = (C<R>*)(base + o_z);
   C<R>* rres = (C<R>*)(base + o_r);
   C<R>* ahr = (C<R>*)(base + o_ahr);
@@ -853,34 +860,50 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
   // ---- forward, keeping every layer's input and pre-activation
   HELM_TRY(col_norm2<R>(ctx, bvec, 1, nb2, st));
   launch(k_palpha, cdiv(B, 64), 64, 0, st, (const double*)nb2, B, s0.n, s0.h * s0.h, in_s, out_s);
-  launch(k_paper_pack<E, R>, dim3(cdiv(Wp, PACK_THREADS), Hp), PACK_THREADS, 0, st, bvec, s0.n, (const double*)in_s,
+  launch(k_paper_pack<T, R>, dim3(cdiv(Wp, PACK_THREADS), Hp), PACK_THREADS, 0, st, bvec, s0.n, (const double*)in_s,
          (const double*)(ctx->chat64), s0.n, (const double2*)(ctx->prof_d + s0.prof_x),
          (const double2*)(ctx->prof_d + s0.prof_y), s0.Nx, s0.Ny, Hp, Wp, B, a[PA_S0]);
+  auto s2d_act = [&](const T* src, T* dst, int C, int h, int w) {  // h, w: source grid
+    const int64_t n = (int64_t)B * (h / 2) * (w / 2) * 4 * C;
+    launch(k_s2d<T>, cdiv(n, 256), 256, 0, st, src, dst, C, B, h / 2, w / 2);
+  };
   auto s2d = [&](const E* src, E* dst, int C, int h, int w) {  // h, w: source grid
     const int64_t n = (int64_t)B * (h / 2) * (w / 2) * 4 * C;
     launch(k_s2d<E>, cdiv(n, 256), 256, 0, st, src, dst, C, B, h / 2, w / 2);
   };
-  auto fwd = [&](int l, const E* i0, int C0, const E* i1, int C1, int h, int w) {
+  helm_status fst = HELM_OK;
+  auto fwd = [&](int l, const T* i0, int C0, const T* i1, int C1, int h, int w) {
     const PaperLayer& L = kP[l];
-    dim3 grid(cdiv((int64_t)B * h * w, PC_THREADS), L.N / 16);
-    E* post = a[l < 4 ? PA_E1 + 2 * l : PA_D3 + (l - 4)];
-    launch(k_pconv_keep<E>, grid, PC_THREADS, 0, st, i0, C0, i1, C1, wts(l), (const double*)P.b5[l], pre[l], post,
-           L.N, L.cout, L.kind == P_UP ? 1 : 0, B, h, w, 5, P.slope[l]);
+    T* post = a[l < 4 ? PA_E1 + 2 * l : PA_D3 + (l - 4)];
+    if constexpr (mixed) {
+      if (fst == HELM_OK)
+        fst = conv_tc_generic(P.wtc[l], P.b32[l], P.err, 5, L.kind == P_UP ? 2 : 0, L.N, L.chunk, i0, C0, i1, C1, post,
+                              B, h, w, 2, (float)P.slope[l], st, false, nullptr, nullptr, pre[l]);
+    } else {
+      dim3 grid(cdiv((int64_t)B * h * w, PC_THREADS), L.N / 16);
+      launch(k_pconv_keep<T>, grid, PC_THREADS, 0, st, i0, C0, i1, C1, wts(l), (const double*)P.b5[l], pre[l], post,
+             L.N, L.cout, L.kind == P_UP ? 1 : 0, B, h, w, 5, P.slope[l]);
+    }
   };
   fwd(0, a[PA_S0], 32, nullptr, 0, H / 2, W / 2);
-  s2d(a[PA_E1], a[PA_S1], 32, H / 2, W / 2);
+  s2d_act(a[PA_E1], a[PA_S1], 32, H / 2, W / 2);
   fwd(1, a[PA_S1], 128, nullptr, 0, H / 4, W / 4);
-  s2d(a[PA_E2], a[PA_S2], 32, H / 4, W / 4);
+  s2d_act(a[PA_E2], a[PA_S2], 32, H / 4, W / 4);
   fwd(2, a[PA_S2], 128, nullptr, 0, H / 8, W / 8);
-  s2d(a[PA_E3], a[PA_S3], 32, H / 8, W / 8);
+  s2d_act(a[PA_E3], a[PA_S3], 32, H / 8, W / 8);
   fwd(3, a[PA_S3], 128, nullptr, 0, H / 16, W / 16);
   fwd(4, a[PA_E4], 32, nullptr, 0, H / 16, W / 16);
   fwd(5, a[PA_D3], 32, a[PA_E3], 32, H / 8, W / 8);
   fwd(6, a[PA_D2], 32, a[PA_E2], 32, H / 4, W / 4);
   fwd(7, a[PA_D1], 32, a[PA_E1], 32, H / 2, W / 2);
-  launch(k_pfinal<E, R>, cdiv((int64_t)B * s0.n, 256), 256, 0, st, (const E*)a[PA_D0],
-         (const double*)P.w5[PAPER_LAYERS - 1], (const double*)P.b5[PAPER_LAYERS - 1], (const double*)out_s, s0.Nx,
-         s0.Ny, Hp, Wp, B, z, s0.n);
+  HELM_TRY(fst);
+  if constexpr (mixed)  // the output layer with the BF16-rounded weights of the preconditioner
+    launch(k_paper_final<T, R>, cdiv((int64_t)B * s0.n, 256), 256, 0, st, (const T*)a[PA_D0], P.wout32,
+           P.wout32 + 64, (const double*)out_s, s0.Nx, s0.Ny, Hp, Wp, B, z, s0.n);
+  else
+    launch(k_pfinal<T, R>, cdiv((int64_t)B * s0.n, 256), 256, 0, st, (const T*)a[PA_D0],
+           (const double*)P.w5[PAPER_LAYERS - 1], (const double*)P.b5[PAPER_LAYERS - 1], (const double*)out_s,
+           s0.Nx, s0.Ny, Hp, Wp, B, z, s0.n);
   HELM_CK_LAUNCH();
   // ---- loss (eq. 9) and the gradient of the network output
   HELM_TRY(residual_op<R>(ctx, z, bvec, rres, 1, sums, st));
@@ -899,7 +922,7 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
   };
   auto prelu_bwd = [&](int l, E* g, int64_t n) {
     const int nb = (int)std::min<int64_t>(NPP, cdiv(n, 256));
-    launch(k_prelu_bwd<E>, nb, 256, 0, st, g, (const E*)pre[l], n, P.slope[l], pp);
+    launch(k_prelu_bwd<E, T>, nb, 256, 0, st, g, (const T*)pre[l], n, P.slope[l], pp);
     return nb;
   };
   auto dgrad = [&](const E* g, int N, int l, E* gin0, int C0, E* gin1, int C1, int h, int w, int ks) {
@@ -911,7 +934,7 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
     launch(k_d2s<E>, cdiv(n, 256), 256, 0, st, gs, gprev, C, B, hi, wi, 1);
   };
   // output layer (1 x 1, N = 2): weights, bias, input gradient
-  HELM_TRY(pwgrad<E>(a[PA_D0], 32, (const E*)nullptr, 0, gy, 2, B, H, W, 1, part, bpart, NSPLIT, gw, gbias, st));
+  HELM_TRY((pwgrad<E, T>(a[PA_D0], 32, (const T*)nullptr, 0, gy, 2, B, H, W, 1, part, bpart, NSPLIT, gw, gbias, st)));
   gather(PAPER_LAYERS - 1, 0);
   dgrad(gy, 2, PAPER_LAYERS - 1, gA, 32, nullptr, 0, H, W, 1);  // gD0 -> gA
   // decoder: l = 7 (d0) .. 4 (d3); the post-activation gradient in gA is on the layer's output grid
@@ -921,10 +944,10 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
     const int64_t nout = (int64_t)B * (2 * h) * (2 * w) * 32;
     const int nparts = prelu_bwd(l, gA, nout);                       // gA: g_pre on the 2h x 2w grid
     s2d(gA, gB, 32, 2 * h, 2 * w);                                   // gB: GEMM columns on h x w (128)
-    const E* in0 = a[l == 4 ? PA_E4 : PA_D3 + (l - 4) - 1];          // decoder input of this layer
-    const E* in1 = l == 4 ? nullptr : a[PA_E4 - 2 * (l - 4)];        // skip (e_3, e_2, e_1 for l = 5, 6, 7)
+    const T* in0 = a[l == 4 ? PA_E4 : PA_D3 + (l - 4) - 1];          // decoder input of this layer
+    const T* in1 = l == 4 ? nullptr : a[PA_E4 - 2 * (l - 4)];        // skip (e_3, e_2, e_1 for l = 5, 6, 7)
     const int C1 = l == 4 ? 0 : 32;
-    HELM_TRY(pwgrad<E>(in0, 32, in1, C1, gB, 128, B, h, w, 5, part, bpart, NSPLIT, gw, gbias, st));
+    HELM_TRY((pwgrad<E, T>(in0, 32, in1, C1, gB, 128, B, h, w, 5, part, bpart, NSPLIT, gw, gbias, st)));
     gather(l, nparts);
     E* ge = gE[7 - l];                                               // e_1 (l = 7) .. e_4 (l = 4) grad
     if (l == 4)
@@ -937,9 +960,9 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
     const int h = H >> (l + 1), w = W >> (l + 1);
     const int64_t nout = (int64_t)B * h * w * 32;
     const int nparts = prelu_bwd(l, gE[l], nout);
-    const E* in = a[PA_S0 + 2 * l];                                   // S0, S1, S2, S3
+    const T* in = a[PA_S0 + 2 * l];                                   // S0, S1, S2, S3
     const int K = l == 0 ? 32 : 128;
-    HELM_TRY(pwgrad<E>(in, K, (const E*)nullptr, 0, gE[l], 32, B, h, w, 5, part, bpart, NSPLIT, gw, gbias, st));
+    HELM_TRY((pwgrad<E, T>(in, K, (const T*)nullptr, 0, gE[l], 32, B, h, w, 5, part, bpart, NSPLIT, gw, gbias, st)));
     gather(l, nparts);
     if (l > 0) {
       dgrad(gE[l], 32, l, gC, 128, nullptr, 0, h, w, 5);             // gradient on S_l (128 channels)

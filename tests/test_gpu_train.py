@@ -189,18 +189,22 @@ def test_paper_network_fp64_loss_and_gradient_match_oracle(helm):
     assert np.abs(g - gr).max() <= 1e-9 * np.abs(gr).max()
 
 
-def test_paper_network_fp32_gradient_and_training(helm):
-    """The FP32 training path of kind 1 gives the oracle's FP64 gradient to FP32 accuracy, and a few
-    AdamW steps lower the batch loss."""
+def test_paper_network_mixed_gradient_and_training(helm):
+    """The mixed training path of kind 1 (the tcgen05 layers in BF16 with FP32 accumulation for the
+    forward, activations and pre-activations kept in BF16, FP32 backward on CUDA cores) matches the
+    oracle's BF16 emulation: loss to 2e-2, gradient cosine > 0.999 and normwise error <= 5e-2 (as for
+    kind 0); a few AdamW steps lower the batch loss."""
     c, b, nx, p, h, om = _batch(B=4, nx=28, p=6, seed=64)
     theta = _theta_paper(helm, 44)
     ctx = _ctx(helm, c, nx, p, h, om)
     net = helm.UNet(theta, kind=1)
     b32 = torch.tensor(b.ravel().astype(np.complex64), device="cuda")
     L, g = helm.helm_loss_grad(ctx, net, b32)
-    Lr, gr, _ = ot.loss_and_grad(theta, b.astype(np.complex64).astype(complex), c, p, h, om, kind=1)
+    Lr, gr, _ = ot.loss_and_grad(theta, b.astype(np.complex64).astype(complex), c, p, h, om, kind=1, bf16=True)
     g = g.cpu().numpy()
-    assert abs(L - Lr) <= 1e-4 * Lr
-    assert np.linalg.norm(g - gr) <= 1e-3 * np.linalg.norm(gr)
+    assert abs(L - Lr) <= 2e-2 * Lr, (L, Lr)
+    cos = g @ gr / (np.linalg.norm(g) * np.linalg.norm(gr))
+    assert cos > 0.999, cos
+    assert np.linalg.norm(g - gr) <= 5e-2 * np.linalg.norm(gr)
     losses = [helm.helm_train_step(ctx, net, b32, lr=1e-3, wd=0.0, clip=1.0)[0] for _ in range(12)]
     assert losses[-1] < 0.9 * losses[0], losses
