@@ -475,7 +475,7 @@ helm_status paper_check(const helm_unet* net, cudaStream_t st) {
 // Each master weight of an 8x8 layer appears exactly once among the 5x5 taps, so its gradient is read
 // back from there (the structural zeros' gradients are dropped).
 
-constexpr int PW_THREADS = 256;  // weight-gradient tile: 16 k x 16 n outputs, 32 pixels per stage
+constexpr int PW_THREADS = 256;  // weight-gradient block: 16 x 16 threads
 
 // Forward GEMM layer on CUDA cores with the pre-activation kept (up: both written depth-to-space).
 template <typename E>
@@ -564,10 +564,12 @@ __global__ void k_prelu_bwd(E* __restrict__ g, const T* __restrict__ pre, int64_
 }
 
 // Weight gradient of a KS x KS GEMM layer: partial[split][tap][k][n] = sum over the split's pixels of
-// in[px + tap][k] g[px][n]; one block per (split, 16 x 16 (k, n) tile, tap).  With tap == ks * ks
-// (an extra grid slice) the block sums g for the bias instead (k tile 0 only).  Each block
-// accumulates its split in E (FP32 on the training path); the splits are summed in FP64.  The
+// in[px + tap][k] g[px][n]; one block per (split, 64 x 64 (k, n) tile, tap), each thread a 4 x 4
+// register tile of outer-product sums over 32-pixel chunks staged in shared memory.  With
+// tap == ks * ks (an extra grid slice) the block sums g for the bias instead (k tile 0 only).  Each
+// block accumulates its split in E (FP32 on the training path); the splits are summed in FP64.  The
 // activations are of type T (E, or BF16 on the mixed path).
+constexpr int PW_TK = 64, PW_TN = 64, PW_PX = 32;
 template <typename E, typename T>
 __global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const T* __restrict__ in0, int C0, const T* __restrict__ in1,
                                                        int C1, const E* __restrict__ g, int N, int B, int H, int W,
@@ -575,53 +577,81 @@ __global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const T* __restrict__ in0
                                                        double* __restrict__ bpartial) {
   const int K = C0 + C1, r = ks / 2;
   const int split = blockIdx.x, tap = blockIdx.z;
-  const int nkt = (K + 15) / 16;
-  const int k0 = (blockIdx.y % nkt) * 16, n0 = (blockIdx.y / nkt) * 16;
-  const int tk = threadIdx.x & 15, tn = threadIdx.x >> 4;
+  const int nkt = (K + PW_TK - 1) / PW_TK;
+  const int k0 = (blockIdx.y % nkt) * PW_TK, n0 = (blockIdx.y / nkt) * PW_TN;
+  const int tk = threadIdx.x & 15, tn = threadIdx.x >> 4;  // this thread: k0 + 4 tk + i, n0 + 4 tn + j
   const int64_t P = (int64_t)B * H * W;
   const int64_t pb = P * split / nsplit, pe = P * (split + 1) / nsplit;
-  __shared__ E xs[32][17];
-  __shared__ E gs[32][17];
+  __shared__ __align__(16) E xs[PW_PX][PW_TK];
+  __shared__ __align__(16) E gs[PW_PX][PW_TN];
+  __shared__ int64_t sq[PW_PX];  // the tap's input pixel of each chunk pixel (-1: outside / past the split)
+  __shared__ int64_t sp[PW_PX];  // the chunk pixel itself (-1: past the split)
   const bool bias = tap == ks * ks;
   if (bias && k0 != 0) return;
   const int dy = bias ? 0 : tap / ks - r, dx = bias ? 0 : tap % ks - r;
-  E acc = 0;
-  for (int64_t p0 = pb; p0 < pe; p0 += 32) {
-    for (int e = threadIdx.x; e < 512; e += PW_THREADS) {
-      const int p = e >> 4, c = e & 15;
-      const int64_t px = p0 + p;
-      E xv = 0, gv = 0;
+  E acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
+  for (int64_t p0 = pb; p0 < pe; p0 += PW_PX) {
+    if (threadIdx.x < PW_PX) {
+      const int64_t px = p0 + threadIdx.x;
+      int64_t q = -1, pp = -1;
       if (px < pe) {
+        pp = px;
         const int x = (int)(px % W);
         const int y = (int)((px / W) % H);
         const int64_t b = px / ((int64_t)W * H);
-        if (n0 + c < N) gv = g[px * N + n0 + c];
-        const int k = k0 + c;
-        if (bias) {
-          xv = E(1);
-        } else if (k < K) {
-          const int yy = y + dy, xx = x + dx;
-          if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
-            const int64_t q = (b * H + yy) * W + xx;
-            xv = (E)to_acc(k < C0 ? in0[q * C0 + k] : in1[q * C1 + (k - C0)]);
-          }
-        }
+        const int yy = y + dy, xx = x + dx;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) q = (b * H + yy) * W + xx;
       }
+      sq[threadIdx.x] = q;
+      sp[threadIdx.x] = pp;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < PW_PX * PW_TK; e += PW_THREADS) {
+      const int p = e / PW_TK, c = e % PW_TK;
+      const int k = k0 + c, n = n0 + c;
+      E xv = 0, gv = 0;
+      if (bias) {
+        xv = (c == 0 && sp[p] >= 0) ? E(1) : E(0);
+      } else if (k < K && sq[p] >= 0) {
+        const int64_t q = sq[p];
+        xv = (E)to_acc(k < C0 ? in0[q * C0 + k] : in1[q * C1 + (k - C0)]);
+      }
+      if (n < N && sp[p] >= 0) gv = g[sp[p] * N + n];
       xs[p][c] = xv;
       gs[p][c] = gv;
     }
     __syncthreads();
-#pragma unroll 8
-    for (int p = 0; p < 32; ++p) acc += xs[p][tk] * gs[p][tn];
+#pragma unroll 4
+    for (int p = 0; p < PW_PX; ++p) {
+      E xv[4], gv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        xv[i] = xs[p][4 * tk + i];
+        gv[i] = gs[p][4 * tn + i];
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += xv[i] * gv[j];
+    }
     __syncthreads();
   }
-  const int k = k0 + tk, n = n0 + tn;
-  if (n >= N) return;
-  if (bias) {
-    if (tk == 0) bpartial[(int64_t)split * N + n] = (double)acc;
-  } else if (k < K) {
-    partial[(((int64_t)split * ks * ks + tap) * K + k) * N + n] = (double)acc;
-  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = k0 + 4 * tk + i, n = n0 + 4 * tn + j;
+      if (n >= N) continue;
+      if (bias) {
+        if (k == 0) bpartial[(int64_t)split * N + n] = (double)acc[i][j];
+      } else if (k < K) {
+        partial[(((int64_t)split * ks * ks + tap) * K + k) * N + n] = (double)acc[i][j];
+      }
+    }
 }
 
 // Sum the split partials in a fixed order: gw[tap][k][n], gb[n].
@@ -641,39 +671,88 @@ __global__ void k_pwgrad_reduce(const double* __restrict__ partial, const double
 }
 
 // Input gradient of a KS x KS GEMM layer: gin[q][k] = sum_{tap, n} W[tap][k][n] g[q - tap][n]; channels
-// k < C0 go to gin0 (C0 per pixel), the rest to gin1.  One thread per (pixel, 16 channels).
+// k < C0 go to gin0 (C0 per pixel), the rest to gin1.  One block per (64 pixels, 64 channels), each
+// thread a 4 x 4 register tile; per tap, 32-column chunks of g (rows of the tap-shifted pixels) and
+// of the tap's weights are staged in shared memory.
+constexpr int PD_PX = 64, PD_TK = 64, PD_NC = 32;
 template <typename E>
-__global__ void __launch_bounds__(PC_THREADS) k_pdgrad(const E* __restrict__ g, int N, const E* __restrict__ w5,
-                                                       E* __restrict__ gin0, int C0, E* __restrict__ gin1, int C1,
-                                                       int B, int H, int W, int ks) {
-  const int64_t pix = blockIdx.x * (int64_t)PC_THREADS + threadIdx.x;
-  if (pix >= (int64_t)B * H * W) return;
-  const int k0 = blockIdx.y * 16;
+__global__ void __launch_bounds__(256) k_pdgrad(const E* __restrict__ g, int N, const E* __restrict__ w5,
+                                                E* __restrict__ gin0, int C0, E* __restrict__ gin1, int C1, int B,
+                                                int H, int W, int ks) {
   const int K = C0 + C1, r = ks / 2;
-  const int x = (int)(pix % W);
-  const int y = (int)((pix / W) % H);
-  const int64_t b = pix / ((int64_t)W * H);
-  E acc[16];
+  const int64_t P = (int64_t)B * H * W;
+  const int64_t q0 = (int64_t)blockIdx.x * PD_PX;
+  const int k0 = blockIdx.y * PD_TK;
+  const int tq = threadIdx.x >> 4, tk = threadIdx.x & 15;  // pixels q0 + 4 tq + i, channels k0 + 4 tk + j
+  __shared__ __align__(16) E gs[PD_PX][PD_NC + 1];
+  __shared__ __align__(16) E ws[PD_NC][PD_TK];
+  __shared__ int sy[PD_PX], sx[PD_PX];
+  __shared__ int64_t sb[PD_PX], ssrc[PD_PX];
+  if (threadIdx.x < PD_PX) {
+    const int64_t q = q0 + threadIdx.x;
+    if (q < P) {
+      sx[threadIdx.x] = (int)(q % W);
+      sy[threadIdx.x] = (int)((q / W) % H);
+      sb[threadIdx.x] = q / ((int64_t)W * H);
+    } else {
+      sb[threadIdx.x] = -1;
+    }
+  }
+  E acc[4][4];
 #pragma unroll
-  for (int k = 0; k < 16; ++k) acc[k] = 0;
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0;
   for (int tap = 0; tap < ks * ks; ++tap) {
-    const int yy = y - (tap / ks - r), xx = x - (tap % ks - r);  // output pixel that read this one at `tap`
-    if (yy < 0 || yy >= H || xx < 0 || xx >= W) continue;
-    const E* gp = g + ((b * H + yy) * W + xx) * N;
+    __syncthreads();
+    if (threadIdx.x < PD_PX) {  // the output pixel that read this one at `tap`
+      int64_t src = -1;
+      if (sb[threadIdx.x] >= 0) {
+        const int yy = sy[threadIdx.x] - (tap / ks - r), xx = sx[threadIdx.x] - (tap % ks - r);
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) src = (sb[threadIdx.x] * H + yy) * W + xx;
+      }
+      ssrc[threadIdx.x] = src;
+    }
     const E* wt = w5 + (int64_t)tap * K * N;
-    for (int n = 0; n < N; ++n) {
-      const E gv = gp[n];
+    for (int nc = 0; nc < N; nc += PD_NC) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < PD_PX * PD_NC; e += 256) {
+        const int p = e / PD_NC, c = e % PD_NC;
+        const int64_t src = ssrc[p];
+        gs[p][c] = (src >= 0 && nc + c < N) ? g[src * N + nc + c] : E(0);
+      }
+      for (int e = threadIdx.x; e < PD_NC * PD_TK; e += 256) {
+        const int c = e / PD_TK, kk = e % PD_TK;
+        const int k = k0 + kk, n = nc + c;
+        ws[c][kk] = (k < K && n < N) ? wt[(int64_t)k * N + n] : E(0);
+      }
+      __syncthreads();
+#pragma unroll 8
+      for (int c = 0; c < PD_NC; ++c) {
+        E gv[4], wv[4];
 #pragma unroll
-      for (int k = 0; k < 16; ++k) acc[k] += gv * wt[(int64_t)(k0 + k) * N + n];
+        for (int i = 0; i < 4; ++i) gv[i] = gs[4 * tq + i][c];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) wv[j] = ws[c][4 * tk + j];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] += gv[i] * wv[j];
+      }
     }
   }
 #pragma unroll
-  for (int k = 0; k < 16; ++k) {
-    const int kk = k0 + k;
-    if (kk < C0)
-      gin0[pix * C0 + kk] = acc[k];
-    else if (kk < K)
-      gin1[pix * C1 + (kk - C0)] = acc[k];
+  for (int i = 0; i < 4; ++i) {
+    const int64_t q = q0 + 4 * tq + i;
+    if (q >= P) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int kk = k0 + 4 * tk + j;
+      if (kk < C0)
+        gin0[q * C0 + kk] = acc[i][j];
+      else if (kk < K)
+        gin1[q * C1 + (kk - C0)] = acc[i][j];
+    }
   }
 }
 
@@ -755,7 +834,7 @@ template <typename E, typename T>
 static helm_status pwgrad(const T* in0, int C0, const T* in1, int C1, const E* g, int N, int B, int H, int W, int ks,
                           double* partial, double* bpartial, int nsplit, double* gw, double* gb, cudaStream_t st) {
   const int K = C0 + C1;
-  dim3 grid(nsplit, ((K + 15) / 16) * ((N + 15) / 16), ks * ks + 1);
+  dim3 grid(nsplit, ((K + PW_TK - 1) / PW_TK) * ((N + PW_TN - 1) / PW_TN), ks * ks + 1);
   launch(k_pwgrad<E, T>, grid, PW_THREADS, 0, st, in0, C0, in1, C1, g, N, B, H, W, ks, nsplit, partial, bpartial);
   const int64_t nw = (int64_t)ks * ks * K * N;
   launch(k_pwgrad_reduce, cdiv(std::max<int64_t>(nw, N), 256), 256, 0, st, (const double*)partial,
@@ -926,8 +1005,8 @@ helm_status paper_loss_grad(helm_ctx* ctx, helm_unet* net, const C<R>* bvec, dou
     return nb;
   };
   auto dgrad = [&](const E* g, int N, int l, E* gin0, int C0, E* gin1, int C1, int h, int w, int ks) {
-    dim3 grid(cdiv((int64_t)B * h * w, PC_THREADS), (C0 + C1 + 15) / 16);
-    launch(k_pdgrad<E>, grid, PC_THREADS, 0, st, g, N, wts(l), gin0, C0, gin1, C1, B, h, w, ks);
+    dim3 grid(cdiv((int64_t)B * h * w, PD_PX), cdiv(C0 + C1, PD_TK));
+    launch(k_pdgrad<E>, grid, 256, 0, st, g, N, wts(l), gin0, C0, gin1, C1, B, h, w, ks);
   };
   auto d2s_acc = [&](const E* gs, E* gprev, int C, int hi, int wi) {  // gs on the half grid hi x wi
     const int64_t n = (int64_t)B * hi * wi * 4 * C;
