@@ -347,6 +347,13 @@ static helm_status grad_buffers(helm_ctx* ctx, int B, int Hp, int Wp, size_t es,
   return HELM_OK;
 }
 
+template <typename E, typename T>
+helm_status conv_wgrad_tiled(const T* in0, int C0, int S0, const T* in1, int C1, int S1, const E* g, int N, int B,
+                             int H, int W, int ks, int nsplit, double* partial, cudaStream_t st);
+template <typename E>
+helm_status conv_dgrad_tiled(const E* g, int N, const E* w, E* gin0, int C0, E* gin1, int C1, int B, int H, int W,
+                             int ks, cudaStream_t st);
+
 static int pick_split(int64_t K, int tiles, int taps) {
   int s = (int)std::max<int64_t>(1, 2048 / std::max(1, tiles * taps));
   s = (int)std::min<int64_t>(s, std::max<int64_t>(1, K / 256));
@@ -376,13 +383,14 @@ struct Backward {
   helm_status wgrad(int l, const T* in0, int C0, int S0, const T* in1, int C1, int S1, const G* g, int h, int w) {
     const LayerDesc& d = kLayers[l];
     int taps = taps_of(d.kind);
-    int tiles = ((d.cin + 15) / 16) * ((d.cout + 15) / 16);
+    // 3x3 layers: 64 x 64 register-tiled blocks (unet_paper.cu); up-convs and the 1x1 layer: 16 x 16
+    int tiles = d.kind == CONV3 ? ((d.cin + 63) / 64) * ((d.cout + 63) / 64) : ((d.cin + 15) / 16) * ((d.cout + 15) / 16);
     int64_t K = (int64_t)B * h * w;
     int ns = pick_split(K, tiles, taps);
     if ((size_t)ns * taps * d.cin * d.cout > GS.wpart_doubles) return fail(HELM_ERR_INVALID_ARG, "wgrad scratch too small");
     dim3 grid(ns, tiles, taps);
     if (d.kind == CONV3)
-      launch(k_wgrad<T, G, CONV3>, grid, 256, 0, st, in0, C0, S0, in1, C1, S1, g, d.cout, B, h, w, ns, taps, GS.wpart);
+      HELM_TRY((conv_wgrad_tiled<G, T>(in0, C0, S0, in1, C1, S1, g, d.cout, B, h, w, 3, ns, GS.wpart, st)));
     else if (d.kind == UP2)
       launch(k_wgrad<T, G, UP2>, grid, 256, 0, st, in0, C0, S0, in1, C1, S1, g, d.cout, B, h, w, ns, taps, GS.wpart);
     else
@@ -402,10 +410,8 @@ struct Backward {
 
   helm_status dgrad3(int l, const G* gpre, G* out0, int C0, G* out1, int C1, int h, int w) {
     const LayerDesc& d = kLayers[l];
-    dim3 grid(cdiv((int64_t)B * h * w, BW_THREADS), d.cin / BW_CT);
-    launch(k_dgrad3<G, A>, grid, BW_THREADS, 0, st, gpre, weights() + net->L.c_w[l], d.cin, d.cout, out0, C0, out1, C1,
-           B, h, w);
-    return HELM_OK;
+    static_assert(std::is_same<A, G>::value, "the tiled input gradient reads weights in the gradient type");
+    return conv_dgrad_tiled<G>(gpre, d.cout, weights() + net->L.c_w[l], out0, C0, out1, C1, B, h, w, 3, st);
   }
 
   helm_status up_dgrad(int l, const G* gout, G* gin, int hi, int wi) {

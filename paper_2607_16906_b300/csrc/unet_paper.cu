@@ -571,9 +571,10 @@ __global__ void k_prelu_bwd(E* __restrict__ g, const T* __restrict__ pre, int64_
 // activations are of type T (E, or BF16 on the mixed path).
 constexpr int PW_TK = 64, PW_TN = 64, PW_PX = 32;
 template <typename E, typename T>
-__global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const T* __restrict__ in0, int C0, const T* __restrict__ in1,
-                                                       int C1, const E* __restrict__ g, int N, int B, int H, int W,
-                                                       int ks, int nsplit, double* __restrict__ partial,
+__global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const T* __restrict__ in0, int C0, int S0,
+                                                       const T* __restrict__ in1, int C1, int S1,
+                                                       const E* __restrict__ g, int N, int B, int H, int W, int ks,
+                                                       int nsplit, double* __restrict__ partial,
                                                        double* __restrict__ bpartial) {
   const int K = C0 + C1, r = ks / 2;
   const int split = blockIdx.x, tap = blockIdx.z;
@@ -618,7 +619,7 @@ __global__ void __launch_bounds__(PW_THREADS) k_pwgrad(const T* __restrict__ in0
         xv = (c == 0 && sp[p] >= 0) ? E(1) : E(0);
       } else if (k < K && sq[p] >= 0) {
         const int64_t q = sq[p];
-        xv = (E)to_acc(k < C0 ? in0[q * C0 + k] : in1[q * C1 + (k - C0)]);
+        xv = (E)to_acc(k < C0 ? in0[q * S0 + k] : in1[q * S1 + (k - C0)]);
       }
       if (n < N && sp[p] >= 0) gv = g[sp[p] * N + n];
       xs[p][c] = xv;
@@ -835,13 +836,46 @@ static helm_status pwgrad(const T* in0, int C0, const T* in1, int C1, const E* g
                           double* partial, double* bpartial, int nsplit, double* gw, double* gb, cudaStream_t st) {
   const int K = C0 + C1;
   dim3 grid(nsplit, ((K + PW_TK - 1) / PW_TK) * ((N + PW_TN - 1) / PW_TN), ks * ks + 1);
-  launch(k_pwgrad<E, T>, grid, PW_THREADS, 0, st, in0, C0, in1, C1, g, N, B, H, W, ks, nsplit, partial, bpartial);
+  launch(k_pwgrad<E, T>, grid, PW_THREADS, 0, st, in0, C0, C0, in1, C1, C1, g, N, B, H, W, ks, nsplit, partial,
+         bpartial);
   const int64_t nw = (int64_t)ks * ks * K * N;
   launch(k_pwgrad_reduce, cdiv(std::max<int64_t>(nw, N), 256), 256, 0, st, (const double*)partial,
          (const double*)bpartial, nsplit, nw, N, gw, gb);
   HELM_CK_LAUNCH();
   return HELM_OK;
 }
+
+// The tiled gradient kernels for the 3x3 layers of network kind 0 (train.cu): weight-gradient split
+// partials [split][tap][C0 + C1][N] (in0 / in1 with channel strides S0 / S1; no bias slice) and the
+// input gradient of a ks x ks conv with weights [tap][K][N].
+template <typename E, typename T>
+helm_status conv_wgrad_tiled(const T* in0, int C0, int S0, const T* in1, int C1, int S1, const E* g, int N, int B,
+                             int H, int W, int ks, int nsplit, double* partial, cudaStream_t st) {
+  const int K = C0 + C1;
+  dim3 grid(nsplit, ((K + PW_TK - 1) / PW_TK) * ((N + PW_TN - 1) / PW_TN), ks * ks);
+  launch(k_pwgrad<E, T>, grid, PW_THREADS, 0, st, in0, C0, S0, in1, C1, S1, g, N, B, H, W, ks, nsplit, partial,
+         (double*)nullptr);
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+template helm_status conv_wgrad_tiled<float, __nv_bfloat16>(const __nv_bfloat16*, int, int, const __nv_bfloat16*, int,
+                                                            int, const float*, int, int, int, int, int, int, double*,
+                                                            cudaStream_t);
+template helm_status conv_wgrad_tiled<double, double>(const double*, int, int, const double*, int, int, const double*,
+                                                      int, int, int, int, int, int, double*, cudaStream_t);
+
+template <typename E>
+helm_status conv_dgrad_tiled(const E* g, int N, const E* w, E* gin0, int C0, E* gin1, int C1, int B, int H, int W,
+                             int ks, cudaStream_t st) {
+  dim3 grid(cdiv((int64_t)B * H * W, PD_PX), cdiv(C0 + C1, PD_TK));
+  launch(k_pdgrad<E>, grid, 256, 0, st, g, N, w, gin0, C0, gin1, C1, B, H, W, ks);
+  HELM_CK_LAUNCH();
+  return HELM_OK;
+}
+template helm_status conv_dgrad_tiled<float>(const float*, int, const float*, float*, int, float*, int, int, int, int,
+                                             int, cudaStream_t);
+template helm_status conv_dgrad_tiled<double>(const double*, int, const double*, double*, int, double*, int, int, int,
+                                              int, int, cudaStream_t);
 
 // Output layer for training: z = out_scale (y0 + i y1), y = D0 Wout + bout with unrounded weights.
 template <typename E, typename R>
