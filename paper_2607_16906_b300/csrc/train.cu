@@ -22,7 +22,7 @@
 namespace helm {
 
 constexpr int BW_THREADS = 128;
-constexpr int BW_CT = 16;  // channels per thread in the dgrad kernels
+constexpr int BW_CT = 16;  // channels per thread in the up-conv input-gradient kernel
 
 // ------------------------------------------------------------------ elementwise / small kernels
 
@@ -69,46 +69,6 @@ __global__ void k_final_dgrad(const G* __restrict__ gy, const A* __restrict__ W,
   A g0 = gy[pix * 2], g1 = gy[pix * 2 + 1];
 #pragma unroll
   for (int ci = 0; ci < 16; ++ci) gin[pix * 16 + ci] = (G)(W[ci * 2] * g0 + W[ci * 2 + 1] * g1);
-}
-
-// 3x3 conv (pad 1) backward to its input: g_in[b,y,x,ci] = sum_{ky,kx,co} W[ky*3+kx][ci][co] g[b,y-ky+1,x-kx+1,co].
-// Channels ci < C0 go to out0 (C0 channels per pixel), the rest to out1 (the concat split).
-template <typename G, typename A>
-__global__ void __launch_bounds__(BW_THREADS) k_dgrad3(const G* __restrict__ gpre, const A* __restrict__ W, int Cin,
-                                                       int Cout, G* __restrict__ out0, int C0, G* __restrict__ out1,
-                                                       int C1, int B, int H, int Wd) {
-  int64_t pix = blockIdx.x * (int64_t)BW_THREADS + threadIdx.x;
-  if (pix >= (int64_t)B * H * Wd) return;
-  int ci0 = blockIdx.y * BW_CT;
-  int x = (int)(pix % Wd);
-  int y = (int)((pix / Wd) % H);
-  int64_t b = pix / ((int64_t)Wd * H);
-  A acc[BW_CT];
-#pragma unroll
-  for (int k = 0; k < BW_CT; ++k) acc[k] = 0;
-  for (int ky = 0; ky < 3; ++ky) {
-    int yo = y - ky + 1;
-    if (yo < 0 || yo >= H) continue;
-    for (int kx = 0; kx < 3; ++kx) {
-      int xo = x - kx + 1;
-      if (xo < 0 || xo >= Wd) continue;
-      const G* gp = gpre + ((b * H + yo) * Wd + xo) * Cout;
-      const A* wt = W + ((int64_t)(ky * 3 + kx) * Cin + ci0) * Cout;
-      for (int co = 0; co < Cout; ++co) {
-        A gv = gp[co];
-#pragma unroll
-        for (int k = 0; k < BW_CT; ++k) acc[k] += wt[(int64_t)k * Cout + co] * gv;
-      }
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < BW_CT; ++k) {
-    int ci = ci0 + k;
-    if (ci < C0)
-      out0[pix * C0 + ci] = (G)acc[k];
-    else if (ci - C0 < C1)
-      out1[pix * C1 + ci - C0] = (G)acc[k];
-  }
 }
 
 // 2x2 stride-2 transposed conv backward to its input:
