@@ -239,12 +239,88 @@ __device__ __forceinline__ void warp_fft_inv(float2 (&a)[E], const float2* tw, i
   }
 }
 
-// t = (1/s) D((1/s) D t) on one line held by the warp; inv_s[n] = 1/s at point n.
+// 32-point transforms of the 32 registers of a lane (W_32^m = W_1024^(32 m)): DIF, natural order in,
+// bit-reversed out; DIT with conjugate twiddles, bit-reversed in, natural out.
+__device__ __forceinline__ void reg_dif32(float2 (&a)[32], const float2* tw) {
+#pragma unroll
+  for (int half = 16; half >= 1; half >>= 1) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int k = i % half, i0 = (i / half) * 2 * half + k, i1 = i0 + half;
+      const float2 x0 = a[i0], x1 = a[i1];
+      a[i0] = cadd(x0, x1);
+      a[i1] = k == 0 ? csub(x0, x1) : cmul(csub(x0, x1), tw[32 * k * (16 / half)]);
+    }
+  }
+}
+__device__ __forceinline__ void reg_dit32_inv(float2 (&a)[32], const float2* tw) {
+#pragma unroll
+  for (int half = 1; half < 32; half <<= 1) {
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int k = i % half, i0 = (i / half) * 2 * half + k, i1 = i0 + half;
+      const float2 x0 = a[i0];
+      const float2 x1 = k == 0 ? a[i1] : cmul(a[i1], cconj(tw[32 * k * (16 / half)]));
+      a[i0] = cadd(x0, x1);
+      a[i1] = csub(x0, x1);
+    }
+  }
+}
+
+// N = 1024 = 32 x 32 with the transpose through shared memory instead of lane shuffles: forward,
+// in-register DIF over r (register r: frequency k1 = brev_5(r)), twiddles W^(n2 k1), transpose
+// (lane = k1, register = n2), in-register DIF over n2; position (lane, r) then holds X[lane + 32
+// brev_5(r)].  ts: the warp's 32 x 33 scratch (padded pitch: conflict-free in both directions).
+__device__ __forceinline__ void warp_fft1024_fwd(float2 (&a)[32], const float2* tw, float2* ts, int lane) {
+  reg_dif32(a, tw);
+#pragma unroll
+  for (int r = 1; r < 32; ++r) a[r] = cmul(a[r], tw_full<1024>(tw, lane * brev_e<32>(r)));
+#pragma unroll
+  for (int r = 0; r < 32; ++r) ts[brev_e<32>(r) * 33 + lane] = a[r];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 32; ++r) a[r] = ts[lane * 33 + r];
+  __syncwarp();
+  reg_dif32(a, tw);
+}
+// Inverse (no 1/N): position (lane, r) holds the spectrum at lane + 32 brev_5(r) on entry, point
+// lane + 32 r on exit.
+__device__ __forceinline__ void warp_fft1024_inv(float2 (&a)[32], const float2* tw, float2* ts, int lane) {
+  reg_dit32_inv(a, tw);
+#pragma unroll
+  for (int r = 1; r < 32; ++r) a[r] = cmul(a[r], cconj(tw_full<1024>(tw, r * lane)));
+#pragma unroll
+  for (int r = 0; r < 32; ++r) ts[lane * 33 + r] = a[r];
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < 32; ++r) a[r] = ts[brev_e<32>(r) * 33 + lane];
+  __syncwarp();
+  reg_dit32_inv(a, tw);
+}
+
+// t = (1/s) D((1/s) D t) on one line held by the warp; inv_s[n] = 1/s at point n; ts: the warp's
+// transpose scratch (N = 1024 only).
 template <int E>
 __device__ __forceinline__ void warp_derivative_pair(float2 (&a)[E], const float2* tw, const float2* inv_s,
-                                                     float two_pi_over_L, int lane) {
+                                                     float two_pi_over_L, int lane, float2* ts) {
   constexpr int N = 32 * E;
   constexpr int LOGN = 5 + (E >= 2) + (E >= 4) + (E >= 8) + (E >= 16) + (E >= 32);
+  if constexpr (E == 32) {
+#pragma unroll 1
+    for (int rep = 0; rep < 2; ++rep) {
+      warp_fft1024_fwd(a, tw, ts, lane);
+#pragma unroll
+      for (int r = 0; r < 32; ++r) {
+        const int q = lane + 32 * brev_e<32>(r);
+        const float c = q == N / 2 ? 0.0f : (float)(q < N / 2 ? q : q - N) * two_pi_over_L / (float)N;
+        a[r] = make_float2(-c * a[r].y, c * a[r].x);
+      }
+      warp_fft1024_inv(a, tw, ts, lane);
+#pragma unroll
+      for (int r = 0; r < 32; ++r) a[r] = cmul(a[r], inv_s[lane + 32 * r]);
+    }
+    return;
+  }
 #pragma unroll 1
   for (int rep = 0; rep < 2; ++rep) {
     warp_fft_fwd<E>(a, tw, lane);
@@ -271,6 +347,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fourier_xw(const float2* __re
   constexpr int N = 32 * E;
   __shared__ float2 tw[N / 2];
   __shared__ float2 inv_s[N];
+  extern __shared__ __align__(16) unsigned char fxw_smem[];  // N = 1024: 33 x 32 scratch per warp
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
     const float2 s = prof[i];
     const float d = s.x * s.x + s.y * s.y;
@@ -279,6 +356,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fourier_xw(const float2* __re
   }
   __syncthreads();
   const int lane = threadIdx.x & 31;
+  float2* ts = (float2*)fxw_smem + (threadIdx.x >> 5) * (32 * 33);
   const int line = blockIdx.x * FW_WARPS + (threadIdx.x >> 5);
   if (line >= nlines) return;  // whole warps leave; no block-wide barrier follows
   const int rhs = line / Ny, row = line % Ny;
@@ -286,7 +364,7 @@ __global__ void __launch_bounds__(FW_WARPS * 32) k_fourier_xw(const float2* __re
   float2 a[E];
 #pragma unroll
   for (int r = 0; r < E; ++r) a[r] = u[base + lane + 32 * r];
-  warp_derivative_pair<E>(a, tw, inv_s, two_pi_over_L, lane);
+  warp_derivative_pair<E>(a, tw, inv_s, two_pi_over_L, lane, ts);
 #pragma unroll
   for (int r = 0; r < E; ++r) tx[base + lane + 32 * r] = a[r];
 }
@@ -306,6 +384,7 @@ __global__ void __launch_bounds__(FYW_COLS * 32, E >= 32 ? 1 : 2) k_fourier_yw(c
   float2* slab = (float2*)fyw_smem;       // [N][FYW_PITCH]
   float2* tw = slab + N * FYW_PITCH;       // [N / 2]
   float2* inv_s = tw + N / 2;              // [N]
+  float2* tsb = inv_s + N;                 // N = 1024: 33 x 32 transpose scratch per warp
   const int x0 = blockIdx.x * FYW_COLS, rhs = blockIdx.y;
   const int64_t base = rhs * rhs_stride + x0;
   const int cols = min(FYW_COLS, Nx - x0);
@@ -325,7 +404,7 @@ __global__ void __launch_bounds__(FYW_COLS * 32, E >= 32 ? 1 : 2) k_fourier_yw(c
     float2 a[E];
 #pragma unroll
     for (int r = 0; r < E; ++r) a[r] = slab[(lane + 32 * r) * FYW_PITCH + c];
-    warp_derivative_pair<E>(a, tw, inv_s, two_pi_over_L, lane);
+    warp_derivative_pair<E>(a, tw, inv_s, two_pi_over_L, lane, tsb + c * (32 * 33));
 #pragma unroll
     for (int r = 0; r < E; ++r) slab[(lane + 32 * r) * FYW_PITCH + c] = a[r];
   }
@@ -346,12 +425,15 @@ template <int E>
 static void launch_fourier_w(int axis, const float2* x, float2* y, const float* k2, const float2* pr,
                              const float2* tw, int Nx, int Ny, int nrhs, int64_t n, float tpl, cudaStream_t st) {
   constexpr int N = 32 * E;
+  const size_t scratch = E == 32 ? sizeof(float2) * 32 * 33 : 0;  // transpose scratch per warp
   if (axis == 0) {
     const int nlines = Ny * nrhs;
-    launch(k_fourier_xw<E>, (nlines + FW_WARPS - 1) / FW_WARPS, FW_WARPS * 32, 0, st, x, y, pr, tw, Ny, nlines, n,
+    const size_t sm = FW_WARPS * scratch;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(k_fourier_xw<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    launch(k_fourier_xw<E>, (nlines + FW_WARPS - 1) / FW_WARPS, FW_WARPS * 32, sm, st, x, y, pr, tw, Ny, nlines, n,
            tpl);
   } else {
-    const size_t sm = sizeof(float2) * ((size_t)N * FYW_PITCH + N / 2 + N);
+    const size_t sm = sizeof(float2) * ((size_t)N * FYW_PITCH + N / 2 + N) + FYW_COLS * scratch;
     cudaFuncSetAttribute(k_fourier_yw<E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     launch(k_fourier_yw<E>, dim3((Nx + FYW_COLS - 1) / FYW_COLS, nrhs), FYW_COLS * 32, sm, st, x, y, k2, pr, tw, Nx,
            n, tpl);
