@@ -319,20 +319,20 @@ __device__ __forceinline__ void warp_derivative_pair(float2 (&a)[E], const float
 #pragma unroll
       for (int r = 0; r < 32; ++r) a[r] = cmul(a[r], inv_s[lane + 32 * r]);
     }
-    return;
-  }
+  } else {
 #pragma unroll 1
-  for (int rep = 0; rep < 2; ++rep) {
-    warp_fft_fwd<E>(a, tw, lane);
+    for (int rep = 0; rep < 2; ++rep) {
+      warp_fft_fwd<E>(a, tw, lane);
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-      const int q = (int)(__brev((unsigned)(lane + 32 * r)) >> (32 - LOGN));
-      const float c = q == N / 2 ? 0.0f : (float)(q < N / 2 ? q : q - N) * two_pi_over_L / (float)N;
-      a[r] = make_float2(-c * a[r].y, c * a[r].x);
+      for (int r = 0; r < E; ++r) {
+        const int q = (int)(__brev((unsigned)(lane + 32 * r)) >> (32 - LOGN));
+        const float c = q == N / 2 ? 0.0f : (float)(q < N / 2 ? q : q - N) * two_pi_over_L / (float)N;
+        a[r] = make_float2(-c * a[r].y, c * a[r].x);
+      }
+      warp_fft_inv<E>(a, tw, lane);
+#pragma unroll
+      for (int r = 0; r < E; ++r) a[r] = cmul(a[r], inv_s[lane + 32 * r]);
     }
-    warp_fft_inv<E>(a, tw, lane);
-#pragma unroll
-    for (int r = 0; r < E; ++r) a[r] = cmul(a[r], inv_s[lane + 32 * r]);
   }
 }
 
