@@ -176,7 +176,8 @@ HELM_API helm_status helm_unet_create(helm_unet** out, const double* weights_hos
  * layers enc1 enc2 enc3 enc4 dec3 dec2 dec1 dec0 out; conv weights [Cout][Cin][8][8], transposed-conv
  * weights [Cin][Cout][8][8], output weights [2][32].  Kind 1 serves helm_precond_apply and
  * helm_fgmres_solve (BF16 on tcgen05 tensor cores, or FP64 on CUDA cores) and helm_train_step /
- * helm_loss_grad (forward and backward on CUDA cores: FP32 for C64 batches, FP64 for C128). */
+ * helm_loss_grad (C64 batches: forward on the tcgen05 layers in BF16 with FP32 accumulation, the
+ * pre-activations kept in BF16, backward on CUDA cores in FP32; C128: FP64 on CUDA cores). */
 HELM_API size_t helm_unet_param_count_kind(int kind);
 HELM_API helm_status helm_unet_create_kind(helm_unet** out, int kind, const double* weights_host, size_t nweights);
 HELM_API helm_status helm_unet_destroy(helm_unet* net);
@@ -192,7 +193,8 @@ HELM_API helm_status helm_unet_set_weights(helm_unet* net, const double* weights
 /* z = h^2 N_theta(alpha v, c) / alpha per column, alpha = sqrt(n) / ||v|| (eq. 6): the network sees a
  * unit-RMS input and approximates the inverse of the dimensionless operator h^2 A.  dtype HELM_C64:
  * BF16 network with FP32 accumulation (3x3 and up-convs on tcgen05 tensor cores); HELM_C128: FP64
- * network on CUDA cores.  v, z batch vectors; a zero column gives z = 0.
+ * network on CUDA cores.  v, z batch vectors; a zero column gives z = 0 (network kind 1, HELM_C64:
+ * such columns are skipped by every layer, which is how the solver leaves converged columns out).
  * HELM_C64 runs: the second call for the same (network, system, nrhs) captures the network's launch
  * sequence into a CUDA graph that later calls replay on the library's own stream (ordered after and
  * before the caller's stream by events); the first call that meets a new row-tile conv layer shape
