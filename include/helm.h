@@ -309,6 +309,9 @@ HELM_API int helm_tuned_tiles(int* out, int max_entries);
  *               space-to-depth, [B][H][W][32], channel (2 (y % 2) + x % 2) * 8 + c holding input
  *               channel c (5 used of 8) of pixel (y, x) of the 2H x 2W grid.  out: [B][H][W][32].
  *   layer 1..3: enc2..enc4.  in0: the previous encoder output [B][2H][2W][32].  out: [B][H][W][32].
+ *               Layers 0..2 with H and W even run in the phase form the preconditioner uses on its
+ *               16-padded grids (a 3x3 convolution over 4 x 4 input blocks with the 2 x 2 output phases
+ *               as 128 GEMM columns); layer 3 and odd grids in the 5x5 form.
  *   layer 4:    dec3 (8x8 transposed, stride 2, pad 3, PReLU).  in0: [B][H][W][32].  out: [B][2H][2W][32].
  *   layer 5..7: dec2..dec0 on the concatenation [in0, in1], both [B][H][W][32] (in1: the skip
  *               connection).  out: [B][2H][2W][32].

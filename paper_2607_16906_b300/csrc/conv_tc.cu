@@ -44,6 +44,10 @@ struct ConvTcArgs {
   // MODE 0: source 0 is an NHWC tensor of the 2H x 2W grid read as its space-to-depth view (channel
   // chunk kc = input row phase; the map's rows are traversed with stride 2)
   int s2d;
+  // MODE 2, KS = 3: source 0 is an NHWC tensor [B][qf H][qf W][32] read as its phase view (qf = 2 or 4):
+  // chunk kc of GEMM pixel (y, x) is the source pixel (qf y + kc / qf, qf x + kc % qf); the map's rows
+  // and columns are traversed with stride qf.  0: no phase view
+  int qf;
   // optional, per image: an image whose scale is 0 (a converged column of the solver, whose network
   // input scale is zero) is skipped by every role; with the fused output layer its output is zeroed
   const double* img_scale;
@@ -67,9 +71,11 @@ struct TcCfg {
   // column.  The A operand of row block rb and kernel row dy is the same patch 16 (8 rb + dy) pixels
   // further on (a whole number of 8-row swizzle atoms), so every input pixel is loaded
   // (8 RB + 4) / (8 RB) times per chunk instead of 25 times, and every weight tile serves RB blocks.
-  // KS = 3: one stage is one or three taps, each with its own patch and weight tile (RB = 1).
-  static constexpr bool RR = KS == 5;
-  static_assert(RR || RB == 1, "row blocks are a 5x5-layer feature");
+  // KS = 3, MODE 2 (the stride-2 layers read through a phase view): the same row reuse with a
+  // (8 RB + 2)-row patch and 3 weight tiles per stage.
+  // KS = 3 otherwise: one stage is one or three taps, each with its own patch and weight tile (RB = 1).
+  static constexpr bool RR = KS == 5 || (KS == 3 && MODE == 2);
+  static_assert(RR || RB == 1, "row blocks need the row-reuse stages");
   static constexpr int A_ROWS = RR ? 8 * RB + KS - 1 : 8;
   static constexpr int A_BYTES = A_ROWS * 16 * CHUNK * 2;
   static constexpr int B_BYTES = N * CHUNK * 2;
@@ -77,7 +83,9 @@ struct TcCfg {
   // round trip carries three MMAs; one tap otherwise
   static constexpr int TPS = RR ? KS : ((MODE == 0 && KS == 3 && CHUNK <= 32) ? 3 : 1);
   static constexpr int STAGE_BYTES = RR ? A_BYTES + KS * B_BYTES : TPS * (A_BYTES + B_BYTES);
-  static constexpr int BUDGET = RR ? 200 * 1024 : 96 * 1024;
+  // shared memory for the stage ring: the phase-view layers (many small stages per tile) take one
+  // stage more than 200 KB would give
+  static constexpr int BUDGET = RR ? (KS == 3 ? 220 * 1024 : 200 * 1024) : 96 * 1024;
   static constexpr int STAGES = (BUDGET / STAGE_BYTES) > 8 ? 8 : (BUDGET / STAGE_BYTES);
   static constexpr int ACC_COLS = RB * N;  // one tile's accumulators
   static constexpr int TMEM_COLS = 2 * ACC_COLS < 32 ? 32 : 2 * ACC_COLS;
@@ -173,7 +181,10 @@ __global__ void __launch_bounds__(192, 1) k_conv_tc(const __grid_constant__ CUte
             if constexpr (Cfg::RR) {
               // kernel column dx = tg: the (8 + KS - 1)-row patch and the KS weight tiles (dy, dx)
               unsigned char* sb = sa + Cfg::A_BYTES;
-              if (MODE == 0 && a.s2d)
+              if (MODE == 2 && a.qf)
+                tma_load_4d(sa, src, &full[stage], 0, a.qf * (x0 + tg - KS / 2) + kc % a.qf,
+                            a.qf * (y0 - KS / 2) + kc / a.qf, b);
+              else if (MODE == 0 && a.s2d)
                 tma_load_4d(sa, src, &full[stage], 0, x0 + tg - KS / 2, 2 * (y0 - KS / 2) + kc, b);
               else
                 tma_load_4d(sa, src, &full[stage], c0, x0 + tg - KS / 2, y0 - KS / 2, b);
@@ -579,6 +590,22 @@ static helm_status act_map_s2d(CUtensorMap* m, const void* ptr, int chunk, int B
   return HELM_OK;
 }
 
+// The phase view of an NHWC BF16 tensor [B][Hs][Ws][32] on the (Hs / f) x (Ws / f) grid: one box is the
+// patch of one phase (sy, sx), its source rows and columns traversed with stride f from f Y + sy and
+// f X + sx; each pixel holds the source pixel's 32 channels.
+static helm_status act_map_phase(CUtensorMap* m, const void* ptr, int f, int B, int Hs, int Ws, int rows) {
+  cuuint64_t dims[4] = {32, (cuuint64_t)Ws, (cuuint64_t)Hs, (cuuint64_t)B};
+  cuuint64_t strides[3] = {64, (cuuint64_t)Ws * 64, (cuuint64_t)Hs * Ws * 64};
+  cuuint32_t box[4] = {32, (cuuint32_t)(16 * f), (cuuint32_t)(rows * f), 1};
+  cuuint32_t es[4] = {1, (cuuint32_t)f, (cuuint32_t)f, 1};
+  CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(ptr), dims, strides, box, es,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS)
+    return fail(HELM_ERR_CUDA, "cuTensorMapEncodeTiled (phase view) failed: " + std::to_string((int)r));
+  return HELM_OK;
+}
+
 static helm_status weight_map(CUtensorMap* m, const void* ptr, int N, int chunk, int nk, int taps = 9) {
   cuuint64_t dims[3] = {(cuuint64_t)chunk, (cuuint64_t)N, (cuuint64_t)(taps * nk)};
   cuuint64_t strides[2] = {(cuuint64_t)chunk * 2, (cuuint64_t)N * chunk * 2};
@@ -797,6 +824,41 @@ helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* e
     case 25200000 + 128 * 100 + 32: return launch_tc<128, 32, 2, 5, 2>(m0, m1, mw, a, st);
     default: return fail(HELM_ERR_INVALID_ARG, "conv_tc_generic: no kernel for this shape");
   }
+}
+
+// An 8x8 stride-2 layer of network kind 1 as a 3x3 convolution of the phase view of its input
+// (f = 2: the space-to-depth-packed network input, 32 channels = 2 x 2 phases x 8; f = 4: a 32-channel
+// activation): GEMM grid H x W (the output grid is 2H x 2W), N = 128 columns = 2 x 2 output phases x 32
+// channels written depth-to-space, K = f^2 chunks of 32 per tap, weights `wq` [tap][kc][n][32] BF16.
+// Epilogue: bias + PReLU(slope); optional per-image skip and pre-activation store as conv_tc_generic.
+helm_status conv_tc_phase(const __nv_bfloat16* wq, const float* bias, int* err, int f, const void* in, void* out,
+                          int B, int H, int W, float slope, cudaStream_t st, const double* img_scale, void* pre_out) {
+  if (f != 2 && f != 4) return fail(HELM_ERR_INVALID_ARG, "conv_tc_phase: phase factor must be 2 or 4");
+  // two row blocks per tile unless the last tile row would waste more than an eighth of the grid's rows
+  const int rb = (H + 15) / 16 * 16 - H <= H / 8 ? 2 : 1;
+  CUtensorMap m0, mw;
+  HELM_TRY(act_map_phase(&m0, in, f, B, f * H, f * W, 8 * rb + 2));
+  HELM_TRY(weight_map(&mw, wq, 128, 32, f * f, 9));
+  ConvTcArgs a{};
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.nk0 = f * f;
+  a.nk1 = 0;
+  a.tiles_x = (W + 15) / 16;
+  a.tiles_y = (H + 8 * rb - 1) / (8 * rb);
+  a.ntiles = B * a.tiles_x * a.tiles_y;
+  a.bias = bias;
+  a.out = (__nv_bfloat16*)out;
+  a.act = 2;
+  a.slope = slope;
+  a.err = err;
+  a.budget = wait_budget();
+  a.skip_first = take_fault(HELM_FAULT_CONV_TILE) ? 1 : 0;
+  a.qf = f;
+  a.img_scale = img_scale;
+  a.pre_out = (__nv_bfloat16*)pre_out;
+  return rb == 2 ? launch_tc<128, 32, 2, 3, 2>(m0, m0, mw, a, st) : launch_tc<128, 32, 2, 3, 1>(m0, m0, mw, a, st);
 }
 
 // Error code left by a timed-out tcgen05 kernel (0 if none); clears it.

@@ -142,6 +142,10 @@ struct PaperNet {
   double* b5[PAPER_LAYERS] = {};          // per-column bias, FP64
   __nv_bfloat16* wtc[PAPER_LAYERS] = {};  // tcgen05 layout [tap][kc][n][c], BF16
   float* b32[PAPER_LAYERS] = {};
+  // encoder layers as 3x3 convolutions of the phase view of their input (conv_tc_phase): [tap][kc][n][c]
+  // BF16 with N = 128 columns (2 x 2 output phases x 32 channels), bias per column in FP32
+  __nv_bfloat16* wq[3] = {};  // enc1..enc3
+  float* bq[3] = {};
   float* wout32 = nullptr;                // output layer, BF16-rounded weights in FP32 + 2 biases
   double slope[PAPER_LAYERS] = {};        // PReLU slopes
   int* err = nullptr;                     // tcgen05 pipeline error code
@@ -153,7 +157,7 @@ struct PaperNet {
 int64_t paper_param_count();
 // Algorithmic flops of one network application per full-resolution pixel: kind 0, its 3x3 / 2x2 /
 // 1x1 layers (2 x 35,408 MACs); kind 1, the 8x8 strided and transposed layers and the output layer
-// (2 x 51,264 MACs; the 5x5 reformulation executes 82,464 MACs, structural zeros included).
+// (2 x 51,264 MACs; the BF16 path executes 88,800 MACs, structural zeros included).
 inline double unet_flop_per_point(int kind) { return kind == 1 ? 102528.0 : 70816.0; }
 helm_status paper_prepare(helm_unet* net, cudaStream_t st);
 void paper_release(helm_unet* net);

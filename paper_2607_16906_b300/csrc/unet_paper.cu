@@ -16,8 +16,14 @@
 //   convT_{8,2,3}(x) = D2S(conv5x5(x)) with 4 C_out output columns: output 2y + q receives input
 //                      y + d through tap t = q + 3 - 2 d; the kernel's epilogue writes column block q to
 //                      output phase q (no separate depth-to-space pass).
-// Mixed path: BF16 activations, tcgen05 GEMMs with FP32 accumulation, PReLU in the epilogue.  Plain
-// path: FP64 on CUDA cores with the same reformulated weights.  Training (the end of this file): FP32
+// Mixed path: BF16 activations, tcgen05 GEMMs with FP32 accumulation, PReLU in the epilogue; there the
+// first three strided layers take a second form with 4x wider GEMM rows (conv_tc_phase):
+//   conv_{8,2,3}(x)  = D2S(conv3x3(S2D_4(x))): a GEMM pixel is a 4 x 4 block of x (16 C_in channels,
+//                      read through a strided tensor-map view), its 128 columns the 2 x 2 output pixels
+//                      of that block (4 x 32); output 2h + p sees input 4 (h + e) + o, e = -1..1, through
+//                      kernel tap t = 4 e + o - 2 p + 3 (5/9 zero).  The N = 128 MMAs need a quarter of the
+//                      N = 32 MMAs' instructions per product.
+// Plain path: FP64 on CUDA cores with the 5x5 weights.  Training (the end of this file): FP32
 // on CUDA cores, forward with the pre-activations kept, backward through the same reformulation.
 #include <math.h>
 
@@ -34,6 +40,9 @@ helm_status conv_tc_generic(const __nv_bfloat16* w_tc, const float* bias, int* e
                             int chunk, const void* in0, int C0, const void* in1, int C1, void* out, int B, int H,
                             int W, int act, float slope, cudaStream_t st, bool s2d0, const RowFinal* fin,
                             const double* img_scale, void* pre_out = nullptr);
+helm_status conv_tc_phase(const __nv_bfloat16* wq, const float* bias, int* err, int f, const void* in, void* out,
+                          int B, int H, int W, float slope, cudaStream_t st, const double* img_scale,
+                          void* pre_out = nullptr);
 
 bool tc_available();
 
@@ -88,6 +97,41 @@ __global__ void k_paper_reform(const double* __restrict__ master, int64_t m_w, i
     }
   }
   w5[e] = v;
+}
+
+// A down layer as a 3x3 convolution of the phase view of its input (the BF16 encoder, conv_tc.cu): GEMM
+// pixel (h, w) produces output pixels (2h + py, 2w + px) in column n = (2 py + px) 32 + co; output row
+// 2h + py reads input rows 2 (2h + py) + t - 3, t = 0..7, which lie in the 4-row blocks h - 1, h, h + 1:
+// input row 4 (h + ey) + oy is kernel row t = 4 ey + oy - 2 py + 3 (zero outside 0..7; 5/9 of the
+// products are structural zeros).  Chunk kc = (sy, sx) of a tap holds, for f = 4, the 32 channels of
+// input pixel (4 (h + ey) + sy, 4 (w + ex) + sx); for f = 2 (the first layer, whose input arrives
+// space-to-depth packed: channel c = (2 ry + rx) 8 + ci of packed pixel (Y, X) is input pixel
+// (2Y + ry, 2X + rx)) the packed pixel (2 (h + ey) + sy, 2 (w + ex) + sx), i.e. oy = 2 sy + ry.
+// Layout [tap][kc][n][c] BF16 (rounded through FP32 like the other layouts); bias per column.
+__global__ void k_paper_phase(const double* __restrict__ master, int64_t m_w, int64_t m_b, int cin, int f,
+                              __nv_bfloat16* __restrict__ wq, float* __restrict__ bq) {
+  const int nk = f * f;
+  const int64_t total = (int64_t)9 * nk * 128 * 32;
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e < 128) bq[e] = (float)master[m_b + e % 32];
+  if (e >= total) return;
+  const int c = (int)(e % 32);
+  const int n = (int)((e / 32) % 128);
+  const int kc = (int)((e / 4096) % nk);
+  const int tap = (int)(e / (4096 * (int64_t)nk));
+  const int ey = tap / 3 - 1, ex = tap % 3 - 1;
+  const int py = n / 64, px = (n / 32) % 2, co = n % 32;
+  const int sy = kc / f, sx = kc % f;
+  int oy = sy, ox = sx, ci = c;
+  if (f == 2) {
+    oy = 2 * sy + c / 16;
+    ox = 2 * sx + (c / 8) % 2;
+    ci = c % 8;
+  }
+  const int ty = 4 * ey + oy - 2 * py + 3, tx = 4 * ex + ox - 2 * px + 3;
+  double v = 0.0;
+  if (ci < cin && ty >= 0 && ty < 8 && tx >= 0 && tx < 8) v = master[m_w + (((int64_t)co * cin + ci) * 8 + ty) * 8 + tx];
+  wq[e] = __float2bfloat16_rn((float)v);
 }
 
 // tcgen05 layout [tap][kc][n][c] in BF16 from w5[tap][k][n]; bias in FP32.
@@ -145,6 +189,16 @@ helm_status paper_prepare(helm_unet* net, cudaStream_t st) {
     if (L.kind != P_OUT)
       launch(k_paper_tc, cdiv(std::max<int64_t>(n5, L.N), 256), 256, 0, st, (const double*)P.w5[l],
              (const double*)P.b5[l], L.K, L.N, L.chunk, P.wtc[l], P.b32[l]);
+    if (L.kind == P_DOWN && l < 3) {
+      const int f = l == 0 ? 2 : 4;
+      const int64_t nq = (int64_t)9 * f * f * 128 * 32;
+      if (!P.wq[l]) {
+        HELM_CK(cudaMalloc(&P.wq[l], sizeof(__nv_bfloat16) * nq));
+        HELM_CK(cudaMalloc(&P.bq[l], sizeof(float) * 128));
+      }
+      launch(k_paper_phase, cdiv(nq, 256), 256, 0, st, (const double*)net->master, P.m_w[l], P.m_b[l], L.cin, f,
+             P.wq[l], P.bq[l]);
+    }
   }
   if (!P.wout32) HELM_CK(cudaMalloc(&P.wout32, sizeof(float) * 66));
   launch(k_paper_out32, 1, 64, 0, st, (const double*)P.w5[PAPER_LAYERS - 1], (const double*)P.b5[PAPER_LAYERS - 1],
@@ -172,6 +226,10 @@ void paper_release(helm_unet* net) {
     cudaFree(P.b5[l]);
     cudaFree(P.wtc[l]);
     cudaFree(P.b32[l]);
+  }
+  for (int l = 0; l < 3; ++l) {
+    cudaFree(P.wq[l]);
+    cudaFree(P.bq[l]);
   }
   cudaFree(P.wout32);
   cudaFree(P.err);
@@ -392,18 +450,25 @@ helm_status paper_precondition(helm_ctx* ctx, const helm_unet* net, int sys, con
     }
   };
   int H = Hp, W = Wp;
-  HELM_TRY(layer(0, PA_S0, 4 * P_X0_CH, -1, 0, PA_E1, H / 2, W / 2));
-  if constexpr (fp64) {
+  if constexpr (!fp64) {
+    // the first three encoder layers as 3x3 convolutions of phase views (N = 128; their output grids
+    // have even sides, Hp and Wp being multiples of 16); the last in the 5x5 form, whose 8 x 16 tiles
+    // fit its small grid better (a quarter of the pixels per GEMM row of the phase form)
+    HELM_TRY(conv_tc_phase(P.wq[0], P.bq[0], P.err, 2, a[PA_S0], a[PA_E1], B, H / 4, W / 4, (float)P.slope[0], st,
+                           in_scale));
+    HELM_TRY(conv_tc_phase(P.wq[1], P.bq[1], P.err, 4, a[PA_E1], a[PA_E2], B, H / 8, W / 8, (float)P.slope[1], st,
+                           in_scale));
+    HELM_TRY(conv_tc_phase(P.wq[2], P.bq[2], P.err, 4, a[PA_E2], a[PA_E3], B, H / 16, W / 16, (float)P.slope[2], st,
+                           in_scale));
+    HELM_TRY(layer(3, PA_E3, 128, -1, 0, PA_E4, H / 16, W / 16, true));
+  } else {
+    HELM_TRY(layer(0, PA_S0, 4 * P_X0_CH, -1, 0, PA_E1, H / 2, W / 2));
     HELM_TRY(s2d(PA_E1, PA_S1, 32, H / 2, W / 2));
     HELM_TRY(layer(1, PA_S1, 128, -1, 0, PA_E2, H / 4, W / 4));
     HELM_TRY(s2d(PA_E2, PA_S2, 32, H / 4, W / 4));
     HELM_TRY(layer(2, PA_S2, 128, -1, 0, PA_E3, H / 8, W / 8));
     HELM_TRY(s2d(PA_E3, PA_S3, 32, H / 8, W / 8));
     HELM_TRY(layer(3, PA_S3, 128, -1, 0, PA_E4, H / 16, W / 16));
-  } else {
-    HELM_TRY(layer(1, PA_E1, 128, -1, 0, PA_E2, H / 4, W / 4, true));
-    HELM_TRY(layer(2, PA_E2, 128, -1, 0, PA_E3, H / 8, W / 8, true));
-    HELM_TRY(layer(3, PA_E3, 128, -1, 0, PA_E4, H / 16, W / 16, true));
   }
   HELM_TRY(layer(4, PA_E4, 32, -1, 0, PA_D3, H / 16, W / 16));      // -> H/8
   HELM_TRY(layer(5, PA_D3, 32, PA_E3, 32, PA_D2, H / 8, W / 8));    // -> H/4
@@ -1129,6 +1194,9 @@ extern "C" helm_status helm_paper_layer_forward(const helm_unet* net, int layer,
     f.zstride = (int64_t)4 * H * W;
     f.io = nullptr;
   }
+  if (l <= 2 && H % 2 == 0 && W % 2 == 0)  // the phase form of enc1..enc3 (output grid with even sides)
+    return conv_tc_phase(P.wq[l], P.bq[l], P.err, l == 0 ? 2 : 4, in0, out, B, H / 2, W / 2, (float)P.slope[l],
+                         (cudaStream_t)stream, nullptr);
   const int C0 = l == 0 ? 4 * P_X0_CH : (l <= 3 ? 128 : 32), C1 = l >= 5 ? 32 : 0;
   return conv_tc_generic(P.wtc[l], P.b32[l], P.err, 5, L.kind == P_UP ? 2 : 0, L.N, L.chunk, in0, C0, in1, C1,
                          fused ? nullptr : out, B, H, W, 2, (float)P.slope[l], (cudaStream_t)stream,

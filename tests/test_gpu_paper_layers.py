@@ -1,12 +1,14 @@
 """Each tensor-core layer of network kind 1 (the paper's variant, Sec. 3.1, Tab. 2) checked on its own
 against the oracle's plain strided and transposed 8x8 convolutions, element by element.
 
-The library computes every 8x8 stride-2 layer as a 5x5 convolution of space-to-depth data (the
-encoder layers 2-4 read their input through a strided tensor-map view, the first layer a tensor the
-input packing writes in that layout) and every transposed layer as a 5x5 convolution written
-depth-to-space; the last one also with the 1x1 output layer fused into its epilogue.  The oracle
-applies the definitions in FP64 to the same BF16 inputs and BF16-rounded weights.  The GEMM grids
-leave ragged tiles in both directions, for each tile height the library picks.
+The library computes the first three 8x8 stride-2 layers, where their output grid has even sides, as
+a 3x3 convolution over 4 x 4 blocks of their input (a strided tensor-map view; the first layer reads the space-to-depth
+packed input through a stride-2 view), with the 2 x 2 output phases as 128 GEMM columns written
+depth-to-space; the last encoder layer and odd grids as a 5x5 convolution of space-to-depth data.  Every transposed
+layer is a 5x5 convolution written depth-to-space; the last one also with the 1x1 output layer fused
+into its epilogue.  The oracle applies the definitions in FP64 to the same BF16 inputs and
+BF16-rounded weights.  The GEMM grids leave ragged tiles in both directions, for each tile height the
+library picks, in both encoder forms.
 
 Bound per element: the final BF16 rounding of the output (2^-8 of the value) plus 2e-5 of the sum of
 the absolute products that make the output (FP32 accumulation).  For the fused output layer the
@@ -23,9 +25,10 @@ from paper_2607_16906_b300 import synth
 
 pytestmark = pytest.mark.gpu
 
-# (B, H, W) of the 5x5 GEMM grid: tiles of one 8 x 16 block (12 x 20, 9 x 33), and grids on which the
-# library stacks 2 or 4 blocks per tile with a ragged last tile row (60 x 20: 4 blocks for the first
-# layer, 2 for the others; 30 x 36: 4 and 2)
+# (B, H, W) of the 5x5 GEMM grid (the encoder's output grid): tiles of one 8 x 16 block (12 x 20, 9 x 33),
+# and grids on which the library stacks 2 or 4 blocks per tile with a ragged last tile row (60 x 20,
+# 30 x 36).  The even grids run enc1..enc3 in the phase form (GEMM grids 6 x 10: one block per tile;
+# 30 x 10 and 15 x 18: two), 9 x 33 and enc4 in the 5x5 form
 GRIDS = ((2, 12, 20), (1, 9, 33), (1, 60, 20), (2, 30, 36))
 NAMES = ("enc1", "enc2", "enc3", "enc4", "dec3", "dec2", "dec1", "dec0")
 

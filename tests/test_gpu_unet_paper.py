@@ -2,8 +2,9 @@
 plain strided / transposed convolutions (oracle/unet_paper.py).
 
 The CUDA path computes every 8x8 stride-2 layer as a 5x5 convolution of space-to-depth rearranged
-data (tcgen05 in BF16, CUDA cores in FP64) and every transposed layer as a 5x5 convolution written
-depth-to-space; the oracle uses the definitions.  FP64: 1e-12 of the column maximum.  BF16 against
+data (CUDA cores in FP64; tcgen05 in BF16 for the last encoder layer) or, the first three in BF16, as
+a 3x3 convolution over 4 x 4 input blocks on tcgen05, and every transposed layer as a 5x5 convolution
+written depth-to-space; the oracle uses the definitions.  FP64: 1e-12 of the column maximum.  BF16 against
 the oracle's BF16 emulation: 2e-2 normwise per column (FP32 summation order flips BF16 roundings,
 which the nonlinear network propagates)."""
 import numpy as np
