@@ -388,15 +388,37 @@ __global__ void __launch_bounds__(FYW_COLS * 32, E >= 32 ? 1 : 2) k_fourier_yw(c
   const int x0 = blockIdx.x * FYW_COLS, rhs = blockIdx.y;
   const int64_t base = rhs * rhs_stride + x0;
   const int cols = min(FYW_COLS, Nx - x0);
-  for (int e = threadIdx.x; e < N * FYW_COLS; e += blockDim.x) {
-    const int j = e / FYW_COLS, c = e % FYW_COLS;
-    if (c < cols) slab[j * FYW_PITCH + c] = u[base + (int64_t)j * Nx + c];
-  }
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    const float2 s = prof[i];
-    const float d = s.x * s.x + s.y * s.y;
-    inv_s[i] = make_float2(s.x / d, -s.y / d);
-    if (i < N / 2) tw[i] = tw_g[i];
+  // The slab's global traffic: thread t serves column t % FYW_COLS and rows t / FYW_COLS + JSTEP k
+  // (the 8 columns of a row are 64 contiguous bytes); its loads are issued BATCH at a time before
+  // any of them is used, so that a thread keeps BATCH DRAM requests in flight instead of one.
+  constexpr int NT = FYW_COLS * 32, JSTEP = NT / FYW_COLS, PER = N / JSTEP, BATCH = PER < 8 ? PER : 8;
+  const int ct = threadIdx.x % FYW_COLS, jt = threadIdx.x / FYW_COLS;
+  if (ct < cols)
+    for (int k0 = 0; k0 < PER; k0 += BATCH) {
+      float2 v[BATCH];
+#pragma unroll
+      for (int k = 0; k < BATCH; ++k) v[k] = u[base + (int64_t)(jt + (k0 + k) * JSTEP) * Nx + ct];
+#pragma unroll
+      for (int k = 0; k < BATCH; ++k) slab[(jt + (k0 + k) * JSTEP) * FYW_PITCH + ct] = v[k];
+    }
+  {
+    constexpr int PI = (N + NT - 1) / NT;
+    float2 sp[PI], tg[PI];
+#pragma unroll
+    for (int k = 0; k < PI; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < N) sp[k] = prof[i];
+      if (i < N / 2) tg[k] = tw_g[i];
+    }
+#pragma unroll
+    for (int k = 0; k < PI; ++k) {
+      const int i = threadIdx.x + k * NT;
+      if (i < N) {
+        const float d = sp[k].x * sp[k].x + sp[k].y * sp[k].y;
+        inv_s[i] = make_float2(sp[k].x / d, -sp[k].y / d);
+      }
+      if (i < N / 2) tw[i] = tg[k];
+    }
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;
@@ -409,16 +431,24 @@ __global__ void __launch_bounds__(FYW_COLS * 32, E >= 32 ? 1 : 2) k_fourier_yw(c
     for (int r = 0; r < E; ++r) slab[(lane + 32 * r) * FYW_PITCH + c] = a[r];
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < N * FYW_COLS; e += blockDim.x) {
-    const int j = e / FYW_COLS, cc = e % FYW_COLS;
-    if (cc >= cols) continue;
-    const int64_t q = base + (int64_t)j * Nx + cc;
-    const int64_t pt = (int64_t)j * Nx + x0 + cc;
-    const float2 uv = u[q];
-    const float kk = k2[pt];
-    const float2 t = cadd(y[q], slab[j * FYW_PITCH + cc]);
-    y[q] = make_float2(-t.x - kk * uv.x, -t.y - kk * uv.y);
-  }
+  if (ct < cols)
+    for (int k0 = 0; k0 < PER; k0 += BATCH) {
+      float2 uv[BATCH], tv[BATCH];
+      float kk[BATCH];
+#pragma unroll
+      for (int k = 0; k < BATCH; ++k) {
+        const int64_t j = jt + (k0 + k) * JSTEP;
+        uv[k] = u[base + j * Nx + ct];
+        tv[k] = y[base + j * Nx + ct];
+        kk[k] = k2[j * Nx + x0 + ct];
+      }
+#pragma unroll
+      for (int k = 0; k < BATCH; ++k) {
+        const int j = jt + (k0 + k) * JSTEP;
+        const float2 t = cadd(tv[k], slab[j * FYW_PITCH + ct]);
+        y[base + (int64_t)j * Nx + ct] = make_float2(-t.x - kk[k] * uv[k].x, -t.y - kk[k] * uv[k].y);
+      }
+    }
 }
 
 template <int E>
