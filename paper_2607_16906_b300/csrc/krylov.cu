@@ -438,28 +438,43 @@ __global__ void __launch_bounds__(MD_THREADS) k_dsweepA(const C<R>* __restrict__
   }
 }
 
-// Sum sweep-A partials over chunks: red[(col * 2 + t) * ldq + i], i <= nv (one block per column).
-// Grid (ceil(2 (nv + 1) / blockDim), ncol): one thread per value, four independent partial sums
-// over the chunks (fixed order, so the result is deterministic).
-__global__ void k_dreduce(const double2* __restrict__ partial, int ndc, int ldq, int nv,
-                          const ColState* __restrict__ st, double2* __restrict__ red) {
+// Sum sweep-A partials over chunks: red[(col * 2 + t) * ldq + i], i <= nv.  Grid
+// (ceil(2 (nv + 1) / 32), ncol), DR_WARPS warps per block: lane l of every warp serves value
+// 32 blockIdx.x + l (consecutive values: coalesced loads), warp w sums chunks w, w + DR_WARPS, ...
+// in four independent partial sums, and warp 0 adds the warps' sums in warp order — a fixed order,
+// so the result is deterministic, with ndc / DR_WARPS loads per thread on the critical path.
+constexpr int DR_WARPS = 8;
+__global__ void __launch_bounds__(DR_WARPS * 32) k_dreduce(const double2* __restrict__ partial, int ndc, int ldq,
+                                                           int nv, const ColState* __restrict__ st,
+                                                           double2* __restrict__ red) {
   const int col = blockIdx.y;
-  if (!st[col].active) return;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= 2 * (nv + 1)) return;
+  if (!st[col].active) return;  // whole block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int e = blockIdx.x * 32 + lane;
+  const bool valid = e < 2 * (nv + 1);
   const int t = e / (nv + 1), i = e % (nv + 1);
-  const double2* p = partial + ((int64_t)col * ndc * 2 + t) * ldq + i;
-  const int64_t step = (int64_t)2 * ldq;
   double2 s0 = make_double2(0, 0), s1 = s0, s2 = s0, s3 = s0;
-  int c = 0;
-  for (; c + 4 <= ndc; c += 4) {
-    s0 = cadd(s0, p[(c + 0) * step]);
-    s1 = cadd(s1, p[(c + 1) * step]);
-    s2 = cadd(s2, p[(c + 2) * step]);
-    s3 = cadd(s3, p[(c + 3) * step]);
+  if (valid) {
+    const double2* p = partial + ((int64_t)col * ndc * 2 + t) * ldq + i;
+    const int64_t step = (int64_t)2 * ldq;
+    int c = warp;
+    for (; c + 3 * DR_WARPS < ndc; c += 4 * DR_WARPS) {
+      s0 = cadd(s0, p[(c + 0 * DR_WARPS) * step]);
+      s1 = cadd(s1, p[(c + 1 * DR_WARPS) * step]);
+      s2 = cadd(s2, p[(c + 2 * DR_WARPS) * step]);
+      s3 = cadd(s3, p[(c + 3 * DR_WARPS) * step]);
+    }
+    for (; c < ndc; c += DR_WARPS) s0 = cadd(s0, p[c * step]);
   }
-  for (; c < ndc; ++c) s0 = cadd(s0, p[c * step]);
-  red[((int64_t)col * 2 + t) * ldq + i] = cadd(cadd(s0, s1), cadd(s2, s3));
+  __shared__ double2 sw[DR_WARPS][32];
+  sw[warp][lane] = cadd(cadd(s0, s1), cadd(s2, s3));
+  __syncthreads();
+  if (warp == 0 && valid) {
+    double2 r = sw[0][lane];
+#pragma unroll
+    for (int w = 1; w < DR_WARPS; ++w) r = cadd(r, sw[w][lane]);
+    red[((int64_t)col * 2 + t) * ldq + i] = r;
+  }
 }
 
 // One block per column: finalise column j-1 (when a pending vector exists), Givens on it, build the
@@ -758,18 +773,25 @@ __global__ void __launch_bounds__(RED_THREADS) k_dsweepB(const C<R>* __restrict_
   block_reduce_store<1>(s, npartial + (int64_t)col * nch + chunk);
 }
 
-// Network input scale for the pending vector: in_scale = sqrt(n) / ||u_{j+1}||.
-__global__ void k_nscale(int ncol, const double* __restrict__ npartial, int nch, const ColState* __restrict__ st,
-                         const ColDesc* __restrict__ cols, double* __restrict__ in_scale) {
-  int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= ncol) return;
+// Network input scale for the pending vector: in_scale = sqrt(n) / ||u_{j+1}||.  One warp per column
+// (blocks of NS_WARPS warps): lane l sums the chunk partials l, l + 32, ..., then a shuffle tree in a
+// fixed order.
+constexpr int NS_WARPS = 4;
+__global__ void __launch_bounds__(NS_WARPS * 32) k_nscale(int ncol, const double* __restrict__ npartial, int nch,
+                                                          const ColState* __restrict__ st,
+                                                          const ColDesc* __restrict__ cols,
+                                                          double* __restrict__ in_scale) {
+  const int col = blockIdx.x * NS_WARPS + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (col >= ncol) return;  // whole warps; no block-wide barrier follows
   if (!st[col].active) {
-    in_scale[col] = 0.0;
+    if (lane == 0) in_scale[col] = 0.0;
     return;
   }
   double nn = 0;
-  for (int c = 0; c < nch; ++c) nn += npartial[(int64_t)col * nch + c];
-  in_scale[col] = nn > 0 ? sqrt((double)cols[col].len / nn) : 0.0;
+  for (int c = lane; c < nch; c += 32) nn += npartial[(int64_t)col * nch + c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nn += __shfl_down_sync(0xffffffffu, nn, o);
+  if (lane == 0) in_scale[col] = nn > 0 ? sqrt((double)cols[col].len / nn) : 0.0;
 }
 
 // y = R^{-1} g (k x k upper triangular), ycoef_i = beta * y_i.
@@ -1202,15 +1224,15 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
         HELM_CK(cudaMemsetAsync(W.nactive, 0, sizeof(int), stream));
         launch(k_dsweepA<R>, dgrid, MD_THREADS, ds_smem, stream, (const C<R>*)W.V, vst, nv,
                (const C<R>*)(has_u ? Uj : nullptr), (const C<R>*)W.w, ctx->cols_dev, W.st, P, ndc, W.partial, ldq);
-        launch(k_dreduce, dim3(cdiv(2 * (nv + 1), 128), ncol), 128, 0, stream, (const double2*)W.partial, ndc, ldq,
-               nv, W.st, W.red);
+        launch(k_dreduce, dim3(cdiv(2 * (nv + 1), 32), ncol), DR_WARPS * 32, 0, stream, (const double2*)W.partial,
+               ndc, ldq, nv, W.st, W.red);
         launch(k_dcoef<R>, ncol, DC_THREADS, dc_smem(nv), stream, j, nv, has_u, 1, ncol, m, (const double2*)W.red, ldq,
                W.Rm, W.cs, W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps, W.hist0);
         launch(k_dsweepB<R>, vgrid, RED_THREADS, 2 * sizeof(C<R>) * nv, stream, (const C<R>*)W.V, vst, nv,
                has_u ? Uj : nullptr, (const C<R>*)W.w, W.V + (int64_t)(j + 1) * vst, (const C<R>*)W.ca,
                (const C<R>*)W.cb, (const double2*)W.sc, ldq, ctx->cols_dev, W.st, nch, W.npartial);
-        launch(k_nscale, cdiv(ncol, 64), 64, 0, stream, ncol, (const double*)W.npartial, nch, W.st, ctx->cols_dev,
-               W.in_scale);
+        launch(k_nscale, cdiv(ncol, NS_WARPS), NS_WARPS * 32, 0, stream, ncol, (const double*)W.npartial, nch, W.st,
+               ctx->cols_dev, W.in_scale);
         HELM_CK_LAUNCH();
         prof_end(ctx, PH_ORTH, stream);
         HELM_TRY(poll(j));
@@ -1221,8 +1243,8 @@ helm_status fgmres_solve(helm_ctx* ctx, const helm_unet* net, const double2* b, 
       launch(k_dsweepA<R>, dgrid, MD_THREADS, ds_smem, stream, (const C<R>*)W.V, vst, m,
              (const C<R>*)(W.V + (int64_t)m * vst), (const C<R>*)nullptr, ctx->cols_dev, W.st, P, ndc, W.partial,
              ldq);
-      launch(k_dreduce, dim3(cdiv(2 * (m + 1), 128), ncol), 128, 0, stream, (const double2*)W.partial, ndc, ldq, m,
-             W.st, W.red);
+      launch(k_dreduce, dim3(cdiv(2 * (m + 1), 32), ncol), DR_WARPS * 32, 0, stream, (const double2*)W.partial, ndc,
+             ldq, m, W.st, W.red);
       launch(k_dcoef<R>, ncol, DC_THREADS, dc_smem(m), stream, m, m, 1, 0, ncol, m, (const double2*)W.red, ldq, W.Rm,
              W.cs, W.sn, W.g, W.st, W.ca, W.cb, W.sc, W.nactive, breakdown_eps, W.hist0);
       HELM_CK_LAUNCH();
