@@ -271,8 +271,8 @@ static helm_status launch_stencil_tma(const float2* x, float2* y, const float* k
 //
 // The tile height trades halo re-reads ((TH + 2) / TH rows loaded per row) against the number of
 // tiles in flight per SM (shared memory per stage).  On the first call for a grid shape (Nx, Ny,
-// nrhs, adjoint, k^2 staged) every candidate runs once untimed and once timed with CUDA events on the
-// caller's stream, and the fastest is kept.  Every candidate computes each point with the same
+// nrhs, adjoint, k^2 staged) every candidate runs once untimed and then three times timed with CUDA
+// events on the caller's stream, in interleaved rounds, and the lowest total is kept.  Every candidate computes each point with the same
 // arithmetic, so the choice never changes a result.  HELM_AUTOTUNE=0 keeps the first candidate, as do
 // calls during a stream capture.
 
@@ -334,25 +334,28 @@ static helm_status stencil_tuned(const float2* x, float2* y, const float* k2, co
   cudaEvent_t e0, e1;
   HELM_CK(cudaEventCreate(&e0));
   HELM_CK(cudaEventCreate(&e1));
-  int best = 0;
-  float best_ms = 0.f;
   helm_status rc = HELM_OK;
-  for (size_t i = 0; i < cands.size() && rc == HELM_OK; ++i) {
-    rc = cands[i].fn(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, 0, st);  // set-up, warm-up
-    if (rc != HELM_OK) break;
-    cudaEventRecord(e0, st);
+  for (size_t i = 0; i < cands.size() && rc == HELM_OK; ++i)  // set-up, warm-up
     rc = cands[i].fn(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, 0, st);
-    cudaEventRecord(e1, st);
-    float ms = 0.f;
-    if (rc == HELM_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
-        (i == 0 || ms < best_ms)) {
-      best = (int)i;
-      best_ms = ms;
+  // ST_ROUNDS timed rounds over all candidates (interleaved, so that each candidate meets the same mix
+  // of cache states), the lowest total wins
+  constexpr int ST_ROUNDS = 3;
+  std::vector<float> total(cands.size(), 0.f);
+  for (int r = 0; r < ST_ROUNDS && rc == HELM_OK; ++r)
+    for (size_t i = 0; i < cands.size() && rc == HELM_OK; ++i) {
+      cudaEventRecord(e0, st);
+      rc = cands[i].fn(x, y, k2, px, py, ux, uy, Nx, Ny, nrhs, inv_h2, err, budget, 0, st);
+      cudaEventRecord(e1, st);
+      float ms = 0.f;
+      if (rc == HELM_OK && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+        total[i] += ms;
     }
-  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != HELM_OK) return rc;
+  int best = 0;
+  for (size_t i = 1; i < cands.size(); ++i)
+    if (total[i] < total[best]) best = (int)i;
   std::lock_guard<std::mutex> lk(g_st_mu);
   g_st_choice[key] = best;
   return HELM_OK;
