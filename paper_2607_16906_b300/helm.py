@@ -272,10 +272,23 @@ HELM_PAPER_LAYER_DEC0_FINAL = 8
 
 def helm_paper_layer_forward(net, layer, in0: torch.Tensor, out: torch.Tensor, B, H, W, in1=None, stream=None):
     """One layer of network kind 1 on NHWC bfloat16 CUDA tensors (helm_paper_layer_forward in
-    include/helm.h); H x W is the layer's 5x5 GEMM grid."""
+    include/helm.h); H x W is the layer's 5x5 GEMM grid.  The tensors' sizes and types are checked
+    here (the library reads and writes them through raw pointers)."""
     for t in (in0, out) + ((in1,) if in1 is not None else ()):
         if not t.is_cuda or not t.is_contiguous():
             raise ValueError("layer tensors must be contiguous CUDA tensors")
+    if 0 <= layer <= HELM_PAPER_LAYER_DEC0_FINAL and min(B, H, W) >= 1:
+        fused = layer == HELM_PAPER_LAYER_DEC0_FINAL
+        l = 7 if fused else layer
+        small, large = B * H * W * 32, B * 4 * H * W * 32  # 32 channels on the H x W / 2H x 2W grid
+        need = [(in0, "in0", large if 1 <= l <= 3 else small, torch.bfloat16),
+                (out, "out", small if l <= 3 else (B * 4 * H * W * 2 if fused else large),
+                 torch.float32 if fused else torch.bfloat16)]
+        if in1 is not None:
+            need.append((in1, "in1", small, torch.bfloat16))
+        for t, name, n, dt in need:
+            if t.dtype != dt or t.numel() < n:
+                raise ValueError(f"helm_paper_layer_forward: {name} must be a {dt} tensor of at least {n} elements")
     _check(_lib.helm_paper_layer_forward(net.handle, layer, _dev_ptr(in0),
                                          _dev_ptr(in1) if in1 is not None else None, _dev_ptr(out), B, H, W,
                                          _stream(stream)))

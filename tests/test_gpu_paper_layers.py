@@ -134,8 +134,13 @@ def test_paper_last_layer_with_fused_output(helm, net_theta, grid):
 def test_paper_layer_rejects_bad_arguments(helm, net_theta):
     net, _ = net_theta
     t = torch.zeros(1, 8, 16, 32, dtype=torch.bfloat16, device="cuda")
+    big = torch.zeros(1, 16, 32, 32, dtype=torch.bfloat16, device="cuda")
     with pytest.raises(helm.HelmError, match="in1"):
-        helm.helm_paper_layer_forward(net, 5, t, t, 1, 8, 16)          # decoder concat without the skip
+        helm.helm_paper_layer_forward(net, 5, t, big, 1, 8, 16)        # decoder concat without the skip
+    with pytest.raises(ValueError, match="out"):
+        helm.helm_paper_layer_forward(net, 5, t, t, 1, 8, 16, in1=t)   # output smaller than 2H x 2W x 32
+    with pytest.raises(ValueError, match="in0"):
+        helm.helm_paper_layer_forward(net, 1, t, t, 1, 8, 16)          # encoder input smaller than 2H x 2W
     with pytest.raises(helm.HelmError, match="range"):
         helm.helm_paper_layer_forward(net, 9, t, t, 1, 8, 16)
     k0 = helm.UNet(synth.kaiming_uniform_params(helm.weight_segments(), 1))
