@@ -10,6 +10,7 @@ Batch vectors are CUDA tensors of dtype complex64 (HELM_C64) or complex128 (HELM
 from __future__ import annotations
 
 import ctypes as ct
+import functools
 import os
 from dataclasses import dataclass
 
@@ -256,10 +257,27 @@ def helm_relres_noalloc(ctx: Context, x: torch.Tensor, b: torch.Tensor, out: tor
 def helm_unet_layer_forward(net, layer, in0: torch.Tensor, out: torch.Tensor, B, H, W, in1=None, variant=0,
                             stream=None):
     """One layer of the BF16 network on NHWC bfloat16 CUDA tensors (helm_unet_layer_forward in
-    include/helm.h); returns the rows per tile of the row-tile kernel that ran (0: 9-box kernel)."""
+    include/helm.h); returns the rows per tile of the row-tile kernel that ran (0: 9-box kernel).
+    The tensors' sizes and types are checked here (the library reads and writes them through raw
+    pointers)."""
     for t in (in0, out) + ((in1,) if in1 is not None else ()):
         if not t.is_cuda or not t.is_contiguous():
             raise ValueError("layer tensors must be contiguous CUDA tensors")
+    if 0 <= layer <= HELM_LAYER_DEC1B_FINAL and min(B, H, W) >= 1:
+        fused = layer == HELM_LAYER_DEC1B_FINAL
+        l = 16 if fused else layer
+        ci, co, kind = _unet_layers()[l]
+        concat = l in (9, 12, 15)  # dec3a, dec2a, dec1a: [up-sampled decoder, skip]
+        c0 = 16 if l == 0 else (ci // 2 if concat else ci)  # the input tensor has 16 channels (3 used)
+        px = B * H * W
+        need = [(in0, "in0", px * c0, torch.bfloat16),
+                (out, "out", px * 2 if fused else px * co * (4 if kind == 1 else 1),
+                 torch.float32 if fused else torch.bfloat16)]
+        if concat and in1 is not None:
+            need.append((in1, "in1", px * (ci // 2), torch.bfloat16))
+        for t, name, n, dt in need:
+            if t.dtype != dt or t.numel() < n:
+                raise ValueError(f"helm_unet_layer_forward: {name} must be a {dt} tensor of at least {n} elements")
     ry = ct.c_int()
     _check(_lib.helm_unet_layer_forward(net.handle, layer, variant, _dev_ptr(in0),
                                         _dev_ptr(in1) if in1 is not None else None, _dev_ptr(out), B, H, W,
@@ -315,6 +333,11 @@ def network_kind(nparams: int) -> int:
         if int(_lib.helm_unet_param_count_kind(kind)) == int(nparams):
             return kind
     return 0
+
+
+@functools.lru_cache(maxsize=1)
+def _unet_layers():
+    return tuple(helm_unet_layers())
 
 
 def helm_unet_layers():

@@ -154,3 +154,8 @@ def test_layer_entry_rejects_what_it_cannot_run(helm, net_theta):
         helm.helm_unet_layer_forward(net, 6, x, y, 1, 8, 8, variant=1)
     with pytest.raises(helm.HelmError):
         helm.helm_unet_layer_forward(net, 18, x, y, 1, 8, 8)
+    small = torch.zeros(100, dtype=torch.bfloat16, device="cuda")
+    with pytest.raises(ValueError, match="out"):   # output smaller than B H W C_out (checked before the call)
+        helm.helm_unet_layer_forward(net, 4, x, small, 2, 8, 8)
+    with pytest.raises(ValueError, match="in0"):   # up-conv input smaller than B H W C_in
+        helm.helm_unet_layer_forward(net, 8, x, y, 2, 8, 8)
