@@ -327,6 +327,18 @@ def fourier_leg(helm, h, omega, peaks, nrhs=8, reps=10):
             "kernels": f"k_fourier_x + k_fourier_y (FP32, 1024^2 x {nrhs} RHS)", "l2": "flushed before each launch"}
 
 
+# Network kind 1, MACs per full-resolution pixel.  Algorithmic: 8x8 down layers 64 C_in 32 per output
+# pixel at 1/4, 1/16, 1/64, 1/256 of the pixels (C_in = 5, 32, 32, 32), up layers 64 C_in 32 per input
+# pixel at 1/256, 1/64, 1/16, 1/4 (C_in = 32, 64, 64, 64), output layer 32 x 2: 51,264.  Executed on
+# the tensor cores (structural zeros included): enc1..enc3 9 taps x K x 128 columns at 1/16, 1/64,
+# 1/256 (K = 128, 512, 512), enc4 25 x 128 x 32 at 1/256, up layers 25 x K x 128 at 1/256, 1/64, 1/16,
+# 1/4 (K = 32, 64, 64, 64), output layer: 88,800.
+PAPER_NET_ALG_MACS = (64 * 32 * (5 / 4 + 32 * (1 / 16 + 1 / 64 + 1 / 256)) +
+                      64 * 32 * (32 / 256 + 64 / 64 + 64 / 16 + 64 / 4) + 64)
+PAPER_NET_EXE_MACS = (9 * 128 * 128 / 16 + 9 * 512 * 128 * (1 / 64 + 1 / 256) + 25 * 128 * 32 / 256 +
+                      25 * 128 * (32 / 256 + 64 / 64 + 64 / 16 + 64 / 4) + 64)
+
+
 def paper_net_leg(helm, ctx, nrhs, peaks, reps=5):
     """The paper's U-Net variant (network kind 1, seeded weights): one BF16 application to `nrhs`
     right-hand sides of the context, against the measured burst BF16 rate on the algorithmic flops of
@@ -340,14 +352,7 @@ def paper_net_leg(helm, ctx, nrhs, peaks, reps=5):
     pz = torch.empty_like(pv)
     helm.helm_precond_apply(ctx, pn, pv, pz, nrhs)
     p_ms = timed_flushed(lambda: helm.helm_precond_apply(ctx, pn, pv, pz, nrhs), reps)
-    # algorithmic MACs per full-resolution pixel: 8x8 down layers 64 C_in 32 per output pixel at 1/4,
-    # 1/16, 1/64, 1/256 of the pixels (C_in = 5, 32, 32, 32), up layers 64 C_in 32 per input pixel at
-    # 1/256, 1/64, 1/16, 1/4 (C_in = 32, 64, 64, 64), output 32 x 2: 51,264
-    alg = 64 * 32 * (5 / 4 + 32 * (1 / 16 + 1 / 64 + 1 / 256)) + 64 * 32 * (32 / 256 + 64 / 64 + 64 / 16 + 64 / 4) + 64
-    # executed GEMM MACs: enc1..enc3 9 taps x K x 128 columns at 1/16, 1/64, 1/256 (K = 128, 512, 512),
-    # enc4 25 x 128 x 32 at 1/256, up layers 25 x K x 128 at 1/256, 1/64, 1/16, 1/4 (K = 32, 64, 64, 64)
-    exe = (9 * 128 * 128 / 16 + 9 * 512 * 128 * (1 / 64 + 1 / 256) + 25 * 128 * 32 / 256 +
-           25 * 128 * (32 / 256 + 64 / 64 + 64 / 16 + 64 / 4) + 64)
+    alg, exe = PAPER_NET_ALG_MACS, PAPER_NET_EXE_MACS
     pk = peaks.get("bf16_tflops", 1800.0)
     px = ctx.npts * nrhs
     a_tf = 2.0 * alg * px / (p_ms / 1e3) / 1e12

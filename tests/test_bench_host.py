@@ -37,3 +37,29 @@ def test_reference_arm_line():
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"]
+
+
+def test_network_flop_accounting_matches_the_oracle_network():
+    """The algorithmic MACs per full-resolution pixel the bench reports network kind 1 against (Sec. 3.1,
+    Tab. 2) equal a count over the shapes of the oracle's forward pass on a 32 x 32 input: an 8x8
+    strided layer does 64 C_in C_out per output pixel, a transposed one 64 C_in C_out per input pixel,
+    the 1x1 output layer C_in C_out per pixel."""
+    import numpy as np
+    from oracle import unet_paper as up
+    from paper_2607_16906_b300 import synth
+    theta = synth.kaiming_uniform_params(up.param_segments(), 42)
+    x = synth.rng_for(5).standard_normal((1, 5, 32, 32))
+    _, act = up.forward(theta, x, keep=True)
+    macs = 0
+    for name, kind, ci, co in up.LAYERS:
+        xin, pre = act[name]
+        assert xin.shape[1] == ci
+        if kind == "down":
+            macs += pre.shape[2] * pre.shape[3] * 64 * ci * co
+        elif kind == "up":
+            macs += xin.shape[2] * xin.shape[3] * 64 * ci * co
+        else:
+            macs += xin.shape[2] * xin.shape[3] * ci * co
+    assert macs / (32 * 32) == bench.PAPER_NET_ALG_MACS == 51264
+    # every executed product of the reformulated GEMMs is a product of the 8x8 layers or a structural zero
+    assert bench.PAPER_NET_EXE_MACS >= bench.PAPER_NET_ALG_MACS
