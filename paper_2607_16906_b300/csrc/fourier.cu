@@ -13,9 +13,11 @@
 //   y pass: the same derivative pair along the columns -> t_y; then y = -(t_x + t_y) - k^2 u.
 // FP32 with sides of 32 or more: one warp transforms one line held in registers (lane l, register r
 // hold element l + 32 r): an in-register E-point FFT over r (E = N / 32), the twiddles of the
-// N = 32 E split, and a 32-point FFT across the lanes by shuffles; the x pass reads its rows straight
-// into registers, the y pass stages 8 columns of the whole height in shared memory (64-byte row
-// segments, a padded pitch so the column reads are free of bank conflicts).  FP64 and sides of 16:
+// N = 32 E split, and a 32-point FFT across the lanes by shuffles (for 1024-point lines a transpose
+// of the 32 x 32 split through a per-warp shared-memory tile instead, so the second factor is also an
+// in-register FFT); the x pass reads its rows straight into registers, the y pass stages 8 columns of
+// the whole height in shared memory (64-byte row segments, a padded pitch so the column reads are
+// free of bank conflicts), each thread keeping 8 loads in flight.  FP64 and sides of 16:
 // block-wide radix-2 FFTs in shared memory (one block per row; 16 (FP32) or 8 (FP64) columns).
 // Twiddle tables exp(-2 pi i t / N), t < N/2, are computed once per grid side on the host in FP64
 // and staged into shared memory by every block.  HBM traffic per point: x pass 16 B (FP32), y pass
