@@ -6,7 +6,9 @@
 // (out-of-image rows/columns arrive as zeros, which is the conv's zero padding) and one TMA load
 // brings the tap's N x chunk weight tile; both land in shared memory in the swizzled K-major layout
 // that tcgen05.mma reads directly.  A concat input (decoder levels) is two sources whose chunks are
-// consumed one after the other, so the concat is never materialised.
+// consumed one after the other, so the concat is never materialised.  The same kernel runs network
+// kind 1 (unet_paper.cu): its 5x5 layers with row-reuse stages (TcCfg, KS = 5) and its first three
+// encoder layers as 3x3 convolutions of a strided phase view of their input (MODE 2, ConvTcArgs::qf).
 //
 // Persistent kernel, one CTA per SM slot, 6 warps:
 //   warp 0  TMA producer (one elected lane), STAGES-deep smem ring (full/empty mbarriers);
