@@ -16,7 +16,8 @@
 //   warps 2-5  epilogue: tcgen05.ld of the 128 x N accumulator (warp w reads TMEM lanes
 //           32 (w % 4) .. +31), bias, ReLU, BF16 rounding, NHWC stores.
 // Two TMEM accumulators alternate so the epilogue of one tile overlaps the MMAs of the next.
-// Every mbarrier wait is bounded (about one second of clock64); on a timeout the kernel records an
+// Every mbarrier wait is bounded (a run-time budget of clock64 cycles, ConvTcArgs::budget, about one
+// second by default; the drain waits always the full second); on a timeout the kernel records an
 // error code, stops issuing work, waits (bounded) for its own copies in flight, frees TMEM and exits.
 #include <cuda.h>
 
