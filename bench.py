@@ -38,7 +38,7 @@ STENCIL_BYTES_FP32 = 16.0           # read z (8 B) + write A z (8 B) per point; 
 # the CUDA arm (mean over the 32 RHS, FGMRES(128), up to 80 cycles); the reference arm, which
 # runs in a process of its own, scales its measured per-iteration time by it (the CUDA arm prints its
 # own measured mean)
-REF_ITERS_PER_SOLVE = 4967
+REF_ITERS_PER_SOLVE = 4964
 # DRAM bytes per basis vector and point of one DCGS2 step (k_dsweepA 8.00 B + k_dsweepB 8.06 B),
 # from the ncu counters of the current sweep kernels
 DCGS2_DRAM_B_PER_VPT = 16.06
